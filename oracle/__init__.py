@@ -1,0 +1,191 @@
+"""CPU oracle for the tensor-core beamformer (arXiv 2505.03269).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the library.  It shares
+no code with the CUDA path.  The arithmetic lives in ``tcbf_oracle.c``
+(FP64 / int64 loops, compiled with gcc); this module only builds, loads and
+marshals it, plus the paper's 1-bit popcount identities in ``onebit.py``.
+
+Functions and the passages they follow:
+  cgemm(W, X)            Eq. 3 with the complex product of Sec. III-B, FP64
+  cgemm_points(W, X, p)  Eq. 3 at chosen output points
+  bgemm(Wb, Xb, K)       Eq. 3 over 1-bit values of Fig. 1, exact int64
+  pack_signs(V, ...)     1-bit sign quantisation, Sec. III-D / Sec. V-A
+  weights(geom)          w = A exp(-2 pi i f tau), Eq. 1-2
+  half_to_double(h)      IEEE binary16 decoding (the FP16 storage format)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tcbf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile tcbf_oracle.c with gcc (OpenMP, no fast-math: IEEE FP64)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+           "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_half_to_double.restype = ctypes.c_double
+        lib.oracle_half_to_double.argtypes = [ctypes.c_uint16]
+        lib.oracle_cgemm_f64.argtypes = [i64, i64, i64, i64, i64, p, p, p]
+        lib.oracle_cgemm_f16.argtypes = [i64, i64, i64, i64, i64, p, p, p, p, p]
+        lib.oracle_cgemm_f16_points.argtypes = [i64, i64, i64, i64, i64, p, p, i64, p, p]
+        lib.oracle_bgemm.argtypes = [i64, i64, i64, i64, i64, i64, p, p, p]
+        lib.oracle_pack_signs_f16.argtypes = [i64, i64, i64, ctypes.c_int, i64, p, p]
+        lib.oracle_weights.argtypes = [i64, i64, i64, p, p, ctypes.c_int, p, ctypes.c_double, p]
+        for f in ("oracle_cgemm_f64", "oracle_cgemm_f16", "oracle_cgemm_f16_points",
+                  "oracle_bgemm", "oracle_pack_signs_f16", "oracle_weights"):
+            getattr(lib, f).restype = None
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def half_to_double(h: np.ndarray) -> np.ndarray:
+    """Decode binary16 bit patterns (uint16) one by one."""
+    lib = _load()
+    flat = np.ascontiguousarray(h, dtype=np.uint16).ravel()
+    return np.array([lib.oracle_half_to_double(int(v)) for v in flat]).reshape(h.shape)
+
+
+def _as_complex_pairs_f64(A: np.ndarray) -> np.ndarray:
+    if np.iscomplexobj(A):
+        out = np.empty(A.shape + (2,), dtype=np.float64)
+        out[..., 0] = A.real
+        out[..., 1] = A.imag
+        return out
+    return np.ascontiguousarray(A, dtype=np.float64)
+
+
+def _to_complex(P: np.ndarray) -> np.ndarray:
+    return P[..., 0] + 1j * P[..., 1]
+
+
+def cgemm(W: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Y[b] = W[b'] X[b] (Eq. 3), FP64, returned as complex128 [B, M, N].
+
+    W: [Bw, M, K, 2] and X: [B, K, N, 2] interleaved pairs, either float16
+    (decoded exactly to FP64) or float64; complex arrays are accepted too.
+    Batch b uses weight matrix b // (B // Bw)."""
+    lib = _load()
+    if W.dtype == np.float16 and X.dtype == np.float16:
+        Bw, M, K, _ = W.shape
+        B, K2, N, _ = X.shape
+        assert K == K2 and B % Bw == 0
+        Y = np.empty((B, M, N, 2), np.float64)
+        wd = np.empty(M * K * 2, np.float64)
+        xd = np.empty(K * N * 2, np.float64)
+        Wc = np.ascontiguousarray(W).view(np.uint16)
+        Xc = np.ascontiguousarray(X).view(np.uint16)
+        lib.oracle_cgemm_f16(B, M, N, K, Bw, _ptr(Wc), _ptr(Xc), _ptr(Y), _ptr(wd), _ptr(xd))
+        return _to_complex(Y)
+    Wd = _as_complex_pairs_f64(W)
+    Xd = _as_complex_pairs_f64(X)
+    Bw, M, K, _ = Wd.shape
+    B, K2, N, _ = Xd.shape
+    assert K == K2 and B % Bw == 0
+    Y = np.empty((B, M, N, 2), np.float64)
+    lib.oracle_cgemm_f64(B, M, N, K, Bw, _ptr(Wd), _ptr(Xd), _ptr(Y))
+    return _to_complex(Y)
+
+
+def cgemm_points(W: np.ndarray, X: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Eq. 3 evaluated only at output points pts [P, 3] = (b, m, n); FP16 inputs."""
+    lib = _load()
+    assert W.dtype == np.float16 and X.dtype == np.float16
+    Bw, M, K, _ = W.shape
+    B, _, N, _ = X.shape
+    pts = np.ascontiguousarray(pts, dtype=np.int64)
+    out = np.empty((len(pts), 2), np.float64)
+    Wc = np.ascontiguousarray(W).view(np.uint16)
+    Xc = np.ascontiguousarray(X).view(np.uint16)
+    lib.oracle_cgemm_f16_points(B, M, N, K, Bw, _ptr(Wc), _ptr(Xc), len(pts), _ptr(pts), _ptr(out))
+    return _to_complex(out)
+
+
+def bgemm(Wb: np.ndarray, Xb: np.ndarray, K: int) -> np.ndarray:
+    """Exact 1-bit complex product (Fig. 1 values, Eq. 3), int64 [B, M, N, 2].
+
+    Wb: [Bw, 2, M, Kw] and Xb: [B, 2, N, Kw] uint32 packed planes."""
+    lib = _load()
+    Bw, _, M, Kw = Wb.shape
+    B, _, N, Kw2 = Xb.shape
+    assert Kw == Kw2 and B % Bw == 0 and K <= 32 * Kw
+    Y = np.empty((B, M, N, 2), np.int64)
+    Wc = np.ascontiguousarray(Wb, dtype=np.uint32)
+    Xc = np.ascontiguousarray(Xb, dtype=np.uint32)
+    lib.oracle_bgemm(B, M, N, K, Bw, Kw, _ptr(Wc), _ptr(Xc), _ptr(Y))
+    return Y
+
+
+def pack_signs(V: np.ndarray, k_is_row: bool, Kw: int) -> np.ndarray:
+    """Sign-quantise interleaved complex FP16 V [B, R, C, 2] into packed
+    planes [B, 2, rows, Kw].  k_is_row=False packs along C (weights, rows =
+    beams); k_is_row=True packs along R and transposes (data, rows = samples)."""
+    lib = _load()
+    assert V.dtype == np.float16
+    B, R, C, _ = V.shape
+    rows = C if k_is_row else R
+    out = np.empty((B, 2, rows, Kw), np.uint32)
+    Vc = np.ascontiguousarray(V).view(np.uint16)
+    lib.oracle_pack_signs_f16(B, R, C, int(k_is_row), Kw, _ptr(Vc), _ptr(out))
+    return out
+
+
+def weights(rx_pos, targets, freqs, near_field: bool, c: float) -> np.ndarray:
+    """w[b,m,k] = A exp(-2 pi i f[b,k] tau[m,k]) in FP64 -> complex128 [Bw, M, K]."""
+    lib = _load()
+    rx = np.ascontiguousarray(rx_pos, dtype=np.float64)
+    tg = np.ascontiguousarray(targets, dtype=np.float64)
+    fr = np.ascontiguousarray(freqs, dtype=np.float64)
+    K = rx.shape[0]
+    M = tg.shape[0]
+    Bw = fr.shape[0]
+    assert fr.shape[1] == K
+    out = np.empty((Bw, M, K, 2), np.float64)
+    lib.oracle_weights(Bw, M, K, _ptr(rx), _ptr(tg), int(near_field), _ptr(fr), float(c), _ptr(out))
+    return _to_complex(out)
+
+
+def weights_fp16(rx_pos, targets, freqs, near_field: bool, c: float) -> np.ndarray:
+    """The FP64 weights rounded once to FP16 (round-to-nearest-even),
+    interleaved [Bw, M, K, 2] — the expected output of the weights kernel."""
+    w = weights(rx_pos, targets, freqs, near_field, c)
+    out = np.empty(w.shape + (2,), np.float16)
+    out[..., 0] = w.real
+    out[..., 1] = w.imag
+    return out
+
+
+def rel_frobenius(Y: np.ndarray, Yref: np.ndarray) -> float:
+    """||Y - Yref||_F / ||Yref||_F over real and imaginary parts, FP64."""
+    d = np.asarray(Y, np.complex128) - np.asarray(Yref, np.complex128)
+    return float(np.sqrt(np.sum(np.abs(d) ** 2)) / np.sqrt(np.sum(np.abs(Yref) ** 2)))

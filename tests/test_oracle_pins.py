@@ -1,0 +1,313 @@
+"""Pins for the CPU oracle, against facts that do not come from the oracle.
+
+Each test checks the oracle against something fixed by the paper or by
+mathematics: brute force on tiny inputs, a library routine on a special
+case, closed forms (identity weights, integer inputs, plane-wave coherent
+gain, matched 1-bit conjugate), the paper's worked example (Table II) and
+its popcount identities (Eq. 4-6), exhaustive 1-bit enumeration, and
+IEEE binary16 decoding against numpy over all 65536 patterns.
+"""
+import cmath
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import onebit
+import tcbf_inputs as ti
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- binary16
+def test_half_decode_exhaustive_against_numpy():
+    h = np.arange(65536, dtype=np.uint32).astype(np.uint16)
+    mine = oracle.half_to_double(h)
+    ref = h.view(np.float16).astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(mine), nan)
+    assert np.array_equal(mine[~nan], ref[~nan])
+    # signed zero keeps its sign
+    assert math.copysign(1.0, mine[0x8000]) == -1.0
+
+
+# ----------------------------------------------------------- complex GEMM
+def _brute(W, X):
+    """Eq. 3 with Python complex numbers, no arrays."""
+    Bw, M, K = W.shape
+    B, _, N = X.shape
+    Y = np.zeros((B, M, N), complex)
+    for b in range(B):
+        for m in range(M):
+            for n in range(N):
+                s = 0j
+                for k in range(K):
+                    s += complex(W[b // (B // Bw), m, k]) * complex(X[b, k, n])
+                Y[b, m, n] = s
+    return Y
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+def test_cgemm_brute_force_tiny(K):
+    g = np.random.default_rng(K)
+    B, Bw, M, N = 4, 2, 3, 5
+    W = g.standard_normal((Bw, M, K)) + 1j * g.standard_normal((Bw, M, K))
+    X = g.standard_normal((B, K, N)) + 1j * g.standard_normal((B, K, N))
+    Y = oracle.cgemm(W, X)
+    Yb = _brute(W, X)
+    assert np.allclose(Y, Yb, rtol=1e-14, atol=1e-14)
+
+
+def test_cgemm_matches_library_matmul():
+    g = np.random.default_rng(7)
+    B, M, K, N = 3, 17, 33, 29
+    W = g.standard_normal((B, M, K)) + 1j * g.standard_normal((B, M, K))
+    X = g.standard_normal((B, K, N)) + 1j * g.standard_normal((B, K, N))
+    Y = oracle.cgemm(W, X)
+    assert np.allclose(Y, W @ X, rtol=1e-12, atol=1e-12)
+
+
+def test_cgemm_fp16_path_equals_decoded_fp64_path():
+    W, X = ti.small_fp16(seed=3, M=9, K=21, N=13, B=2)
+    Y16 = oracle.cgemm(W, X)
+    Y64 = oracle.cgemm(W.astype(np.float64), X.astype(np.float64))
+    assert np.array_equal(Y16, Y64)
+
+
+def test_cgemm_points_equal_full():
+    W, X = ti.small_fp16(seed=4, M=11, K=37, N=19, B=3)
+    Y = oracle.cgemm(W, X)
+    g = np.random.default_rng(0)
+    pts = np.stack([g.integers(0, 3, 50), g.integers(0, 11, 50), g.integers(0, 19, 50)], 1)
+    P = oracle.cgemm_points(W, X, pts)
+    assert np.array_equal(P, Y[pts[:, 0], pts[:, 1], pts[:, 2]])
+
+
+def test_identity_weights_return_x_exactly():
+    K, N = 24, 40
+    W = np.zeros((1, K, K, 2), np.float16)
+    W[0, np.arange(K), np.arange(K), 0] = 1.0
+    _, X = ti.small_fp16(seed=1, M=1, K=K, N=N)
+    Y = oracle.cgemm(W, X)
+    Xc = X[..., 0].astype(np.float64) + 1j * X[..., 1].astype(np.float64)
+    assert np.array_equal(Y, Xc)
+
+
+def test_integer_inputs_exact():
+    g = ti.rng(5)
+    W = ti.integer_complex_fp16(g, (2, 6, 50))
+    X = ti.integer_complex_fp16(g, (2, 50, 7))
+    Y = oracle.cgemm(W, X)
+    wi = W.astype(np.int64)
+    xi = X.astype(np.int64)
+    re = wi[..., 0] @ xi[..., 0] - wi[..., 1] @ xi[..., 1]
+    im = wi[..., 0] @ xi[..., 1] + wi[..., 1] @ xi[..., 0]
+    assert np.array_equal(Y.real, re.astype(np.float64))
+    assert np.array_equal(Y.imag, im.astype(np.float64))
+
+
+def test_batch_weight_sharing():
+    g = np.random.default_rng(9)
+    B, Bw, M, K, N = 6, 3, 4, 5, 7
+    W = g.standard_normal((Bw, M, K)) + 1j * g.standard_normal((Bw, M, K))
+    X = g.standard_normal((B, K, N)) + 1j * g.standard_normal((B, K, N))
+    Y = oracle.cgemm(W, X)
+    for b in range(B):
+        assert np.allclose(Y[b], W[b // 2] @ X[b], rtol=1e-13, atol=1e-13)
+
+
+def test_conjugation_symmetry_and_linearity():
+    g = np.random.default_rng(11)
+    W = g.standard_normal((1, 5, 6)) + 1j * g.standard_normal((1, 5, 6))
+    X = g.standard_normal((1, 6, 4)) + 1j * g.standard_normal((1, 6, 4))
+    X2 = g.standard_normal((1, 6, 4)) + 1j * g.standard_normal((1, 6, 4))
+    Y = oracle.cgemm(W, X)
+    assert np.allclose(oracle.cgemm(W.conj(), X.conj()), Y.conj(), rtol=1e-14, atol=1e-14)
+    a = 0.3 - 1.7j
+    assert np.allclose(oracle.cgemm(W, a * X + X2), a * Y + oracle.cgemm(W, X2),
+                       rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- weights
+def test_plane_wave_on_axis_gives_coherent_gain_K():
+    """x_k = exp(+2 pi i f tau_k) s; steering the beam at the source gives y = K s."""
+    K, f, c = 96, 150e6, ti.SPEED_OF_LIGHT
+    g = np.random.default_rng(3)
+    pos = np.zeros((K, 3))
+    pos[:, 0] = g.uniform(-1000, 1000, K)
+    pos[:, 1] = g.uniform(-1000, 1000, K)
+    theta = 0.2
+    s_dir = np.array([[math.sin(theta), 0.0, math.cos(theta)]])
+    w = oracle.weights(pos, s_dir, np.full((1, K), f), False, c)        # [1,1,K]
+    tau = pos @ s_dir[0] / c
+    s = 0.7 - 0.2j
+    x = (np.exp(2j * np.pi * f * tau) * s).reshape(1, K, 1)
+    y = oracle.cgemm(w, x)[0, 0, 0]
+    assert abs(y - K * s) <= 1e-11 * K
+
+
+def test_weights_unit_modulus_and_zero_delay():
+    geom = ti.radio_geometry(seed=0, n_beams=16, n_stations=12, n_channels=3)
+    w = oracle.weights(geom.rx_pos, geom.targets, geom.freqs, False, geom.c)
+    assert np.allclose(np.abs(w), 1.0, atol=1e-14)
+    # a receiver at the reference point has zero delay: w = 1
+    pos = geom.rx_pos.copy()
+    pos[0] = 0.0
+    w0 = oracle.weights(pos, geom.targets, geom.freqs, False, geom.c)
+    assert np.all(w0[:, :, 0] == 1.0)
+
+
+def test_weights_match_library_exp():
+    geom = ti.ultrasound_geometry(n_elements=8, n_bins=4, grid=(3, 2, 4))
+    w = oracle.weights(geom.rx_pos, geom.targets, geom.freqs, True, geom.c)
+    d = np.linalg.norm(geom.targets[:, None, :] - geom.rx_pos[None, :, :], axis=2)
+    ref = np.exp(-2j * np.pi * geom.freqs[0][None, :] * d / geom.c) / d
+    assert np.allclose(w[0], ref, rtol=1e-12, atol=0)
+    assert np.allclose(np.abs(w[0]), 1.0 / d, rtol=1e-14)
+
+
+def test_weights_quarter_cycle_large_phase():
+    """f tau = n + 1/4 with n ~ 1e6 gives w = -i exactly after FP16 rounding."""
+    pos = np.array([[1.0, 0.0, 0.0]])
+    tgt = np.array([[1.0, 0.0, 0.0]])
+    f = np.array([[1_000_000.25]])
+    w16 = oracle.weights_fp16(pos, tgt, f, False, 1.0)
+    assert float(w16[0, 0, 0, 0]) == 0.0 and float(w16[0, 0, 0, 1]) == -1.0
+    f = np.array([[1_000_000.5]])      # half cycle: w = -1
+    w16 = oracle.weights_fp16(pos, tgt, f, False, 1.0)
+    assert float(w16[0, 0, 0, 0]) == -1.0 and float(w16[0, 0, 0, 1]) == 0.0
+
+
+# ----------------------------------------------------------------- 1-bit
+def _read_table2():
+    rows, scal = [], {}
+    with open(os.path.join(GOLDEN, "table2_1bit_dot.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            t = line.split()
+            if t[0].isdigit():
+                rows.append([int(v) for v in t])
+            else:
+                scal[t[0]] = int(t[1])
+    return rows, scal
+
+
+def test_table2_worked_example():
+    rows, scal = _read_table2()
+    K = len(rows)
+    a = sum(r[4] << r[0] for r in rows)
+    b = sum(r[5] << r[0] for r in rows)
+    assert onebit.values(a, K) == [r[1] for r in rows]
+    assert onebit.values(b, K) == [r[2] for r in rows]
+    assert onebit.popc(a ^ b) == scal["popc"]
+    assert onebit.dot_xor(a, b, K) == scal["eq4"] == scal["dot"]
+    assert onebit.dot_and(a, b, K) == scal["dot"]
+    # through the int64 oracle: imaginary planes all +1 gives
+    # Re = A.B - K and Im = sum A + sum B (Sec. III-B product)
+    Wb = np.zeros((1, 2, 1, 4), np.uint32)
+    Xb = np.zeros((1, 2, 1, 4), np.uint32)
+    Wb[0, 0, 0, 0], Wb[0, 1, 0, 0] = a, 0xF
+    Xb[0, 0, 0, 0], Xb[0, 1, 0, 0] = b, 0xF
+    Y = oracle.bgemm(Wb, Xb, K)
+    assert Y[0, 0, 0, 0] == scal["dot"] - K
+    assert Y[0, 0, 0, 1] == sum(r[1] for r in rows) + sum(r[2] for r in rows)
+
+
+def test_eq4_equals_eq6_random():
+    g = np.random.default_rng(1)
+    for _ in range(2000):
+        K = int(g.integers(1, 300))
+        a = int(g.integers(0, 2**62)) | (int(g.integers(0, 2**62)) << 62)
+        b = int(g.integers(0, 2**62)) | (int(g.integers(0, 2**62)) << 62)
+        v = sum(x * y for x, y in zip(onebit.values(a, K), onebit.values(b, K)))
+        assert onebit.dot_xor(a, b, K) == v == onebit.dot_and(a, b, K)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+def test_bgemm_exhaustive_small_K(K):
+    """All 4^K complex 1-bit vectors against all 4^K: the int64 oracle equals
+    explicit +-1 complex arithmetic and the paper's Eq. 5 for several pads."""
+    n = 4 ** K
+    vecs = list(itertools.product(range(1 << K), repeat=2))          # (re bits, im bits)
+    Wb = np.zeros((1, 2, n, 4), np.uint32)
+    Xb = np.zeros((1, 2, n, 4), np.uint32)
+    for i, (r, im) in enumerate(vecs):
+        Wb[0, 0, i, 0], Wb[0, 1, i, 0] = r, im
+        Xb[0, 0, i, 0], Xb[0, 1, i, 0] = r, im
+    Y = oracle.bgemm(Wb, Xb, K)
+    vals = [np.array(onebit.values(r, K)) + 1j * np.array(onebit.values(im, K)) for r, im in vecs]
+    V = np.array(vals)                                               # [n, K] complex
+    ref = V @ V.T                                                    # W rows times X columns
+    assert np.array_equal(Y[0, :, :, 0], ref.real.astype(np.int64))
+    assert np.array_equal(Y[0, :, :, 1], ref.imag.astype(np.int64))
+    g = np.random.default_rng(K)
+    for _ in range(300):
+        i, j = int(g.integers(n)), int(g.integers(n))
+        (ar, ai), (br, bi) = vecs[i], vecs[j]
+        for pad in (0, 1, 5, 32 - K, 128 - K):
+            assert onebit.complex_dot_padded(ar, ai, br, bi, K, pad) == tuple(Y[0, i, j])
+
+
+def test_bgemm_matched_conjugate_gives_2K():
+    K = 77
+    g = ti.rng(2)
+    Xb = ti.random_sign_words(g, (1, 2, 5, ti.words_per_row(K)))
+    Wb = Xb.copy()
+    Wb[:, 1] = ~Wb[:, 1]                 # conj: same real bits, flipped imaginary bits
+    Y = oracle.bgemm(Wb, Xb, K)
+    assert np.all(np.diagonal(Y[0, :, :, 0]) == 2 * K)
+    assert np.all(np.diagonal(Y[0, :, :, 1]) == 0)
+
+
+def test_bgemm_ignores_bits_beyond_K():
+    K = 45
+    g = ti.rng(3)
+    Wb, Xb = ti.onebit_block(seed=3, B=2, M=6, K=K, N=7)
+    Y = oracle.bgemm(Wb, Xb, K)
+    kw = Wb.shape[-1]
+    keep = np.zeros(kw, np.uint32)
+    keep[0] = 0xFFFFFFFF
+    keep[1] = (1 << (K - 32)) - 1
+    Y2 = oracle.bgemm(Wb & keep, Xb & keep, K)
+    assert np.array_equal(Y, Y2)
+    # and it equals Python complex arithmetic on the unpacked values
+    def unpack(row):
+        return np.array([(1 if (int(row[k // 32]) >> (k % 32)) & 1 else -1) for k in range(K)])
+    for b in range(2):
+        for m in range(6):
+            w = unpack(Wb[b, 0, m]) + 1j * unpack(Wb[b, 1, m])
+            for n in range(7):
+                x = unpack(Xb[b, 0, n]) + 1j * unpack(Xb[b, 1, n])
+                y = np.sum(w * x)
+                assert (Y[b, m, n, 0], Y[b, m, n, 1]) == (int(y.real), int(y.imag))
+
+
+def test_pack_signs_definition():
+    """Sign convention: +0 and -0 both give +1 (bit 1); any negative value,
+    however small, gives -1 (bit 0). Expected bits are tabulated by hand."""
+    table = [(0.0, 1), (-0.0, 1), (6e-8, 1), (-6e-8, 0), (65504.0, 1), (-65504.0, 0),
+             (np.inf, 1), (-np.inf, 0), (0.5, 1), (-0.5, 0), (3.0, 1), (-2.0, 0)]
+    K = 40
+    g = np.random.default_rng(4)
+    idx = g.integers(0, len(table), (1, 3, K, 2))
+    V = np.empty((1, 3, K, 2), np.float16)
+    bit = np.empty((1, 3, K, 2), np.int64)
+    for i, (v, bt) in enumerate(table):
+        V[idx == i] = v
+        bit[idx == i] = bt
+    Kw = ti.words_per_row(K)
+    P = oracle.pack_signs(V, k_is_row=False, Kw=Kw)
+    for r in range(3):
+        for p in range(2):
+            want = [0] * Kw
+            for k in range(K):
+                want[k // 32] |= int(bit[0, r, k, p]) << (k % 32)
+            assert [int(v) for v in P[0, p, r]] == want
+    # transposed packing equals packing of the explicit transpose
+    T = oracle.pack_signs(np.ascontiguousarray(V.transpose(0, 2, 1, 3)), k_is_row=True, Kw=Kw)
+    assert np.array_equal(T, P)
