@@ -1,0 +1,184 @@
+/*
+ * tcbf.h — C ABI of the GB300 tensor-core beamformer.
+ *
+ * Beamforming of many samples at once is the complex matrix product
+ * Y = W X (Sec. II, Eq. 3): W holds the steering weights (M beams x K
+ * receivers), X the sensor samples (K receivers x N samples), Y the beams
+ * (M x N).  A problem is a batch of such products (Sec. III: "batch size
+ * option"; Sec. V-B: batch = polarisations x channels).  As in Sec. III the
+ * caller supplies inputs, outputs and their shapes; the library chooses
+ * kernels and tile shapes.
+ *
+ * Conventions that hold for every call:
+ *  - All buffers are owned by the caller.  Unless stated otherwise a pointer
+ *    argument is DEVICE memory of the plan's device, 256-byte aligned (any
+ *    torch/cudaMalloc allocation is).  The plan owns only host state plus a
+ *    small device status word.
+ *  - Calls that take a stream are asynchronous and stream-ordered; argument
+ *    errors are returned synchronously and nothing is launched.  Errors that
+ *    only the device can see (a bounded wait that ran out) are recorded in
+ *    the plan's status word and read by tcbf_last_device_error().
+ *  - No call aborts, exits or traps.
+ *  - Complex values are interleaved (re, im) unless stated otherwise; all
+ *    matrices are row-major and batches are contiguous.
+ *  - Shapes are any value >= 1; padding is internal.
+ *  - Throughput is counted as 8*batch*M*N*K useful operations (Sec. IV-A).
+ */
+#ifndef TCBF_H
+#define TCBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tcbf_plan_s *tcbf_plan_t;
+/* A cudaStream_t passed as an opaque handle; NULL is the legacy default stream. */
+typedef void *tcbf_stream_t;
+
+typedef enum {
+    TCBF_OK = 0,
+    TCBF_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, bad shape, wrong mode for this call */
+    TCBF_ERR_UNSUPPORTED = 2,  /* no GPU, not sm_103, or a shape beyond the library limits */
+    TCBF_ERR_OOM = 3,          /* the plan's small device allocation failed */
+    TCBF_ERR_BUDGET = 4,       /* serving admission: request exceeds the memory budget */
+    TCBF_ERR_CUDA = 5,         /* a CUDA runtime/driver call failed */
+    TCBF_ERR_TIMEOUT = 6,      /* a device-side bounded wait ran out (see tcbf_last_device_error) */
+    TCBF_ERR_DEVICE = 7        /* another device-side check failed */
+} tcbf_status;
+
+typedef enum {
+    TCBF_MODE_FP16 = 0,        /* FP16 planar re/im inputs, FP32 accumulate (Sec. III) */
+    TCBF_MODE_FP8SPLIT = 1,    /* e4m3 hi+lo split of each operand, FP32 accumulate (FP8: Sec. VI) */
+    TCBF_MODE_1BIT = 2         /* +-1+-i values, one bit per component, exact int32 (Sec. III-D) */
+} tcbf_mode;
+
+/* Source element types accepted by tcbf_transpose_pack. */
+typedef enum {
+    TCBF_SRC_CF16 = 0,         /* interleaved complex FP16: 4 bytes per value */
+    TCBF_SRC_CF32 = 1          /* interleaved complex FP32: 8 bytes per value, rounded RN to FP16 */
+} tcbf_src_type;
+
+typedef struct {
+    int64_t batch;      /* number of independent products in the problem (>= 1) */
+    int64_t M;          /* beams (rows of W and Y) */
+    int64_t N;          /* samples (columns of X and Y) */
+    int64_t K;          /* receivers (summed over) */
+    int64_t w_batches;  /* distinct weight matrices; batch b uses W[b / (batch / w_batches)].
+                           0 means batch. Must divide batch. */
+    int32_t mode;       /* tcbf_mode */
+    uint32_t flags;     /* reserved, must be 0 */
+} tcbf_problem;
+
+/*
+ * Packed operand layouts (produced by tcbf_transpose_pack or
+ * tcbf_weights_from_geometry, consumed by tcbf_beamform_*).  The GEMM
+ * needs its inputs split into real and imaginary planes (Sec. VI) and tiled
+ * in device memory (Sec. III); here both operands are stored K-contiguous:
+ *   FP16 W : [w_batches][2][M][Kp] binary16, Kp = K rounded up to 8, zero pad
+ *   FP16 X : [batch][2][N][Kp]     binary16 (X transposed: samples are rows)
+ *   1-bit W: [w_batches][2][M][Kw] uint32,   Kw = 4 * ceil(K / 128)
+ *   1-bit X: [batch][2][N][Kw]     uint32
+ * Plane 0 is the real part, plane 1 the imaginary part.  1-bit element k
+ * of a row is bit (k % 32) of word (k / 32); bit 1 is +1, bit 0 is -1
+ * (Fig. 1).  Bits at k >= K are ignored by the GEMM.
+ *   FP8-split W/X: per row r and plane p, the element v is represented as
+ *   (hi + lo) * 2^-e[r] with hi, lo e4m3: layout [rows-batches][2 planes]
+ *   [2 (hi, lo)][rows][Kp] bytes followed by int8 exponents e per (batch,
+ *   plane, row); see tcbf_packed_size.
+ */
+
+/* Create a plan for problem *p on CUDA device `device`.  Validates the
+ * shape, checks for an sm_103 device and allocates the plan's 256-byte
+ * device status word.  *out is set to NULL on error. */
+tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p, int device);
+
+/* Destroy a plan (NULL is accepted).  The caller must not have work that
+ * uses the plan in flight. */
+tcbf_status tcbf_plan_destroy(tcbf_plan_t plan);
+
+/* Bytes of the packed operand `which` (0 = W, 1 = X) for this plan. */
+tcbf_status tcbf_packed_size(tcbf_plan_t plan, int which, size_t *bytes);
+
+/* Bytes of caller-provided workspace the beamform calls need (currently 0). */
+tcbf_status tcbf_workspace_size(tcbf_plan_t plan, size_t *bytes);
+
+/*
+ * Transpose/pack kernel (Sec. III: "the matrix-matrix multiplication kernel
+ * requires that the input matrices are tiled in device memory ... handled
+ * through a transpose kernel"; for 1-bit "32 consecutive 1-bit samples must
+ * be stored in a single 32-bit integer").
+ *   which = 0: src is W, [w_batches][M][K] complex of type src_type;
+ *   which = 1: src is X, [batch][K][N] complex of type src_type.
+ *   dst: packed layout of the plan's mode (see above), tcbf_packed_size bytes.
+ * FP16/FP8 modes de-interleave (and for X transpose) into planes; 1-bit mode
+ * keeps only the sign of each component (v >= 0 -> bit 1, so -0 -> +1;
+ * NaN -> bit 0) and packs 32 per word along K.  src and dst must not overlap.
+ */
+tcbf_status tcbf_transpose_pack(tcbf_plan_t plan, int which, int src_type, const void *src,
+                                void *dst, tcbf_stream_t stream);
+
+/*
+ * FP16 complex GEMM, Y[b] = W[b'] X[b] (Eq. 3), four real tensor-core MMAs
+ * per complex tile (Sec. III-B) accumulated in FP32.
+ *   Wp, Xp: FP16 packed operands of this plan (mode TCBF_MODE_FP16).
+ *   Y: [batch][M][N] interleaved complex FP32 (8 bytes per value), written
+ *      in full.  Y must not overlap Wp or Xp.
+ */
+tcbf_status tcbf_beamform_fp16(tcbf_plan_t plan, const void *Wp, const void *Xp, float *Y,
+                               tcbf_stream_t stream);
+
+/*
+ * Split-FP8 complex GEMM: Y ~= Wh Xh + Wh Xl + Wl Xh summed in FP32 and
+ * scaled back (FP8 formats: Sec. VI future work).  Wp, Xp: FP8-split packed
+ * operands of this plan (mode TCBF_MODE_FP8SPLIT).  Y as for FP16.
+ */
+tcbf_status tcbf_beamform_fp8split(tcbf_plan_t plan, const void *Wp, const void *Xp, float *Y,
+                                   tcbf_stream_t stream);
+
+/*
+ * 1-bit complex GEMM (Sec. III-D, Eq. 4-6), exact.  Wbits, Xbits: 1-bit
+ * packed operands (mode TCBF_MODE_1BIT).  Y: [batch][M][N] interleaved
+ * int32 pairs (re, im), each |value| <= 2K.
+ */
+tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbits, const uint32_t *Xbits,
+                               int32_t *Y, tcbf_stream_t stream);
+
+/*
+ * Steering weights from geometry (Eq. 1-2): for weight batch b, beam m and
+ * receiver k,
+ *   far field  (near_field = 0): tau = (p_k . s_m) / c, A = 1, s_m a unit direction;
+ *   near field (near_field = 1): d = |t_m - p_k|, tau = d / c, A = 1 / d;
+ *   w = A exp(-2 pi i f[b,k] tau).
+ * The phase f*tau is formed and reduced modulo one cycle in FP64; sine and
+ * cosine of the reduced phase are taken in FP32.  Inputs are device FP64
+ * arrays: rx_pos [K][3] (m), targets [M][3], freqs [w_batches][K] (Hz);
+ * c in m/s.  Wp_out receives W packed for the plan's mode (FP16 planes,
+ * sign bits, or FP8 split), tcbf_packed_size(plan, 0) bytes.
+ */
+tcbf_status tcbf_weights_from_geometry(tcbf_plan_t plan, const double *rx_pos,
+                                       const double *targets, int near_field,
+                                       const double *freqs, double c, void *Wp_out,
+                                       tcbf_stream_t stream);
+
+/* Synchronise the plan's device, read and clear its device status word.
+ * Returns TCBF_OK, TCBF_ERR_TIMEOUT or TCBF_ERR_DEVICE. */
+tcbf_status tcbf_last_device_error(tcbf_plan_t plan);
+
+/* Static text for a status code. */
+const char *tcbf_status_string(tcbf_status s);
+
+/* Number of kernel configurations (tile shapes) the plan's mode offers,
+ * the one in use, and a way to pick one (the autotuner's hook). */
+tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count);
+tcbf_status tcbf_plan_get_config(tcbf_plan_t plan, int *config);
+tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config);
+/* Human-readable description of configuration `config` (static string). */
+const char *tcbf_config_name(tcbf_plan_t plan, int config);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCBF_H */

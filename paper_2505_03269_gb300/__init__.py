@@ -1,0 +1,12 @@
+"""GB300 (sm_103a) tensor-core beamformer: Y = W X as a batched complex GEMM.
+
+The compute path is the CUDA library ``libtcbf.so`` (C ABI in
+``include/tcbf.h``); ``binding`` is its ctypes shim and ``api`` a small
+torch-facing convenience layer on top of it.  Nothing here computes on the
+CPU: without the built library or a GPU every call raises.
+"""
+from .binding import (MODE_1BIT, MODE_FP8SPLIT, MODE_FP16, SRC_CF16, SRC_CF32, Plan,  # noqa: F401
+                      TcbfError, load, status_string)
+
+__all__ = ["Plan", "TcbfError", "load", "status_string", "MODE_FP16", "MODE_FP8SPLIT",
+           "MODE_1BIT", "SRC_CF16", "SRC_CF32"]

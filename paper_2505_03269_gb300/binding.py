@@ -1,0 +1,200 @@
+"""ctypes binding of libtcbf.so (include/tcbf.h), same names as the C ABI.
+
+Argument marshalling only: every step of the beamforming path runs in the
+library's CUDA kernels.  Tensors are passed as raw device pointers with
+``tensor.data_ptr()`` and the stream as ``torch.cuda.current_stream()``'s
+handle; torch provides device memory and streams, nothing else.  There is
+no fallback: if the library or a GPU is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtcbf.so")
+
+TCBF_OK = 0
+STATUS_NAMES = {0: "TCBF_OK", 1: "TCBF_ERR_INVALID_ARG", 2: "TCBF_ERR_UNSUPPORTED",
+                3: "TCBF_ERR_OOM", 4: "TCBF_ERR_BUDGET", 5: "TCBF_ERR_CUDA",
+                6: "TCBF_ERR_TIMEOUT", 7: "TCBF_ERR_DEVICE"}
+MODE_FP16, MODE_FP8SPLIT, MODE_1BIT = 0, 1, 2
+SRC_CF16, SRC_CF32 = 0, 1
+
+# every symbol include/tcbf.h declares
+EXPORTED = [
+    "tcbf_plan_create", "tcbf_plan_destroy", "tcbf_packed_size", "tcbf_workspace_size",
+    "tcbf_transpose_pack", "tcbf_beamform_fp16", "tcbf_beamform_fp8split",
+    "tcbf_beamform_1bit", "tcbf_weights_from_geometry", "tcbf_last_device_error",
+    "tcbf_status_string", "tcbf_plan_num_configs", "tcbf_plan_get_config",
+    "tcbf_plan_set_config", "tcbf_config_name",
+]
+
+
+class TcbfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("M", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("K", ctypes.c_int64), ("w_batches", ctypes.c_int64),
+                ("mode", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libtcbf.so (build it first with paper_2505_03269_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtcbf.so is not built ({path}); run "
+                           "python -c 'import __graft_entry__ as g; g.build()'")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "tcbf_plan_create": [ctypes.POINTER(vp), ctypes.POINTER(Problem), i32],
+        "tcbf_plan_destroy": [vp],
+        "tcbf_packed_size": [vp, i32, ctypes.POINTER(ctypes.c_size_t)],
+        "tcbf_workspace_size": [vp, ctypes.POINTER(ctypes.c_size_t)],
+        "tcbf_transpose_pack": [vp, i32, i32, vp, vp, vp],
+        "tcbf_beamform_fp16": [vp, vp, vp, vp, vp],
+        "tcbf_beamform_fp8split": [vp, vp, vp, vp, vp],
+        "tcbf_beamform_1bit": [vp, vp, vp, vp, vp],
+        "tcbf_weights_from_geometry": [vp, vp, vp, i32, vp, ctypes.c_double, vp, vp],
+        "tcbf_last_device_error": [vp],
+        "tcbf_plan_num_configs": [vp, ctypes.POINTER(i32)],
+        "tcbf_plan_get_config": [vp, ctypes.POINTER(i32)],
+        "tcbf_plan_set_config": [vp, i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.tcbf_status_string.argtypes = [ctypes.c_int]
+    lib.tcbf_status_string.restype = ctypes.c_char_p
+    lib.tcbf_config_name.argtypes = [vp, ctypes.c_int]
+    lib.tcbf_config_name.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != TCBF_OK:
+        raise TcbfError(status, where)
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor / int / None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A tcbf plan: one problem shape, mode and device."""
+
+    def __init__(self, batch, M, N, K, mode=MODE_FP16, w_batches=0, device=0):
+        lib = load()
+        self._lib = lib
+        self.problem = Problem(batch, M, N, K, w_batches, mode, 0)
+        h = ctypes.c_void_p()
+        _check(lib.tcbf_plan_create(ctypes.byref(h), ctypes.byref(self.problem), device),
+               "tcbf_plan_create")
+        self.handle = h
+        self.batch, self.M, self.N, self.K = batch, M, N, K
+        self.w_batches = w_batches or batch
+        self.mode = mode
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.tcbf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --------------------------------------------------------------- sizes
+    def packed_size(self, which: int) -> int:
+        n = ctypes.c_size_t()
+        _check(self._lib.tcbf_packed_size(self.handle, which, ctypes.byref(n)), "tcbf_packed_size")
+        return n.value
+
+    @property
+    def Kp(self):
+        return (self.K + 7) // 8 * 8
+
+    @property
+    def Kw(self):
+        return (self.K + 127) // 128 * 4
+
+    # ------------------------------------------------------------- kernels
+    def transpose_pack(self, which, src, dst, src_type=SRC_CF16, stream=None):
+        _check(self._lib.tcbf_transpose_pack(self.handle, which, src_type, _ptr(src), _ptr(dst),
+                                             _stream(stream)), "tcbf_transpose_pack")
+
+    def beamform_fp16(self, Wp, Xp, Y, stream=None):
+        _check(self._lib.tcbf_beamform_fp16(self.handle, _ptr(Wp), _ptr(Xp), _ptr(Y),
+                                            _stream(stream)), "tcbf_beamform_fp16")
+
+    def beamform_fp8split(self, Wp, Xp, Y, stream=None):
+        _check(self._lib.tcbf_beamform_fp8split(self.handle, _ptr(Wp), _ptr(Xp), _ptr(Y),
+                                                _stream(stream)), "tcbf_beamform_fp8split")
+
+    def beamform_1bit(self, Wb, Xb, Y, stream=None):
+        _check(self._lib.tcbf_beamform_1bit(self.handle, _ptr(Wb), _ptr(Xb), _ptr(Y),
+                                            _stream(stream)), "tcbf_beamform_1bit")
+
+    def weights_from_geometry(self, rx_pos, targets, near_field, freqs, c, Wp, stream=None):
+        _check(self._lib.tcbf_weights_from_geometry(
+            self.handle, _ptr(rx_pos), _ptr(targets), int(near_field), _ptr(freqs), float(c),
+            _ptr(Wp), _stream(stream)), "tcbf_weights_from_geometry")
+
+    def last_device_error(self) -> int:
+        return self._lib.tcbf_last_device_error(self.handle)
+
+    # ------------------------------------------------------------- configs
+    def num_configs(self) -> int:
+        n = ctypes.c_int()
+        _check(self._lib.tcbf_plan_num_configs(self.handle, ctypes.byref(n)), "num_configs")
+        return n.value
+
+    def get_config(self) -> int:
+        n = ctypes.c_int()
+        _check(self._lib.tcbf_plan_get_config(self.handle, ctypes.byref(n)), "get_config")
+        return n.value
+
+    def set_config(self, c: int):
+        _check(self._lib.tcbf_plan_set_config(self.handle, int(c)), "set_config")
+
+    def config_name(self, c: int) -> str:
+        return self._lib.tcbf_config_name(self.handle, int(c)).decode()
+
+
+def status_string(s: int) -> str:
+    return load().tcbf_status_string(int(s)).decode()

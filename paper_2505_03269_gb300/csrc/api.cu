@@ -1,0 +1,288 @@
+// api.cu — the C ABI (include/tcbf.h): plan validation and bookkeeping,
+// argument checks, tensor-map encoding and kernel dispatch.  Host code only.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <new>
+
+#include "tcbf_internal.h"
+
+namespace tcbf {
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Makes the plan's device current for the duration of a call.
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        ok_ = (prev_ == dev) || cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev_ >= 0) cudaSetDevice(prev_);
+    }
+    bool ok() const { return ok_; }
+
+  private:
+    int prev_ = -1;
+    bool ok_ = false;
+};
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+constexpr int64_t kMaxDim = int64_t(1) << 30;   // per-dimension limit (int32 tile indexing)
+
+tcbf_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TCBF_OK;
+    if (e == cudaErrorMemoryAllocation) return TCBF_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
+        e == cudaErrorNoKernelImageForDevice || e == cudaErrorNotSupported)
+        return TCBF_ERR_UNSUPPORTED;
+    return TCBF_ERR_CUDA;
+}
+
+size_t packed_bytes(const tcbf_plan_s &pl, int which) {
+    const tcbf_problem &p = pl.p;
+    const int64_t nb = which == 0 ? p.w_batches : p.batch;
+    const int64_t rows = which == 0 ? p.M : p.N;
+    switch (p.mode) {
+        case TCBF_MODE_FP16:
+            return static_cast<size_t>(nb * 2 * rows * pl.Kp * 2);
+        case TCBF_MODE_1BIT:
+            return static_cast<size_t>(nb * 2 * rows * pl.Kw * 4);
+        default:
+            return 0;
+    }
+}
+
+}  // namespace
+
+CUresult encode_tiled(CUtensorMap *map, CUtensorMapDataType type, uint32_t rank, void *gaddr,
+                      const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box,
+                      CUtensorMapSwizzle swizzle) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return CUDA_ERROR_NOT_SUPPORTED;
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return fn(map, type, rank, gaddr, reinterpret_cast<const cuuint64_t *>(dims),
+              reinterpret_cast<const cuuint64_t *>(strides_bytes),
+              reinterpret_cast<const cuuint32_t *>(box), estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+}  // namespace tcbf
+
+using namespace tcbf;
+
+TCBF_EXPORT const char *tcbf_status_string(tcbf_status s) {
+    switch (s) {
+        case TCBF_OK: return "ok";
+        case TCBF_ERR_INVALID_ARG: return "invalid argument";
+        case TCBF_ERR_UNSUPPORTED: return "unsupported (device or shape)";
+        case TCBF_ERR_OOM: return "out of device memory";
+        case TCBF_ERR_BUDGET: return "over memory budget";
+        case TCBF_ERR_CUDA: return "CUDA error";
+        case TCBF_ERR_TIMEOUT: return "device-side wait timed out";
+        case TCBF_ERR_DEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p, int device) {
+    if (!out) return TCBF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!p) return TCBF_ERR_INVALID_ARG;
+    tcbf_problem q = *p;
+    if (q.w_batches == 0) q.w_batches = q.batch;
+    if (q.batch < 1 || q.M < 1 || q.N < 1 || q.K < 1 || q.w_batches < 1) return TCBF_ERR_INVALID_ARG;
+    if (q.batch % q.w_batches != 0) return TCBF_ERR_INVALID_ARG;
+    if (q.mode != TCBF_MODE_FP16 && q.mode != TCBF_MODE_FP8SPLIT && q.mode != TCBF_MODE_1BIT)
+        return TCBF_ERR_INVALID_ARG;
+    if (q.flags != 0) return TCBF_ERR_INVALID_ARG;
+    if (q.M > kMaxDim || q.N > kMaxDim || q.K > kMaxDim || q.batch > 65535)
+        return TCBF_ERR_UNSUPPORTED;
+    if (q.mode == TCBF_MODE_FP8SPLIT) return TCBF_ERR_UNSUPPORTED;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TCBF_ERR_UNSUPPORTED;
+    if (device < 0 || device >= ndev) return TCBF_ERR_INVALID_ARG;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return TCBF_ERR_CUDA;
+    if (prop.major != 10 || prop.minor != 3) return TCBF_ERR_UNSUPPORTED;   // sm_103 only
+
+    auto *pl = new (std::nothrow) tcbf_plan_s;
+    if (!pl) return TCBF_ERR_OOM;
+    pl->p = q;
+    pl->device = device;
+    pl->num_sms = prop.multiProcessorCount;
+    pl->per_w = q.batch / q.w_batches;
+    pl->Kp = round_up(q.K, 8);
+    pl->Kw = round_up(q.K, 128) / 32;
+    pl->config = 0;
+    {
+        DeviceGuard g(device);
+        if (!g.ok()) {
+            delete pl;
+            return TCBF_ERR_CUDA;
+        }
+        if (cudaMalloc(&pl->status, 256) != cudaSuccess) {
+            delete pl;
+            return TCBF_ERR_OOM;
+        }
+        if (cudaMemset(pl->status, 0, 256) != cudaSuccess) {
+            cudaFree(pl->status);
+            delete pl;
+            return TCBF_ERR_CUDA;
+        }
+    }
+    *out = pl;
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_plan_destroy(tcbf_plan_t plan) {
+    if (!plan) return TCBF_OK;
+    {
+        DeviceGuard g(plan->device);
+        if (plan->status) cudaFree(plan->status);
+    }
+    delete plan;
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_packed_size(tcbf_plan_t plan, int which, size_t *bytes) {
+    if (!plan || !bytes || (which != 0 && which != 1)) return TCBF_ERR_INVALID_ARG;
+    *bytes = packed_bytes(*plan, which);
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_workspace_size(tcbf_plan_t plan, size_t *bytes) {
+    if (!plan || !bytes) return TCBF_ERR_INVALID_ARG;
+    *bytes = 0;
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_transpose_pack(tcbf_plan_t plan, int which, int src_type,
+                                            const void *src, void *dst, tcbf_stream_t stream) {
+    if (!plan || !src || !dst || (which != 0 && which != 1)) return TCBF_ERR_INVALID_ARG;
+    if (src_type != TCBF_SRC_CF16 && src_type != TCBF_SRC_CF32) return TCBF_ERR_INVALID_ARG;
+    if (!aligned16(src) || !aligned16(dst)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    switch (plan->p.mode) {
+        case TCBF_MODE_FP16:
+            e = which == 0 ? launch_pack_f16_w(*plan, src_type, src, dst, s)
+                           : launch_pack_f16_x(*plan, src_type, src, dst, s);
+            break;
+        case TCBF_MODE_1BIT:
+            e = which == 0 ? launch_pack_bits_w(*plan, src_type, src, dst, s)
+                           : launch_pack_bits_x(*plan, src_type, src, dst, s);
+            break;
+        default:
+            return TCBF_ERR_UNSUPPORTED;
+    }
+    return from_cuda(e);
+}
+
+TCBF_EXPORT tcbf_status tcbf_beamform_fp16(tcbf_plan_t plan, const void *Wp, const void *Xp,
+                                           float *Y, tcbf_stream_t stream) {
+    if (!plan || !Wp || !Xp || !Y) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_FP16) return TCBF_ERR_INVALID_ARG;
+    if (!aligned16(Wp) || !aligned16(Xp) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(launch_gemm_f16(*plan, Wp, Xp, Y, static_cast<cudaStream_t>(stream)));
+}
+
+TCBF_EXPORT tcbf_status tcbf_beamform_fp8split(tcbf_plan_t plan, const void *Wp, const void *Xp,
+                                               float *Y, tcbf_stream_t stream) {
+    if (!plan || !Wp || !Xp || !Y) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_FP8SPLIT) return TCBF_ERR_INVALID_ARG;
+    (void)stream;
+    return TCBF_ERR_UNSUPPORTED;
+}
+
+TCBF_EXPORT tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbits,
+                                           const uint32_t *Xbits, int32_t *Y,
+                                           tcbf_stream_t stream) {
+    if (!plan || !Wbits || !Xbits || !Y) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_1BIT) return TCBF_ERR_INVALID_ARG;
+    (void)stream;
+    return TCBF_ERR_UNSUPPORTED;
+}
+
+TCBF_EXPORT tcbf_status tcbf_weights_from_geometry(tcbf_plan_t plan, const double *rx_pos,
+                                                   const double *targets, int near_field,
+                                                   const double *freqs, double c, void *Wp_out,
+                                                   tcbf_stream_t stream) {
+    if (!plan || !rx_pos || !targets || !freqs || !Wp_out) return TCBF_ERR_INVALID_ARG;
+    if (near_field != 0 && near_field != 1) return TCBF_ERR_INVALID_ARG;
+    if (!(c > 0.0)) return TCBF_ERR_INVALID_ARG;
+    if (!aligned16(Wp_out) || (reinterpret_cast<uintptr_t>(rx_pos) & 7u) ||
+        (reinterpret_cast<uintptr_t>(targets) & 7u) || (reinterpret_cast<uintptr_t>(freqs) & 7u))
+        return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(launch_weights(*plan, rx_pos, targets, near_field, freqs, c, Wp_out,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
+TCBF_EXPORT tcbf_status tcbf_last_device_error(tcbf_plan_t plan) {
+    if (!plan) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TCBF_ERR_CUDA;
+    uint32_t word = 0;
+    if (cudaMemcpy(&word, plan->status, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TCBF_ERR_CUDA;
+    if (word == 0) return TCBF_OK;
+    cudaMemset(plan->status, 0, sizeof(word));
+    return (word & 0xffu) ? TCBF_ERR_TIMEOUT : TCBF_ERR_DEVICE;
+}
+
+TCBF_EXPORT tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count) {
+    if (!plan || !count) return TCBF_ERR_INVALID_ARG;
+    *count = plan->p.mode == TCBF_MODE_FP16 ? gemm_f16_num_configs() : 1;
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_plan_get_config(tcbf_plan_t plan, int *config) {
+    if (!plan || !config) return TCBF_ERR_INVALID_ARG;
+    *config = plan->config;
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
+    if (!plan) return TCBF_ERR_INVALID_ARG;
+    int n = 0;
+    tcbf_plan_num_configs(plan, &n);
+    if (config < 0 || config >= n) return TCBF_ERR_INVALID_ARG;
+    plan->config = config;
+    return TCBF_OK;
+}
+
+TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
+    if (!plan) return "invalid";
+    if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
+    return config == 0 ? "default" : "invalid";
+}

@@ -1,0 +1,347 @@
+// gemm_f16.cu — FP16 complex GEMM on the sm_103a tensor cores (tcgen05).
+//
+// Y[b] = W[b'] X[b] (Eq. 3) with the complex product of Sec. III-B built
+// from four real MMAs per K step, accumulated in FP32 in tensor memory:
+//     D_re += Wr Xr,  D_re += (-Wi) Xi,  D_im += Wr Xi,  D_im += Wi Xr.
+// The paper negates Im in registers (its step 3); here the MMA instruction
+// descriptor's negate-A bit does it, so no operand is modified.
+//
+// Persistent, warp-specialised kernel (one CTA per SM, 192 threads):
+//   warp 0      TMA producer: both planes of a W tile (128 x 64) and of an
+//               X tile (BN x 64) per stage into a STAGES-deep shared-memory
+//               ring (Sec. III-C: multi-stage buffers filled asynchronously)
+//   warp 1      TMEM owner and single-thread MMA issuer
+//   warps 2-5   epilogue: TMEM -> registers -> interleaved complex64 Y
+// Tiles (batch, m-tile, n-tile) are strided over the CTAs; the two TMEM
+// accumulator sets are double-buffered when they fit, so the epilogue of
+// one tile overlaps the MMAs of the next.  All waits are bounded.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "ptx.cuh"
+#include "tcbf_internal.h"
+
+namespace tcbf {
+namespace {
+
+using namespace dev;
+
+constexpr int BM = 128;        // rows of W per tile (TMEM lanes)
+constexpr int BK = 64;         // K elements per stage: one 128-byte swizzled row
+constexpr int kThreads = 192;
+
+struct GemmArgs {
+    float *Y;
+    uint32_t *status;
+    int M, N, K;
+    int per_w;
+    int m_tiles, n_tiles;
+    int num_kb;
+    int total_tiles;
+};
+
+constexpr int pow2_cols(int c) {
+    return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512;
+}
+
+template <int BN, int STAGES>
+struct Cfg {
+    static constexpr int A_PLANE = BM * BK * 2;              // bytes of one W plane tile
+    static constexpr int B_PLANE = BN * BK * 2;              // bytes of one X plane tile
+    static constexpr int A_BYTES = 2 * A_PLANE;
+    static constexpr int B_BYTES = 2 * B_PLANE;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int ACC_BUFS = (4 * BN <= 512) ? 2 : 1;
+    static constexpr int TMEM_COLS = pow2_cols(ACC_BUFS * 2 * BN);
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 256 + 1024;
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M=128");
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
+
+__device__ __forceinline__ void decode_tile(int t, const GemmArgs &a, int &b, int &mt, int &nt) {
+    nt = t % a.n_tiles;
+    const int rest = t / a.n_tiles;
+    mt = rest % a.m_tiles;
+    b = rest / a.m_tiles;
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    cgemm_f16_kernel(const __grid_constant__ CUtensorMap tmW,
+                     const __grid_constant__ CUtensorMap tmX, const GemmArgs args) {
+    using C = Cfg<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+    const uint32_t s0 = smem_u32(smem);
+
+    // barrier block after the stage ring
+    const uint32_t bar0 = s0 + STAGES * C::STAGE_BYTES;
+    const uint32_t full0 = bar0;                       // STAGES x 8 bytes
+    const uint32_t empty0 = full0 + 8 * STAGES;        // STAGES x 8
+    const uint32_t tfull0 = empty0 + 8 * STAGES;       // 2 x 8
+    const uint32_t tempty0 = tfull0 + 16;              // 2 x 8
+    const uint32_t done_bar = tempty0 + 16;            // 8
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + STAGES * C::STAGE_BYTES + 16 * STAGES + 40);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 128);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmW);
+        tma_prefetch_desc(&tmX);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
+                int b, mt, nt;
+                decode_tile(t, args, b, mt, nt);
+                const int bw = b / args.per_w;
+                for (int kb = 0; kb < args.num_kb; ++kb) {
+                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = full0 + 8 * stage;
+                    const uint32_t dst = s0 + stage * C::STAGE_BYTES;
+                    mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
+                    tma_load_3d(dst, &tmW, fb, kb * BK, mt * BM, 2 * bw);
+                    tma_load_3d(dst + C::A_BYTES, &tmX, fb, kb * BK, nt * BN, 2 * b);
+                    ++issued;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutProducer);
+                *abort_flag = 1;
+                // let every copy this thread started land before the CTA exits
+                for (int s = 0; s < STAGES; ++s) {
+                    if (issued > static_cast<uint32_t>(s)) {
+                        const uint32_t count = (issued - s + STAGES - 1) / STAGES;
+                        if (!mbar_wait(full0 + 8 * s, (count - 1) & 1u))
+                            atomicOr(args.status, kErrTimeoutDrain);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t kIdesc = idesc_f32acc(BM, BN, 0, false);
+            constexpr uint32_t kIdescNeg = idesc_f32acc(BM, BN, 0, true);
+            int stage = 0;
+            uint32_t phase = 0;
+            int local = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x, ++local) {
+                const int acc = local % C::ACC_BUFS;
+                const uint32_t aphase = (local / C::ACC_BUFS) & 1;
+                if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_re = tmem_base + acc * 2 * BN;
+                const uint32_t d_im = d_re + BN;
+                for (int kb = 0; kb < args.num_kb; ++kb) {
+                    if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = s0 + stage * C::STAGE_BYTES;
+                    const uint32_t bx = a + C::A_BYTES;
+                    const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
+                    for (int j = 0; j < ksteps; ++j) {
+                        const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
+                        const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
+                        const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
+                        const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
+                        const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
+                        mma_f16(d_re, ar, br, kIdesc, accum);
+                        mma_f16(d_re, ai, bi, kIdescNeg, 1u);
+                        mma_f16(d_im, ar, bi, kIdesc, accum);
+                        mma_f16(d_im, ai, br, kIdesc, 1u);
+                    }
+                    mma_commit(empty0 + 8 * stage);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(tfull0 + 8 * acc);
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutMma);
+                *abort_flag = 1;
+            }
+            // every MMA issued must finish before tensor memory is released
+            mma_commit(done_bar);
+            if (!mbar_wait(done_bar, 0)) atomicOr(args.status, kErrTimeoutDrain);
+        }
+    } else {
+        // --------------------------------------------------------- epilogue
+        const int quarter = warp & 3;                // TMEM lanes this warp may access
+        const int row = quarter * 32 + lane;
+        const bool vec_ok = (args.N & 1) == 0;       // float4 stores need 16-byte aligned rows
+        int local = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < args.total_tiles; t += gridDim.x, ++local) {
+            const int acc = local % C::ACC_BUFS;
+            const uint32_t aphase = (local / C::ACC_BUFS) & 1;
+            if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            int b, mt, nt;
+            decode_tile(t, args, b, mt, nt);
+            const int m = mt * BM + row;
+            const uint32_t tbase =
+                tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * 2 * BN;
+            float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
+#pragma unroll 1
+            for (int c = 0; c < BN / 16; ++c) {
+                float re[16], im[16];
+                tmem_ld_2x16(tbase + c * 16, tbase + BN + c * 16, re, im);
+                const int n0 = nt * BN + c * 16;
+                if (m < args.M && n0 < args.N) {
+                    if (vec_ok && n0 + 16 <= args.N) {
+                        float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (n0 + i < args.N) {
+                                yrow[2 * (n0 + i)] = re[i];
+                                yrow[2 * (n0 + i) + 1] = im[i];
+                            }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty0 + 8 * acc);
+        }
+        if (!ok && lane == 0) {
+            atomicOr(args.status, kErrTimeoutEpilogue);
+            *abort_flag = 1;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, C::TMEM_COLS);
+    }
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                       cudaStream_t s) {
+    using C = Cfg<BN, STAGES>;
+    const tcbf_problem &p = pl.p;
+    CUtensorMap tmW, tmX;
+    {
+        const uint64_t dims[3] = {static_cast<uint64_t>(pl.Kp), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(2 * p.w_batches)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(pl.Kp * 2),
+                                     static_cast<uint64_t>(p.M * pl.Kp * 2)};
+        const uint32_t box[3] = {BK, BM, 2};
+        if (encode_tiled(&tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Wp), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const uint64_t dims[3] = {static_cast<uint64_t>(pl.Kp), static_cast<uint64_t>(p.N),
+                                  static_cast<uint64_t>(2 * p.batch)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(pl.Kp * 2),
+                                     static_cast<uint64_t>(p.N * pl.Kp * 2)};
+        const uint32_t box[3] = {BK, BN, 2};
+        if (encode_tiled(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Xp), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    GemmArgs a;
+    a.Y = Y;
+    a.status = pl.status;
+    a.M = static_cast<int>(p.M);
+    a.N = static_cast<int>(p.N);
+    a.K = static_cast<int>(p.K);
+    a.per_w = static_cast<int>(pl.per_w);
+    a.m_tiles = static_cast<int>(ceil_div(p.M, BM));
+    a.n_tiles = static_cast<int>(ceil_div(p.N, BN));
+    a.num_kb = static_cast<int>(ceil_div(p.K, BK));
+    const int64_t total = static_cast<int64_t>(a.m_tiles) * a.n_tiles * p.batch;
+    if (total > 0x7fffffff) return cudaErrorInvalidValue;
+    a.total_tiles = static_cast<int>(total);
+    auto kern = cgemm_f16_kernel<BN, STAGES>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int grid = static_cast<int>(std::min<int64_t>(total, pl.num_sms));
+    kern<<<grid, kThreads, C::SMEM_BYTES, s>>>(tmW, tmX, a);
+    return cudaGetLastError();
+}
+
+struct ConfigEntry {
+    const char *name;
+    cudaError_t (*fn)(const tcbf_plan_s &, const void *, const void *, float *, cudaStream_t);
+};
+
+const ConfigEntry kConfigs[] = {
+    {"f16 BM128 BN128 BK64 stages3 tmem-double", launch_cfg<128, 3>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single", launch_cfg<256, 2>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double", launch_cfg<64, 4>},
+};
+
+}  // namespace
+
+int gemm_f16_num_configs() { return static_cast<int>(sizeof(kConfigs) / sizeof(kConfigs[0])); }
+
+const char *gemm_f16_config_name(int config) {
+    if (config < 0 || config >= gemm_f16_num_configs()) return "invalid";
+    return kConfigs[config].name;
+}
+
+cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                            cudaStream_t s) {
+    const int c = (pl.config >= 0 && pl.config < gemm_f16_num_configs()) ? pl.config : 0;
+    return kConfigs[c].fn(pl, Wp, Xp, Y, s);
+}
+
+}  // namespace tcbf

@@ -1,0 +1,55 @@
+// tcbf_internal.h — host-side plan state and kernel launchers shared by
+// the library's translation units (not part of the public ABI).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/tcbf.h"
+
+#define TCBF_EXPORT extern "C" __attribute__((visibility("default")))
+
+struct tcbf_plan_s {
+    tcbf_problem p;          // validated copy; w_batches filled in
+    int device = 0;
+    int num_sms = 0;
+    int64_t per_w = 1;       // batch / w_batches
+    int64_t Kp = 0;          // K rounded up to 8 (FP16 / FP8 row length, elements)
+    int64_t Kw = 0;          // 1-bit row length in 32-bit words (multiple of 4)
+    int config = 0;          // kernel configuration (tile shape) in use
+    uint32_t *status = nullptr;   // device status word (256 bytes)
+};
+
+namespace tcbf {
+
+constexpr int kNumSmsGb300 = 152;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// cuTensorMapEncodeTiled fetched from the driver at first use.
+CUresult encode_tiled(CUtensorMap *map, CUtensorMapDataType type, uint32_t rank, void *gaddr,
+                      const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box,
+                      CUtensorMapSwizzle swizzle);
+
+// Launchers (return a cudaError_t from the launch).
+cudaError_t launch_pack_f16_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                              cudaStream_t s);
+cudaError_t launch_pack_f16_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                              cudaStream_t s);
+cudaError_t launch_pack_bits_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s);
+cudaError_t launch_pack_bits_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s);
+
+int gemm_f16_num_configs();
+const char *gemm_f16_config_name(int config);
+cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                            cudaStream_t s);
+
+cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double *tg,
+                           int near_field, const double *freqs, double c, void *Wp,
+                           cudaStream_t s);
+
+}  // namespace tcbf

@@ -1,0 +1,131 @@
+// weights.cu — steering weights from geometry (Eq. 1-2).
+//
+// For weight batch b, beam/voxel m and receiver k:
+//   far field : tau = (p_k . s_m) / c,        A = 1
+//   near field: d = |t_m - p_k|, tau = d / c, A = 1 / d
+//   w = A exp(-2 pi i f[b,k] tau)
+// The phase phi = f tau (cycles) is formed in FP64 and reduced exactly to
+// r = phi - rint(phi) in [-1/2, 1/2] (Sterbenz: the subtraction is exact),
+// the only FP64 step; sin/cos of 2 pi r come from CUDA's sincospif in FP32.
+// Output goes straight into the GEMM's packed W layout, so W needs no
+// separate transpose/pack pass:
+//   FP16 mode : planes [Bw][2][M][Kp], one thread per 8 consecutive k
+//   1-bit mode: sign planes [Bw][2][M][Kw], one warp per 32 consecutive k
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "tcbf_internal.h"
+
+namespace tcbf {
+namespace {
+
+struct Geo {
+    const double *rx;
+    const double *tg;
+    const double *freqs;
+    double inv_c;
+    double c;
+    int near_field;
+    int64_t M;
+    int K;
+};
+
+// Weight as FP32 (re, im).
+__device__ __forceinline__ void weight(const Geo &g, int64_t bw, int64_t m, int k, float &re,
+                                       float &im) {
+    const double px = g.rx[3 * k], py = g.rx[3 * k + 1], pz = g.rx[3 * k + 2];
+    const double tx = g.tg[3 * m], ty = g.tg[3 * m + 1], tz = g.tg[3 * m + 2];
+    double tau, amp;
+    if (g.near_field) {
+        const double dx = tx - px, dy = ty - py, dz = tz - pz;
+        const double d = sqrt(dx * dx + dy * dy + dz * dz);
+        tau = d / g.c;
+        amp = 1.0 / d;
+    } else {
+        tau = (px * tx + py * ty + pz * tz) / g.c;
+        amp = 1.0;
+    }
+    const double phi = g.freqs[bw * g.K + k] * tau;
+    const double r = phi - rint(phi);
+    float s, co;
+    sincospif(static_cast<float>(2.0 * r), &s, &co);
+    const float a = static_cast<float>(amp);
+    re = a * co;
+    im = -a * s;
+}
+
+__global__ void weights_f16_kernel(Geo g, __half *__restrict__ dst, int64_t Bw, int Kp) {
+    const int64_t chunks = Kp / 8;
+    const int64_t total = Bw * g.M * chunks;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int k0 = static_cast<int>(i % chunks) * 8;
+        const int64_t r = i / chunks;
+        const int64_t m = r % g.M, bw = r / g.M;
+        __align__(16) __half re[8], im[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float wr = 0.f, wi = 0.f;
+            if (k0 + j < g.K) weight(g, bw, m, k0 + j, wr, wi);
+            re[j] = __float2half_rn(wr);
+            im[j] = __float2half_rn(wi);
+        }
+        *reinterpret_cast<uint4 *>(dst + (static_cast<size_t>(bw * 2 + 0) * g.M + m) * Kp + k0) =
+            *reinterpret_cast<const uint4 *>(re);
+        *reinterpret_cast<uint4 *>(dst + (static_cast<size_t>(bw * 2 + 1) * g.M + m) * Kp + k0) =
+            *reinterpret_cast<const uint4 *>(im);
+    }
+}
+
+__global__ void weights_bits_kernel(Geo g, uint32_t *__restrict__ dst, int64_t Bw, int Kw) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = Bw * g.M * Kw;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < total;
+         i += warps_total) {
+        const int w = static_cast<int>(i % Kw);
+        const int64_t r = i / Kw;
+        const int64_t m = r % g.M, bw = r / g.M;
+        const int k = 32 * w + lane;
+        float wr = -1.f, wi = -1.f;
+        if (k < g.K) weight(g, bw, m, k, wr, wi);
+        const uint32_t br = __ballot_sync(0xffffffffu, k < g.K && wr >= 0.f);
+        const uint32_t bi = __ballot_sync(0xffffffffu, k < g.K && wi >= 0.f);
+        if (lane == 0) {
+            dst[(static_cast<size_t>(bw * 2 + 0) * g.M + m) * Kw + w] = br;
+            dst[(static_cast<size_t>(bw * 2 + 1) * g.M + m) * Kw + w] = bi;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double *tg,
+                           int near_field, const double *freqs, double c, void *Wp,
+                           cudaStream_t s) {
+    Geo g;
+    g.rx = rx;
+    g.tg = tg;
+    g.freqs = freqs;
+    g.c = c;
+    g.inv_c = 1.0 / c;
+    g.near_field = near_field;
+    g.M = pl.p.M;
+    g.K = static_cast<int>(pl.p.K);
+    const int64_t Bw = pl.p.w_batches;
+    if (pl.p.mode == TCBF_MODE_1BIT) {
+        const int64_t work = Bw * pl.p.M * pl.Kw * 32;
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(pl.num_sms) * 32)));
+        weights_bits_kernel<<<grid, 256, 0, s>>>(g, static_cast<uint32_t *>(Wp), Bw, int(pl.Kw));
+    } else if (pl.p.mode == TCBF_MODE_FP16) {
+        const int64_t work = Bw * pl.p.M * (pl.Kp / 8);
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(pl.num_sms) * 32)));
+        weights_f16_kernel<<<grid, 256, 0, s>>>(g, static_cast<__half *>(Wp), Bw, int(pl.Kp));
+    } else {
+        return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tcbf

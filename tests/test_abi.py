@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU,
+exports every symbol include/tcbf.h declares, and rejects bad arguments
+with status codes before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2505_03269_gb300 import binding
+from paper_2505_03269_gb300 import build as tcbf_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    tcbf_build.build()
+    return binding.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tcbf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tcbf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(binding.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert binding.status_string(s)
+    assert binding.status_string(99) == "unknown status"
+
+
+def _create(lib, **kw):
+    p = binding.Problem(kw.get("batch", 1), kw.get("M", 4), kw.get("N", 4), kw.get("K", 4),
+                        kw.get("w_batches", 0), kw.get("mode", 0), kw.get("flags", 0))
+    h = ctypes.c_void_p(123)
+    st = lib.tcbf_plan_create(ctypes.byref(h), ctypes.byref(p), 0)
+    return st, h
+
+
+@pytest.mark.parametrize("bad", [dict(M=0), dict(N=0), dict(K=0), dict(batch=0),
+                                 dict(batch=4, w_batches=3), dict(mode=7), dict(flags=1),
+                                 dict(M=-5)])
+def test_plan_create_rejects_bad_shapes(lib, bad):
+    st, h = _create(lib, **bad)
+    assert st == 1          # TCBF_ERR_INVALID_ARG, before any device query
+    assert h.value is None
+
+
+def test_null_arguments(lib):
+    assert lib.tcbf_plan_create(None, None, 0) == 1
+    h = ctypes.c_void_p()
+    assert lib.tcbf_plan_create(ctypes.byref(h), None, 0) == 1
+    n = ctypes.c_size_t()
+    assert lib.tcbf_packed_size(None, 0, ctypes.byref(n)) == 1
+    assert lib.tcbf_workspace_size(None, ctypes.byref(n)) == 1
+    assert lib.tcbf_transpose_pack(None, 0, 0, None, None, None) == 1
+    assert lib.tcbf_beamform_fp16(None, None, None, None, None) == 1
+    assert lib.tcbf_beamform_fp8split(None, None, None, None, None) == 1
+    assert lib.tcbf_beamform_1bit(None, None, None, None, None) == 1
+    assert lib.tcbf_weights_from_geometry(None, None, None, 0, None, 1.0, None, None) == 1
+    assert lib.tcbf_last_device_error(None) == 1
+    assert lib.tcbf_plan_destroy(None) == 0
+
+
+def test_no_device_reports_unsupported(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, h = _create(lib)
+    assert st == 2 and h.value is None
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2505_03269_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
+                assert "tcbf_oracle" not in txt and "liboracle" not in txt, f
