@@ -50,6 +50,8 @@ def _load():
             return _lib
         lib = ctypes.CDLL(build())
         i64, p = ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_num_threads.argtypes = []
         lib.oracle_half_to_double.restype = ctypes.c_double
         lib.oracle_half_to_double.argtypes = [ctypes.c_uint16]
         lib.oracle_cgemm_f64.argtypes = [i64, i64, i64, i64, i64, p, p, p]
@@ -67,6 +69,11 @@ def _load():
 
 def _ptr(a: np.ndarray):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def num_threads() -> int:
+    """Threads the oracle's OpenMP loops run on."""
+    return int(_load().oracle_num_threads())
 
 
 def half_to_double(h: np.ndarray) -> np.ndarray:

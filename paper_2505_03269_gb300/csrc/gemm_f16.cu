@@ -33,6 +33,7 @@ constexpr int kThreads = 192;
 
 struct GemmArgs {
     float *Y;
+    int tma_store;             // 1: Y written by TMA bulk tensor stores (needs N even)
     uint32_t *status;
     int M, N, K;
     int per_w;
@@ -54,7 +55,8 @@ struct Cfg {
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int ACC_BUFS = (4 * BN <= 512) ? 2 : 1;
     static constexpr int TMEM_COLS = pow2_cols(ACC_BUFS * 2 * BN);
-    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 256 + 1024;
+    static constexpr int STAGING_BYTES = 4 * 2 * 4096;        // 4 epilogue warps x 2 x (32 rows x 128 B)
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M=128");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
@@ -69,21 +71,24 @@ __device__ __forceinline__ void decode_tile(int t, const GemmArgs &a, int &b, in
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_f16_kernel(const __grid_constant__ CUtensorMap tmW,
-                     const __grid_constant__ CUtensorMap tmX, const GemmArgs args) {
+                     const __grid_constant__ CUtensorMap tmX,
+                     const __grid_constant__ CUtensorMap tmY, const GemmArgs args) {
     using C = Cfg<BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
     const uint32_t s0 = smem_u32(smem);
 
-    // barrier block after the stage ring
-    const uint32_t bar0 = s0 + STAGES * C::STAGE_BYTES;
+    // output staging after the stage ring, then the barrier block
+    const uint32_t staging0 = s0 + STAGES * C::STAGE_BYTES;
+    const uint32_t bar0 = staging0 + C::STAGING_BYTES;
     const uint32_t full0 = bar0;                       // STAGES x 8 bytes
     const uint32_t empty0 = full0 + 8 * STAGES;        // STAGES x 8
     const uint32_t tfull0 = empty0 + 8 * STAGES;       // 2 x 8
     const uint32_t tempty0 = tfull0 + 16;              // 2 x 8
     const uint32_t done_bar = tempty0 + 16;            // 8
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + STAGES * C::STAGE_BYTES + 16 * STAGES + 40);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + STAGES * C::STAGE_BYTES +
+                                                       C::STAGING_BYTES + 16 * STAGES + 40);
     volatile uint32_t *abort_flag = tmem_slot + 1;
 
     const int warp = threadIdx.x >> 5;
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_mbar_init();
         tma_prefetch_desc(&tmW);
         tma_prefetch_desc(&tmX);
+        if (args.tma_store) tma_prefetch_desc(&tmY);
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
@@ -212,10 +218,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // --------------------------------------------------------- epilogue
-        const int quarter = warp & 3;                // TMEM lanes this warp may access
+        // Each warp owns 32 accumulator rows (its TMEM lane quarter).  Per
+        // 16-column chunk it loads re and im, interleaves them into complex64
+        // and either stages the 32 x 128-byte block in shared memory (128-byte
+        // swizzle, conflict-free) for one TMA bulk tensor store, or (odd N)
+        // stores its row directly.
+        const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const bool vec_ok = (args.N & 1) == 0;       // float4 stores need 16-byte aligned rows
+        const uint32_t stage_buf = staging0 + (warp - 2) * 8192;
+        const bool vec_ok = (args.N & 1) == 0;
         int local = 0;
+        int chunk_count = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < args.total_tiles; t += gridDim.x, ++local) {
             const int acc = local % C::ACC_BUFS;
@@ -236,7 +249,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float re[16], im[16];
                 tmem_ld_2x16(tbase + c * 16, tbase + BN + c * 16, re, im);
                 const int n0 = nt * BN + c * 16;
-                if (m < args.M && n0 < args.N) {
+                if (args.tma_store) {
+                    if (n0 < args.N) {
+                        const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
+                        if (lane == 0) bulk_wait_read<1>();     // buffer's previous store has read it
+                        __syncwarp();
+                        const uint32_t rbase = buf + lane * 128;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            st_shared_v4(rbase + ((j ^ (lane & 7)) << 4), re[2 * j], im[2 * j],
+                                         re[2 * j + 1], im[2 * j + 1]);
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_3d(&tmY, buf, 2 * n0, mt * BM + quarter * 32, b);
+                            bulk_commit();
+                        }
+                        ++chunk_count;
+                    }
+                } else if (m < args.M && n0 < args.N) {
                     if (vec_ok && n0 + 16 <= args.N) {
                         float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
 #pragma unroll
@@ -255,6 +286,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             mbar_arrive(tempty0 + 8 * acc);
         }
+        if (args.tma_store && lane == 0) bulk_wait<0>();   // all of this warp's stores done
+        __syncwarp();
         if (!ok && lane == 0) {
             atomicOr(args.status, kErrTimeoutEpilogue);
             *abort_flag = 1;
@@ -296,8 +329,23 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
+    CUtensorMap tmY;
+    const int tma_store = (p.N % 2 == 0) ? 1 : 0;
+    if (tma_store) {
+        const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(p.batch)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(p.N * 8),
+                                     static_cast<uint64_t>(p.M * p.N * 8)};
+        const uint32_t box[3] = {32, 32, 1};
+        if (encode_tiled(&tmY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Y, dims, strides, box,
+                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
+        tmY = tmX;   // unused
+    }
     GemmArgs a;
     a.Y = Y;
+    a.tma_store = tma_store;
     a.status = pl.status;
     a.M = static_cast<int>(p.M);
     a.N = static_cast<int>(p.N);
@@ -314,7 +362,7 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = static_cast<int>(std::min<int64_t>(total, pl.num_sms));
-    kern<<<grid, kThreads, C::SMEM_BYTES, s>>>(tmW, tmX, a);
+    kern<<<grid, kThreads, C::SMEM_BYTES, s>>>(tmW, tmX, tmY, a);
     return cudaGetLastError();
 }
 

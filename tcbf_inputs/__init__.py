@@ -121,16 +121,39 @@ def radio_geometry(seed=0, n_beams=1024, n_stations=288, n_channels=256):
     return Geometry(pos, dirs, freqs, False, SPEED_OF_LIGHT)
 
 
+def batch_rng(seed: int, b: int) -> np.random.Generator:
+    """Independent stream for batch b (so any subset of batches can be
+    regenerated alone, and batches can be drawn in parallel)."""
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, b])))
+
+
+def radio_x_batch(seed, b, n_stations=288, n_samples=4096):
+    """Samples of batch b: complex Gaussian FP16 [K, N, 2]."""
+    return complex_gaussian_fp16(batch_rng(seed, b), (n_stations, n_samples))
+
+
+def radio_x(seed=1, batches=512, n_stations=288, n_samples=4096, out=None, threads=None):
+    """X for all batches, [B, K, N, 2] FP16, drawn batch by batch in parallel."""
+    import concurrent.futures as cf
+    import os
+    if out is None:
+        out = np.empty((batches, n_stations, n_samples, 2), np.float16)
+
+    def one(b):
+        out[b] = radio_x_batch(seed, b, n_stations, n_samples)
+
+    with cf.ThreadPoolExecutor(threads or min(32, os.cpu_count() or 4)) as ex:
+        list(ex.map(one, range(batches)))
+    return out
+
+
 def radio_block(seed=0, n_beams=1024, n_stations=288, n_samples=4096,
                 n_channels=256, n_pols=2, make_x=True):
     """Batched radio block: batch index b = 2*channel + pol; both
     polarisations of a channel share that channel's weights.  X is
     complex Gaussian FP16 [B, K, N, 2] with B = channels * pols."""
     geom = radio_geometry(seed, n_beams, n_stations, n_channels)
-    X = None
-    if make_x:
-        g = rng(seed + 1)
-        X = complex_gaussian_fp16(g, (n_channels * n_pols, n_stations, n_samples))
+    X = radio_x(seed + 1, n_channels * n_pols, n_stations, n_samples) if make_x else None
     return geom, X
 
 
