@@ -170,6 +170,36 @@ tcbf_status tcbf_last_device_error(tcbf_plan_t plan);
 /* Static text for a status code. */
 const char *tcbf_status_string(tcbf_status s);
 
+/*
+ * FP16 beamform that allocates no device memory.  The paper has no
+ * counterpart; this call exists for callers that cannot allocate device
+ * memory when they beamform: code running while a stream is being captured
+ * into a CUDA graph, real-time acquisition loops where the implicit device
+ * synchronisation of cudaMalloc/cudaFree would break their timing, and
+ * plug-ins whose host framework owns the device memory budget.  It needs no
+ * plan and no packed-sample buffer: the packed samples and the device status
+ * word go into one file-scope static device array, 64 MiB of packed samples
+ * plus 256 bytes, which every GPU that loads the library holds until the
+ * process exits.
+ *   p:       problem (mode TCBF_MODE_FP16), validated as by tcbf_plan_create.
+ *   Wp:      packed FP16 weights (tcbf_transpose_pack / tcbf_weights_from_geometry
+ *            of a plan with the same problem).
+ *   X:       [batch][K][N] interleaved complex samples of type src_type (tcbf_src_type).
+ *   Y:       [batch][M][N] interleaved complex FP32 output.
+ *   check:   0 = return after launching; nonzero = wait for the stream and
+ *            report a device-side timeout as TCBF_ERR_TIMEOUT.
+ * Returns TCBF_ERR_BUDGET (nothing launched) when batch*2*N*round_up(K,8)*2
+ * bytes of packed samples exceed 64 MiB.  The first call on a device looks
+ * up the array's device address and the device's properties; make that
+ * first call before any stream capture.  Every call uses the same array and
+ * clears the status word it needs; the packed-sample region keeps the last
+ * call's contents.  Calls whose work overlaps on the GPU (other streams, or
+ * other host threads) race on the array and must be serialised by the caller.
+ */
+tcbf_status tcbf_beamform_fp16_noalloc(const tcbf_problem *p, int device, const void *Wp,
+                                       const void *X, int src_type, float *Y, int check,
+                                       tcbf_stream_t stream);
+
 /* Number of kernel configurations (tile shapes) the plan's mode offers,
  * the one in use, and a way to pick one (the autotuner's hook). */
 tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count);

@@ -27,7 +27,7 @@ EXPORTED = [
     "tcbf_transpose_pack", "tcbf_beamform_fp16", "tcbf_beamform_fp8split",
     "tcbf_beamform_1bit", "tcbf_weights_from_geometry", "tcbf_last_device_error",
     "tcbf_status_string", "tcbf_plan_num_configs", "tcbf_plan_get_config",
-    "tcbf_plan_set_config", "tcbf_config_name",
+    "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
 ]
 
 
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_plan_num_configs": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_get_config": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_set_config": [vp, i32],
+        "tcbf_beamform_fp16_noalloc": [ctypes.POINTER(Problem), i32, vp, vp, i32, vp, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -194,6 +195,16 @@ class Plan:
 
     def config_name(self, c: int) -> str:
         return self._lib.tcbf_config_name(self.handle, int(c)).decode()
+
+
+def beamform_fp16_noalloc(batch, M, N, K, Wp, X, Y, w_batches=0, device=0,
+                          src_type=SRC_CF16, check=True, stream=None) -> int:
+    """tcbf_beamform_fp16_noalloc: no plan, no packed-sample buffer, no
+    device allocation; returns the raw status code."""
+    lib = load()
+    prob = Problem(batch, M, N, K, w_batches, MODE_FP16, 0)
+    return lib.tcbf_beamform_fp16_noalloc(ctypes.byref(prob), device, _ptr(Wp), _ptr(X),
+                                          src_type, _ptr(Y), int(bool(check)), _stream(stream))
 
 
 def status_string(s: int) -> str:
