@@ -277,6 +277,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
     int n = 0;
     tcbf_plan_num_configs(plan, &n);
     if (config < 0 || config >= n) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode == TCBF_MODE_FP16 && !gemm_f16_config_valid(config, plan->p.K))
+        return TCBF_ERR_INVALID_ARG;
     plan->config = config;
     return TCBF_OK;
 }

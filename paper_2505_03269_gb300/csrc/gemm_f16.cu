@@ -15,6 +15,13 @@
 // Tiles (batch, m-tile, n-tile) are strided over the CTAs; the two TMEM
 // accumulator sets are double-buffered when they fit, so the epilogue of
 // one tile overlaps the MMAs of the next.  All waits are bounded.
+//
+// Long K: the tensor core's FP32 accumulation truncates, so its relative
+// error grows linearly with K (measured ~2.4e-9 K, biased toward zero).
+// For K > kPromoteK the K loop is cut into chunks of kChunkBlocks stages;
+// each chunk accumulates from zero into a TMEM partial P and the epilogue
+// warps add P into a running sum S (second TMEM region) with FP32
+// round-to-nearest adds, so the error stays at the chunk's level.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -30,6 +37,8 @@ using namespace dev;
 constexpr int BM = 128;        // rows of W per tile (TMEM lanes)
 constexpr int BK = 64;         // K elements per stage: one 128-byte swizzled row
 constexpr int kThreads = 192;
+constexpr int kPromoteK = 4096;     // K above this is accumulated in promoted chunks
+constexpr int kChunkBlocks = 32;    // stages (x 64 K) per promoted chunk
 
 struct GemmArgs {
     float *Y;
@@ -39,6 +48,8 @@ struct GemmArgs {
     int per_w;
     int m_tiles, n_tiles;
     int num_kb;
+    int kc_blocks;             // stages per accumulation chunk (num_kb when not promoting)
+    int chunks;                // accumulation chunks per tile
     int total_tiles;
 };
 
@@ -167,46 +178,51 @@ __global__ void __launch_bounds__(kThreads, 1)
             constexpr uint32_t kIdescNeg = idesc_f32acc(BM, BN, 0, true);
             int stage = 0;
             uint32_t phase = 0;
-            int local = 0;
+            int ev = 0;                                  // accumulator hand-offs so far
+            const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
             bool ok = true;
-            for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x, ++local) {
-                const int acc = local % C::ACC_BUFS;
-                const uint32_t aphase = (local / C::ACC_BUFS) & 1;
-                if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d_re = tmem_base + acc * 2 * BN;
-                const uint32_t d_im = d_re + BN;
-                for (int kb = 0; kb < args.num_kb; ++kb) {
-                    if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
+            for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
+                for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+                    const int acc = ev % nbuf;
+                    const uint32_t aphase = (ev / nbuf) & 1;
+                    if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a = s0 + stage * C::STAGE_BYTES;
-                    const uint32_t bx = a + C::A_BYTES;
-                    const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
-                    for (int j = 0; j < ksteps; ++j) {
-                        const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
-                        const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
-                        const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
-                        const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
-                        const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
-                        mma_f16(d_re, ar, br, kIdesc, accum);
-                        mma_f16(d_re, ai, bi, kIdescNeg, 1u);
-                        mma_f16(d_im, ar, bi, kIdesc, accum);
-                        mma_f16(d_im, ai, br, kIdesc, 1u);
+                    const uint32_t d_re = tmem_base + acc * 2 * BN;
+                    const uint32_t d_im = d_re + BN;
+                    const int kb0 = ch * args.kc_blocks;
+                    const int kb1 = min(args.num_kb, kb0 + args.kc_blocks);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a = s0 + stage * C::STAGE_BYTES;
+                        const uint32_t bx = a + C::A_BYTES;
+                        const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
+                        for (int j = 0; j < ksteps; ++j) {
+                            const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
+                            const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
+                            const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
+                            const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
+                            const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
+                            mma_f16(d_re, ar, br, kIdesc, accum);
+                            mma_f16(d_re, ai, bi, kIdescNeg, 1u);
+                            mma_f16(d_im, ar, bi, kIdesc, accum);
+                            mma_f16(d_im, ai, br, kIdesc, 1u);
+                        }
+                        mma_commit(empty0 + 8 * stage);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
-                    mma_commit(empty0 + 8 * stage);
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
+                    if (!ok) break;
+                    mma_commit(tfull0 + 8 * acc);
                 }
-                if (!ok) break;
-                mma_commit(tfull0 + 8 * acc);
             }
             if (!ok) {
                 atomicOr(args.status, kErrTimeoutMma);
@@ -227,64 +243,99 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int row = quarter * 32 + lane;
         const uint32_t stage_buf = staging0 + (warp - 2) * 8192;
         const bool vec_ok = (args.N & 1) == 0;
-        int local = 0;
+        int ev = 0;
+        const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
+        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+        const uint32_t tS = tmem_base + lane_off + 2 * BN;    // running sum (promotion only)
         int chunk_count = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < args.total_tiles; t += gridDim.x, ++local) {
-            const int acc = local % C::ACC_BUFS;
-            const uint32_t aphase = (local / C::ACC_BUFS) & 1;
-            if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
+        for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
             int b, mt, nt;
             decode_tile(t, args, b, mt, nt);
             const int m = mt * BM + row;
-            const uint32_t tbase =
-                tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + acc * 2 * BN;
             float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
+            for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+                const int acc = ev % nbuf;
+                const uint32_t aphase = (ev / nbuf) & 1;
+                if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tP = tmem_base + lane_off + acc * 2 * BN;
+                if (ch + 1 < args.chunks) {
+                    // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
 #pragma unroll 1
-            for (int c = 0; c < BN / 16; ++c) {
-                float re[16], im[16];
-                tmem_ld_2x16(tbase + c * 16, tbase + BN + c * 16, re, im);
-                const int n0 = nt * BN + c * 16;
-                if (args.tma_store) {
-                    if (n0 < args.N) {
-                        const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
-                        if (lane == 0) bulk_wait_read<1>();     // buffer's previous store has read it
-                        __syncwarp();
-                        const uint32_t rbase = buf + lane * 128;
+                    for (int g = 0; g < BN / 16; ++g) {
+                        float pr[16], pi[16];
+                        tmem_ld_2x16(tP + g * 16, tP + BN + g * 16, pr, pi);
+                        if (ch > 0) {
+                            float sr[16], si[16];
+                            tmem_ld_2x16(tS + g * 16, tS + BN + g * 16, sr, si);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            st_shared_v4(rbase + ((j ^ (lane & 7)) << 4), re[2 * j], im[2 * j],
-                                         re[2 * j + 1], im[2 * j + 1]);
-                        fence_async_smem();
-                        __syncwarp();
-                        if (lane == 0) {
-                            tma_store_3d(&tmY, buf, 2 * n0, mt * BM + quarter * 32, b);
-                            bulk_commit();
-                        }
-                        ++chunk_count;
-                    }
-                } else if (m < args.M && n0 < args.N) {
-                    if (vec_ok && n0 + 16 <= args.N) {
-                        float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (n0 + i < args.N) {
-                                yrow[2 * (n0 + i)] = re[i];
-                                yrow[2 * (n0 + i) + 1] = im[i];
+                            for (int i = 0; i < 16; ++i) {
+                                pr[i] = __fadd_rn(sr[i], pr[i]);
+                                pi[i] = __fadd_rn(si[i], pi[i]);
                             }
+                        }
+                        tmem_st_2x16(tS + g * 16, tS + BN + g * 16, pr, pi);
+                    }
+                    tmem_st_wait();
+                    tc_fence_before();
+                    mbar_arrive(tempty0 + 8 * acc);
+                    continue;
+                }
+#pragma unroll 1
+                for (int c = 0; c < BN / 16; ++c) {
+                    float re[16], im[16];
+                    tmem_ld_2x16(tP + c * 16, tP + BN + c * 16, re, im);
+                    if (args.chunks > 1) {
+                        float sr[16], si[16];
+                        tmem_ld_2x16(tS + c * 16, tS + BN + c * 16, sr, si);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            re[i] = __fadd_rn(sr[i], re[i]);
+                            im[i] = __fadd_rn(si[i], im[i]);
+                        }
+                    }
+                    const int n0 = nt * BN + c * 16;
+                    if (args.tma_store) {
+                        if (n0 < args.N) {
+                            const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
+                            if (lane == 0) bulk_wait_read<1>();   // buffer's previous store has read it
+                            __syncwarp();
+                            const uint32_t rbase = buf + lane * 128;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                st_shared_v4(rbase + ((j ^ (lane & 7)) << 4), re[2 * j], im[2 * j],
+                                             re[2 * j + 1], im[2 * j + 1]);
+                            fence_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                tma_store_3d(&tmY, buf, 2 * n0, mt * BM + quarter * 32, b);
+                                bulk_commit();
+                            }
+                            ++chunk_count;
+                        }
+                    } else if (m < args.M && n0 < args.N) {
+                        if (vec_ok && n0 + 16 <= args.N) {
+                            float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if (n0 + i < args.N) {
+                                    yrow[2 * (n0 + i)] = re[i];
+                                    yrow[2 * (n0 + i) + 1] = im[i];
+                                }
+                        }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(tempty0 + 8 * acc);
             }
-            tc_fence_before();
-            mbar_arrive(tempty0 + 8 * acc);
         }
         if (args.tma_store && lane == 0) bulk_wait<0>();   // all of this warp's stores done
         __syncwarp();
@@ -354,6 +405,13 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     a.m_tiles = static_cast<int>(ceil_div(p.M, BM));
     a.n_tiles = static_cast<int>(ceil_div(p.N, BN));
     a.num_kb = static_cast<int>(ceil_div(p.K, BK));
+    if (p.K > kPromoteK) {
+        if (4 * BN > 512) return cudaErrorInvalidConfiguration;   // no TMEM room for the sum
+        a.kc_blocks = kChunkBlocks;
+    } else {
+        a.kc_blocks = a.num_kb;
+    }
+    a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
     const int64_t total = static_cast<int64_t>(a.m_tiles) * a.n_tiles * p.batch;
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
@@ -368,13 +426,14 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
 
 struct ConfigEntry {
     const char *name;
+    int bn;
     cudaError_t (*fn)(const tcbf_plan_s &, const void *, const void *, float *, cudaStream_t);
 };
 
 const ConfigEntry kConfigs[] = {
-    {"f16 BM128 BN128 BK64 stages3 tmem-double", launch_cfg<128, 3>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single", launch_cfg<256, 2>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double", launch_cfg<64, 4>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double", 128, launch_cfg<128, 3>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single", 256, launch_cfg<256, 2>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double", 64, launch_cfg<64, 4>},
 };
 
 }  // namespace
@@ -384,6 +443,11 @@ int gemm_f16_num_configs() { return static_cast<int>(sizeof(kConfigs) / sizeof(k
 const char *gemm_f16_config_name(int config) {
     if (config < 0 || config >= gemm_f16_num_configs()) return "invalid";
     return kConfigs[config].name;
+}
+
+bool gemm_f16_config_valid(int config, int64_t K) {
+    if (config < 0 || config >= gemm_f16_num_configs()) return false;
+    return K <= kPromoteK || kConfigs[config].bn <= 128;
 }
 
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,

@@ -193,6 +193,26 @@ __device__ __forceinline__ void tmem_ld_2x16(uint32_t ta, uint32_t tb, float (&a
         : "memory");
 }
 
+// Two 32-lane x 16-column fp32 stores into tensor memory.
+__device__ __forceinline__ void tmem_st_2x16(uint32_t ta, uint32_t tb, const float (&a)[16],
+                                             const float (&b)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], "
+        "{%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33};" ::"r"(ta),
+        "r"(tb), "f"(a[0]), "f"(a[1]), "f"(a[2]), "f"(a[3]), "f"(a[4]), "f"(a[5]), "f"(a[6]),
+        "f"(a[7]), "f"(a[8]), "f"(a[9]), "f"(a[10]), "f"(a[11]), "f"(a[12]), "f"(a[13]),
+        "f"(a[14]), "f"(a[15]), "f"(b[0]), "f"(b[1]), "f"(b[2]), "f"(b[3]), "f"(b[4]),
+        "f"(b[5]), "f"(b[6]), "f"(b[7]), "f"(b[8]), "f"(b[9]), "f"(b[10]), "f"(b[11]),
+        "f"(b[12]), "f"(b[13]), "f"(b[14]), "f"(b[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // -------------------------------------------------------------- descriptors
 // Shared-memory matrix descriptor for a K-major operand tile stored with the
 // 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms

@@ -45,6 +45,7 @@ cudaError_t launch_pack_bits_x(const tcbf_plan_s &pl, int src_type, const void *
 
 int gemm_f16_num_configs();
 const char *gemm_f16_config_name(int config);
+bool gemm_f16_config_valid(int config, int64_t K);
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s);
 

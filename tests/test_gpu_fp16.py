@@ -94,3 +94,31 @@ def test_fp32_source_rounds_to_nearest():
     Y = _run(W32, X32, src_type=SRC_CF32)
     Yref = oracle.cgemm(W32.astype(np.float16), X32.astype(np.float16))
     assert oracle.rel_frobenius(Y, Yref) <= TOL
+
+
+@pytest.mark.parametrize("config", [0, 2])
+@pytest.mark.parametrize("K", [4100, 8192, 16384])
+def test_long_k_within_tolerance(config, K):
+    """Above K = 4096 the partial sums are promoted to FP32 every 2048 K;
+    the error must stay within the FP16 tolerance at any K."""
+    W, _ = ti.small_fp16(seed=K, M=256, K=K, N=8)
+    X = ti.complex_gaussian_fp16(ti.rng(K + 1), (1, K, 192))
+    Y = _run(W, X, config=config)
+    Yref = oracle.cgemm(W, X)
+    assert oracle.rel_frobenius(Y, Yref) <= TOL
+
+
+def test_long_k_integer_inputs_bit_exact():
+    """Integer partial sums stay exact through the promotion."""
+    g = ti.rng(12)
+    W = ti.integer_complex_fp16(g, (1, 130, 9000), lo=-2, hi=2)
+    X = ti.integer_complex_fp16(g, (1, 9000, 70), lo=-2, hi=2)
+    Y = _run(W, X)
+    assert np.array_equal(Y, oracle.cgemm(W, X))
+
+
+def test_wide_tile_rejected_for_long_k():
+    from paper_2505_03269_gb300 import MODE_FP16, Plan, TcbfError
+    with Plan(1, 128, 128, 8192, MODE_FP16) as plan:
+        with pytest.raises(TcbfError):
+            plan.set_config(1)
