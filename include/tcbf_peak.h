@@ -1,0 +1,36 @@
+/*
+ * tcbf_peak.h — on-chip peak microbenchmarks of the GB300 build.
+ *
+ * Like the paper's tensor-core micro-benchmarks (Sec. III-A, Table I) they
+ * keep operands on chip so memory bandwidth does not limit them; they supply
+ * the per-precision peak denominators and the measurements behind the 1-bit
+ * kernel choice (Sec. III-D/E).
+ */
+#ifndef TCBF_PEAK_H
+#define TCBF_PEAK_H
+
+#include "tcbf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Run microbenchmark `kind` once for warm-up and once timed (CUDA events) on
+ * device `device`, one CTA per SM for the tcgen05 kinds, 4 x 256-thread
+ * blocks per SM for the warp-level kinds:
+ *   0 tcgen05 kind::f16 M128 N256 K16, 1 tcgen05 kind::f8f6f4 (E4M3) M128 N256 K32,
+ *   2 tcgen05 kind::i8 (not available on sm_103a: always TCBF_ERR_UNSUPPORTED),
+ *   3 mma.sync m16n8k16 f16->f32,
+ *   4 mma.sync m16n8k256 b1 AND-popc, 5 CUDA-core popc(xor) on 32-bit words.
+ * iters: MMAs (or loop trips) per issuing thread.  On success *seconds is the
+ * timed launch's duration and *ops the operations it performed (2 per
+ * multiply-accumulate).  Allocates and frees a 256-byte status word.
+ * Returns TCBF_ERR_UNSUPPORTED on a device other than sm_103.
+ */
+tcbf_status tcbf_peak_run(int kind, int device, int iters, double *seconds, double *ops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCBF_PEAK_H */

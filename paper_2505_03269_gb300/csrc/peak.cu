@@ -1,0 +1,214 @@
+// peak.cu — tensor and integer peak microbenchmarks for sm_103a.
+//
+// As in the paper's micro-benchmarks (Sec. III-A, Table I), operands stay
+// on chip: no global memory is touched inside the timed loops.  They give
+// the "% of peak" denominators for each precision and the evidence for the
+// choice of the 1-bit path (Sec. III-D/E: b1 AND-popc MMAs versus the
+// alternatives on this architecture).
+//   kind 0: tcgen05.mma kind::f16   M128 N256 K16  (FP16 in, FP32 accumulate)
+//   kind 1: tcgen05.mma kind::f8f6f4 M128 N256 K32 (E4M3 in, FP32 accumulate)
+//   kind 2: tcgen05.mma kind::i8 — not available: ptxas rejects ".kind::i8"
+//           for sm_103a, so the call reports TCBF_ERR_UNSUPPORTED
+//   kind 3: mma.sync m16n8k16 f16 -> f32 (legacy warp MMA)
+//   kind 4: mma.sync m16n8k256 b1 AND-popc -> s32 (legacy warp MMA)
+//   kind 5: CUDA-core popc of XOR on 32-bit words
+// Ops are counted as 2 per multiply-accumulate (b1: per bit product).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/tcbf_peak.h"
+#include "ptx.cuh"
+#include "tcbf_internal.h"
+
+namespace tcbf {
+namespace {
+
+using namespace dev;
+
+// One CTA per SM; thread 0 issues `iters` MMAs on zeroed 128x128B (A) and
+// 256x128B (B) swizzled tiles into a 256-column FP32/S32 accumulator.
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *status) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
+    const uint32_t s0 = smem_u32(smem);
+    const uint32_t a_addr = s0, b_addr = s0 + 16384;          // 16 KB + 32 KB tiles
+    const uint32_t bar = s0 + 49152;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 49152 + 64);
+    // operands: hashed values of magnitude in [0.5, 1) with random signs
+    // (FP16 pairs for kind 0, E4M3 bytes for kind 1), so the timed loop
+    // draws realistic power
+    for (int i = threadIdx.x; i < 49152 / 4; i += blockDim.x) {
+        const uint32_t h = (i + 1) * 0x9E3779B9u;
+        reinterpret_cast<uint32_t *>(smem)[i] =
+            KIND == 0 ? ((h & 0x83FF83FFu) | 0x38003800u) : ((h & 0x87878787u) | 0x30303030u);
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    fence_async_smem();
+    if (threadIdx.x < 32) {
+        tmem_alloc(smem_u32(slot), 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    if (threadIdx.x == 0) {
+        const uint64_t ad = sdesc_kmajor_sw128(a_addr);
+        const uint64_t bd = sdesc_kmajor_sw128(b_addr);
+        if (KIND == 0) {
+            constexpr uint32_t id = idesc_f32acc(128, 256, 0, false);
+            for (int i = 0; i < iters; ++i) mma_f16(tmem, ad, bd, id, i > 0);
+        } else if (KIND == 1) {
+            constexpr uint32_t id = idesc_f32acc(128, 256, 0, false);   // e4m3 x e4m3
+            for (int i = 0; i < iters; ++i) mma_f8f6f4(tmem, ad, bd, id, i > 0);
+        }
+        mma_commit(bar);
+        if (!mbar_wait(bar, 0)) atomicOr(status, kErrTimeoutMma);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// Legacy warp MMAs: every warp keeps 4 independent accumulators in flight.
+template <int KIND>
+__global__ void __launch_bounds__(256) warp_peak_kernel(int iters, int seed, uint32_t *sink) {
+    uint32_t a0 = seed * 0x9E3779B9u + threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u;
+    uint32_t b0 = a0 ^ 0x5bd1e995u, b1 = b0 * 3u;
+    if (KIND == 3) {
+        float acc[4][4] = {};
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, "
+                    "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                    : "+f"(acc[j][0]), "+f"(acc[j][1]), "+f"(acc[j][2]), "+f"(acc[j][3])
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+        float s = 0.f;
+        for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < 4; ++q) s += acc[j][q];
+        if (s == 123.456f) sink[0] = 1;
+    } else if (KIND == 4) {
+        int acc[4][4] = {};
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                asm volatile(
+                    "mma.sync.aligned.m16n8k256.row.col.s32.b1.b1.s32.and.popc {%0,%1,%2,%3}, "
+                    "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                    : "+r"(acc[j][0]), "+r"(acc[j][1]), "+r"(acc[j][2]), "+r"(acc[j][3])
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+        int s = 0;
+        for (int j = 0; j < 4; ++j)
+            for (int q = 0; q < 4; ++q) s += acc[j][q];
+        if (s == 123456789) sink[0] = 1;
+    } else {
+        uint32_t acc[8] = {};
+        uint32_t x[8];
+        for (int j = 0; j < 8; ++j) x[j] = a0 * (j + 1);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += __popc(x[j] ^ b0), x[j] += b1;
+        }
+        uint32_t s = 0;
+        for (int j = 0; j < 8; ++j) s += acc[j];
+        if (s == 0xdeadbeefu) sink[0] = 1;
+    }
+}
+
+}  // namespace
+}  // namespace tcbf
+
+using namespace tcbf;
+
+TCBF_EXPORT tcbf_status tcbf_peak_run(int kind, int device, int iters, double *seconds,
+                                      double *ops) {
+    if (!seconds || !ops || kind < 0 || kind > 5 || iters < 1) return TCBF_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TCBF_ERR_UNSUPPORTED;
+    if (device < 0 || device >= ndev) return TCBF_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    int sms = 0, major = 0, minor = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    tcbf_status st = TCBF_OK;
+    uint32_t *status = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (major != 10 || minor != 3 || kind == 2) st = TCBF_ERR_UNSUPPORTED;
+    if (st == TCBF_OK && (cudaMalloc(&status, 256) != cudaSuccess ||
+                          cudaMemset(status, 0, 256) != cudaSuccess))
+        st = TCBF_ERR_OOM;
+    if (st == TCBF_OK) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const int smem = 49152 + 128 + 1024;
+        double per_launch = 0;
+        auto launch = [&](void) -> cudaError_t {
+            switch (kind) {
+                case 0:
+                    cudaFuncSetAttribute(tc_peak_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                    tc_peak_kernel<0><<<sms, 128, smem>>>(iters, status);
+                    per_launch = 2.0 * 128 * 256 * 16 * double(iters) * sms;
+                    break;
+                case 1:
+                    cudaFuncSetAttribute(tc_peak_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                    tc_peak_kernel<1><<<sms, 128, smem>>>(iters, status);
+                    per_launch = 2.0 * 128 * 256 * 32 * double(iters) * sms;
+                    break;
+                case 3:
+                    warp_peak_kernel<3><<<sms * 4, 256>>>(iters, 1, status);
+                    per_launch = 2.0 * 16 * 8 * 16 * 4 * double(iters) * (sms * 4 * 8);
+                    break;
+                case 4:
+                    warp_peak_kernel<4><<<sms * 4, 256>>>(iters, 1, status);
+                    per_launch = 2.0 * 16 * 8 * 256 * 4 * double(iters) * (sms * 4 * 8);
+                    break;
+                default:
+                    warp_peak_kernel<5><<<sms * 4, 256>>>(iters, 1, status);
+                    // one popc of a 32-bit XOR = 32 one-bit products
+                    per_launch = 2.0 * 32 * 8 * double(iters) * (sms * 4 * 256);
+                    break;
+            }
+            return cudaGetLastError();
+        };
+        cudaError_t e = launch();   // warm-up
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) {
+            cudaEventRecord(e0);
+            e = launch();
+            cudaEventRecord(e1);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        }
+        if (e != cudaSuccess) {
+            st = TCBF_ERR_CUDA;
+        } else {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            *seconds = ms * 1e-3;
+            *ops = per_launch;
+            uint32_t word = 0;
+            cudaMemcpy(&word, status, 4, cudaMemcpyDeviceToHost);
+            if (word & 0xffu) st = TCBF_ERR_TIMEOUT;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (status) cudaFree(status);
+    cudaSetDevice(prev);
+    return st;
+}

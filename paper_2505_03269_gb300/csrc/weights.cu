@@ -47,9 +47,17 @@ __device__ __forceinline__ void weight(const Geo &g, int64_t bw, int64_t m, int 
         amp = 1.0;
     }
     const double phi = g.freqs[bw * g.K + k] * tau;
-    const double r = phi - rint(phi);
-    float s, co;
-    sincospif(static_cast<float>(2.0 * r), &s, &co);
+    const double t = 2.0 * (phi - rint(phi));         // half-turns in [-1, 1], exact
+    // The FP32 argument t_hi drops up to 2^-25 half-turns; that residual is
+    // added back to first order, sin(pi(h + l)) ~ sin(pi h) + pi l cos(pi h)
+    // and cos(pi(h + l)) ~ cos(pi h) - pi l sin(pi h), so components near
+    // zero keep their relative accuracy (|pi l| < 1e-7, the square ~1e-14).
+    const float t_hi = static_cast<float>(t);
+    const float pl = 3.14159265358979f * static_cast<float>(t - static_cast<double>(t_hi));
+    float s0, c0;
+    sincospif(t_hi, &s0, &c0);
+    const float s = fmaf(c0, pl, s0);
+    const float co = fmaf(-s0, pl, c0);
     const float a = static_cast<float>(amp);
     re = a * co;
     im = -a * s;

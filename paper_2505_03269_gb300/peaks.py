@@ -1,0 +1,60 @@
+"""Run the library's on-chip peak microbenchmarks (include/tcbf_peak.h) and
+print one JSON object: TeraOps/s per kind, with the SM clock seen.
+
+  python -m paper_2505_03269_gb300.peaks [--device D] [--scale S]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import subprocess
+
+from . import binding
+from . import build as tcbf_build
+
+KINDS = {
+    0: ("tcgen05_f16_m128n256k16", 40000),
+    1: ("tcgen05_f8f6f4_e4m3_m128n256k32", 40000),
+    2: ("tcgen05_i8", 1),
+    3: ("mma_sync_f16_m16n8k16", 20000),
+    4: ("mma_sync_b1_and_m16n8k256", 20000),
+    5: ("cuda_core_popc_xor32", 20000),
+}
+
+
+def sm_clock(device: int):
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(device), "--query-gpu=clocks.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=10).stdout.strip()
+        return float(out)
+    except Exception:
+        return None
+
+
+def run(device: int = 0, scale: float = 1.0) -> dict:
+    tcbf_build.build()
+    lib = binding.load()
+    f = lib.tcbf_peak_run
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    res = {}
+    for kind, (name, iters) in KINDS.items():
+        sec, ops = ctypes.c_double(), ctypes.c_double()
+        st = f(kind, device, max(1, int(iters * scale)), ctypes.byref(sec), ctypes.byref(ops))
+        if st != 0:
+            res[name] = {"status": binding.STATUS_NAMES.get(st, st)}
+            continue
+        res[name] = {"tops": ops.value / sec.value / 1e12, "seconds": sec.value,
+                     "sm_mhz_after": sm_clock(device)}
+    return res
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--scale", type=float, default=1.0)
+    a = ap.parse_args()
+    print(json.dumps(run(a.device, a.scale)))
