@@ -121,6 +121,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     if (q.M > kMaxDim || q.N > kMaxDim || q.K > kMaxDim || q.batch > 65535)
         return TCBF_ERR_UNSUPPORTED;
     if (q.mode == TCBF_MODE_FP8SPLIT) return TCBF_ERR_UNSUPPORTED;
+    // 1-bit sums are exact integers in the FP32 accumulators while 2K < 2^24
+    if (q.mode == TCBF_MODE_1BIT && q.K > (int64_t(1) << 22)) return TCBF_ERR_UNSUPPORTED;
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TCBF_ERR_UNSUPPORTED;
@@ -227,8 +229,10 @@ TCBF_EXPORT tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbi
                                            tcbf_stream_t stream) {
     if (!plan || !Wbits || !Xbits || !Y) return TCBF_ERR_INVALID_ARG;
     if (plan->p.mode != TCBF_MODE_1BIT) return TCBF_ERR_INVALID_ARG;
-    (void)stream;
-    return TCBF_ERR_UNSUPPORTED;
+    if (!aligned16(Wbits) || !aligned16(Xbits) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(launch_gemm_1bit(*plan, Wbits, Xbits, Y, static_cast<cudaStream_t>(stream)));
 }
 
 TCBF_EXPORT tcbf_status tcbf_weights_from_geometry(tcbf_plan_t plan, const double *rx_pos,
@@ -262,7 +266,9 @@ TCBF_EXPORT tcbf_status tcbf_last_device_error(tcbf_plan_t plan) {
 
 TCBF_EXPORT tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count) {
     if (!plan || !count) return TCBF_ERR_INVALID_ARG;
-    *count = plan->p.mode == TCBF_MODE_FP16 ? gemm_f16_num_configs() : 1;
+    *count = plan->p.mode == TCBF_MODE_FP16   ? gemm_f16_num_configs()
+             : plan->p.mode == TCBF_MODE_1BIT ? gemm_1bit_num_configs()
+                                              : 1;
     return TCBF_OK;
 }
 
@@ -286,5 +292,6 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
 TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
     if (!plan) return "invalid";
     if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
+    if (plan->p.mode == TCBF_MODE_1BIT) return gemm_1bit_config_name(config);
     return config == 0 ? "default" : "invalid";
 }

@@ -1,0 +1,421 @@
+// gemm_1bit.cu — exact 1-bit complex GEMM on the sm_103a tensor cores.
+//
+// Values are +-1 +-i, one bit per component (Fig. 1: bit 1 = +1, bit 0 = -1).
+// The paper computes the real dot products K - 2 popc(A xor B) (Eq. 4) with
+// b1 tensor-core MMAs, or the AND form (Eq. 6) on Hopper.  On this GPU the
+// legacy b1 AND-popc MMA measures 146 TeraOps/s against 4788 for FP8
+// tcgen05 MMAs (peak microbenchmarks), and tcgen05 has no integer kind, so
+// the bits are expanded on chip to E4M3 +-1.0 (0 for k >= K, so no padding
+// correction as in Eq. 5 is needed) and multiplied with kind::f8f6f4 into
+// FP32 accumulators.  Every partial sum is an integer of magnitude <= 2K,
+// exact in FP32 for K < 2^23, so the result equals K - 2 Hamming exactly.
+//
+// Warp roles (288 threads, one CTA per SM, persistent over tiles):
+//   warp 0      TMEM owner and single-thread MMA issuer (4 real MMAs per
+//               K step, negate-A for -Im(W) Im(X), as in the FP16 kernel)
+//   warps 1-4   converters: 16-byte loads of packed words (L2-resident),
+//               expansion to E4M3 in the 128-byte-swizzled K-major layout
+//               the MMA reads, one stage of 128 K per ring slot
+//   warps 5-8   epilogue: TMEM -> int32 pairs -> staged TMA stores
+#include <algorithm>
+#include <cstring>
+
+#include "ptx.cuh"
+#include "tcbf_internal.h"
+
+namespace tcbf {
+namespace {
+
+using namespace dev;
+
+constexpr int BM = 128;
+constexpr int BKE = 128;             // K elements per stage (one 128-byte E4M3 row)
+constexpr int kThreads = 288;
+constexpr int kConv = 128;           // converter threads
+
+struct Args1 {
+    int32_t *Y;
+    const uint32_t *Wb;
+    const uint32_t *Xb;
+    uint32_t *status;
+    int tma_store;
+    int M, N, K, Kw;
+    int per_w;
+    int m_tiles, n_tiles, num_kb, total_tiles;
+};
+
+template <int BN, int STAGES>
+struct Cfg1 {
+    static constexpr int A_PLANE = BM * BKE;
+    static constexpr int B_PLANE = BN * BKE;
+    static constexpr int A_BYTES = 2 * A_PLANE;
+    static constexpr int STAGE_BYTES = A_BYTES + 2 * B_PLANE;
+    static constexpr int ACC_BUFS = (4 * BN <= 512) ? 2 : 1;
+    static constexpr int TMEM_COLS = ACC_BUFS * 2 * BN <= 256 ? 256 : 512;
+    static constexpr int STAGING_BYTES = 4 * 2 * 4096;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
+
+__device__ __forceinline__ void decode_tile(int t, const Args1 &a, int &b, int &mt, int &nt) {
+    nt = t % a.n_tiles;
+    const int rest = t / a.n_tiles;
+    mt = rest % a.m_tiles;
+    b = rest / a.m_tiles;
+}
+
+// 4 sign bits -> 4 E4M3 bytes: bit 1 -> 0x38 (+1.0), bit 0 -> 0xB8 (-1.0).
+// The multiply places bit j at bit 8j + 7 (copies at offsets 7, 14, 21, 28
+// do not overlap for a 4-bit value).
+__device__ __forceinline__ uint32_t expand4(uint32_t nib) {
+    return 0xB8B8B8B8u ^ ((nib * 0x10204080u) & 0x80808080u);
+}
+
+// 16 sign bits -> 16 E4M3 bytes; bytes whose element index is >= valid are 0.
+__device__ __forceinline__ uint4 expand16(uint32_t bits, int valid) {
+    uint4 v;
+    v.x = expand4(bits & 15u);
+    v.y = expand4((bits >> 4) & 15u);
+    v.z = expand4((bits >> 8) & 15u);
+    v.w = expand4((bits >> 12) & 15u);
+    if (valid < 16) {
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int keep = min(max(valid - 4 * q, 0), 4);   // bytes of this word below K
+            const uint32_t mask = keep >= 4 ? 0xFFFFFFFFu : ((1u << (8 * keep)) - 1u);
+            w[q] &= mask;
+        }
+        v = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    return v;
+}
+
+__device__ __forceinline__ void st_shared_u4(uint32_t addr, uint4 v) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// Expand one row's 128 K (4 words) of one plane into the swizzled slot.
+__device__ __forceinline__ void expand_row(uint32_t row_base, int r, uint4 words, int valid) {
+    const uint32_t w[4] = {words.x, words.y, words.z, words.w};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t bits = (w[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
+        st_shared_u4(row_base + ((c ^ (r & 7)) << 4), expand16(bits, valid - 16 * c));
+    }
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    cgemm_1bit_kernel(const __grid_constant__ CUtensorMap tmY, const Args1 args) {
+    using C = Cfg1<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+    const uint32_t s0 = smem_u32(smem);
+    const uint32_t staging0 = s0 + STAGES * C::STAGE_BYTES;
+    const uint32_t bar0 = staging0 + C::STAGING_BYTES;
+    const uint32_t full0 = bar0;
+    const uint32_t empty0 = full0 + 8 * STAGES;
+    const uint32_t tfull0 = empty0 + 8 * STAGES;
+    const uint32_t tempty0 = tfull0 + 16;
+    const uint32_t done_bar = tempty0 + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + STAGES * C::STAGE_BYTES +
+                                                       C::STAGING_BYTES + 16 * STAGES + 40);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, kConv);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 128);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        if (args.tma_store) tma_prefetch_desc(&tmY);
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t kIdesc = idesc_f32acc(BM, BN, 0, false);     // E4M3 x E4M3
+            constexpr uint32_t kIdescNeg = idesc_f32acc(BM, BN, 0, true);
+            int stage = 0;
+            uint32_t phase = 0;
+            int local = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x, ++local) {
+                const int acc = local % C::ACC_BUFS;
+                const uint32_t aphase = (local / C::ACC_BUFS) & 1;
+                if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_re = tmem_base + acc * 2 * BN;
+                const uint32_t d_im = d_re + BN;
+                for (int kb = 0; kb < args.num_kb; ++kb) {
+                    if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = s0 + stage * C::STAGE_BYTES;
+                    const uint32_t bx = a + C::A_BYTES;
+                    const int ksteps = min(BKE / 32, (args.K - kb * BKE + 31) / 32);
+                    for (int j = 0; j < ksteps; ++j) {
+                        const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
+                        const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
+                        const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
+                        const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
+                        const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
+                        mma_f8f6f4(d_re, ar, br, kIdesc, accum);
+                        mma_f8f6f4(d_re, ai, bi, kIdescNeg, 1u);
+                        mma_f8f6f4(d_im, ar, bi, kIdesc, accum);
+                        mma_f8f6f4(d_im, ai, br, kIdesc, 1u);
+                    }
+                    mma_commit(empty0 + 8 * stage);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(tfull0 + 8 * acc);
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutMma);
+                *abort_flag = 1;
+            }
+            mma_commit(done_bar);
+            if (!mbar_wait(done_bar, 0)) atomicOr(args.status, kErrTimeoutDrain);
+        }
+    } else if (warp <= 4) {
+        // ------------------------------------------------------- converters
+        const int ct = threadIdx.x - 32;               // 0..127: one W row, BN/128 X rows
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
+            int b, mt, nt;
+            decode_tile(t, args, b, mt, nt);
+            const int bw = b / args.per_w;
+            const int mrow = mt * BM + ct;
+            const uint32_t *wr = args.Wb + (static_cast<size_t>(bw * 2) * args.M + mrow) * args.Kw;
+            const uint32_t *wi = wr + static_cast<size_t>(args.M) * args.Kw;
+            for (int kb = 0; kb < args.num_kb; ++kb) {
+                // issue this stage's loads before waiting for the slot
+                const int valid = args.K - kb * BKE;
+                const uint4 zero = make_uint4(0, 0, 0, 0);
+                uint4 aw_r = zero, aw_i = zero;
+                if (mrow < args.M) {
+                    aw_r = __ldg(reinterpret_cast<const uint4 *>(wr + kb * 4));
+                    aw_i = __ldg(reinterpret_cast<const uint4 *>(wi + kb * 4));
+                }
+                uint4 bw_r[BN / 128], bw_i[BN / 128];
+#pragma unroll
+                for (int h = 0; h < BN / 128; ++h) {
+                    const int nrow = nt * BN + ct + 128 * h;
+                    bw_r[h] = zero;
+                    bw_i[h] = zero;
+                    if (nrow < args.N) {
+                        const uint32_t *xr =
+                            args.Xb + (static_cast<size_t>(b * 2) * args.N + nrow) * args.Kw;
+                        const uint32_t *xi = xr + static_cast<size_t>(args.N) * args.Kw;
+                        bw_r[h] = __ldg(reinterpret_cast<const uint4 *>(xr + kb * 4));
+                        bw_i[h] = __ldg(reinterpret_cast<const uint4 *>(xi + kb * 4));
+                    }
+                }
+                if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t a = s0 + stage * C::STAGE_BYTES;
+                // rows beyond M / N expand to zeros (valid = 0)
+                const int va = mrow < args.M ? valid : 0;
+                expand_row(a + ct * 128, ct, aw_r, va);
+                expand_row(a + C::A_PLANE + ct * 128, ct, aw_i, va);
+#pragma unroll
+                for (int h = 0; h < BN / 128; ++h) {
+                    const int r = ct + 128 * h;
+                    const int vb = (nt * BN + r) < args.N ? valid : 0;
+                    expand_row(a + C::A_BYTES + r * 128, r, bw_r[h], vb);
+                    expand_row(a + C::A_BYTES + C::B_PLANE + r * 128, r, bw_i[h], vb);
+                }
+                fence_async_smem();                    // generic writes -> tensor core reads
+                mbar_arrive(full0 + 8 * stage);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+        if (!ok && ct == 0) {
+            atomicOr(args.status, kErrTimeoutProducer);
+            *abort_flag = 1;
+        }
+    } else {
+        // --------------------------------------------------------- epilogue
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t stage_buf = staging0 + (warp - 5) * 8192;
+        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+        int local = 0;
+        int chunk_count = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x, ++local) {
+            const int acc = local % C::ACC_BUFS;
+            const uint32_t aphase = (local / C::ACC_BUFS) & 1;
+            if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            int b, mt, nt;
+            decode_tile(t, args, b, mt, nt);
+            const int m = mt * BM + row;
+            const uint32_t tP = tmem_base + lane_off + acc * 2 * BN;
+            int32_t *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
+#pragma unroll 1
+            for (int c = 0; c < BN / 16; ++c) {
+                float re[16], im[16];
+                tmem_ld_2x16(tP + c * 16, tP + BN + c * 16, re, im);
+                const int n0 = nt * BN + c * 16;
+                if (args.tma_store) {
+                    if (n0 < args.N) {
+                        const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
+                        if (lane == 0) bulk_wait_read<1>();
+                        __syncwarp();
+                        const uint32_t rbase = buf + lane * 128;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            st_shared_u4(rbase + ((j ^ (lane & 7)) << 4),
+                                         make_uint4(__float2int_rn(re[2 * j]), __float2int_rn(im[2 * j]),
+                                                    __float2int_rn(re[2 * j + 1]),
+                                                    __float2int_rn(im[2 * j + 1])));
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_3d(&tmY, buf, 2 * n0, mt * BM + quarter * 32, b);
+                            bulk_commit();
+                        }
+                        ++chunk_count;
+                    }
+                } else if (m < args.M && n0 < args.N) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (n0 + i < args.N) {
+                            yrow[2 * (n0 + i)] = __float2int_rn(re[i]);
+                            yrow[2 * (n0 + i) + 1] = __float2int_rn(im[i]);
+                        }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(tempty0 + 8 * acc);
+        }
+        if (args.tma_store && lane == 0) bulk_wait<0>();
+        __syncwarp();
+        if (!ok && lane == 0) {
+            atomicOr(args.status, kErrTimeoutEpilogue);
+            *abort_flag = 1;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_base, C::TMEM_COLS);
+    }
+}
+
+template <int BN, int STAGES>
+cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb, int32_t *Y,
+                    cudaStream_t s) {
+    using C = Cfg1<BN, STAGES>;
+    const tcbf_problem &p = pl.p;
+    CUtensorMap tmY;
+    const int tma_store = (p.N % 2 == 0) ? 1 : 0;
+    if (tma_store) {
+        const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(p.batch)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(p.N * 8),
+                                     static_cast<uint64_t>(p.M * p.N * 8)};
+        const uint32_t box[3] = {32, 32, 1};
+        if (encode_tiled(&tmY, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, Y, dims, strides, box,
+                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
+        memset(&tmY, 0, sizeof(tmY));
+    }
+    Args1 a;
+    a.Y = Y;
+    a.Wb = Wb;
+    a.Xb = Xb;
+    a.status = pl.status;
+    a.tma_store = tma_store;
+    a.M = static_cast<int>(p.M);
+    a.N = static_cast<int>(p.N);
+    a.K = static_cast<int>(p.K);
+    a.Kw = static_cast<int>(pl.Kw);
+    a.per_w = static_cast<int>(pl.per_w);
+    a.m_tiles = static_cast<int>(ceil_div(p.M, BM));
+    a.n_tiles = static_cast<int>(ceil_div(p.N, BN));
+    a.num_kb = static_cast<int>(ceil_div(p.K, BKE));
+    const int64_t total = static_cast<int64_t>(a.m_tiles) * a.n_tiles * p.batch;
+    if (total > 0x7fffffff) return cudaErrorInvalidValue;
+    a.total_tiles = static_cast<int>(total);
+    auto kern = cgemm_1bit_kernel<BN, STAGES>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int grid = static_cast<int>(std::min<int64_t>(total, pl.num_sms));
+    kern<<<grid, kThreads, C::SMEM_BYTES, s>>>(tmY, a);
+    return cudaGetLastError();
+}
+
+struct Config1 {
+    const char *name;
+    cudaError_t (*fn)(const tcbf_plan_s &, const uint32_t *, const uint32_t *, int32_t *,
+                      cudaStream_t);
+};
+
+const Config1 kConfigs1[] = {
+    {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double", launch1<128, 3>},
+    {"1bit->e4m3 BM128 BN256 BK128 stages2 tmem-single", launch1<256, 2>},
+};
+
+}  // namespace
+
+int gemm_1bit_num_configs() { return static_cast<int>(sizeof(kConfigs1) / sizeof(kConfigs1[0])); }
+
+const char *gemm_1bit_config_name(int config) {
+    if (config < 0 || config >= gemm_1bit_num_configs()) return "invalid";
+    return kConfigs1[config].name;
+}
+
+cudaError_t launch_gemm_1bit(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,
+                             int32_t *Y, cudaStream_t s) {
+    const int c = (pl.config >= 0 && pl.config < gemm_1bit_num_configs()) ? pl.config : 0;
+    return kConfigs1[c].fn(pl, Wb, Xb, Y, s);
+}
+
+}  // namespace tcbf

@@ -49,6 +49,11 @@ bool gemm_f16_config_valid(int config, int64_t K);
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s);
 
+int gemm_1bit_num_configs();
+const char *gemm_1bit_config_name(int config);
+cudaError_t launch_gemm_1bit(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,
+                             int32_t *Y, cudaStream_t s);
+
 cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double *tg,
                            int near_field, const double *freqs, double c, void *Wp,
                            cudaStream_t s);

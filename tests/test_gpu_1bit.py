@@ -1,0 +1,116 @@
+"""1-bit complex beamforming on the GPU against the exact int64 oracle.
+
+Bar: bit-exact int32 output.  Inputs are iid fair bits, including random
+bits beyond K in the last word (they must be ignored), ragged shapes that
+leave partial tiles and partial stages, weight sharing across batches, the
+matched-conjugate closed form, and the full-size 1-bit radio block on
+sampled outputs."""
+import numpy as np
+import pytest
+
+import oracle
+import tcbf_inputs as ti
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import ensure_lib
+    return ensure_lib()
+
+
+def run_1bit(Wb, Xb, K, config=None):
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    Bw, _, M, kw = Wb.shape
+    B, _, N, _ = Xb.shape
+    with Plan(B, M, N, K, MODE_1BIT, w_batches=Bw) as plan:
+        assert plan.Kw == kw
+        if config is not None:
+            plan.set_config(config)
+        Y = torch.full((B, M, N, 2), -7, dtype=torch.int32, device="cuda")
+        plan.beamform_1bit(dev(Wb), dev(Xb), Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        return Y.cpu().numpy().astype(np.int64)
+
+
+@pytest.mark.parametrize("config", [0, 1])
+@pytest.mark.parametrize("B,M,N,K", [(1, 1, 1, 1), (2, 3, 5, 7), (2, 33, 70, 45),
+                                     (1, 128, 256, 1024), (3, 130, 300, 200),
+                                     (2, 200, 64, 129), (1, 64, 1000, 640)])
+def test_random_bits_bit_exact(config, B, M, N, K):
+    Wb, Xb = ti.onebit_block(seed=M + N + K, B=B, M=M, K=K, N=N)
+    Y = run_1bit(Wb, Xb, K, config)
+    assert np.array_equal(Y, oracle.bgemm(Wb, Xb, K))
+
+
+def test_shared_weights_bit_exact():
+    g = ti.rng(4)
+    K = 300
+    Wb = ti.random_sign_words(g, (2, 2, 96, ti.words_per_row(K)))
+    Xb = ti.random_sign_words(g, (6, 2, 150, ti.words_per_row(K)))
+    Y = run_1bit(Wb, Xb, K)
+    assert np.array_equal(Y, oracle.bgemm(Wb, Xb, K))
+
+
+def test_matched_conjugate_gives_2K():
+    K = 1000
+    g = ti.rng(5)
+    Xb = ti.random_sign_words(g, (1, 2, 256, ti.words_per_row(K)))
+    Wb = Xb[:, :, :128].copy()
+    Wb[:, 1] = ~Wb[:, 1]
+    Y = run_1bit(Wb, Xb, K)
+    d = np.arange(128)
+    assert np.all(Y[0, d, d, 0] == 2 * K) and np.all(Y[0, d, d, 1] == 0)
+
+
+def test_pack_then_gemm_pipeline():
+    """Sign-pack FP16 values on the GPU, then the 1-bit GEMM, against the
+    oracle's own sign packing and int64 product."""
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    B, M, N, K = 3, 100, 200, 333
+    W, X = ti.small_fp16(seed=11, M=M, K=K, N=N, B=B)
+    with Plan(B, M, N, K, MODE_1BIT) as plan:
+        Wp = torch.empty(plan.packed_size(0), dtype=torch.uint8, device="cuda")
+        Xp = torch.empty(plan.packed_size(1), dtype=torch.uint8, device="cuda")
+        Y = torch.empty((B, M, N, 2), dtype=torch.int32, device="cuda")
+        plan.transpose_pack(0, dev(W), Wp)
+        plan.transpose_pack(1, dev(X), Xp)
+        plan.beamform_1bit(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        kw = plan.Kw
+        Yg = Y.cpu().numpy().astype(np.int64)
+    Wb = oracle.pack_signs(W, k_is_row=False, Kw=kw)
+    Xb = oracle.pack_signs(X, k_is_row=True, Kw=kw)
+    assert np.array_equal(Yg, oracle.bgemm(Wb, Xb, K))
+
+
+def test_full_size_radio_1bit_sampled():
+    """64 channels x 2048 beams x 1024 receivers x 8192 samples: the whole
+    launch as timed, checked bit-exact on sampled row/column blocks."""
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    B, M, K, N = 64, 2048, 1024, 8192
+    Wb, Xb = ti.onebit_block(seed=0, B=B, M=M, K=K, N=N)
+    with Plan(B, M, N, K, MODE_1BIT) as plan:
+        Y = torch.empty((B, M, N, 2), dtype=torch.int32, device="cuda")
+        plan.beamform_1bit(dev(Wb), dev(Xb), Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        g = np.random.default_rng(0)
+        for _ in range(6):
+            b = int(g.integers(B))
+            ms = np.sort(g.choice(M, 16, replace=False))
+            ns = np.sort(g.choice(N, 16, replace=False))
+            ref = oracle.bgemm(Wb[b:b + 1][:, :, ms], Xb[b:b + 1][:, :, ns], K)[0]
+            got = Y[b][torch.from_numpy(ms).cuda()][:, torch.from_numpy(ns).cuda()]
+            assert np.array_equal(got.cpu().numpy().astype(np.int64), ref)
