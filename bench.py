@@ -11,6 +11,11 @@ one block of samples that is already resident in HBM:
 The weights are computed once from geometry beforehand (they are constant
 over many blocks) and timed separately.
 
+Other workloads (--workload): "ultrasound" (65536 voxels x 16384 x 256
+frames, FP16, near-field model matrix) and "onebit" (64 channels x 2048
+beams x 1024 receivers x 8192 samples, 1-bit; step = sign-pack X + 1-bit
+GEMM).
+
 Metric: TeraOps/s with 8 useful operations per complex multiply-accumulate
 (8 * batch * M * N * K per step).  Prints ONE JSON line on rank 0.
 
@@ -33,17 +38,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Beamforming TeraOps/s (8 ops/cMAC), % tensor peak; served p50/p99 latency"
 UNIT = "TeraOps/s"
+FP8_OVER_BF16 = 4.5 / 2.25     # nominal dense-rate ratio used to scale the measured bf16 peak
 
 WORKLOADS = {
     "radio": dict(
-        B=512, M=1024, N=4096, K=288, w_batches=256, near_field=False,
+        mode="fp16", B=512, M=1024, N=4096, K=288, w_batches=256, geometry="radio",
         desc="radio-astronomy FP16 block: 256 channels x 2 pols = 512 products of "
              "1024 beams x 288 receivers x 4096 samples, weights from geometry "
              "(110-190 MHz, 3 km disk, beams within 5 deg of zenith)"),
     "ultrasound": dict(
-        B=1, M=65536, N=256, K=16384, w_batches=1, near_field=True,
+        mode="fp16", B=1, M=65536, N=256, K=16384, w_batches=1, geometry="ultrasound",
         desc="computational ultrasound FP16: 65536 voxels x 16384 (128 elements x 128 "
              "frequency bins) x 256 frames, near-field model matrix"),
+    "onebit": dict(
+        mode="1bit", B=64, M=2048, N=8192, K=1024, w_batches=64, geometry=None,
+        desc="radio-astronomy 1-bit block: 64 channels x 2048 beams x 1024 receivers x "
+             "8192 samples, +-1+-i values, exact int32 output"),
 }
 
 
@@ -62,6 +72,18 @@ def parse_args():
     ap.add_argument("--batches", type=int, default=None,
                     help="override the number of products (small profiling cases)")
     return ap.parse_args()
+
+
+def workload(args):
+    w = dict(WORKLOADS[args.workload])
+    if args.batches is not None:
+        w["B"] = args.batches
+        if args.workload == "radio":
+            w["w_batches"] = max(1, args.batches // 2)
+        else:
+            w["w_batches"] = min(w["w_batches"], args.batches)
+        w["desc"] += f" [{args.batches} products]"
+    return w
 
 
 def ops_per_step(w):
@@ -89,7 +111,7 @@ def kernel_sources_sha(files):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload):
+def recorded_traffic(kernel, workload_name):
     """DRAM bytes per launch from a committed ncu summary, only if the
     kernel's sources are unchanged since that capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -98,7 +120,7 @@ def recorded_traffic(kernel, workload):
             rec = json.load(fh)[kernel]
     except Exception:
         return None
-    if rec.get("workload") != workload:
+    if rec.get("workload") != workload_name:
         return None
     if rec.get("sources_sha") != kernel_sources_sha(rec.get("sources", [])):
         return None
@@ -147,68 +169,106 @@ class ClockSampler:
         os.unlink(self.tmp.name)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows),
                 "power_w_median": statistics.median(power) if power else None}
 
 
+# ----------------------------------------------------------------- inputs
+def geometry_of(w):
+    import tcbf_inputs as ti
+    if w["geometry"] == "radio":
+        return ti.radio_geometry(0, w["M"], w["K"], max(1, w["B"] // 2))
+    if w["geometry"] == "ultrasound":
+        return ti.ultrasound_geometry()
+    return None
+
+
+def host_x(w):
+    import tcbf_inputs as ti
+    if w["geometry"] == "ultrasound":
+        return ti.ultrasound_frames(1, w["K"], w["N"])
+    return ti.radio_x(1, w["B"], w["K"], w["N"])
+
+
+def onebit_weights(w):
+    import tcbf_inputs as ti
+    return ti.random_sign_words(ti.rng(0), (w["w_batches"], 2, w["M"], ti.words_per_row(w["K"])))
+
+
 # -------------------------------------------------------------- CPU oracle
-def cpu_baseline(w, seconds, seed=0):
-    """Time the FP64 oracle on a bounded sample of the same workload: the
-    first `nb` products (their weights computed by the oracle itself)."""
+def oracle_sample(w, seconds_target):
+    """The oracle on a bounded sample of the workload; returns (ops, seconds, text)."""
     import numpy as np
     import oracle
     import tcbf_inputs as ti
-    geom = ti.radio_geometry(seed, w["M"], w["K"], w["B"] // 2) if not w["near_field"] \
-        else ti.ultrasound_geometry()
+
+    if w["mode"] == "1bit":
+        Wb = onebit_weights(w)[:1]
+        X = ti.radio_x_batch(1, 0, w["K"], w["N"])[None]
+        Xb = oracle.pack_signs(X, k_is_row=True, Kw=Wb.shape[-1])
+
+        def run(rows):
+            t0 = time.perf_counter()
+            oracle.bgemm(Wb[:, :, :rows], Xb, w["K"])
+            return time.perf_counter() - t0
+        rows = 8
+        dt = run(rows)
+        rows = max(8, min(w["M"], int(rows * seconds_target / max(dt, 1e-3))))
+        dt = run(rows)
+        return 8.0 * rows * w["N"] * w["K"], dt, \
+            f"{rows} of {w['M']} beam rows of one product (int64 loops)"
+
+    geom = geometry_of(w)
+    if w["geometry"] == "ultrasound":
+        X = host_x(w)
+
+        def run(rows):
+            Wf = oracle.weights_fp16(geom.rx_pos, geom.targets[:rows], geom.freqs[:1], True, geom.c)
+            t0 = time.perf_counter()
+            oracle.cgemm(Wf, X)
+            return time.perf_counter() - t0
+        rows = 16
+        dt = run(rows)
+        rows = max(16, min(w["M"], int(rows * seconds_target / max(dt, 1e-3))))
+        dt = run(rows)
+        return 8.0 * rows * w["N"] * w["K"], dt, f"{rows} of {w['M']} voxel rows of the product"
+
     per_w = w["B"] // w["w_batches"]
 
     def sample(nb):
         nw = (nb + per_w - 1) // per_w
-        Wf = oracle.weights_fp16(geom.rx_pos, geom.targets, geom.freqs[:nw], geom.near_field, geom.c)
-        if w["near_field"]:
-            X = ti.ultrasound_frames(seed + 1, w["K"], w["N"])[:nb]
-        else:
-            X = np.stack([ti.radio_x_batch(seed + 1, b, w["K"], w["N"]) for b in range(nb)])
+        Wf = oracle.weights_fp16(geom.rx_pos, geom.targets, geom.freqs[:nw], False, geom.c)
+        X = np.stack([ti.radio_x_batch(1, b, w["K"], w["N"]) for b in range(nb)])
         return Wf, X
+    Wf, X = sample(per_w)
+    t0 = time.perf_counter()
+    oracle.cgemm(Wf[:1], X[:per_w])
+    dt1 = (time.perf_counter() - t0) / per_w
+    nb = max(per_w, min(w["B"], int(seconds_target / max(dt1, 1e-3)) // per_w * per_w))
+    Wf, X = sample(nb)
+    t0 = time.perf_counter()
+    oracle.cgemm(Wf, X)
+    dt = time.perf_counter() - t0
+    return 8.0 * nb * w["M"] * w["N"] * w["K"], dt, \
+        f"{nb} of {w['B']} products (whole products, FP64 loops)"
 
-    if w["near_field"]:
-        # one product is the whole workload: time a block of its voxel rows
-        X = ti.ultrasound_frames(seed + 1, w["K"], w["N"])
 
-        def rows_w(rows):
-            return oracle.weights_fp16(geom.rx_pos, geom.targets[:rows], geom.freqs[:1],
-                                       True, geom.c)
-        rows = 16
-        Wf = rows_w(rows)
-        t0 = time.perf_counter()
-        oracle.cgemm(Wf, X)
-        dt = time.perf_counter() - t0
-        rows = max(16, min(w["M"], int(rows * seconds / max(dt, 1e-3))))
-        Wf = rows_w(rows)
-        t0 = time.perf_counter()
-        oracle.cgemm(Wf, X)
-        dt = time.perf_counter() - t0
-        ops = 8.0 * rows * w["N"] * w["K"]
-        desc = f"{rows} of {w['M']} voxel rows of the one product"
-    else:
-        Wf, X = sample(per_w)
-        t0 = time.perf_counter()
-        oracle.cgemm(Wf[:1], X[:per_w])
-        dt1 = (time.perf_counter() - t0) / per_w
-        nb = max(per_w, min(w["B"], int(seconds / max(dt1, 1e-3)) // per_w * per_w))
-        Wf, X = sample(nb)
-        t0 = time.perf_counter()
-        oracle.cgemm(Wf, X)
-        dt = time.perf_counter() - t0
-        ops = 8.0 * nb * w["M"] * w["N"] * w["K"]
-        desc = f"{nb} of {w['B']} products (whole products, FP64 triple loop)"
+def cpu_baseline(w, seconds):
+    import oracle
+    ops, dt, desc = oracle_sample(w, seconds)
     return {"value": ops / dt / 1e12, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle", "sample": desc, "seconds": round(dt, 3),
             "host_cpus": os.cpu_count()}
@@ -216,65 +276,134 @@ def cpu_baseline(w, seconds, seed=0):
 
 def reference_arm(args, w):
     """The oracle as the reference arm: each step one bounded sample."""
-    import numpy as np
     import oracle
-    import tcbf_inputs as ti
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    geom = ti.radio_geometry(0, w["M"], w["K"], w["B"] // 2) if not w["near_field"] \
-        else ti.ultrasound_geometry()
-    Wf = oracle.weights_fp16(geom.rx_pos, geom.targets, geom.freqs[:1], geom.near_field, geom.c)
-    if w["near_field"]:
-        rows = 16
-        Wf = Wf[:, :rows]
-        X = ti.ultrasound_frames(1, w["K"], w["N"])
-        ops = 8.0 * rows * w["N"] * w["K"]
-        desc = f"{rows} voxel rows of the product per step"
-    else:
-        X = ti.radio_x_batch(1, 0, w["K"], w["N"])[None]
-        ops = 8.0 * w["M"] * w["N"] * w["K"]
-        desc = "1 of 512 products per step"
+    target = 0.4      # seconds of oracle work per step
+    _, _, desc = oracle_sample(w, target)
     for _ in range(args.warmup):
-        oracle.cgemm(Wf, X)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.cgemm(Wf, X)
-        times.append(time.perf_counter() - t0)
-    tot = sum(times)
-    value = ops * len(times) / tot / 1e12
+        oracle_sample(w, target)
+    samples = [oracle_sample(w, target) for _ in range(args.steps)]
+    tot_ops = sum(s[0] for s in samples)
+    tot = sum(s[1] for s in samples)
+    value = tot_ops / tot / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "impl": "reference",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(samples),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64" if w["mode"] == "1bit" else "f64", "data": "synthetic",
+        "impl": "reference",
         "config": {"workload": w["desc"], "batch": w["B"], "M": w["M"], "N": w["N"], "K": w["K"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": desc},
+                         "kind": "oracle", "sample": desc + " per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------- GPU
+class GpuWorkload:
+    """Device-resident inputs and the step of one workload."""
+
+    def __init__(self, w, local, config):
+        import numpy as np
+        import torch
+        import paper_2505_03269_gb300 as tcbf
+        self.w = w
+        B, M, N, K, Bw = w["B"], w["M"], w["N"], w["K"], w["w_batches"]
+        self.Xh = host_x(w)
+        self.Xd = torch.from_numpy(self.Xh).cuda()
+        mode = tcbf.MODE_1BIT if w["mode"] == "1bit" else tcbf.MODE_FP16
+        self.plan = tcbf.Plan(B, M, N, K, mode, w_batches=Bw, device=local)
+        if config is not None:
+            self.plan.set_config(config)
+        self.Wp = torch.empty(self.plan.packed_size(0), dtype=torch.uint8, device="cuda")
+        self.Xp = torch.empty(self.plan.packed_size(1), dtype=torch.uint8, device="cuda")
+        ydt = torch.int32 if w["mode"] == "1bit" else torch.float32
+        self.Y = torch.empty((B, M, N, 2), dtype=ydt, device="cuda")
+        self.weights_ms = None
+        if w["mode"] == "1bit":
+            self.Wbits = onebit_weights(w)
+            self.Wp.copy_(torch.from_numpy(self.Wbits.view(np.uint8).ravel()).cuda())
+        else:
+            self.geom = geometry_of(w)
+            rx = torch.from_numpy(self.geom.rx_pos).cuda()
+            tg = torch.from_numpy(self.geom.targets).cuda()
+            fr = torch.from_numpy(np.ascontiguousarray(self.geom.freqs[:Bw])).cuda()
+            args = (rx, tg, self.geom.near_field, fr, self.geom.c, self.Wp)
+            self.plan.weights_from_geometry(*args)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            self.plan.weights_from_geometry(*args)
+            e1.record()
+            torch.cuda.synchronize()
+            self.weights_ms = e0.elapsed_time(e1)
+
+    def pack(self):
+        self.plan.transpose_pack(1, self.Xd, self.Xp)
+
+    def gemm(self):
+        if self.w["mode"] == "1bit":
+            self.plan.beamform_1bit(self.Wp, self.Xp, self.Y)
+        else:
+            self.plan.beamform_fp16(self.Wp, self.Xp, self.Y)
+
+    def step(self):
+        self.pack()
+        self.gemm()
+
+    def gemm_bytes(self):
+        return self.plan.packed_size(0) + self.plan.packed_size(1) + self.Y.numel() * 4
+
+    def parity(self, npts=128):
+        """Sampled outputs against the oracle, which derives everything
+        (weights, sign packing) from the same seeded inputs itself."""
+        import numpy as np
+        import torch
+        import oracle
+        w = self.w
+        B, M, N, K, Bw = w["B"], w["M"], w["N"], w["K"], w["w_batches"]
+        g = np.random.default_rng(123)
+        if w["mode"] == "1bit":
+            bad = 0
+            for _ in range(4):
+                b = int(g.integers(B))
+                ms = np.sort(g.choice(M, 16, replace=False))
+                ns = np.sort(g.choice(N, 16, replace=False))
+                Xb = oracle.pack_signs(np.ascontiguousarray(self.Xh[b:b + 1][:, :, ns]),
+                                       k_is_row=True, Kw=self.Wbits.shape[-1])
+                bw = b // (B // Bw)
+                ref = oracle.bgemm(self.Wbits[bw:bw + 1][:, :, ms], Xb, K)[0]
+                got = self.Y[b][torch.from_numpy(ms).cuda()][:, torch.from_numpy(ns).cuda()]
+                bad += int(np.sum(got.cpu().numpy().astype(np.int64) != ref))
+            return {"points": 4 * 256, "mismatches": bad, "reference": "int64 oracle, exact"}
+        pts = np.stack([g.integers(0, B, npts), g.integers(0, M, npts), g.integers(0, N, npts)], 1)
+        ref = np.empty(npts, np.complex128)
+        geom = self.geom
+        for i, (b, m, n) in enumerate(pts):
+            bw = b // (B // Bw)
+            Wrow = oracle.weights_fp16(geom.rx_pos, geom.targets[m:m + 1], geom.freqs[bw:bw + 1],
+                                       geom.near_field, geom.c)
+            ref[i] = oracle.cgemm_points(Wrow, self.Xh[b:b + 1], np.array([[0, 0, n]]))[0]
+        t = torch.from_numpy(pts).cuda()
+        Yh = self.Y[t[:, 0], t[:, 1], t[:, 2]].double().cpu().numpy()
+        got = Yh[:, 0] + 1j * Yh[:, 1]
+        return {"points": npts, "rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                "reference": "FP64 oracle, its own weights from the same geometry"}
+
+
 def main():
     args = parse_args()
-    w = dict(WORKLOADS[args.workload])
-    if args.batches is not None and args.workload == "radio":
-        w["B"] = args.batches
-        w["w_batches"] = max(1, args.batches // 2)
-        w["desc"] = w["desc"].replace("256 channels x 2 pols = 512", f"{args.batches}")
+    w = workload(args)
     if args.impl == "reference":
         reference_arm(args, w)
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
     import paper_2505_03269_gb300 as tcbf
-    import tcbf_inputs as ti
     from paper_2505_03269_gb300 import build as tcbf_build
 
     rank = int(os.environ.get("RANK", "0"))
@@ -294,41 +423,12 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    B, M, N, K, Bw = w["B"], w["M"], w["N"], w["K"], w["w_batches"]
-    # ---- inputs: geometry and samples (host), then resident on the device
-    if w["near_field"]:
-        geom = ti.ultrasound_geometry()
-        Xh = ti.ultrasound_frames(1, K, N)
-    else:
-        geom = ti.radio_geometry(0, M, K, B // 2)
-        Xh = ti.radio_x(1, B, K, N)
-    Xd = torch.from_numpy(Xh).cuda()
-    plan = tcbf.Plan(B, M, N, K, tcbf.MODE_FP16, w_batches=Bw, device=local)
-    if args.config is not None:
-        plan.set_config(args.config)
-    Wp = torch.empty(plan.packed_size(0), dtype=torch.uint8, device="cuda")
-    Xp = torch.empty(plan.packed_size(1), dtype=torch.uint8, device="cuda")
-    Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
-    rx = torch.from_numpy(geom.rx_pos).cuda()
-    tg = torch.from_numpy(geom.targets).cuda()
-    fr = torch.from_numpy(np.ascontiguousarray(geom.freqs[:Bw])).cuda()
+    gw = GpuWorkload(w, local, args.config)
+    plan = gw.plan
     stream = torch.cuda.current_stream()
-
-    # weights: once, timed on their own
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    plan.weights_from_geometry(rx, tg, w["near_field"], fr, geom.c, Wp)
-    e0.record()
-    plan.weights_from_geometry(rx, tg, w["near_field"], fr, geom.c, Wp)
-    e1.record()
-    torch.cuda.synchronize()
-    weights_ms = e0.elapsed_time(e1)
-
-    def step():
-        plan.transpose_pack(1, Xd, Xp)
-        plan.beamform_fp16(Wp, Xp, Y)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
+        gw.step()
     barrier()
     assert plan.last_device_error() == 0
 
@@ -339,9 +439,9 @@ def main():
     barrier()
     for i in range(args.steps):
         ev[i][0].record(stream)
-        plan.transpose_pack(1, Xd, Xp)
+        gw.pack()
         ev[i][1].record(stream)
-        plan.beamform_fp16(Wp, Xp, Y)
+        gw.gemm()
         ev[i][2].record(stream)
     barrier()
     clocks = sampler.stop()
@@ -352,91 +452,82 @@ def main():
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
+    ms_per_step = float(t.item()) / args.steps
     value = world * ops_per_step(w) / (ms_per_step * 1e-3) / 1e12
 
-    # ---- parity on sampled outputs (full size, the launch configuration timed above)
-    import oracle
-    g = np.random.default_rng(123)
-    npts = 128
-    pts = np.stack([g.integers(0, B, npts), g.integers(0, M, npts), g.integers(0, N, npts)], 1)
-    ref = np.empty(npts, np.complex128)
-    for i, (b, m, n) in enumerate(pts):
-        bw = b // (B // Bw)
-        Wrow = oracle.weights_fp16(geom.rx_pos, geom.targets[m:m + 1], geom.freqs[bw:bw + 1],
-                                   geom.near_field, geom.c)
-        ref[i] = oracle.cgemm_points(Wrow, Xh[b:b + 1], np.array([[0, 0, n]]))[0]
-    ti_ = torch.from_numpy(pts).cuda()
-    Yh = Y[ti_[:, 0], ti_[:, 1], ti_[:, 2]].double().cpu().numpy()
-    got = Yh[:, 0] + 1j * Yh[:, 1]
-    parity = {"points": npts, "rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-              "reference": "FP64 oracle, its own weights from the same geometry"}
+    parity = gw.parity()
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        Xhost = torch.from_numpy(Xh).pin_memory()
-        Yhost = torch.empty((B, M, N, 2), dtype=torch.float32, pin_memory=True)
-        for _ in range(1):
-            Xd.copy_(Xhost, non_blocking=True)
-            step()
-            Yhost.copy_(Y, non_blocking=True)
+        Xhost = torch.from_numpy(gw.Xh).pin_memory()
+        Yhost = torch.empty(gw.Y.shape, dtype=gw.Y.dtype, pin_memory=True)
+
+        def e2e_step():
+            gw.Xd.copy_(Xhost, non_blocking=True)
+            gw.step()
+            Yhost.copy_(gw.Y, non_blocking=True)
+        e2e_step()
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(args.e2e_steps):
-            Xd.copy_(Xhost, non_blocking=True)
-            step()
-            Yhost.copy_(Y, non_blocking=True)
+            e2e_step()
         b.record()
         barrier()
-        e2e_ms = a.elapsed_time(b) / args.e2e_steps
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        te = torch.tensor([a.elapsed_time(b) / args.e2e_steps], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": world * ops_per_step(w) / (float(te.item()) * 1e-3) / 1e12, "unit": UNIT,
-               "h2d_bytes_per_step": int(Xh.nbytes), "d2h_bytes_per_step": int(Y.numel() * 4),
+               "h2d_bytes_per_step": int(gw.Xh.nbytes), "d2h_bytes_per_step": int(gw.Y.numel() * 4),
                "ms_per_step": float(te.item()),
                "how": "pinned host X -> device, pack, beamform, Y -> pinned host, one stream"}
         del Xhost, Yhost
 
     # ---- roofline of the dominant kernel (the GEMM)
     peaks = load_peaks()
-    gemm_bytes = plan.packed_size(0) + plan.packed_size(1) + B * M * N * 8
-    pack_bytes = 2 * plan.packed_size(1)
-    ai = ops_per_step(w) / gemm_bytes
-    ridge = peaks["bf16_tflops"] * 1e12 / (peaks["hbm_gbs"] * 1e9)
-    gemm_tops = ops_per_step(w) / (gemm_ms * 1e-3) / 1e12
-    gemm_gbs = gemm_bytes / (gemm_ms * 1e-3) / 1e9
-    gemm_sources = ["paper_2505_03269_gb300/csrc/gemm_f16.cu", "paper_2505_03269_gb300/csrc/ptx.cuh"]
+    gbytes = gw.gemm_bytes()
+    pack_bytes = gw.Xh.nbytes + plan.packed_size(1)
+    ops = ops_per_step(w)
+    if w["mode"] == "1bit":
+        tensor_peak = peaks["bf16_tflops"] * FP8_OVER_BF16
+        peak_note = "E4M3 tensor peak = measured bf16 burst x nominal fp8/bf16 ratio 2"
+        kname = "cgemm_1bit_kernel"
+    else:
+        tensor_peak = peaks["bf16_tflops"]
+        peak_note = "FP16 tensor peak = measured bf16 burst (same dense rate)"
+        kname = "cgemm_f16_kernel"
+    ai = ops / gbytes
+    ridge = tensor_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
+    gemm_tops = ops / (gemm_ms * 1e-3) / 1e12
+    gemm_gbs = gbytes / (gemm_ms * 1e-3) / 1e9
     if ai < ridge:
         roof = {"bound": "hbm", "achieved": gemm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gemm_gbs / peaks["hbm_gbs"]}
     else:
-        roof = {"bound": "tensor", "achieved": gemm_tops, "peak": peaks["bf16_tflops"],
-                "unit": "TFLOP/s", "frac": gemm_tops / peaks["bf16_tflops"]}
-    roof["traffic"] = recorded_traffic("gemm_f16", args.workload)
-    roof["kernel"] = "cgemm_f16_kernel"
-    roof["algorithmic_bytes"] = gemm_bytes
-    roof["peak_source"] = peaks["source"]
-
+        roof = {"bound": "tensor", "achieved": gemm_tops, "peak": tensor_peak,
+                "unit": "TFLOP/s", "frac": gemm_tops / tensor_peak}
+    roof.update({"traffic": recorded_traffic(kname, args.workload if args.batches is None else None),
+                 "kernel": kname, "algorithmic_bytes": gbytes,
+                 "peak_source": peaks["source"], "tensor_peak_note": peak_note,
+                 "ceiling_tops": min(tensor_peak, ai * peaks["hbm_gbs"] / 1e3)})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": w["desc"], "batch": B, "M": M, "N": N, "K": K, "w_batches": Bw,
-                   "step": "transpose_pack(X) + beamform_fp16 (weights resident)",
+        "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u1" if w["mode"] == "1bit" else "f16",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "batch": w["B"], "M": w["M"], "N": w["N"], "K": w["K"],
+                   "w_batches": w["w_batches"],
+                   "step": "transpose_pack(X) + beamform (weights resident)",
                    "l2": "inputs larger than L2 (X %.2f GB, Y %.1f GB per step)"
-                         % (Xh.nbytes / 1e9, B * M * N * 8 / 1e9),
+                         % (gw.Xh.nbytes / 1e9, gw.Y.numel() * 4 / 1e9),
                    "kernel_config": plan.config_name(plan.get_config()),
                    "parallelism": f"{world} independent replica(s), no collective"},
         "gpu_launches": 2 * args.steps,
         "roofline": roof,
-        "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms, "weights_ms_once": weights_ms,
-                    "gemm_tops": gemm_tops,
-                    "gemm_frac_of_bf16_peak": gemm_tops / peaks["bf16_tflops"],
-                    "gemm_ai_ops_per_byte": ai,
+        "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms, "weights_ms_once": gw.weights_ms,
+                    "gemm_tops": gemm_tops, "gemm_frac_of_tensor_peak": gemm_tops / tensor_peak,
+                    "gemm_gbs": gemm_gbs, "gemm_ai_ops_per_byte": ai,
                     "pack_gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
                     "pack_frac_of_hbm": pack_bytes / (pack_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "clocks": clocks,

@@ -10,13 +10,14 @@
 // FP32 accumulators.  Every partial sum is an integer of magnitude <= 2K,
 // exact in FP32 for K < 2^23, so the result equals K - 2 Hamming exactly.
 //
-// Warp roles (288 threads, one CTA per SM, persistent over tiles):
+// Warp roles (416 threads, one CTA per SM, persistent over tiles):
 //   warp 0      TMEM owner and single-thread MMA issuer (4 real MMAs per
 //               K step, negate-A for -Im(W) Im(X), as in the FP16 kernel)
-//   warps 1-4   converters: 16-byte loads of packed words (L2-resident),
-//               expansion to E4M3 in the 128-byte-swizzled K-major layout
-//               the MMA reads, one stage of 128 K per ring slot
-//   warps 5-8   epilogue: TMEM -> int32 pairs -> staged TMA stores
+//   warps 1-8   converters (4 for W rows, 4 for X rows): 16-byte loads of
+//               packed words (L2-resident), expansion to E4M3 in the
+//               128-byte-swizzled K-major layout the MMA reads, one stage of
+//               128 K per ring slot
+//   warps 9-12  epilogue: TMEM -> int32 pairs -> staged TMA stores
 #include <algorithm>
 #include <cstring>
 
@@ -30,8 +31,10 @@ using namespace dev;
 
 constexpr int BM = 128;
 constexpr int BKE = 128;             // K elements per stage (one 128-byte E4M3 row)
-constexpr int kThreads = 288;
-constexpr int kConv = 128;           // converter threads
+constexpr int kConvW = 128;          // converter threads for W rows
+constexpr int kConvX = 128;          // converter threads for X rows
+constexpr int kConv = kConvW + kConvX;
+constexpr int kThreads = 32 + kConv + 128;
 
 struct Args1 {
     int32_t *Y;
@@ -98,12 +101,76 @@ __device__ __forceinline__ void st_shared_u4(uint32_t addr, uint4 v) {
 }
 
 // Expand one row's 128 K (4 words) of one plane into the swizzled slot.
+// Full stages (valid >= 128) take the unmasked path.
 __device__ __forceinline__ void expand_row(uint32_t row_base, int r, uint4 words, int valid) {
     const uint32_t w[4] = {words.x, words.y, words.z, words.w};
+    const uint32_t sw = static_cast<uint32_t>(r & 7);
+    if (valid >= BKE) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const uint32_t bits = (w[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
-        st_shared_u4(row_base + ((c ^ (r & 7)) << 4), expand16(bits, valid - 16 * c));
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t bits = w[c >> 1] >> (16 * (c & 1));
+            uint4 v;
+            v.x = expand4(bits & 15u);
+            v.y = expand4((bits >> 4) & 15u);
+            v.z = expand4((bits >> 8) & 15u);
+            v.w = expand4((bits >> 12) & 15u);
+            st_shared_u4(row_base + ((c ^ sw) << 4), v);
+        }
+    } else {
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t bits = (w[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
+            st_shared_u4(row_base + ((c ^ sw) << 4), expand16(bits, valid - 16 * c));
+        }
+    }
+}
+
+// Packed words one converter thread needs for one stage: a W row (both
+// planes) for the first kConvW threads, BN/128 X rows for the others, with
+// the number of valid K elements (0 for rows beyond M or N: zeros).
+template <int BN>
+struct StageWords {
+    uint4 re[BN / 128], im[BN / 128];
+    int valid[BN / 128];
+};
+
+// Load stage `i` of this CTA's flattened (tile, stage) sequence.
+template <int BN>
+__device__ __forceinline__ void load_stage(const Args1 &args, int ct, int i, int iters,
+                                           StageWords<BN> &w) {
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int h = 0; h < BN / 128; ++h) {
+        w.re[h] = w.im[h] = zero;
+        w.valid[h] = 0;
+    }
+    if (i >= iters) return;
+    const int t = blockIdx.x + (i / args.num_kb) * gridDim.x;
+    const int kb = i % args.num_kb;
+    int b, mt, nt;
+    decode_tile(t, args, b, mt, nt);
+    const int valid = args.K - kb * BKE;
+    if (ct < kConvW) {
+        const int mrow = mt * BM + ct;
+        if (mrow < args.M) {
+            const uint32_t *wr = args.Wb +
+                (static_cast<size_t>((b / args.per_w) * 2) * args.M + mrow) * args.Kw + kb * 4;
+            w.re[0] = __ldg(reinterpret_cast<const uint4 *>(wr));
+            w.im[0] = __ldg(reinterpret_cast<const uint4 *>(wr + static_cast<size_t>(args.M) * args.Kw));
+            w.valid[0] = valid;
+        }
+        return;
+    }
+#pragma unroll
+    for (int h = 0; h < BN / 128; ++h) {
+        const int nrow = nt * BN + (ct - kConvW) + 128 * h;
+        if (nrow < args.N) {
+            const uint32_t *xr =
+                args.Xb + (static_cast<size_t>(b * 2) * args.N + nrow) * args.Kw + kb * 4;
+            w.re[h] = __ldg(reinterpret_cast<const uint4 *>(xr));
+            w.im[h] = __ldg(reinterpret_cast<const uint4 *>(xr + static_cast<size_t>(args.N) * args.Kw));
+            w.valid[h] = valid;
+        }
     }
 }
 
@@ -207,65 +274,47 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(done_bar);
             if (!mbar_wait(done_bar, 0)) atomicOr(args.status, kErrTimeoutDrain);
         }
-    } else if (warp <= 4) {
+    } else if (warp <= kConv / 32) {
         // ------------------------------------------------------- converters
-        const int ct = threadIdx.x - 32;               // 0..127: one W row, BN/128 X rows
+        // The (tile, stage) sequence of this CTA is flattened and the packed
+        // words of stage i + 2 are loaded while stage i is expanded, so the
+        // L2 latency of the 16-byte loads is covered.
+        const int ct = threadIdx.x - 32;               // 0..255: W rows, then X rows
+        const int my_tiles = (args.total_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        const int iters = my_tiles * args.num_kb;
+        StageWords<BN> cur, nxt;
+        load_stage<BN>(args, ct, 0, iters, cur);
+        load_stage<BN>(args, ct, 1, iters, nxt);
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
-            int b, mt, nt;
-            decode_tile(t, args, b, mt, nt);
-            const int bw = b / args.per_w;
-            const int mrow = mt * BM + ct;
-            const uint32_t *wr = args.Wb + (static_cast<size_t>(bw * 2) * args.M + mrow) * args.Kw;
-            const uint32_t *wi = wr + static_cast<size_t>(args.M) * args.Kw;
-            for (int kb = 0; kb < args.num_kb; ++kb) {
-                // issue this stage's loads before waiting for the slot
-                const int valid = args.K - kb * BKE;
-                const uint4 zero = make_uint4(0, 0, 0, 0);
-                uint4 aw_r = zero, aw_i = zero;
-                if (mrow < args.M) {
-                    aw_r = __ldg(reinterpret_cast<const uint4 *>(wr + kb * 4));
-                    aw_i = __ldg(reinterpret_cast<const uint4 *>(wi + kb * 4));
-                }
-                uint4 bw_r[BN / 128], bw_i[BN / 128];
+        for (int i = 0; i < iters; ++i) {
+            StageWords<BN> ahead;
+            load_stage<BN>(args, ct, i + 2, iters, ahead);
+            if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            const uint32_t a = s0 + stage * C::STAGE_BYTES;
+            if (ct < kConvW) {
+                expand_row(a + ct * 128, ct, cur.re[0], cur.valid[0]);
+                expand_row(a + C::A_PLANE + ct * 128, ct, cur.im[0], cur.valid[0]);
+            } else {
 #pragma unroll
                 for (int h = 0; h < BN / 128; ++h) {
-                    const int nrow = nt * BN + ct + 128 * h;
-                    bw_r[h] = zero;
-                    bw_i[h] = zero;
-                    if (nrow < args.N) {
-                        const uint32_t *xr =
-                            args.Xb + (static_cast<size_t>(b * 2) * args.N + nrow) * args.Kw;
-                        const uint32_t *xi = xr + static_cast<size_t>(args.N) * args.Kw;
-                        bw_r[h] = __ldg(reinterpret_cast<const uint4 *>(xr + kb * 4));
-                        bw_i[h] = __ldg(reinterpret_cast<const uint4 *>(xi + kb * 4));
-                    }
-                }
-                if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t a = s0 + stage * C::STAGE_BYTES;
-                // rows beyond M / N expand to zeros (valid = 0)
-                const int va = mrow < args.M ? valid : 0;
-                expand_row(a + ct * 128, ct, aw_r, va);
-                expand_row(a + C::A_PLANE + ct * 128, ct, aw_i, va);
-#pragma unroll
-                for (int h = 0; h < BN / 128; ++h) {
-                    const int r = ct + 128 * h;
-                    const int vb = (nt * BN + r) < args.N ? valid : 0;
-                    expand_row(a + C::A_BYTES + r * 128, r, bw_r[h], vb);
-                    expand_row(a + C::A_BYTES + C::B_PLANE + r * 128, r, bw_i[h], vb);
-                }
-                fence_async_smem();                    // generic writes -> tensor core reads
-                mbar_arrive(full0 + 8 * stage);
-                if (++stage == STAGES) {
-                    stage = 0;
-                    phase ^= 1u;
+                    const int r = ct - kConvW + 128 * h;
+                    expand_row(a + C::A_BYTES + r * 128, r, cur.re[h], cur.valid[h]);
+                    expand_row(a + C::A_BYTES + C::B_PLANE + r * 128, r, cur.im[h], cur.valid[h]);
                 }
             }
+            fence_async_smem();                        // generic writes -> tensor core reads
+            mbar_arrive(full0 + 8 * stage);
+            if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1u;
+            }
+            cur = nxt;
+            nxt = ahead;
         }
         if (!ok && ct == 0) {
             atomicOr(args.status, kErrTimeoutProducer);
@@ -275,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // --------------------------------------------------------- epilogue
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const uint32_t stage_buf = staging0 + (warp - 5) * 8192;
+        const uint32_t stage_buf = staging0 + (warp - 1 - kConv / 32) * 8192;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
         int local = 0;
         int chunk_count = 0;
@@ -399,8 +448,8 @@ struct Config1 {
 };
 
 const Config1 kConfigs1[] = {
-    {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double", launch1<128, 3>},
     {"1bit->e4m3 BM128 BN256 BK128 stages2 tmem-single", launch1<256, 2>},
+    {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double", launch1<128, 3>},
 };
 
 }  // namespace
