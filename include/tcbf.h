@@ -208,6 +208,43 @@ tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config);
 /* Human-readable description of configuration `config` (static string). */
 const char *tcbf_config_name(tcbf_plan_t plan, int config);
 
+/*
+ * Uneven batches (Sec. V-B: every channel/polarisation is one product; here
+ * each may have its own beam count).  rows: HOST array of `batch` entries,
+ * 1 <= rows[b] <= M; NULL returns to uniform batches.  Layouts keep M rows
+ * per batch; the kernels compute only the tiles covering rows[b] rows, all
+ * batches still in one persistent launch.  Rows m >= rows[b] of Y[b] up to
+ * the next multiple of 128 are overwritten with unspecified values; rows
+ * beyond that are left untouched.  Allocates a (batch+1)-int device table
+ * owned by the plan (synchronous).
+ */
+tcbf_status tcbf_plan_set_batch_rows(tcbf_plan_t plan, const int64_t *rows);
+
+/*
+ * Autotuner (Sec. IV-A: the work per block and the number of buffers are
+ * tuned per GPU and shape).  Times every valid configuration of the plan's
+ * mode with CUDA events on `stream` (one warm-up launch, then `reps`
+ * launches) on the caller's packed operands and output, selects the fastest
+ * and leaves it set on the plan.  Synchronises the stream.  *best receives
+ * the chosen configuration; ms_per_config (nullable, tcbf_plan_num_configs
+ * entries) the mean milliseconds per launch, -1 for configurations not
+ * valid for this shape.  Y is overwritten.  Modes FP16 and 1-bit.
+ */
+tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const void *Xp, void *Y, int reps,
+                          tcbf_stream_t stream, int *best, float *ms_per_config);
+
+/*
+ * Capture one step into a CUDA graph owned by the plan: the transpose/pack
+ * of X_src into Xp (skipped when X_src is NULL) followed by the beamform of
+ * Wp and Xp into Y, with the plan's current configuration.  Pointers are
+ * baked into the graph; replace the graph by capturing again.  Modes FP16
+ * and 1-bit.  tcbf_graph_launch replays it on `stream` (one launch of the
+ * whole step; TCBF_ERR_INVALID_ARG if nothing was captured).
+ */
+tcbf_status tcbf_graph_capture(tcbf_plan_t plan, const void *X_src, int src_type, void *Xp,
+                               const void *Wp, void *Y);
+tcbf_status tcbf_graph_launch(tcbf_plan_t plan, tcbf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

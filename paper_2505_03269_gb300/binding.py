@@ -28,6 +28,7 @@ EXPORTED = [
     "tcbf_beamform_1bit", "tcbf_weights_from_geometry", "tcbf_last_device_error",
     "tcbf_status_string", "tcbf_plan_num_configs", "tcbf_plan_get_config",
     "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
+    "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
 ]
 
 
@@ -71,6 +72,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_plan_get_config": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_set_config": [vp, i32],
         "tcbf_beamform_fp16_noalloc": [ctypes.POINTER(Problem), i32, vp, vp, i32, vp, i32, vp],
+        "tcbf_plan_set_batch_rows": [vp, vp],
+        "tcbf_autotune": [vp, vp, vp, vp, i32, vp, ctypes.POINTER(i32), vp],
+        "tcbf_graph_capture": [vp, vp, i32, vp, vp, vp],
+        "tcbf_graph_launch": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -195,6 +200,34 @@ class Plan:
 
     def config_name(self, c: int) -> str:
         return self._lib.tcbf_config_name(self.handle, int(c)).decode()
+
+    # ------------------------------------------- uneven batches, tuning, graphs
+    def set_batch_rows(self, rows):
+        """Per-batch beam counts (host sequence of ints), or None for uniform."""
+        if rows is None:
+            _check(self._lib.tcbf_plan_set_batch_rows(self.handle, None), "set_batch_rows")
+            return
+        arr = (ctypes.c_int64 * len(rows))(*[int(r) for r in rows])
+        _check(self._lib.tcbf_plan_set_batch_rows(self.handle, ctypes.cast(arr, ctypes.c_void_p)),
+               "set_batch_rows")
+
+    def autotune(self, Wp, Xp, Y, reps=3, stream=None):
+        """Time every valid configuration; the fastest stays set.  Returns
+        (best, [ms per configuration, -1 where not valid])."""
+        n = self.num_configs()
+        ms = (ctypes.c_float * n)()
+        best = ctypes.c_int()
+        _check(self._lib.tcbf_autotune(self.handle, _ptr(Wp), _ptr(Xp), _ptr(Y), int(reps),
+                                       _stream(stream), ctypes.byref(best),
+                                       ctypes.cast(ms, ctypes.c_void_p)), "tcbf_autotune")
+        return best.value, list(ms)
+
+    def graph_capture(self, Xsrc, Xp, Wp, Y, src_type=SRC_CF16):
+        _check(self._lib.tcbf_graph_capture(self.handle, _ptr(Xsrc), int(src_type), _ptr(Xp),
+                                            _ptr(Wp), _ptr(Y)), "tcbf_graph_capture")
+
+    def graph_launch(self, stream=None):
+        _check(self._lib.tcbf_graph_launch(self.handle, _stream(stream)), "tcbf_graph_launch")
 
 
 def beamform_fp16_noalloc(batch, M, N, K, Wp, X, Y, w_batches=0, device=0,

@@ -164,6 +164,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_destroy(tcbf_plan_t plan) {
     if (!plan) return TCBF_OK;
     {
         DeviceGuard g(plan->device);
+        if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
+        if (plan->m_prefix) cudaFree(plan->m_prefix);
         if (plan->status) cudaFree(plan->status);
     }
     delete plan;
@@ -285,7 +287,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
     if (config < 0 || config >= n) return TCBF_ERR_INVALID_ARG;
     if (plan->p.mode == TCBF_MODE_FP16 && !gemm_f16_config_valid(config, plan->p.K))
         return TCBF_ERR_INVALID_ARG;
-    plan->config = config;
+    plan->config = config;   // a captured graph keeps the configuration it was captured with
     return TCBF_OK;
 }
 
@@ -294,4 +296,168 @@ TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
     if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
     if (plan->p.mode == TCBF_MODE_1BIT) return gemm_1bit_config_name(config);
     return config == 0 ? "default" : "invalid";
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batches, autotuning and graph capture.
+// ---------------------------------------------------------------------------
+namespace {
+
+cudaError_t launch_beamform(const tcbf_plan_s &pl, const void *Wp, const void *Xp, void *Y,
+                            cudaStream_t s) {
+    if (pl.p.mode == TCBF_MODE_FP16)
+        return launch_gemm_f16(pl, Wp, Xp, static_cast<float *>(Y), s);
+    if (pl.p.mode == TCBF_MODE_1BIT)
+        return launch_gemm_1bit(pl, static_cast<const uint32_t *>(Wp),
+                                static_cast<const uint32_t *>(Xp), static_cast<int32_t *>(Y), s);
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_pack_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                          cudaStream_t s) {
+    if (pl.p.mode == TCBF_MODE_FP16) return launch_pack_f16_x(pl, src_type, src, dst, s);
+    if (pl.p.mode == TCBF_MODE_1BIT) return launch_pack_bits_x(pl, src_type, src, dst, s);
+    return cudaErrorNotSupported;
+}
+
+bool config_ok(const tcbf_plan_s &pl, int c) {
+    if (pl.p.mode == TCBF_MODE_FP16) return gemm_f16_config_valid(c, pl.p.K);
+    if (pl.p.mode == TCBF_MODE_1BIT) return c >= 0 && c < gemm_1bit_num_configs();
+    return c == 0;
+}
+
+}  // namespace
+
+TCBF_EXPORT tcbf_status tcbf_plan_set_batch_rows(tcbf_plan_t plan, const int64_t *rows) {
+    if (!plan) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    if (!rows) {
+        if (plan->m_prefix) cudaFree(plan->m_prefix);
+        plan->m_prefix = nullptr;
+        plan->m_tiles_sum = 0;
+        return TCBF_OK;
+    }
+    const int64_t B = plan->p.batch;
+    int *host = new (std::nothrow) int[B + 1];
+    if (!host) return TCBF_ERR_OOM;
+    int64_t acc = 0;
+    host[0] = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        if (rows[b] < 1 || rows[b] > plan->p.M) {
+            delete[] host;
+            return TCBF_ERR_INVALID_ARG;
+        }
+        acc += ceil_div(rows[b], 128);
+        if (acc > 0x3fffffff) {
+            delete[] host;
+            return TCBF_ERR_UNSUPPORTED;
+        }
+        host[b + 1] = static_cast<int>(acc);
+    }
+    if (!plan->m_prefix && cudaMalloc(&plan->m_prefix, sizeof(int) * (B + 1)) != cudaSuccess) {
+        plan->m_prefix = nullptr;
+        delete[] host;
+        return TCBF_ERR_OOM;
+    }
+    const cudaError_t e =
+        cudaMemcpy(plan->m_prefix, host, sizeof(int) * (B + 1), cudaMemcpyHostToDevice);
+    delete[] host;
+    if (e != cudaSuccess) return TCBF_ERR_CUDA;
+    plan->m_tiles_sum = acc;
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const void *Xp, void *Y,
+                                      int reps, tcbf_stream_t stream, int *best,
+                                      float *ms_per_config) {
+    if (!plan || !Wp || !Xp || !Y || reps < 1) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_FP16 && plan->p.mode != TCBF_MODE_1BIT)
+        return TCBF_ERR_UNSUPPORTED;
+    if (!aligned16(Wp) || !aligned16(Xp) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int n = 0;
+    tcbf_plan_num_configs(plan, &n);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return TCBF_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return TCBF_ERR_CUDA;
+    }
+    const int saved = plan->config;
+    int best_c = -1;
+    float best_ms = 0.f;
+    tcbf_status st = TCBF_OK;
+    for (int c = 0; c < n && st == TCBF_OK; ++c) {
+        if (ms_per_config) ms_per_config[c] = -1.f;
+        if (!config_ok(*plan, c)) continue;
+        plan->config = c;
+        cudaError_t e = launch_beamform(*plan, Wp, Xp, Y, s);        // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_beamform(*plan, Wp, Xp, Y, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            st = from_cuda(e);
+            break;
+        }
+        ms /= reps;
+        if (ms_per_config) ms_per_config[c] = ms;
+        if (best_c < 0 || ms < best_ms) {
+            best_c = c;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan->config = (st == TCBF_OK && best_c >= 0) ? best_c : saved;
+    if (best) *best = plan->config;
+    return st;
+}
+
+TCBF_EXPORT tcbf_status tcbf_graph_capture(tcbf_plan_t plan, const void *X_src, int src_type,
+                                           void *Xp, const void *Wp, void *Y) {
+    if (!plan || !Xp || !Wp || !Y) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_FP16 && plan->p.mode != TCBF_MODE_1BIT)
+        return TCBF_ERR_UNSUPPORTED;
+    if (X_src && src_type != TCBF_SRC_CF16 && src_type != TCBF_SRC_CF32) return TCBF_ERR_INVALID_ARG;
+    if ((X_src && !aligned16(X_src)) || !aligned16(Xp) || !aligned16(Wp) || !aligned16(Y))
+        return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    if (plan->graph_exec) {
+        cudaGraphExecDestroy(plan->graph_exec);
+        plan->graph_exec = nullptr;
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return TCBF_ERR_CUDA;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaError_t le = cudaSuccess;
+    if (e == cudaSuccess) {
+        if (X_src) le = launch_pack_x(*plan, src_type, X_src, Xp, cs);
+        if (le == cudaSuccess) le = launch_beamform(*plan, Wp, Xp, Y, cs);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess && le == cudaSuccess)
+            e = cudaGraphInstantiate(&plan->graph_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    cudaStreamDestroy(cs);
+    if (le != cudaSuccess) e = le;
+    if (e != cudaSuccess) {
+        plan->graph_exec = nullptr;
+        return from_cuda(e);
+    }
+    return TCBF_OK;
+}
+
+TCBF_EXPORT tcbf_status tcbf_graph_launch(tcbf_plan_t plan, tcbf_stream_t stream) {
+    if (!plan || !plan->graph_exec) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(cudaGraphLaunch(plan->graph_exec, static_cast<cudaStream_t>(stream)));
 }

@@ -22,6 +22,7 @@
 #include <cstring>
 
 #include "ptx.cuh"
+#include "tiles.cuh"
 #include "tcbf_internal.h"
 
 namespace tcbf {
@@ -44,7 +45,8 @@ struct Args1 {
     int tma_store;
     int M, N, K, Kw;
     int per_w;
-    int m_tiles, n_tiles, num_kb, total_tiles;
+    TileMap tiles;
+    int num_kb, total_tiles;
 };
 
 template <int BN, int STAGES>
@@ -61,10 +63,7 @@ struct Cfg1 {
 };
 
 __device__ __forceinline__ void decode_tile(int t, const Args1 &a, int &b, int &mt, int &nt) {
-    nt = t % a.n_tiles;
-    const int rest = t / a.n_tiles;
-    mt = rest % a.m_tiles;
-    b = rest / a.m_tiles;
+    tile_decode(a.tiles, t, b, mt, nt);
 }
 
 // 4 sign bits -> 4 E4M3 bytes: bit 1 -> 0x38 (+1.0), bit 0 -> 0xB8 (-1.0).
@@ -398,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int BN, int STAGES>
 cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb, int32_t *Y,
-                    cudaStream_t s) {
+                    cudaStream_t s, int raster) {
     using C = Cfg1<BN, STAGES>;
     const tcbf_problem &p = pl.p;
     CUtensorMap tmY;
@@ -426,10 +425,14 @@ cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *X
     a.K = static_cast<int>(p.K);
     a.Kw = static_cast<int>(pl.Kw);
     a.per_w = static_cast<int>(pl.per_w);
-    a.m_tiles = static_cast<int>(ceil_div(p.M, BM));
-    a.n_tiles = static_cast<int>(ceil_div(p.N, BN));
+    a.tiles.prefix = pl.m_prefix;
+    a.tiles.batch = static_cast<int>(p.batch);
+    a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, BM));
+    a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, BN));
+    a.tiles.raster = raster;
     a.num_kb = static_cast<int>(ceil_div(p.K, BKE));
-    const int64_t total = static_cast<int64_t>(a.m_tiles) * a.n_tiles * p.batch;
+    const int64_t total = (pl.m_prefix ? pl.m_tiles_sum : int64_t(a.tiles.m_tiles) * p.batch) *
+                          a.tiles.n_tiles;
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
     auto kern = cgemm_1bit_kernel<BN, STAGES>;
@@ -443,13 +446,16 @@ cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *X
 
 struct Config1 {
     const char *name;
+    int raster;
     cudaError_t (*fn)(const tcbf_plan_s &, const uint32_t *, const uint32_t *, int32_t *,
-                      cudaStream_t);
+                      cudaStream_t, int);
 };
 
 const Config1 kConfigs1[] = {
-    {"1bit->e4m3 BM128 BN256 BK128 stages2 tmem-single", launch1<256, 2>},
-    {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double", launch1<128, 3>},
+    {"1bit->e4m3 BM128 BN256 BK128 stages2 tmem-single n-fastest", 0, launch1<256, 2>},
+    {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double n-fastest", 0, launch1<128, 3>},
+    {"1bit->e4m3 BM128 BN256 BK128 stages2 tmem-single m-fastest", 1, launch1<256, 2>},
+    {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double m-fastest", 1, launch1<128, 3>},
 };
 
 }  // namespace
@@ -464,7 +470,7 @@ const char *gemm_1bit_config_name(int config) {
 cudaError_t launch_gemm_1bit(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,
                              int32_t *Y, cudaStream_t s) {
     const int c = (pl.config >= 0 && pl.config < gemm_1bit_num_configs()) ? pl.config : 0;
-    return kConfigs1[c].fn(pl, Wb, Xb, Y, s);
+    return kConfigs1[c].fn(pl, Wb, Xb, Y, s, kConfigs1[c].raster);
 }
 
 }  // namespace tcbf

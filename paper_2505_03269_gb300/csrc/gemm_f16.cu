@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "ptx.cuh"
+#include "tiles.cuh"
 #include "tcbf_internal.h"
 
 namespace tcbf {
@@ -46,7 +47,7 @@ struct GemmArgs {
     uint32_t *status;
     int M, N, K;
     int per_w;
-    int m_tiles, n_tiles;
+    TileMap tiles;
     int num_kb;
     int kc_blocks;             // stages per accumulation chunk (num_kb when not promoting)
     int chunks;                // accumulation chunks per tile
@@ -73,10 +74,7 @@ struct Cfg {
 };
 
 __device__ __forceinline__ void decode_tile(int t, const GemmArgs &a, int &b, int &mt, int &nt) {
-    nt = t % a.n_tiles;
-    const int rest = t / a.n_tiles;
-    mt = rest % a.m_tiles;
-    b = rest / a.m_tiles;
+    tile_decode(a.tiles, t, b, mt, nt);
 }
 
 template <int BN, int STAGES>
@@ -356,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int BN, int STAGES>
 cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
-                       cudaStream_t s) {
+                       cudaStream_t s, int raster) {
     using C = Cfg<BN, STAGES>;
     const tcbf_problem &p = pl.p;
     CUtensorMap tmW, tmX;
@@ -402,8 +400,11 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     a.N = static_cast<int>(p.N);
     a.K = static_cast<int>(p.K);
     a.per_w = static_cast<int>(pl.per_w);
-    a.m_tiles = static_cast<int>(ceil_div(p.M, BM));
-    a.n_tiles = static_cast<int>(ceil_div(p.N, BN));
+    a.tiles.prefix = pl.m_prefix;
+    a.tiles.batch = static_cast<int>(p.batch);
+    a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, BM));
+    a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, BN));
+    a.tiles.raster = raster;
     a.num_kb = static_cast<int>(ceil_div(p.K, BK));
     if (p.K > kPromoteK) {
         if (4 * BN > 512) return cudaErrorInvalidConfiguration;   // no TMEM room for the sum
@@ -412,7 +413,8 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
         a.kc_blocks = a.num_kb;
     }
     a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
-    const int64_t total = static_cast<int64_t>(a.m_tiles) * a.n_tiles * p.batch;
+    const int64_t total = (pl.m_prefix ? pl.m_tiles_sum : int64_t(a.tiles.m_tiles) * p.batch) *
+                          a.tiles.n_tiles;
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
     auto kern = cgemm_f16_kernel<BN, STAGES>;
@@ -427,13 +429,17 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
 struct ConfigEntry {
     const char *name;
     int bn;
-    cudaError_t (*fn)(const tcbf_plan_s &, const void *, const void *, float *, cudaStream_t);
+    int raster;
+    cudaError_t (*fn)(const tcbf_plan_s &, const void *, const void *, float *, cudaStream_t, int);
 };
 
 const ConfigEntry kConfigs[] = {
-    {"f16 BM128 BN128 BK64 stages3 tmem-double", 128, launch_cfg<128, 3>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single", 256, launch_cfg<256, 2>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double", 64, launch_cfg<64, 4>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4>},
 };
 
 }  // namespace
@@ -453,7 +459,7 @@ bool gemm_f16_config_valid(int config, int64_t K) {
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s) {
     const int c = (pl.config >= 0 && pl.config < gemm_f16_num_configs()) ? pl.config : 0;
-    return kConfigs[c].fn(pl, Wp, Xp, Y, s);
+    return kConfigs[c].fn(pl, Wp, Xp, Y, s, kConfigs[c].raster);
 }
 
 }  // namespace tcbf

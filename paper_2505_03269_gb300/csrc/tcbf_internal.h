@@ -19,6 +19,11 @@ struct tcbf_plan_s {
     int64_t Kw = 0;          // 1-bit row length in 32-bit words (multiple of 4)
     int config = 0;          // kernel configuration (tile shape) in use
     uint32_t *status = nullptr;   // device status word (256 bytes)
+    // uneven batches: per-batch row counts and the device m-tile prefix
+    int *m_prefix = nullptr;      // device [batch + 1], nullptr when all batches have M rows
+    int64_t m_tiles_sum = 0;
+    // captured step (tcbf_graph_capture)
+    cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace tcbf {
