@@ -432,28 +432,60 @@ def main():
     barrier()
     assert plan.last_device_error() == 0
 
-    # ---- timed region: K steps, events around each kernel on the launch stream
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    sampler = ClockSampler(local)
-    sampler.start()
-    barrier()
-    for i in range(args.steps):
-        ev[i][0].record(stream)
-        gw.pack()
-        ev[i][1].record(stream)
-        gw.gemm()
-        ev[i][2].record(stream)
-    barrier()
-    clocks = sampler.stop()
+    def timed(nsteps, sample_clocks=False):
+        """nsteps steps with events around each kernel on the launch stream."""
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nsteps)]
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+        barrier()
+        for i in range(nsteps):
+            ev[i][0].record(stream)
+            gw.pack()
+            ev[i][1].record(stream)
+            gw.gemm()
+            ev[i][2].record(stream)
+        barrier()
+        clk = sampler.stop() if sampler else None
+        total = ev[0][0].elapsed_time(ev[-1][2])
+        return (total, statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                statistics.mean(e[1].elapsed_time(e[2]) for e in ev), clk)
+
+    # ---- the fixed default configuration against the autotuned one
+    tuning = None
+    if args.config is None:
+        d_total, _, d_gemm, _ = timed(max(3, args.steps // 4))
+        default_name = plan.config_name(plan.get_config())
+        from paper_2505_03269_gb300 import tuner
+        entry = tuner.tune(plan, gw.Wp, gw.Xp, gw.Y, reps=3, store=False)
+        tuning = {"default": {"config": default_name, "gemm_ms": d_gemm},
+                  "tuned": {"config": entry["name"]}, "ms_per_config": entry["ms"]}
+        for _ in range(2):
+            gw.step()
+
+    # ---- timed region: K steps (tuned configuration), clocks sampled
+    total_ms, pack_ms, gemm_ms, clocks = timed(args.steps, sample_clocks=True)
     status = plan.last_device_error()
-    total_ms = ev[0][0].elapsed_time(ev[-1][2])
-    pack_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
-    gemm_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_per_step = float(t.item()) / args.steps
     value = world * ops_per_step(w) / (ms_per_step * 1e-3) / 1e12
+    if tuning is not None:
+        tuning["tuned"]["gemm_ms"] = gemm_ms
+        tuning["speedup_gemm"] = tuning["default"]["gemm_ms"] / gemm_ms
+
+    # ---- the same step replayed as one captured CUDA graph
+    plan.graph_capture(gw.Xd, gw.Xp, gw.Wp, gw.Y)
+    plan.graph_launch()
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        plan.graph_launch()
+    g1.record(stream)
+    barrier()
+    graph_ms = g0.elapsed_time(g1) / args.steps
 
     parity = gw.parity()
 
@@ -531,6 +563,10 @@ def main():
                     "pack_gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
                     "pack_frac_of_hbm": pack_bytes / (pack_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
         "clocks": clocks,
+        "autotune": tuning,
+        "graph_step": {"ms_per_step": graph_ms,
+                       "value": world * ops / (graph_ms * 1e-3) / 1e12,
+                       "how": "tcbf_graph_capture of pack + beamform, replayed K times"},
         "device_status": status,
         "parity_sampled": parity,
         "e2e": e2e,
