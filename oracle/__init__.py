@@ -196,3 +196,67 @@ def rel_frobenius(Y: np.ndarray, Yref: np.ndarray) -> float:
     """||Y - Yref||_F / ||Yref||_F over real and imaginary parts, FP64."""
     d = np.asarray(Y, np.complex128) - np.asarray(Yref, np.complex128)
     return float(np.sqrt(np.sum(np.abs(d) ** 2)) / np.sqrt(np.sum(np.abs(Yref) ** 2)))
+
+
+# ---------------------------------------------------------------- split FP8
+def e4m3_round(v: np.ndarray) -> np.ndarray:
+    """Round doubles to E4M3 (nearest, ties to even fraction, saturating at 448)."""
+    lib = _load()
+    f = lib.oracle_e4m3_round
+    f.restype = ctypes.c_double
+    f.argtypes = [ctypes.c_double]
+    flat = np.asarray(v, np.float64).ravel()
+    return np.array([f(float(x)) for x in flat]).reshape(np.shape(v))
+
+
+def split_exponent(amax: float) -> int:
+    lib = _load()
+    f = lib.oracle_split_exponent
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_double]
+    return int(f(float(amax)))
+
+
+def split_rows(V16: np.ndarray):
+    """V16 [R, K, 2] FP16 rows -> (hi, lo) [R, K, 2] doubles of the scaled
+    values and exps [R]: v = (hi + lo) 2^-e approximately."""
+    lib = _load()
+    f = lib.oracle_split_rows
+    f.restype = None
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    R, K, _ = V16.shape
+    src = np.ascontiguousarray(V16).view(np.uint16)
+    hi = np.empty((R, K, 2), np.float64)
+    lo = np.empty((R, K, 2), np.float64)
+    ex = np.empty(R, np.int32)
+    f(R, K, _ptr(src), _ptr(hi), _ptr(lo), _ptr(ex))
+    return hi, lo, ex
+
+
+def split_operands(W16: np.ndarray, X16: np.ndarray):
+    """Split W rows (per beam) and X columns (per sample) of FP16 operands.
+    Returns (Wh, Wl, eW) with W* [Bw, M, K, 2], eW [Bw, M], and
+    (Xh, Xl, eX) with X* [B, K, N, 2], eX [B, N]."""
+    Bw, M, K, _ = W16.shape
+    B, _, N, _ = X16.shape
+    Wh, Wl, eW = split_rows(W16.reshape(Bw * M, K, 2))
+    XT = np.ascontiguousarray(X16.transpose(0, 2, 1, 3)).reshape(B * N, K, 2)
+    Xh, Xl, eX = split_rows(XT)
+    def back(A):
+        return np.ascontiguousarray(A.reshape(B, N, K, 2).transpose(0, 2, 1, 3))
+    return ((Wh.reshape(Bw, M, K, 2), Wl.reshape(Bw, M, K, 2), eW.reshape(Bw, M)),
+            (back(Xh), back(Xl), eX.reshape(B, N)))
+
+
+def cgemm_split(W16: np.ndarray, X16: np.ndarray, products: int = 3) -> np.ndarray:
+    """Split-FP8 beamforming in FP64: Y = 2^-(eW+eX) (Wh Xh + Wh Xl + Wl Xh)
+    (products=3) or with Wl Xl added (products=4); complex128 [B, M, N]."""
+    (Wh, Wl, eW), (Xh, Xl, eX) = split_operands(W16, X16)
+    Y = cgemm(Wh, Xh) + cgemm(Wh, Xl) + cgemm(Wl, Xh)
+    if products == 4:
+        Y = Y + cgemm(Wl, Xl)
+    B = X16.shape[0]
+    per_w = B // W16.shape[0]
+    scale_w = np.repeat(eW, per_w, axis=0)                     # [B, M]
+    return Y * np.ldexp(1.0, -(scale_w[:, :, None] + eX[:, None, :]))

@@ -228,3 +228,65 @@ EXPORT void oracle_weights(int64_t Bw, int64_t M, int64_t K, const double *rx, c
                 out[((b * M + m) * K + k) * 2 + 1] = -amp * sin(phase);
             }
 }
+
+/* ------------------------------------------------------------------------
+ * Split-FP8 (the paper names 8-bit float formats as future work, Sec. VI).
+ * E4M3: 1 sign bit, 4 exponent bits (bias 7), 3 fraction bits; normal values
+ * (1 + f/8) 2^(E-7) for E = 1..15 (largest finite 448 = 1.75 * 2^8, the code
+ * with E = 15 and f = 7 being NaN), subnormals (f/8) 2^-6.  Rounding is to
+ * the nearest representable value, ties to an even fraction; magnitudes
+ * beyond 448 saturate to 448.
+ * ---------------------------------------------------------------------- */
+EXPORT double oracle_e4m3_round(double v)
+{
+    if (v != v) return v;
+    const double a = fabs(v);
+    if (a >= 448.0) return v < 0 ? -448.0 : 448.0;
+    if (a == 0.0) return v;
+    int q;
+    frexp(a, &q);                      /* a = m 2^q, m in [0.5, 1): a in [2^(q-1), 2^q) */
+    int e = q - 1;                     /* a in [2^e, 2^(e+1)) */
+    if (e < -6) e = -6;                /* subnormal range shares the spacing of 2^-6 */
+    const double ulp = ldexp(1.0, e - 3);
+    const double n = a / ulp;          /* exact: a power-of-two scaling */
+    double r = floor(n);
+    const double frac = n - r;
+    if (frac > 0.5 || (frac == 0.5 && fmod(r, 2.0) != 0.0)) r += 1.0;
+    double out = r * ulp;
+    if (out > 448.0) out = 448.0;
+    return v < 0 ? -out : out;
+}
+
+/* The largest integer e with amax * 2^e <= 448 (0 for amax == 0). */
+EXPORT int oracle_split_exponent(double amax)
+{
+    if (!(amax > 0.0)) return 0;
+    int e = (int)floor(log2(448.0 / amax));
+    while (ldexp(amax, e) > 448.0) --e;
+    while (ldexp(amax, e + 1) <= 448.0) ++e;
+    return e;
+}
+
+/* Split rows of interleaved complex FP16 values into E4M3 hi and lo parts:
+ * per row (over k < K and both planes) the scale exponent e, then
+ * hi = RN(v 2^e), lo = RN(v 2^e - hi).  rows: [R][K] complex;
+ * hi, lo: [R][K][2] doubles (scaled values); exps: [R]. */
+EXPORT void oracle_split_rows(int64_t R, int64_t K, const uint16_t *src, double *hi, double *lo,
+                              int32_t *exps)
+{
+    for (int64_t r = 0; r < R; ++r) {
+        double amax = 0.0;
+        for (int64_t i = 0; i < 2 * K; ++i) {
+            const double a = fabs(oracle_half_to_double(src[r * 2 * K + i]));
+            if (a > amax) amax = a;
+        }
+        const int e = oracle_split_exponent(amax);
+        exps[r] = e;
+        for (int64_t i = 0; i < 2 * K; ++i) {
+            const double v = ldexp(oracle_half_to_double(src[r * 2 * K + i]), e);
+            const double h = oracle_e4m3_round(v);
+            hi[r * 2 * K + i] = h;
+            lo[r * 2 * K + i] = oracle_e4m3_round(v - h);
+        }
+    }
+}

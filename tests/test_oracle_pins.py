@@ -311,3 +311,64 @@ def test_pack_signs_definition():
     # transposed packing equals packing of the explicit transpose
     T = oracle.pack_signs(np.ascontiguousarray(V.transpose(0, 2, 1, 3)), k_is_row=True, Kw=Kw)
     assert np.array_equal(T, P)
+
+
+# ----------------------------------------------------------- split FP8 oracle
+def test_e4m3_rounding_matches_library_cast():
+    """Against torch's float8_e4m3fn conversion (round to nearest even) on a
+    dense set of values inside the finite range, including every E4M3 value
+    and every midpoint between neighbours."""
+    torch = pytest.importorskip("torch")
+    codes = torch.arange(256, dtype=torch.int32).to(torch.uint8).view(torch.float8_e4m3fn)
+    vals = codes.to(torch.float64).numpy()
+    vals = np.unique(vals[np.isfinite(vals)])
+    mids = (vals[1:] + vals[:-1]) / 2
+    g = np.random.default_rng(0)
+    rnd = g.uniform(-448, 448, 20000) * np.exp(g.uniform(-12, 0, 20000))
+    x = np.concatenate([vals, mids, mids + 1e-9, mids - 1e-9, rnd])
+    x = x[np.abs(x) <= 448]
+    ref = torch.from_numpy(x).to(torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    # the float32 step may move values within 1e-9 of a midpoint; keep exact ones
+    exact = torch.from_numpy(x).to(torch.float32).to(torch.float64).numpy() == x
+    assert np.array_equal(oracle.e4m3_round(x[exact]), ref[exact])
+    assert oracle.e4m3_round(np.array([449.0, -1e6]))[0] == 448.0
+
+
+def test_split_exponent_definition():
+    for amax in [1e-7, 0.001, 0.99, 1.0, 3.5, 447.9, 448.0, 448.1, 65504.0]:
+        e = oracle.split_exponent(amax)
+        assert amax * 2.0 ** e <= 448.0 < amax * 2.0 ** (e + 1)
+    assert oracle.split_exponent(0.0) == 0
+
+
+def test_split_is_exact_for_short_significands():
+    """Values with at most 8 significant bits (after scaling) are hi + lo exactly."""
+    g = np.random.default_rng(1)
+    mant = g.integers(128, 256, (3, 40, 2)) * g.choice([-1, 1], (3, 40, 2))
+    V = (mant * np.ldexp(1.0, g.integers(-12, -2, (3, 40, 2)))).astype(np.float16)
+    hi, lo, e = oracle.split_rows(V)
+    back = (hi + lo) * np.ldexp(1.0, -e)[:, None, None]
+    assert np.array_equal(back, V.astype(np.float64))
+
+
+def test_split_four_products_equal_product_of_reconstructions():
+    """(Wh + Wl)(Xh + Xl) = WhXh + WhXl + WlXh + WlXl, scaled back."""
+    W, X = ti.small_fp16(seed=31, M=7, K=33, N=9, B=2)
+    (Wh, Wl, eW), (Xh, Xl, eX) = oracle.split_operands(W, X)
+    Wr = (Wh + Wl) * np.ldexp(1.0, -eW)[..., None, None]
+    Xr = (Xh + Xl) * np.ldexp(1.0, -eX)[:, None, :, None]
+    ref = oracle.cgemm(Wr, Xr)
+    Y4 = oracle.cgemm_split(W, X, products=4)
+    assert np.allclose(Y4, ref, rtol=1e-13, atol=1e-13)
+    # the three-product form differs from it by exactly the dropped Wl Xl term
+    Y3 = oracle.cgemm_split(W, X, products=3)
+    drop = oracle.cgemm(Wl, Xl) * np.ldexp(1.0, -(eW[:, :, None] + eX[:, None, :]))
+    assert np.allclose(Y3 + drop, Y4, rtol=1e-13, atol=1e-13)
+
+
+def test_split_error_level_on_gaussian_data():
+    """Characterises the method's accuracy (no paper value exists): the
+    three-product hi+lo split of FP16 data lands near 1e-3 relative."""
+    W, X = ti.small_fp16(seed=32, M=32, K=256, N=64)
+    err = oracle.rel_frobenius(oracle.cgemm_split(W, X), oracle.cgemm(W, X))
+    assert 1e-4 < err < 5e-3
