@@ -84,10 +84,15 @@ typedef struct {
  * Plane 0 is the real part, plane 1 the imaginary part.  1-bit element k
  * of a row is bit (k % 32) of word (k / 32); bit 1 is +1, bit 0 is -1
  * (Fig. 1).  Bits at k >= K are ignored by the GEMM.
- *   FP8-split W/X: per row r and plane p, the element v is represented as
- *   (hi + lo) * 2^-e[r] with hi, lo e4m3: layout [rows-batches][2 planes]
- *   [2 (hi, lo)][rows][Kp] bytes followed by int8 exponents e per (batch,
- *   plane, row); see tcbf_packed_size.
+ *   FP8-split W: [w_batches][2][M][Kb2] bytes, X: [batch][2][N][Kb2] bytes,
+ *   Kb2 = 2 * (K rounded up to 64): each row holds K in blocks of 64
+ *   elements, 64 E4M3 "hi" bytes followed by 64 E4M3 "lo" bytes.  After the
+ *   bytes come int32 scale exponents, one per row ([w_batches][M] or
+ *   [batch][N], shared by both planes): e is the largest integer with
+ *   amax * 2^e <= 448 (amax over the row's K elements of both planes, after
+ *   rounding to FP16), hi = RN_e4m3(v 2^e), lo = RN_e4m3(v 2^e - hi), both
+ *   saturating, so v ~ (hi + lo) 2^-e.  tcbf_packed_size includes the
+ *   exponents.
  */
 
 /* Create a plan for problem *p on CUDA device `device`.  Validates the
@@ -228,7 +233,7 @@ tcbf_status tcbf_plan_set_batch_rows(tcbf_plan_t plan, const int64_t *rows);
  * and leaves it set on the plan.  Synchronises the stream.  *best receives
  * the chosen configuration; ms_per_config (nullable, tcbf_plan_num_configs
  * entries) the mean milliseconds per launch, -1 for configurations not
- * valid for this shape.  Y is overwritten.  Modes FP16 and 1-bit.
+ * valid for this shape.  Y is overwritten.  All modes.
  */
 tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const void *Xp, void *Y, int reps,
                           tcbf_stream_t stream, int *best, float *ms_per_config);
@@ -237,9 +242,9 @@ tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const void *Xp, void
  * Capture one step into a CUDA graph owned by the plan: the transpose/pack
  * of X_src into Xp (skipped when X_src is NULL) followed by the beamform of
  * Wp and Xp into Y, with the plan's current configuration.  Pointers are
- * baked into the graph; replace the graph by capturing again.  Modes FP16
- * and 1-bit.  tcbf_graph_launch replays it on `stream` (one launch of the
- * whole step; TCBF_ERR_INVALID_ARG if nothing was captured).
+ * baked into the graph; replace the graph by capturing again.  All modes.
+ * tcbf_graph_launch replays it on `stream` (one launch of the whole step;
+ * TCBF_ERR_INVALID_ARG if nothing was captured).
  */
 tcbf_status tcbf_graph_capture(tcbf_plan_t plan, const void *X_src, int src_type, void *Xp,
                                const void *Wp, void *Y);

@@ -70,6 +70,8 @@ size_t packed_bytes(const tcbf_plan_s &pl, int which) {
             return static_cast<size_t>(nb * 2 * rows * pl.Kp * 2);
         case TCBF_MODE_1BIT:
             return static_cast<size_t>(nb * 2 * rows * pl.Kw * 4);
+        case TCBF_MODE_FP8SPLIT:   // hi/lo bytes, then one int32 scale exponent per row
+            return static_cast<size_t>(nb * 2 * rows * pl.Kb2 + nb * rows * 4);
         default:
             return 0;
     }
@@ -120,7 +122,6 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     if (q.flags != 0) return TCBF_ERR_INVALID_ARG;
     if (q.M > kMaxDim || q.N > kMaxDim || q.K > kMaxDim || q.batch > 65535)
         return TCBF_ERR_UNSUPPORTED;
-    if (q.mode == TCBF_MODE_FP8SPLIT) return TCBF_ERR_UNSUPPORTED;
     // 1-bit sums are exact integers in the FP32 accumulators while 2K < 2^24
     if (q.mode == TCBF_MODE_1BIT && q.K > (int64_t(1) << 22)) return TCBF_ERR_UNSUPPORTED;
 
@@ -139,6 +140,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     pl->per_w = q.batch / q.w_batches;
     pl->Kp = round_up(q.K, 8);
     pl->Kw = round_up(q.K, 128) / 32;
+    pl->Kb2 = 2 * round_up(q.K, 64);
     pl->config = 0;
     {
         DeviceGuard g(device);
@@ -202,6 +204,10 @@ TCBF_EXPORT tcbf_status tcbf_transpose_pack(tcbf_plan_t plan, int which, int src
             e = which == 0 ? launch_pack_bits_w(*plan, src_type, src, dst, s)
                            : launch_pack_bits_x(*plan, src_type, src, dst, s);
             break;
+        case TCBF_MODE_FP8SPLIT:
+            e = which == 0 ? launch_pack_split8_w(*plan, src_type, src, dst, s)
+                           : launch_pack_split8_x(*plan, src_type, src, dst, s);
+            break;
         default:
             return TCBF_ERR_UNSUPPORTED;
     }
@@ -222,8 +228,10 @@ TCBF_EXPORT tcbf_status tcbf_beamform_fp8split(tcbf_plan_t plan, const void *Wp,
                                                float *Y, tcbf_stream_t stream) {
     if (!plan || !Wp || !Xp || !Y) return TCBF_ERR_INVALID_ARG;
     if (plan->p.mode != TCBF_MODE_FP8SPLIT) return TCBF_ERR_INVALID_ARG;
-    (void)stream;
-    return TCBF_ERR_UNSUPPORTED;
+    if (!aligned16(Wp) || !aligned16(Xp) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(launch_gemm_split8(*plan, Wp, Xp, Y, static_cast<cudaStream_t>(stream)));
 }
 
 TCBF_EXPORT tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbits,
@@ -268,9 +276,7 @@ TCBF_EXPORT tcbf_status tcbf_last_device_error(tcbf_plan_t plan) {
 
 TCBF_EXPORT tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count) {
     if (!plan || !count) return TCBF_ERR_INVALID_ARG;
-    *count = plan->p.mode == TCBF_MODE_FP16   ? gemm_f16_num_configs()
-             : plan->p.mode == TCBF_MODE_1BIT ? gemm_1bit_num_configs()
-                                              : 1;
+    *count = plan->p.mode == TCBF_MODE_1BIT ? gemm_1bit_num_configs() : gemm_f16_num_configs();
     return TCBF_OK;
 }
 
@@ -285,7 +291,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
     int n = 0;
     tcbf_plan_num_configs(plan, &n);
     if (config < 0 || config >= n) return TCBF_ERR_INVALID_ARG;
-    if (plan->p.mode == TCBF_MODE_FP16 && !gemm_f16_config_valid(config, plan->p.K))
+    if (plan->p.mode != TCBF_MODE_1BIT && !gemm_f16_config_valid(config, plan->p.K))
         return TCBF_ERR_INVALID_ARG;
     plan->config = config;   // a captured graph keeps the configuration it was captured with
     return TCBF_OK;
@@ -295,7 +301,7 @@ TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
     if (!plan) return "invalid";
     if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
     if (plan->p.mode == TCBF_MODE_1BIT) return gemm_1bit_config_name(config);
-    return config == 0 ? "default" : "invalid";
+    return gemm_split8_config_name(config);
 }
 
 // ---------------------------------------------------------------------------
@@ -310,20 +316,19 @@ cudaError_t launch_beamform(const tcbf_plan_s &pl, const void *Wp, const void *X
     if (pl.p.mode == TCBF_MODE_1BIT)
         return launch_gemm_1bit(pl, static_cast<const uint32_t *>(Wp),
                                 static_cast<const uint32_t *>(Xp), static_cast<int32_t *>(Y), s);
-    return cudaErrorNotSupported;
+    return launch_gemm_split8(pl, Wp, Xp, static_cast<float *>(Y), s);
 }
 
 cudaError_t launch_pack_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
                           cudaStream_t s) {
     if (pl.p.mode == TCBF_MODE_FP16) return launch_pack_f16_x(pl, src_type, src, dst, s);
     if (pl.p.mode == TCBF_MODE_1BIT) return launch_pack_bits_x(pl, src_type, src, dst, s);
-    return cudaErrorNotSupported;
+    return launch_pack_split8_x(pl, src_type, src, dst, s);
 }
 
 bool config_ok(const tcbf_plan_s &pl, int c) {
-    if (pl.p.mode == TCBF_MODE_FP16) return gemm_f16_config_valid(c, pl.p.K);
     if (pl.p.mode == TCBF_MODE_1BIT) return c >= 0 && c < gemm_1bit_num_configs();
-    return c == 0;
+    return gemm_f16_config_valid(c, pl.p.K);
 }
 
 }  // namespace
@@ -372,8 +377,6 @@ TCBF_EXPORT tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const vo
                                       int reps, tcbf_stream_t stream, int *best,
                                       float *ms_per_config) {
     if (!plan || !Wp || !Xp || !Y || reps < 1) return TCBF_ERR_INVALID_ARG;
-    if (plan->p.mode != TCBF_MODE_FP16 && plan->p.mode != TCBF_MODE_1BIT)
-        return TCBF_ERR_UNSUPPORTED;
     if (!aligned16(Wp) || !aligned16(Xp) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     if (!g.ok()) return TCBF_ERR_CUDA;
@@ -422,8 +425,6 @@ TCBF_EXPORT tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const vo
 TCBF_EXPORT tcbf_status tcbf_graph_capture(tcbf_plan_t plan, const void *X_src, int src_type,
                                            void *Xp, const void *Wp, void *Y) {
     if (!plan || !Xp || !Wp || !Y) return TCBF_ERR_INVALID_ARG;
-    if (plan->p.mode != TCBF_MODE_FP16 && plan->p.mode != TCBF_MODE_1BIT)
-        return TCBF_ERR_UNSUPPORTED;
     if (X_src && src_type != TCBF_SRC_CF16 && src_type != TCBF_SRC_CF32) return TCBF_ERR_INVALID_ARG;
     if ((X_src && !aligned16(X_src)) || !aligned16(Xp) || !aligned16(Wp) || !aligned16(Y))
         return TCBF_ERR_INVALID_ARG;

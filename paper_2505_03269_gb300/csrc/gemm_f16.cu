@@ -6,6 +6,13 @@
 // The paper negates Im in registers (its step 3); here the MMA instruction
 // descriptor's negate-A bit does it, so no operand is modified.
 //
+// Split-FP8 (8-bit float formats are the paper's future work, Sec. VI): the
+// same kernel with SPLIT = true reads packed rows of 64-element K blocks of
+// 64 E4M3 "hi" bytes then 64 "lo" bytes (the same 128-byte swizzled rows and
+// TMA boxes as FP16), issues Wh Xh + Wh Xl + Wl Xh as 12 kind::f8f6f4 MMAs
+// per 32-element K step, and rescales each output by 2^-(eW[m] + eX[n]),
+// the per-row power-of-two scales of the split.
+//
 // Persistent, warp-specialised kernel (one CTA per SM, 192 threads):
 //   warp 0      TMA producer: both planes of a W tile (128 x 64) and of an
 //               X tile (BN x 64) per stage into a STAGES-deep shared-memory
@@ -43,6 +50,8 @@ constexpr int kChunkBlocks = 32;    // stages (x 64 K) per promoted chunk
 
 struct GemmArgs {
     float *Y;
+    const int32_t *w_exps;     // split-FP8 scale exponents [w_batches][M] (else unused)
+    const int32_t *x_exps;     // split-FP8 scale exponents [batch][N]
     int tma_store;             // 1: Y written by TMA bulk tensor stores (needs N even)
     uint32_t *status;
     int M, N, K;
@@ -73,13 +82,16 @@ struct Cfg {
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
+// 2^-e as a float (|e| <= 100, so the result is a normal power of two).
+__device__ __forceinline__ float pow2_neg(int e) { return __int_as_float((127 - e) << 23); }
+
 __device__ __forceinline__ void decode_tile(int t, const GemmArgs &a, int &b, int &mt, int &nt) {
     tile_decode(a.tiles, t, b, mt, nt);
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
-    cgemm_f16_kernel(const __grid_constant__ CUtensorMap tmW,
+    cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmW,
                      const __grid_constant__ CUtensorMap tmX,
                      const __grid_constant__ CUtensorMap tmY, const GemmArgs args) {
     using C = Cfg<BN, STAGES>;
@@ -147,8 +159,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t fb = full0 + 8 * stage;
                     const uint32_t dst = s0 + stage * C::STAGE_BYTES;
                     mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
-                    tma_load_3d(dst, &tmW, fb, kb * BK, mt * BM, 2 * bw);
-                    tma_load_3d(dst + C::A_BYTES, &tmX, fb, kb * BK, nt * BN, 2 * b);
+                    // x: 128 bytes per stage in both formats (64 FP16, or 64 hi + 64 lo bytes)
+                    const int x = kb * (SPLIT ? 128 : BK);
+                    tma_load_3d(dst, &tmW, fb, x, mt * BM, 2 * bw);
+                    tma_load_3d(dst + C::A_BYTES, &tmX, fb, x, nt * BN, 2 * b);
                     ++issued;
                     if (++stage == STAGES) {
                         stage = 0;
@@ -200,17 +214,39 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tc_fence_after();
                         const uint32_t a = s0 + stage * C::STAGE_BYTES;
                         const uint32_t bx = a + C::A_BYTES;
-                        const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
-                        for (int j = 0; j < ksteps; ++j) {
-                            const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
-                            const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
-                            const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
-                            const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
-                            const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
-                            mma_f16(d_re, ar, br, kIdesc, accum);
-                            mma_f16(d_re, ai, bi, kIdescNeg, 1u);
-                            mma_f16(d_im, ar, bi, kIdesc, accum);
-                            mma_f16(d_im, ai, br, kIdesc, 1u);
+                        if (!SPLIT) {
+                            const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
+                            for (int j = 0; j < ksteps; ++j) {
+                                const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
+                                const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
+                                const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
+                                const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
+                                const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
+                                mma_f16(d_re, ar, br, kIdesc, accum);
+                                mma_f16(d_re, ai, bi, kIdescNeg, 1u);
+                                mma_f16(d_im, ar, bi, kIdesc, accum);
+                                mma_f16(d_im, ai, br, kIdesc, 1u);
+                            }
+                        } else {
+                            // 32 E4M3 per step; (W part, X part) byte offsets:
+                            // (hi, hi), (hi, lo), (lo, hi)
+                            const int ksteps = min(2, (args.K - kb * 64 + 31) / 32);
+                            for (int j = 0; j < ksteps; ++j) {
+#pragma unroll
+                                for (int pr = 0; pr < 3; ++pr) {
+                                    const uint32_t wo = (pr == 2 ? 64u : 0u) + 32u * j;
+                                    const uint32_t xo = (pr == 1 ? 64u : 0u) + 32u * j;
+                                    const uint64_t ar = sdesc_kmajor_sw128(a + wo);
+                                    const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + wo);
+                                    const uint64_t br = sdesc_kmajor_sw128(bx + xo);
+                                    const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + xo);
+                                    const uint32_t accum = (kb > kb0 || j > 0 || pr > 0) ? 1u : 0u;
+                                    mma_f8f6f4(d_re, ar, br, kIdesc, accum);
+                                    mma_f8f6f4(d_re, ai, bi, kIdescNeg, 1u);
+                                    mma_f8f6f4(d_im, ar, bi, kIdesc, accum);
+                                    mma_f8f6f4(d_im, ai, br, kIdesc, 1u);
+                                }
+                            }
                         }
                         mma_commit(empty0 + 8 * stage);
                         if (++stage == STAGES) {
@@ -252,6 +288,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             decode_tile(t, args, b, mt, nt);
             const int m = mt * BM + row;
             float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
+            float row_scale = 1.f;
+            if (SPLIT && m < args.M)
+                row_scale = pow2_neg(__ldg(args.w_exps + static_cast<size_t>(b / args.per_w) * args.M + m));
             for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
                 const int acc = ev % nbuf;
                 const uint32_t aphase = (ev / nbuf) & 1;
@@ -297,6 +336,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     const int n0 = nt * BN + c * 16;
+                    if (SPLIT) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int n = min(n0 + i, args.N - 1);
+                            const float f = row_scale * pow2_neg(__ldg(args.x_exps + static_cast<size_t>(b) * args.N + n));
+                            re[i] *= f;
+                            im[i] *= f;
+                        }
+                    }
                     if (args.tma_store) {
                         if (n0 < args.N) {
                             const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
@@ -352,29 +400,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool SPLIT>
 cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                        cudaStream_t s, int raster) {
+    // row length in elements of the tensor map: FP16 elements or split-FP8 bytes
+    const int64_t row = SPLIT ? pl.Kb2 : pl.Kp;
+    const CUtensorMapDataType dt = SPLIT ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const int64_t esz = SPLIT ? 1 : 2;
     using C = Cfg<BN, STAGES>;
     const tcbf_problem &p = pl.p;
     CUtensorMap tmW, tmX;
     {
-        const uint64_t dims[3] = {static_cast<uint64_t>(pl.Kp), static_cast<uint64_t>(p.M),
+        const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.M),
                                   static_cast<uint64_t>(2 * p.w_batches)};
-        const uint64_t strides[2] = {static_cast<uint64_t>(pl.Kp * 2),
-                                     static_cast<uint64_t>(p.M * pl.Kp * 2)};
-        const uint32_t box[3] = {BK, BM, 2};
-        if (encode_tiled(&tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Wp), dims,
+        const uint64_t strides[2] = {static_cast<uint64_t>(row * esz),
+                                     static_cast<uint64_t>(p.M * row * esz)};
+        const uint32_t box[3] = {static_cast<uint32_t>(128 / esz), BM, 2};
+        if (encode_tiled(&tmW, dt, 3, const_cast<void *>(Wp), dims,
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
     {
-        const uint64_t dims[3] = {static_cast<uint64_t>(pl.Kp), static_cast<uint64_t>(p.N),
+        const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.N),
                                   static_cast<uint64_t>(2 * p.batch)};
-        const uint64_t strides[2] = {static_cast<uint64_t>(pl.Kp * 2),
-                                     static_cast<uint64_t>(p.N * pl.Kp * 2)};
-        const uint32_t box[3] = {BK, BN, 2};
-        if (encode_tiled(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Xp), dims,
+        const uint64_t strides[2] = {static_cast<uint64_t>(row * esz),
+                                     static_cast<uint64_t>(p.N * row * esz)};
+        const uint32_t box[3] = {static_cast<uint32_t>(128 / esz), BN, 2};
+        if (encode_tiled(&tmX, dt, 3, const_cast<void *>(Xp), dims,
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
@@ -394,6 +446,12 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     }
     GemmArgs a;
     a.Y = Y;
+    a.w_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) +
+                                                        p.w_batches * 2 * p.M * row)
+                     : nullptr;
+    a.x_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Xp) +
+                                                        p.batch * 2 * p.N * row)
+                     : nullptr;
     a.tma_store = tma_store;
     a.status = pl.status;
     a.M = static_cast<int>(p.M);
@@ -417,7 +475,7 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
                           a.tiles.n_tiles;
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
-    auto kern = cgemm_f16_kernel<BN, STAGES>;
+    auto kern = cgemm_tc_kernel<BN, STAGES, SPLIT>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -434,12 +492,22 @@ struct ConfigEntry {
 };
 
 const ConfigEntry kConfigs[] = {
-    {"f16 BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4>},
-    {"f16 BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, false>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, false>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, false>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, false>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, false>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, false>},
+};
+
+// split-FP8: the same tile shapes, index for index
+const ConfigEntry kConfigsSplit[] = {
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, true>},
+    {"fp8split BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, true>},
+    {"fp8split BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, true>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, true>},
+    {"fp8split BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, true>},
+    {"fp8split BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, true>},
 };
 
 }  // namespace
@@ -454,6 +522,17 @@ const char *gemm_f16_config_name(int config) {
 bool gemm_f16_config_valid(int config, int64_t K) {
     if (config < 0 || config >= gemm_f16_num_configs()) return false;
     return K <= kPromoteK || kConfigs[config].bn <= 128;
+}
+
+const char *gemm_split8_config_name(int config) {
+    if (config < 0 || config >= gemm_f16_num_configs()) return "invalid";
+    return kConfigsSplit[config].name;
+}
+
+cudaError_t launch_gemm_split8(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                               cudaStream_t s) {
+    const int c = (pl.config >= 0 && pl.config < gemm_f16_num_configs()) ? pl.config : 0;
+    return kConfigsSplit[c].fn(pl, Wp, Xp, Y, s, kConfigsSplit[c].raster);
 }
 
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,

@@ -255,3 +255,208 @@ cudaError_t launch_pack_bits_x(const tcbf_plan_s &pl, int src_type, const void *
 }
 
 }  // namespace tcbf
+
+// ===========================================================================
+// Split-FP8 packing.  Each packed row (one beam of W, one sample of X, one
+// plane) holds K in 64-element blocks of 64 E4M3 "hi" bytes then 64 E4M3
+// "lo" bytes; int32 scale exponents follow the data, one per row (shared by
+// both planes).  With e the largest integer such that amax * 2^e <= 448
+// (amax over the row's K elements and both planes), hi = RN(v 2^e) and
+// lo = RN(v 2^e - hi), both saturating.  FP32 sources are first rounded to
+// FP16, so every mode sees the same input values.
+// ===========================================================================
+#include <cuda_fp8.h>
+
+namespace tcbf {
+namespace {
+
+__device__ __forceinline__ int split_exponent(float amax) {
+    if (!(amax > 0.f)) return 0;
+    int q;
+    const float f = frexpf(amax, &q);          // amax = f 2^q, f in [0.5, 1)
+    int e = (f <= 0.875f) ? 9 - q : 8 - q;     // 448 = 0.875 * 2^9
+    return max(-100, min(100, e));
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+__device__ __forceinline__ uint8_t e4m3(float x) {
+    return static_cast<uint8_t>(__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3));
+}
+
+__device__ __forceinline__ float e4m3_to_float(uint8_t b) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw(b, __NV_E4M3)));
+}
+
+// hi and lo bytes of one value already scaled by 2^e
+__device__ __forceinline__ void split_value(float v, uint8_t &hi, uint8_t &lo) {
+    hi = e4m3(v);
+    lo = e4m3(v - e4m3_to_float(hi));
+}
+
+template <typename S>
+__device__ __forceinline__ float2 load_f16_value(const void *src, size_t i) {
+    __half re, im;
+    S::load_h(src, i, re, im);
+    return make_float2(__half2float(re), __half2float(im));
+}
+
+// W rows (no transpose): one warp per row.
+template <typename S>
+__global__ void split8_rows_kernel(const void *__restrict__ src, uint8_t *__restrict__ dst,
+                                   int32_t *__restrict__ exps, int64_t rows, int64_t M, int K,
+                                   int Kb2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < rows;
+         r += warps_total) {
+        float amax = 0.f;
+        for (int k = lane; k < K; k += 32) {
+            const float2 v = load_f16_value<S>(src, static_cast<size_t>(r) * K + k);
+            amax = fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        const int e = split_exponent(amax);
+        const float s = pow2f(e);
+        const int64_t bw = r / M, m = r % M;
+        uint8_t *row_re = dst + (static_cast<size_t>(bw * 2 + 0) * M + m) * Kb2;
+        uint8_t *row_im = dst + (static_cast<size_t>(bw * 2 + 1) * M + m) * Kb2;
+        for (int j = 0; j < Kb2 / 128; ++j) {
+            uint8_t h[2][2], l[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = 64 * j + 2 * lane + q;
+                float2 v = make_float2(0.f, 0.f);
+                if (k < K) v = load_f16_value<S>(src, static_cast<size_t>(r) * K + k);
+                split_value(v.x * s, h[0][q], l[0][q]);
+                split_value(v.y * s, h[1][q], l[1][q]);
+            }
+            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 2 * lane) = h[0][0] | (h[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 2 * lane) = h[1][0] | (h[1][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+        }
+        if (lane == 0) exps[r] = e;
+    }
+}
+
+// X columns: per (batch, sample) scale exponent over K, one thread each
+// (consecutive threads read consecutive samples of a row of X).
+template <typename S>
+__global__ void split8_amax_x_kernel(const void *__restrict__ src, int32_t *__restrict__ exps,
+                                     int64_t B, int K, int N) {
+    const int64_t total = B * N;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t b = i / N, n = i % N;
+        float amax = 0.f;
+        for (int k = 0; k < K; ++k) {
+            const float2 v = load_f16_value<S>(src, (static_cast<size_t>(b) * K + k) * N + n);
+            amax = fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        exps[i] = split_exponent(amax);
+    }
+}
+
+// X transpose + split: 64 (k) x 64 (n) tiles; each output row of a tile is
+// one K block: 64 hi bytes and 64 lo bytes per plane.
+template <typename S>
+__global__ void __launch_bounds__(256) split8_pack_x_kernel(const void *__restrict__ src,
+                                                           uint8_t *__restrict__ dst,
+                                                           const int32_t *__restrict__ exps,
+                                                           int K, int N, int Kb2, int k_tiles,
+                                                           int n_tiles) {
+    __shared__ __half sre[TT][TPITCH];
+    __shared__ __half sim[TT][TPITCH];
+    const int tid = threadIdx.x;
+    const int64_t b = blockIdx.y;
+    const int64_t tiles_per_b = int64_t(k_tiles) * n_tiles;
+    for (int64_t t = blockIdx.x; t < tiles_per_b; t += gridDim.x) {
+        const int kt = static_cast<int>(t / n_tiles);
+        const int nt = static_cast<int>(t % n_tiles);
+        const int k0 = kt * TT, n0 = nt * TT;
+        const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kk = ty + 16 * i;
+            const int k = k0 + kk;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int nn = tx * 4 + q;
+                const int n = n0 + nn;
+                __half re = __float2half_rn(0.f), im = __float2half_rn(0.f);
+                if (k < K && n < N) S::load_h(src, (static_cast<size_t>(b) * K + k) * N + n, re, im);
+                sre[nn][kk] = re;
+                sim[nn][kk] = im;
+            }
+        }
+        __syncthreads();
+        // thread -> (row nn, 16-byte chunk c of 8: 4 hi chunks then 4 lo chunks)
+        const int c = tid & 7;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int nn = (tid >> 3) + 32 * h;
+            const int n = n0 + nn;
+            if (n < N) {
+                const float s = pow2f(exps[b * N + n]);
+                const int kc = 16 * (c & 3);
+                const bool want_lo = c >= 4;
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    __align__(16) uint8_t out[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float v = __half2float(p == 0 ? sre[nn][kc + j] : sim[nn][kc + j]) * s;
+                        uint8_t hi, lo;
+                        split_value(v, hi, lo);
+                        out[j] = want_lo ? lo : hi;
+                    }
+                    uint8_t *row = dst + (static_cast<size_t>(b * 2 + p) * N + n) * Kb2 + kt * 128;
+                    *reinterpret_cast<uint4 *>(row + 16 * c) = *reinterpret_cast<const uint4 *>(out);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_split8_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                                 cudaStream_t s) {
+    const int64_t rows = pl.p.w_batches * pl.p.M;
+    const int Kb2 = static_cast<int>(pl.Kb2);
+    auto *d = static_cast<uint8_t *>(dst);
+    auto *ex = reinterpret_cast<int32_t *>(d + rows * 2 * Kb2);
+    const int grid = grid_for(rows * 32, 256, pl.num_sms);
+    if (src_type == TCBF_SRC_CF16)
+        split8_rows_kernel<CF16><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, int(pl.p.K), Kb2);
+    else
+        split8_rows_kernel<CF32><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, int(pl.p.K), Kb2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                                 cudaStream_t s) {
+    const int64_t B = pl.p.batch, N = pl.p.N;
+    const int Kb2 = static_cast<int>(pl.Kb2);
+    auto *d = static_cast<uint8_t *>(dst);
+    auto *ex = reinterpret_cast<int32_t *>(d + B * 2 * N * Kb2);
+    const int g1 = grid_for(B * N, 256, pl.num_sms);
+    const int k_tiles = Kb2 / 128;
+    const int n_tiles = static_cast<int>(ceil_div(N, TT));
+    const int64_t per_b = int64_t(k_tiles) * n_tiles;
+    const int bx = static_cast<int>(std::min<int64_t>(per_b, std::max<int64_t>(1, int64_t(pl.num_sms) * 8 / std::max<int64_t>(1, std::min<int64_t>(B, 8)))));
+    dim3 grid(bx, static_cast<unsigned>(B));
+    if (src_type == TCBF_SRC_CF16) {
+        split8_amax_x_kernel<CF16><<<g1, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N));
+        split8_pack_x_kernel<CF16><<<grid, 256, 0, s>>>(src, d, ex, int(pl.p.K), int(N), Kb2, k_tiles, n_tiles);
+    } else {
+        split8_amax_x_kernel<CF32><<<g1, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N));
+        split8_pack_x_kernel<CF32><<<grid, 256, 0, s>>>(src, d, ex, int(pl.p.K), int(N), Kb2, k_tiles, n_tiles);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tcbf

@@ -17,6 +17,7 @@ struct tcbf_plan_s {
     int64_t per_w = 1;       // batch / w_batches
     int64_t Kp = 0;          // K rounded up to 8 (FP16 / FP8 row length, elements)
     int64_t Kw = 0;          // 1-bit row length in 32-bit words (multiple of 4)
+    int64_t Kb2 = 0;         // split-FP8 row length in bytes: 2 * K rounded up to 64
     int config = 0;          // kernel configuration (tile shape) in use
     uint32_t *status = nullptr;   // device status word (256 bytes)
     // uneven batches: per-batch row counts and the device m-tile prefix
@@ -48,9 +49,17 @@ cudaError_t launch_pack_bits_w(const tcbf_plan_s &pl, int src_type, const void *
 cudaError_t launch_pack_bits_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
                                cudaStream_t s);
 
+cudaError_t launch_pack_split8_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                                 cudaStream_t s);
+cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                                 cudaStream_t s);
+cudaError_t launch_gemm_split8(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                               cudaStream_t s);
+
 int gemm_f16_num_configs();
 const char *gemm_f16_config_name(int config);
 bool gemm_f16_config_valid(int config, int64_t K);
+const char *gemm_split8_config_name(int config);   // split-FP8 uses the FP16 tile table
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s);
 

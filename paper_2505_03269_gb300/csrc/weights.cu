@@ -12,6 +12,7 @@
 //   FP16 mode : planes [Bw][2][M][Kp], one thread per 8 consecutive k
 //   1-bit mode: sign planes [Bw][2][M][Kw], one warp per 32 consecutive k
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -24,7 +25,6 @@ struct Geo {
     const double *rx;
     const double *tg;
     const double *freqs;
-    double inv_c;
     double c;
     int near_field;
     int64_t M;
@@ -107,6 +107,66 @@ __global__ void weights_bits_kernel(Geo g, uint32_t *__restrict__ dst, int64_t B
     }
 }
 
+// Split-FP8: one warp per (weight batch, beam) row; the weights are computed
+// twice, first for the row's largest magnitude (the scale exponent), then
+// for the hi/lo bytes, in the packed layout of the transpose/pack kernel.
+__device__ __forceinline__ void split_bytes(float v, uint8_t &hi, uint8_t &lo) {
+    hi = static_cast<uint8_t>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
+    const float h = __half2float(__half(__nv_cvt_fp8_to_halfraw(hi, __NV_E4M3)));
+    lo = static_cast<uint8_t>(__nv_cvt_float_to_fp8(v - h, __NV_SATFINITE, __NV_E4M3));
+}
+
+__global__ void weights_split8_kernel(Geo g, uint8_t *__restrict__ dst, int32_t *__restrict__ exps,
+                                      int64_t Bw, int Kb2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = Bw * g.M;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < rows;
+         r += warps_total) {
+        const int64_t m = r % g.M, bw = r / g.M;
+        float amax = 0.f;
+        for (int k = lane; k < g.K; k += 32) {
+            float wr, wi;
+            weight(g, bw, m, k, wr, wi);
+            // the FP16 value the other modes would see
+            wr = __half2float(__float2half_rn(wr));
+            wi = __half2float(__float2half_rn(wi));
+            amax = fmaxf(amax, fmaxf(fabsf(wr), fabsf(wi)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        int e = 0;
+        if (amax > 0.f) {
+            int q;
+            const float f = frexpf(amax, &q);
+            e = max(-100, min(100, (f <= 0.875f) ? 9 - q : 8 - q));
+        }
+        const float s = __int_as_float((127 + e) << 23);
+        uint8_t *row_re = dst + (static_cast<size_t>(bw * 2 + 0) * g.M + m) * Kb2;
+        uint8_t *row_im = dst + (static_cast<size_t>(bw * 2 + 1) * g.M + m) * Kb2;
+        for (int j = 0; j < Kb2 / 128; ++j) {
+            uint8_t h[2][2], l[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = 64 * j + 2 * lane + q;
+                float wr = 0.f, wi = 0.f;
+                if (k < g.K) {
+                    weight(g, bw, m, k, wr, wi);
+                    wr = __half2float(__float2half_rn(wr));
+                    wi = __half2float(__float2half_rn(wi));
+                }
+                split_bytes(wr * s, h[0][q], l[0][q]);
+                split_bytes(wi * s, h[1][q], l[1][q]);
+            }
+            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 2 * lane) = h[0][0] | (h[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 2 * lane) = h[1][0] | (h[1][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+        }
+        if (lane == 0) exps[r] = e;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double *tg,
@@ -117,7 +177,6 @@ cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double
     g.tg = tg;
     g.freqs = freqs;
     g.c = c;
-    g.inv_c = 1.0 / c;
     g.near_field = near_field;
     g.M = pl.p.M;
     g.K = static_cast<int>(pl.p.K);
@@ -131,7 +190,12 @@ cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(pl.num_sms) * 32)));
         weights_f16_kernel<<<grid, 256, 0, s>>>(g, static_cast<__half *>(Wp), Bw, int(pl.Kp));
     } else {
-        return cudaErrorNotSupported;
+        const int64_t rows = Bw * pl.p.M;
+        const int Kb2 = static_cast<int>(pl.Kb2);
+        auto *d = static_cast<uint8_t *>(Wp);
+        auto *ex = reinterpret_cast<int32_t *>(d + rows * 2 * Kb2);
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, int64_t(pl.num_sms) * 32)));
+        weights_split8_kernel<<<grid, 256, 0, s>>>(g, d, ex, Bw, Kb2);
     }
     return cudaGetLastError();
 }

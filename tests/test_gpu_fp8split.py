@@ -1,0 +1,116 @@
+"""Split-FP8 mode on the GPU.
+
+Two references: the oracle's own split arithmetic (E4M3 hi+lo with per-row
+power-of-two scales, Y = 2^-(eW+eX)(Wh Xh + Wh Xl + Wl Xh) in FP64), which
+the GPU must match within the FP32-accumulation tolerance of the 16-bit
+mode (2e-5), and the plain FP64 product of the FP16 inputs, whose distance
+is the method's accuracy (stated, not a parity bar: ~1e-3)."""
+import numpy as np
+import pytest
+
+import oracle
+import tcbf_inputs as ti
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import ensure_lib
+    return ensure_lib()
+
+
+def _plan(B, M, N, K, Bw=0):
+    from paper_2505_03269_gb300 import MODE_FP8SPLIT, Plan
+    return Plan(B, M, N, K, MODE_FP8SPLIT, w_batches=Bw)
+
+
+def _decode_split(raw, nb, rows, K):
+    """Packed split bytes -> (hi, lo) [nb, 2, rows, K] doubles and exps [nb, rows]."""
+    import torch
+    Kb2 = 2 * ((K + 63) // 64 * 64)
+    data = raw[: nb * 2 * rows * Kb2].reshape(nb, 2, rows, Kb2 // 128, 2, 64)
+    vals = torch.from_numpy(np.ascontiguousarray(data)).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    hi = vals[..., 0, :].reshape(nb, 2, rows, -1)[..., :K]
+    lo = vals[..., 1, :].reshape(nb, 2, rows, -1)[..., :K]
+    ex = raw[nb * 2 * rows * Kb2:].view(np.int32).reshape(nb, rows)
+    return hi, lo, ex
+
+
+def _run(W, X, config=None):
+    import torch
+    from gpu_util import dev
+    Bw, M, K, _ = W.shape
+    B, _, N, _ = X.shape
+    with _plan(B, M, N, K, Bw) as plan:
+        if config is not None:
+            plan.set_config(config)
+        Wp = torch.empty(plan.packed_size(0), dtype=torch.uint8, device="cuda")
+        Xp = torch.empty(plan.packed_size(1), dtype=torch.uint8, device="cuda")
+        Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
+        plan.transpose_pack(0, dev(W), Wp)
+        plan.transpose_pack(1, dev(X), Xp)
+        plan.beamform_fp8split(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        Yh = Y.cpu().numpy().astype(np.float64)
+        return Yh[..., 0] + 1j * Yh[..., 1], Wp.cpu().numpy(), Xp.cpu().numpy()
+
+
+@pytest.mark.parametrize("B,M,N,K", [(1, 3, 5, 7), (2, 70, 130, 100), (2, 128, 256, 288)])
+def test_split_pack_matches_oracle_exactly(B, M, N, K):
+    W, X = ti.small_fp16(seed=M + K, M=M, K=K, N=N, B=B)
+    X[0, 0, :3, 0] = np.array([0.0, -0.0, 6e-8], np.float16)
+    _, Wraw, Xraw = _run(W, X)
+    (Wh, Wl, eW), (Xh, Xl, eX) = oracle.split_operands(W, X)
+    hi, lo, ex = _decode_split(Wraw, B, M, K)
+    assert np.array_equal(ex, eW)
+    assert np.array_equal(hi, Wh.transpose(0, 3, 1, 2)) and np.array_equal(lo, Wl.transpose(0, 3, 1, 2))
+    hi, lo, ex = _decode_split(Xraw, B, N, K)
+    assert np.array_equal(ex, eX)
+    assert np.array_equal(hi, Xh.transpose(0, 3, 2, 1)) and np.array_equal(lo, Xl.transpose(0, 3, 2, 1))
+
+
+@pytest.mark.parametrize("config", [0, 1, 3])
+@pytest.mark.parametrize("B,Bw,M,N,K", [(1, 1, 64, 1024, 128), (4, 2, 130, 300, 200),
+                                        (1, 1, 5, 7, 3)])
+def test_split_gemm_matches_split_oracle(config, B, Bw, M, N, K):
+    W, _ = ti.small_fp16(seed=B * M + K, M=M, K=K, N=8, B=Bw)
+    X = ti.complex_gaussian_fp16(ti.rng(N + K), (B, K, N))
+    Y, _, _ = _run(W, X, config)
+    assert oracle.rel_frobenius(Y, oracle.cgemm_split(W, X)) <= TOL
+    err = oracle.rel_frobenius(Y, oracle.cgemm(W, X))
+    assert err < 5e-3          # the method's own accuracy (about 1e-3)
+
+
+def test_split_long_k_promoted():
+    W, _ = ti.small_fp16(seed=40, M=256, K=5000, N=8)
+    X = ti.complex_gaussian_fp16(ti.rng(41), (1, 5000, 128))
+    Y, _, _ = _run(W, X)
+    assert oracle.rel_frobenius(Y, oracle.cgemm_split(W, X)) <= TOL
+
+
+def test_split_weights_from_geometry():
+    """Split weights straight from geometry against the oracle's FP16 weights
+    split by the oracle (entries whose FP16 weight differs by an ulp may differ)."""
+    import torch
+    from gpu_util import dev
+    geom = ti.ultrasound_geometry(n_elements=32, n_bins=16, grid=(8, 8, 4))
+    M, K = geom.targets.shape[0], geom.rx_pos.shape[0]
+    with _plan(1, M, 8, K) as plan:
+        Wp = torch.empty(plan.packed_size(0), dtype=torch.uint8, device="cuda")
+        plan.weights_from_geometry(dev(geom.rx_pos), dev(geom.targets), True,
+                                   dev(np.ascontiguousarray(geom.freqs)), geom.c, Wp)
+        torch.cuda.synchronize()
+        raw = Wp.cpu().numpy()
+    hi, lo, ex = _decode_split(raw, 1, M, K)
+    W16 = oracle.weights_fp16(geom.rx_pos, geom.targets, geom.freqs, True, geom.c)
+    Wh, Wl, eW = oracle.split_rows(W16.reshape(M, K, 2))
+    assert np.mean(ex[0] == eW) >= 0.99
+    same = (hi[0].transpose(1, 2, 0) == Wh) & (lo[0].transpose(1, 2, 0) == Wl)
+    assert np.mean(same) >= 0.999
