@@ -584,7 +584,9 @@ def main():
                          % (gw.Xh.nbytes / 1e9, gw.Y.numel() * 4 / 1e9),
                    "kernel_config": plan.config_name(plan.get_config()),
                    "parallelism": f"{world} independent replica(s), no collective"},
-        "gpu_launches": 2 * args.steps,
+        # kernels per step: pack(X) + GEMM; split-FP8 packs X in three kernels
+        # (column maxima, pack, exponents) after a memset
+        "gpu_launches": (4 if w["mode"] == "fp8split" else 2) * args.steps,
         "roofline": roof,
         "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms, "weights_ms_once": gw.weights_ms,
                     "gemm_useful_tops": ops / (gemm_ms * 1e-3) / 1e12,

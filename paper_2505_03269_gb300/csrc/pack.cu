@@ -341,22 +341,35 @@ __global__ void split8_rows_kernel(const void *__restrict__ src, uint8_t *__rest
     }
 }
 
-// X columns: per (batch, sample) scale exponent over K, one thread each
-// (consecutive threads read consecutive samples of a row of X).
+// X columns: the largest magnitude per (batch, sample) over K, reduced in
+// parallel: each thread scans 256 rows of one sample (consecutive threads
+// read consecutive samples of a row of X) and folds its maximum into the
+// exponent slot with an integer atomic max (valid for non-negative floats),
+// which holds the float's bits until split8_exps_kernel converts it.
 template <typename S>
-__global__ void split8_amax_x_kernel(const void *__restrict__ src, int32_t *__restrict__ exps,
-                                     int64_t B, int K, int N) {
-    const int64_t total = B * N;
+__global__ void split8_amax_x_kernel(const void *__restrict__ src, int32_t *__restrict__ slot,
+                                     int64_t B, int K, int N, int k_chunks) {
+    const int64_t total = B * N * k_chunks;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
          i += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t b = i / N, n = i % N;
+        const int64_t n = i % N;
+        const int64_t rest = i / N;
+        const int kc = static_cast<int>(rest % k_chunks);
+        const int64_t b = rest / k_chunks;
         float amax = 0.f;
-        for (int k = 0; k < K; ++k) {
+        const int k1 = min(K, (kc + 1) * 256);
+        for (int k = kc * 256; k < k1; ++k) {
             const float2 v = load_f16_value<S>(src, (static_cast<size_t>(b) * K + k) * N + n);
             amax = fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
-        exps[i] = split_exponent(amax);
+        atomicMax(slot + b * N + n, __float_as_int(amax));
     }
+}
+
+__global__ void split8_exps_kernel(int32_t *__restrict__ slot, int64_t rows) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < rows;
+         i += int64_t(gridDim.x) * blockDim.x)
+        slot[i] = split_exponent(__int_as_float(slot[i]));
 }
 
 // X transpose + split: 64 (k) x 64 (n) tiles; each output row of a tile is
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(256) split8_pack_x_kernel(const void *__restri
             const int nn = (tid >> 3) + 32 * h;
             const int n = n0 + nn;
             if (n < N) {
-                const float s = pow2f(exps[b * N + n]);
+                const float s = pow2f(split_exponent(__int_as_float(exps[b * N + n])));
                 const int kc = 16 * (c & 3);
                 const bool want_lo = c >= 4;
 #pragma unroll
@@ -449,13 +462,18 @@ cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void
     const int64_t per_b = int64_t(k_tiles) * n_tiles;
     const int bx = static_cast<int>(std::min<int64_t>(per_b, std::max<int64_t>(1, int64_t(pl.num_sms) * 8 / std::max<int64_t>(1, std::min<int64_t>(B, 8)))));
     dim3 grid(bx, static_cast<unsigned>(B));
+    const int k_chunks = static_cast<int>(ceil_div(pl.p.K, 256));
+    const int g_amax = grid_for(B * N * k_chunks, 256, pl.num_sms);
+    cudaError_t e = cudaMemsetAsync(ex, 0, sizeof(int32_t) * B * N, s);
+    if (e != cudaSuccess) return e;
     if (src_type == TCBF_SRC_CF16) {
-        split8_amax_x_kernel<CF16><<<g1, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N));
+        split8_amax_x_kernel<CF16><<<g_amax, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N), k_chunks);
         split8_pack_x_kernel<CF16><<<grid, 256, 0, s>>>(src, d, ex, int(pl.p.K), int(N), Kb2, k_tiles, n_tiles);
     } else {
-        split8_amax_x_kernel<CF32><<<g1, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N));
+        split8_amax_x_kernel<CF32><<<g_amax, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N), k_chunks);
         split8_pack_x_kernel<CF32><<<grid, 256, 0, s>>>(src, d, ex, int(pl.p.K), int(N), Kb2, k_tiles, n_tiles);
     }
+    split8_exps_kernel<<<g1, 256, 0, s>>>(ex, B * N);
     return cudaGetLastError();
 }
 
