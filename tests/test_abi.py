@@ -19,19 +19,26 @@ def lib():
     return binding.load()
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "tcbf.h")).read()
+def declared_functions(header="tcbf.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(tcbf_[a-z0-9_]+)\s*\(", src)))
 
 
+def all_headers():
+    return sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+
+
 def test_header_and_binding_agree():
     assert declared_functions() == sorted(binding.EXPORTED)
+    from paper_2505_03269_gb300 import serve
+    assert declared_functions("tcbf_server.h") == sorted(serve.SERVER_SYMBOLS)
 
 
 def test_every_declared_symbol_is_exported(lib):
-    for name in declared_functions():
-        assert hasattr(lib, name), name
+    for h in all_headers():
+        for name in declared_functions(h):
+            assert hasattr(lib, name), (h, name)
 
 
 def test_status_strings(lib):
