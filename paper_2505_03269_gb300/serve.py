@@ -201,11 +201,12 @@ def summarize(arr, cnt=None):
     return out
 
 
-def measure(n_requests=600, load=0.8, arena_gb=120.0, num_streams=8, seed=1):
+def measure(n_requests=600, loads=(0.5, 0.8, 0.95, 1.5, 3.0), arena_gb=120.0, num_streams=8,
+            seed=1):
     """Capacity of the serial FP16 baseline (all requests at t = 0, one at a
-    time, one stream), then the same Poisson stream at `load` x that capacity
-    through the continuous-batching server (mixed modes) and through the
-    serial FP16 baseline."""
+    time, one stream), then the same request stream with Poisson arrivals at
+    each load (x that capacity) through the continuous-batching server (mixed
+    modes) and through the serial FP16 baseline."""
     import torch
     sets = make_weight_sets()
     reqs = make_stream(seed=seed, n_requests=n_requests)
@@ -217,26 +218,32 @@ def measure(n_requests=600, load=0.8, arena_gb=120.0, num_streams=8, seed=1):
         g.standard_normal((Kmax, Nmax, 2)).astype(np.float16)).pin_memory()
     host_y = torch.empty((Mmax, Nmax, 2), dtype=torch.float32, pin_memory=True)
     arena = int(arena_gb * 1e9)
-    base, bc = run_stream(reqs, sets, None, arena, 1, 1, MODE_FP16, host_x, host_y)
+    base, _ = run_stream(reqs, sets, None, arena, 1, 1, MODE_FP16, host_x, host_y)
     capacity = len(reqs) / (base[:, 2].max() - base[:, 0].min())
-    rate = load * capacity
-    cont, cc = run_stream(reqs, sets, rate, arena, num_streams, 0, None, host_x, host_y)
-    serial, sc = run_stream(reqs, sets, rate, arena, 1, 1, MODE_FP16, host_x, host_y)
-    return {
-        "stream": {"requests": n_requests, "weight_sets": len(sets), "load": load,
-                   "rate_per_s": rate, "baseline_capacity_per_s": capacity,
-                   "modes": "70% FP16 / 20% split-FP8 / 10% 1-bit", "arena_gb": arena_gb,
-                   "streams": num_streams, "host_y": "one shared pinned sink (results discarded)"},
-        "continuous_batching": summarize(cont, cc),
-        "serial_fp16_one_per_launch": summarize(serial, sc),
-    }
+    sat, sc = run_stream(reqs, sets, None, arena, num_streams, 0, None, host_x, host_y)
+    out = {"stream": {"requests": n_requests, "weight_sets": len(sets),
+                      "modes": "70% FP16 / 20% split-FP8 / 10% 1-bit", "arena_gb": arena_gb,
+                      "streams": num_streams, "baseline_capacity_per_s": capacity,
+                      "host_y": "one shared pinned sink (results discarded)"},
+           "all_at_once": {"continuous_batching": summarize(sat, sc),
+                           "serial_fp16_one_per_launch": summarize(base)},
+           "loads": []}
+    for load in loads:
+        rate = load * capacity
+        cont, cc = run_stream(reqs, sets, rate, arena, num_streams, 0, None, host_x, host_y)
+        serial, scc = run_stream(reqs, sets, rate, arena, 1, 1, MODE_FP16, host_x, host_y)
+        out["loads"].append({"load": load, "rate_per_s": rate,
+                             "continuous_batching": summarize(cont, cc),
+                             "serial_fp16_one_per_launch": summarize(serial, scc)})
+    return out
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--requests", type=int, default=600)
-    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--loads", type=str, default="0.5,0.8,0.95,1.5,3.0")
     ap.add_argument("--arena-gb", type=float, default=120.0)
     ap.add_argument("--streams", type=int, default=8)
     a = ap.parse_args()
-    print(json.dumps(measure(a.requests, a.load, a.arena_gb, a.streams)))
+    loads = tuple(float(x) for x in a.loads.split(","))
+    print(json.dumps(measure(a.requests, loads, a.arena_gb, a.streams)))
