@@ -89,7 +89,7 @@ __device__ __forceinline__ void decode_tile(int t, const GemmArgs &a, int &b, in
     tile_decode(a.tiles, t, b, mt, nt);
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmW,
                      const __grid_constant__ CUtensorMap tmX,
@@ -115,10 +115,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
+    // Clusters of CL CTAs along M share each X tile: every CTA loads a 1/CL
+    // row slice and multicasts it to all, and every CTA's MMA completion is
+    // committed to all CTAs' empty barriers (count CL).  The cluster walks
+    // cluster tiles (batch, group of CL m-tiles, n-tile) in lockstep.
+    const int rank = CL > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+    const int t_first = CL > 1 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+    const int t_step = CL > 1 ? static_cast<int>(nclusters_x()) : static_cast<int>(gridDim.x);
+    constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
+    auto decode = [&](int t, int &b, int &mt, int &nt) {
+        if (CL == 1) {
+            decode_tile(t, args, b, mt, nt);
+        } else {
+            const int groups = (args.tiles.m_tiles + CL - 1) / CL;
+            const int per_b = groups * args.tiles.n_tiles;
+            b = t / per_b;
+            const int local = t - b * per_b;
+            nt = local % args.tiles.n_tiles;
+            mt = (local / args.tiles.n_tiles) * CL + rank;
+        }
+    };
+
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, CL);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
@@ -137,6 +158,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync();            // peers' barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -147,9 +169,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t issued = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
+            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
                 int b, mt, nt;
-                decode_tile(t, args, b, mt, nt);
+                decode(t, b, mt, nt);
                 const int bw = b / args.per_w;
                 for (int kb = 0; kb < args.num_kb; ++kb) {
                     if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
@@ -162,7 +184,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // x: 128 bytes per stage in both formats (64 FP16, or 64 hi + 64 lo bytes)
                     const int x = kb * (SPLIT ? 128 : BK);
                     tma_load_3d(dst, &tmW, fb, x, mt * BM, 2 * bw);
-                    tma_load_3d(dst + C::A_BYTES, &tmX, fb, x, nt * BN, 2 * b);
+                    if (CL == 1) {
+                        tma_load_3d(dst + C::A_BYTES, &tmX, fb, x, nt * BN, 2 * b);
+                    } else {
+                        constexpr int kRows = BN / CL;
+#pragma unroll
+                        for (int pl = 0; pl < 2; ++pl)
+                            tma_load_3d_mc(dst + C::A_BYTES + pl * C::B_PLANE + rank * kRows * 128,
+                                           &tmX, fb, x, nt * BN + rank * kRows, 2 * b + pl, kMask);
+                    }
                     ++issued;
                     if (++stage == STAGES) {
                         stage = 0;
@@ -181,6 +211,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                             atomicOr(args.status, kErrTimeoutDrain);
                     }
                 }
+            } else if (CL > 1) {
+                // every CTA's release of every slot this CTA filled has arrived,
+                // so no peer still signals into this CTA's barriers
+                for (int s = 0; s < STAGES; ++s) {
+                    if (issued > static_cast<uint32_t>(s)) {
+                        const uint32_t count = (issued - s + STAGES - 1) / STAGES;
+                        if (!mbar_wait(empty0 + 8 * s, (count - 1) & 1u))
+                            atomicOr(args.status, kErrTimeoutDrain);
+                    }
+                }
             }
         }
     } else if (warp == 1) {
@@ -193,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int ev = 0;                                  // accumulator hand-offs so far
             const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
             bool ok = true;
-            for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
+            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
                 for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
                     const int acc = ev % nbuf;
                     const uint32_t aphase = (ev / nbuf) & 1;
@@ -248,7 +288,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 }
                             }
                         }
-                        mma_commit(empty0 + 8 * stage);
+                        if (CL == 1)
+                            mma_commit(empty0 + 8 * stage);
+                        else
+                            mma_commit_mc(empty0 + 8 * stage, kMask);
                         if (++stage == STAGES) {
                             stage = 0;
                             phase ^= 1u;
@@ -283,9 +326,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t tS = tmem_base + lane_off + 2 * BN;    // running sum (promotion only)
         int chunk_count = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
+        for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
             int b, mt, nt;
-            decode_tile(t, args, b, mt, nt);
+            decode(t, b, mt, nt);
             const int m = mt * BM + row;
             float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
             float row_scale = 1.f;
@@ -393,6 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync();            // no CTA leaves while peers may signal it
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -400,9 +444,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, bool SPLIT, int CL>
 cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                        cudaStream_t s, int raster) {
+    if (CL > 1 && pl.m_prefix)   // uneven batches walk per-batch m-tiles: no clusters
+        return launch_cfg<BN, STAGES, SPLIT, 1>(pl, Wp, Xp, Y, s, raster);
     // row length in elements of the tensor map: FP16 elements or split-FP8 bytes
     const int64_t row = SPLIT ? pl.Kb2 : pl.Kp;
     const CUtensorMapDataType dt = SPLIT ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -425,7 +471,9 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
                                   static_cast<uint64_t>(2 * p.batch)};
         const uint64_t strides[2] = {static_cast<uint64_t>(row * esz),
                                      static_cast<uint64_t>(p.N * row * esz)};
-        const uint32_t box[3] = {static_cast<uint32_t>(128 / esz), BN, 2};
+        // clusters: each CTA loads a BN/CL-row slice of one plane per multicast
+        const uint32_t box[3] = {static_cast<uint32_t>(128 / esz),
+                                 static_cast<uint32_t>(BN / CL), CL == 1 ? 2u : 1u};
         if (encode_tiled(&tmX, dt, 3, const_cast<void *>(Xp), dims,
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
@@ -471,16 +519,43 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
         a.kc_blocks = a.num_kb;
     }
     a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
-    const int64_t total = (pl.m_prefix ? pl.m_tiles_sum : int64_t(a.tiles.m_tiles) * p.batch) *
-                          a.tiles.n_tiles;
+    const int64_t m_units = CL == 1 ? (pl.m_prefix ? pl.m_tiles_sum : int64_t(a.tiles.m_tiles) * p.batch)
+                                    : ceil_div(a.tiles.m_tiles, CL) * p.batch;
+    const int64_t total = m_units * a.tiles.n_tiles;     // tiles, or cluster tiles
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
-    auto kern = cgemm_tc_kernel<BN, STAGES, SPLIT>;
+    auto kern = cgemm_tc_kernel<BN, STAGES, SPLIT, CL>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const int grid = static_cast<int>(std::min<int64_t>(total, pl.num_sms));
-    kern<<<grid, kThreads, C::SMEM_BYTES, s>>>(tmW, tmX, tmY, a);
+    if (CL == 1) {
+        const int grid = static_cast<int>(std::min<int64_t>(total, pl.num_sms));
+        kern<<<grid, kThreads, C::SMEM_BYTES, s>>>(tmW, tmX, tmY, a);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = C::SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // persistent grid: as many clusters as can be resident at once
+    static int max_clusters[64] = {};
+    int &mc = max_clusters[pl.device & 63];
+    if (mc == 0) {
+        cfg.gridDim = dim3(pl.num_sms / CL * CL);
+        e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (mc < 1) return cudaErrorInvalidConfiguration;
+    }
+    cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(total, mc)) * CL);
+    e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -492,22 +567,26 @@ struct ConfigEntry {
 };
 
 const ConfigEntry kConfigs[] = {
-    {"f16 BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, false>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, false>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, false>},
-    {"f16 BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, false>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, false>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, false>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, false, 1>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, false, 1>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, false, 1>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, false, 1>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, false, 1>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, false, 1>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, false, 2>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, false, 4>},
 };
 
 // split-FP8: the same tile shapes, index for index
 const ConfigEntry kConfigsSplit[] = {
-    {"fp8split BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, true>},
-    {"fp8split BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, true>},
-    {"fp8split BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, true>},
-    {"fp8split BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, true>},
-    {"fp8split BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, true>},
-    {"fp8split BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, true>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, true, 1>},
+    {"fp8split BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, true, 1>},
+    {"fp8split BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, true, 1>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, true, 1>},
+    {"fp8split BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, true, 1>},
+    {"fp8split BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, true, 1>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, true, 2>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, true, 4>},
 };
 
 }  // namespace
