@@ -22,7 +22,8 @@ extern "C" {
  *   0 tcgen05 kind::f16 M128 N256 K16, 1 tcgen05 kind::f8f6f4 (E4M3) M128 N256 K32,
  *   2 tcgen05 kind::i8 (not available on sm_103a: always TCBF_ERR_UNSUPPORTED),
  *   3 mma.sync m16n8k16 f16->f32,
- *   4 mma.sync m16n8k256 b1 AND-popc, 5 CUDA-core popc(xor) on 32-bit words.
+ *   4 mma.sync m16n8k256 b1 AND-popc, 5 CUDA-core popc(xor) on 32-bit words,
+ *   6 tcgen05 kind::f16 M128 N128 K16 (the beamformer's one-SM tile MMA).
  * iters: MMAs (or loop trips) per issuing thread.  On success *seconds is the
  * timed launch's duration and *ops the operations it performed (2 per
  * multiply-accumulate).  Allocates and frees a 256-byte status word.

@@ -444,6 +444,360 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ===========================================================================
+// Two-SM tiles (cta_group::2).  A cluster of two CTAs on two SMs computes a
+// 256 x BN tile with M = 256 MMAs issued by the even CTA: each CTA holds 128
+// rows of W (A) and BN/2 rows of X (half of B) at the same shared-memory
+// offsets, and its tensor memory holds its 128 rows x BN columns of Re and
+// Im.  Per SM the tensor core then reads A 128 x K and B BN/2 x K per MMA, a
+// quarter less shared-memory traffic than a one-SM 128 x BN tile, with the
+// same double-buffered accumulators.  Both CTAs' TMA loads complete on the
+// even CTA's full barrier; its MMA completions are committed to both CTAs'
+// empty and accumulator barriers; both CTAs' epilogues release an
+// accumulator on the even CTA's barrier.
+// ===========================================================================
+template <int BN, int STAGES>
+struct CfgPair {
+    static constexpr int A_PLANE = BM * BK * 2;
+    static constexpr int B_PLANE = (BN / 2) * BK * 2;
+    static constexpr int A_BYTES = 2 * A_PLANE;
+    static constexpr int STAGE_BYTES = A_BYTES + 2 * B_PLANE;     // per CTA
+    static constexpr int ACC_BUFS = (4 * BN <= 512) ? 2 : 1;
+    static constexpr int TMEM_COLS = pow2_cols(ACC_BUFS * 2 * BN);
+    static constexpr int STAGING_BYTES = 4 * 2 * 4096;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
+    static_assert(BN % 32 == 0 && BN <= 256, "pair N");
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
+
+template <int BN, int STAGES, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1)
+    cgemm_pair_kernel(const __grid_constant__ CUtensorMap tmW,
+                      const __grid_constant__ CUtensorMap tmX,
+                      const __grid_constant__ CUtensorMap tmY, const GemmArgs args) {
+    using C = CfgPair<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+    const uint32_t s0 = smem_u32(smem);
+    const uint32_t staging0 = s0 + STAGES * C::STAGE_BYTES;
+    const uint32_t bar0 = staging0 + C::STAGING_BYTES;
+    const uint32_t full0 = bar0;
+    const uint32_t empty0 = full0 + 8 * STAGES;
+    const uint32_t tfull0 = empty0 + 8 * STAGES;
+    const uint32_t tempty0 = tfull0 + 16;
+    const uint32_t done_bar = tempty0 + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + STAGES * C::STAGE_BYTES +
+                                                       C::STAGING_BYTES + 16 * STAGES + 40);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int rank = static_cast<int>(cluster_ctarank());
+    const bool leader = rank == 0;
+    const int t_first = static_cast<int>(cluster_id_x());
+    const int t_step = static_cast<int>(nclusters_x());
+    constexpr uint16_t kBoth = 3;
+    // (batch, 256-row pair tile, n-tile) of pair tile t, n fastest
+    auto decode = [&](int t, int &b, int &mp, int &nt) {
+        const int groups = (args.tiles.m_tiles + 1) / 2;
+        const int per_b = groups * args.tiles.n_tiles;
+        b = t / per_b;
+        const int local = t - b * per_b;
+        nt = local % args.tiles.n_tiles;
+        mp = local / args.tiles.n_tiles;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);          // used in the even CTA
+            mbar_init(empty0 + 8 * s, 1);         // the even CTA's commit, both CTAs
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 8);        // 4 epilogue warps x 2 CTAs (even CTA)
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmW);
+        tma_prefetch_desc(&tmX);
+        if (args.tma_store) tma_prefetch_desc(&tmY);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t full0_lead = mapa_shared(full0, 0);
+    const uint32_t tempty0_lead = mapa_shared(tempty0, 0);
+
+    if (warp == 0) {
+        // --------------------------------------------- TMA producer, both CTAs
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0;
+            bool ok = true;
+            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
+                int b, mp, nt;
+                decode(t, b, mp, nt);
+                const int bw = b / args.per_w;
+                for (int kb = 0; kb < args.num_kb; ++kb) {
+                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = full0_lead + 8 * stage;
+                    if (leader) mbar_arrive_expect_tx(full0 + 8 * stage, 2 * C::STAGE_BYTES);
+                    const uint32_t dst = s0 + stage * C::STAGE_BYTES;
+                    const int x = kb * (SPLIT ? 128 : BK);
+                    tma_load_3d_pair(dst, &tmW, fb, x, mp * 256 + 128 * rank, 2 * bw);
+                    tma_load_3d_pair(dst + C::A_BYTES, &tmX, fb, x, nt * BN + rank * (BN / 2), 2 * b);
+                    ++issued;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutProducer);
+                *abort_flag = 1;
+                if (leader) {
+                    for (int s = 0; s < STAGES; ++s) {
+                        if (issued > static_cast<uint32_t>(s)) {
+                            const uint32_t count = (issued - s + STAGES - 1) / STAGES;
+                            if (!mbar_wait(full0 + 8 * s, (count - 1) & 1u))
+                                atomicOr(args.status, kErrTimeoutDrain);
+                        }
+                    }
+                }
+            } else {
+                // the even CTA's release of every slot this CTA filled has arrived
+                for (int s = 0; s < STAGES; ++s) {
+                    if (issued > static_cast<uint32_t>(s)) {
+                        const uint32_t count = (issued - s + STAGES - 1) / STAGES;
+                        if (!mbar_wait(empty0 + 8 * s, (count - 1) & 1u))
+                            atomicOr(args.status, kErrTimeoutDrain);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------ MMA issuer, even CTA only
+        if (lane == 0 && leader) {
+            constexpr uint32_t kIdesc = idesc_f32acc(256, BN, 0, false);
+            constexpr uint32_t kIdescNeg = idesc_f32acc(256, BN, 0, true);
+            int stage = 0;
+            uint32_t phase = 0;
+            int ev = 0;
+            const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
+            bool ok = true;
+            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
+                for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+                    const int acc = ev % nbuf;
+                    const uint32_t aphase = (ev / nbuf) & 1;
+                    if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_re = tmem_base + acc * 2 * BN;
+                    const uint32_t d_im = d_re + BN;
+                    const int kb0 = ch * args.kc_blocks;
+                    const int kb1 = min(args.num_kb, kb0 + args.kc_blocks);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a = s0 + stage * C::STAGE_BYTES;
+                        const uint32_t bx = a + C::A_BYTES;
+                        if (!SPLIT) {
+                            const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
+                            for (int j = 0; j < ksteps; ++j) {
+                                const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
+                                const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
+                                const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
+                                const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
+                                const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
+                                mma_f16_pair(d_re, ar, br, kIdesc, accum);
+                                mma_f16_pair(d_re, ai, bi, kIdescNeg, 1u);
+                                mma_f16_pair(d_im, ar, bi, kIdesc, accum);
+                                mma_f16_pair(d_im, ai, br, kIdesc, 1u);
+                            }
+                        } else {
+                            const int ksteps = min(2, (args.K - kb * 64 + 31) / 32);
+                            for (int j = 0; j < ksteps; ++j) {
+#pragma unroll
+                                for (int pr = 0; pr < 3; ++pr) {
+                                    const uint32_t wo = (pr == 2 ? 64u : 0u) + 32u * j;
+                                    const uint32_t xo = (pr == 1 ? 64u : 0u) + 32u * j;
+                                    const uint64_t ar = sdesc_kmajor_sw128(a + wo);
+                                    const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + wo);
+                                    const uint64_t br = sdesc_kmajor_sw128(bx + xo);
+                                    const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + xo);
+                                    const uint32_t accum = (kb > kb0 || j > 0 || pr > 0) ? 1u : 0u;
+                                    mma_f8f6f4_pair(d_re, ar, br, kIdesc, accum);
+                                    mma_f8f6f4_pair(d_re, ai, bi, kIdescNeg, 1u);
+                                    mma_f8f6f4_pair(d_im, ar, bi, kIdesc, accum);
+                                    mma_f8f6f4_pair(d_im, ai, br, kIdesc, 1u);
+                                }
+                            }
+                        }
+                        mma_commit_pair(empty0 + 8 * stage, kBoth);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit_pair(tfull0 + 8 * acc, kBoth);
+                }
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutMma);
+                *abort_flag = 1;
+            }
+            mma_commit_pair(done_bar, 1);
+            if (!mbar_wait(done_bar, 0)) atomicOr(args.status, kErrTimeoutDrain);
+        }
+    } else {
+        // ------------------------------------------------- epilogue, both CTAs
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t stage_buf = staging0 + (warp - 2) * 8192;
+        const bool vec_ok = (args.N & 1) == 0;
+        int ev = 0;
+        const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
+        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+        const uint32_t tS = tmem_base + lane_off + 2 * BN;
+        int chunk_count = 0;
+        bool ok = true;
+        for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
+            int b, mp, nt;
+            decode(t, b, mp, nt);
+            const int mrow0 = mp * 256 + 128 * rank;           // this CTA's first row
+            const int m = mrow0 + row;
+            float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
+            float row_scale = 1.f;
+            if (SPLIT && m < args.M)
+                row_scale = pow2_neg(__ldg(args.w_exps + static_cast<size_t>(b / args.per_w) * args.M + m));
+            for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+                const int acc = ev % nbuf;
+                const uint32_t aphase = (ev / nbuf) & 1;
+                if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tP = tmem_base + lane_off + acc * 2 * BN;
+                if (ch + 1 < args.chunks) {
+#pragma unroll 1
+                    for (int g = 0; g < BN / 16; ++g) {
+                        float pr[16], pi[16];
+                        tmem_ld_2x16(tP + g * 16, tP + BN + g * 16, pr, pi);
+                        if (ch > 0) {
+                            float sr[16], si[16];
+                            tmem_ld_2x16(tS + g * 16, tS + BN + g * 16, sr, si);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                pr[i] = __fadd_rn(sr[i], pr[i]);
+                                pi[i] = __fadd_rn(si[i], pi[i]);
+                            }
+                        }
+                        tmem_st_2x16(tS + g * 16, tS + BN + g * 16, pr, pi);
+                    }
+                    tmem_st_wait();
+                } else {
+#pragma unroll 1
+                    for (int c = 0; c < BN / 16; ++c) {
+                        float re[16], im[16];
+                        tmem_ld_2x16(tP + c * 16, tP + BN + c * 16, re, im);
+                        if (args.chunks > 1) {
+                            float sr[16], si[16];
+                            tmem_ld_2x16(tS + c * 16, tS + BN + c * 16, sr, si);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                re[i] = __fadd_rn(sr[i], re[i]);
+                                im[i] = __fadd_rn(si[i], im[i]);
+                            }
+                        }
+                        const int n0 = nt * BN + c * 16;
+                        if (SPLIT) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const int n = min(n0 + i, args.N - 1);
+                                const float f = row_scale * pow2_neg(__ldg(args.x_exps + static_cast<size_t>(b) * args.N + n));
+                                re[i] *= f;
+                                im[i] *= f;
+                            }
+                        }
+                        if (args.tma_store) {
+                            if (n0 < args.N) {
+                                const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
+                                if (lane == 0) bulk_wait_read<1>();
+                                __syncwarp();
+                                const uint32_t rbase = buf + lane * 128;
+#pragma unroll
+                                for (int j = 0; j < 8; ++j)
+                                    st_shared_v4(rbase + ((j ^ (lane & 7)) << 4), re[2 * j], im[2 * j],
+                                                 re[2 * j + 1], im[2 * j + 1]);
+                                fence_async_smem();
+                                __syncwarp();
+                                if (lane == 0) {
+                                    tma_store_3d(&tmY, buf, 2 * n0, mrow0 + quarter * 32, b);
+                                    bulk_commit();
+                                }
+                                ++chunk_count;
+                            }
+                        } else if (m < args.M && n0 < args.N) {
+                            if (vec_ok && n0 + 16 <= args.N) {
+                                float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
+#pragma unroll
+                                for (int i = 0; i < 8; ++i)
+                                    dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    if (n0 + i < args.N) {
+                                        yrow[2 * (n0 + i)] = re[i];
+                                        yrow[2 * (n0 + i) + 1] = im[i];
+                                    }
+                            }
+                        }
+                    }
+                }
+                // this warp is done with the accumulator: release it on the even CTA
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(tempty0_lead + 8 * acc);
+            }
+        }
+        if (args.tma_store && lane == 0) bulk_wait<0>();
+        __syncwarp();
+        if (!ok && lane == 0) {
+            atomicOr(args.status, kErrTimeoutEpilogue);
+            *abort_flag = 1;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();                       // no CTA leaves while its peer may signal it
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
+    }
+}
+
 template <int BN, int STAGES, bool SPLIT, int CL>
 cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                        cudaStream_t s, int raster) {
@@ -559,6 +913,109 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     return cudaGetLastError();
 }
 
+template <int BN, int STAGES, bool SPLIT>
+cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                        cudaStream_t s, int raster) {
+    if (pl.m_prefix)   // uneven batches walk per-batch m-tiles: one-SM tiles
+        return launch_cfg<BN, 3, SPLIT, 1>(pl, Wp, Xp, Y, s, raster);
+    using C = CfgPair<BN, STAGES>;
+    const int64_t row = SPLIT ? pl.Kb2 : pl.Kp;
+    const CUtensorMapDataType dt = SPLIT ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const int64_t esz = SPLIT ? 1 : 2;
+    const tcbf_problem &p = pl.p;
+    CUtensorMap tmW, tmX, tmY;
+    {
+        const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(2 * p.w_batches)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(row * esz),
+                                     static_cast<uint64_t>(p.M * row * esz)};
+        const uint32_t box[3] = {static_cast<uint32_t>(128 / esz), BM, 2};
+        if (encode_tiled(&tmW, dt, 3, const_cast<void *>(Wp), dims, strides, box,
+                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.N),
+                                  static_cast<uint64_t>(2 * p.batch)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(row * esz),
+                                     static_cast<uint64_t>(p.N * row * esz)};
+        const uint32_t box[3] = {static_cast<uint32_t>(128 / esz), BN / 2, 2};   // this CTA's half
+        if (encode_tiled(&tmX, dt, 3, const_cast<void *>(Xp), dims, strides, box,
+                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const int tma_store = (p.N % 2 == 0) ? 1 : 0;
+    if (tma_store) {
+        const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(p.batch)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(p.N * 8),
+                                     static_cast<uint64_t>(p.M * p.N * 8)};
+        const uint32_t box[3] = {32, 32, 1};
+        if (encode_tiled(&tmY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Y, dims, strides, box,
+                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
+        tmY = tmX;   // unused
+    }
+    GemmArgs a;
+    a.Y = Y;
+    a.w_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) +
+                                                        p.w_batches * 2 * p.M * row)
+                     : nullptr;
+    a.x_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Xp) +
+                                                        p.batch * 2 * p.N * row)
+                     : nullptr;
+    a.tma_store = tma_store;
+    a.status = pl.status;
+    a.M = static_cast<int>(p.M);
+    a.N = static_cast<int>(p.N);
+    a.K = static_cast<int>(p.K);
+    a.per_w = static_cast<int>(pl.per_w);
+    a.tiles.prefix = nullptr;
+    a.tiles.batch = static_cast<int>(p.batch);
+    a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, BM));
+    a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, BN));
+    a.tiles.raster = 0;
+    a.num_kb = static_cast<int>(ceil_div(p.K, BK));
+    if (p.K > kPromoteK) {
+        if (4 * BN > 512) return cudaErrorInvalidConfiguration;
+        a.kc_blocks = kChunkBlocks;
+    } else {
+        a.kc_blocks = a.num_kb;
+    }
+    a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
+    const int64_t total = ceil_div(a.tiles.m_tiles, 2) * p.batch * a.tiles.n_tiles;
+    if (total > 0x7fffffff) return cudaErrorInvalidValue;
+    a.total_tiles = static_cast<int>(total);
+    auto kern = cgemm_pair_kernel<BN, STAGES, SPLIT>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = C::SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters[64] = {};
+    int &mc = max_clusters[pl.device & 63];
+    if (mc == 0) {
+        cfg.gridDim = dim3(pl.num_sms / 2 * 2);
+        e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (mc < 1) return cudaErrorInvalidConfiguration;
+    }
+    cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(total, mc)) * 2);
+    e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 struct ConfigEntry {
     const char *name;
     int bn;
@@ -575,6 +1032,7 @@ const ConfigEntry kConfigs[] = {
     {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, false, 1>},
     {"f16 BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, false, 2>},
     {"f16 BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, false, 4>},
+    {"f16 2-SM pair BM256 BN128 BK64 stages4 tmem-double", 128, 0, launch_pair<128, 4, false>},
 };
 
 // split-FP8: the same tile shapes, index for index
@@ -587,6 +1045,7 @@ const ConfigEntry kConfigsSplit[] = {
     {"fp8split BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, true, 1>},
     {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, true, 2>},
     {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, true, 4>},
+    {"fp8split 2-SM pair BM256 BN128 BK64 stages4 tmem-double", 128, 0, launch_pair<128, 4, true>},
 };
 
 }  // namespace

@@ -12,6 +12,7 @@
 //   kind 3: mma.sync m16n8k16 f16 -> f32 (legacy warp MMA)
 //   kind 4: mma.sync m16n8k256 b1 AND-popc -> s32 (legacy warp MMA)
 //   kind 5: CUDA-core popc of XOR on 32-bit words
+//   kind 6: tcgen05.mma kind::f16   M128 N128 K16  (the beamformer's tile MMA)
 // Ops are counted as 2 per multiply-accumulate (b1: per bit product).
 #include <cuda_runtime.h>
 
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *st
     for (int i = threadIdx.x; i < 49152 / 4; i += blockDim.x) {
         const uint32_t h = (i + 1) * 0x9E3779B9u;
         reinterpret_cast<uint32_t *>(smem)[i] =
-            KIND == 0 ? ((h & 0x83FF83FFu) | 0x38003800u) : ((h & 0x87878787u) | 0x30303030u);
+            KIND == 1 ? ((h & 0x87878787u) | 0x30303030u) : ((h & 0x83FF83FFu) | 0x38003800u);
     }
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -63,6 +64,9 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *st
         const uint64_t bd = sdesc_kmajor_sw128(b_addr);
         if (KIND == 0) {
             constexpr uint32_t id = idesc_f32acc(128, 256, 0, false);
+            for (int i = 0; i < iters; ++i) mma_f16(tmem, ad, bd, id, i > 0);
+        } else if (KIND == 6) {
+            constexpr uint32_t id = idesc_f32acc(128, 128, 0, false);
             for (int i = 0; i < iters; ++i) mma_f16(tmem, ad, bd, id, i > 0);
         } else if (KIND == 1) {
             constexpr uint32_t id = idesc_f32acc(128, 256, 0, false);   // e4m3 x e4m3
@@ -135,7 +139,7 @@ using namespace tcbf;
 
 TCBF_EXPORT tcbf_status tcbf_peak_run(int kind, int device, int iters, double *seconds,
                                       double *ops) {
-    if (!seconds || !ops || kind < 0 || kind > 5 || iters < 1) return TCBF_ERR_INVALID_ARG;
+    if (!seconds || !ops || kind < 0 || kind > 6 || iters < 1) return TCBF_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TCBF_ERR_UNSUPPORTED;
     if (device < 0 || device >= ndev) return TCBF_ERR_INVALID_ARG;
@@ -169,6 +173,11 @@ TCBF_EXPORT tcbf_status tcbf_peak_run(int kind, int device, int iters, double *s
                     cudaFuncSetAttribute(tc_peak_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
                     tc_peak_kernel<1><<<sms, 128, smem>>>(iters, status);
                     per_launch = 2.0 * 128 * 256 * 32 * double(iters) * sms;
+                    break;
+                case 6:
+                    cudaFuncSetAttribute(tc_peak_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                    tc_peak_kernel<6><<<sms, 128, smem>>>(iters, status);
+                    per_launch = 2.0 * 128 * 128 * 16 * double(iters) * sms;
                     break;
                 case 3:
                     warp_peak_kernel<3><<<sms * 4, 256>>>(iters, 1, status);

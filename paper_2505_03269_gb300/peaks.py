@@ -20,6 +20,7 @@ KINDS = {
     3: ("mma_sync_f16_m16n8k16", 20000),
     4: ("mma_sync_b1_and_m16n8k256", 20000),
     5: ("cuda_core_popc_xor32", 20000),
+    6: ("tcgen05_f16_m128n128k16", 80000),
 }
 
 

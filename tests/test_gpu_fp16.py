@@ -36,7 +36,7 @@ def test_small_fp16_workload():
     assert oracle.rel_frobenius(Y, Yref) <= TOL
 
 
-@pytest.mark.parametrize("config", [0, 1, 2, 6, 7])
+@pytest.mark.parametrize("config", [0, 1, 2, 6, 7, 8])
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (3, 5, 7), (17, 33, 127), (129, 130, 288),
                                    (127, 257, 129), (200, 96, 64), (64, 1024, 200)])
 def test_ragged_shapes(config, M, N, K):
@@ -46,7 +46,7 @@ def test_ragged_shapes(config, M, N, K):
     assert oracle.rel_frobenius(Y, Yref) <= TOL
 
 
-@pytest.mark.parametrize("config", [0, 1, 2, 6, 7])
+@pytest.mark.parametrize("config", [0, 1, 2, 6, 7, 8])
 def test_integer_inputs_bit_exact(config):
     g = ti.rng(1)
     W = ti.integer_complex_fp16(g, (2, 150, 300))
@@ -96,7 +96,7 @@ def test_fp32_source_rounds_to_nearest():
     assert oracle.rel_frobenius(Y, Yref) <= TOL
 
 
-@pytest.mark.parametrize("config", [0, 2, 7])
+@pytest.mark.parametrize("config", [0, 2, 7, 8])
 @pytest.mark.parametrize("K", [4100, 8192, 16384])
 def test_long_k_within_tolerance(config, K):
     """Above K = 4096 the partial sums are promoted to FP32 every 2048 K;
