@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunk", type=int, default=0,
+                    help="batches per chunk of the end-to-end host pipeline (0: about batch / 16)")
     ap.add_argument("--mode", choices=["fp16", "fp8split"], default=None,
                     help="arithmetic of the FP workloads (default fp16)")
     ap.add_argument("--batches", type=int, default=None,
@@ -420,6 +422,7 @@ def main():
         reference_arm(args, w)
         return
 
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -514,26 +517,43 @@ def main():
     if not args.no_e2e:
         Xhost = torch.from_numpy(gw.Xh).pin_memory()
         Yhost = torch.empty(gw.Y.shape, dtype=gw.Y.dtype, pin_memory=True)
+        src_type = 1 if gw.Xh.dtype == np.float32 else 0
 
         def e2e_step():
-            gw.Xd.copy_(Xhost, non_blocking=True)
-            gw.step()
-            Yhost.copy_(gw.Y, non_blocking=True)
+            gw.plan.beamform_host(Xhost, gw.Wp, Yhost, chunk=args.e2e_chunk, src_type=src_type,
+                                  stream=stream)
         e2e_step()
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
+        a.record(stream)
         for _ in range(args.e2e_steps):
             e2e_step()
-        b.record()
+        b.record(stream)
         barrier()
+        # the host link's own device-to-host rate (one plain copy of up to 4 GiB of Y),
+        # the floor the step's Y copy-out cannot beat
+        nl = min(gw.Y.numel(), 1 << 30)
+        ysrc, ydst = gw.Y.view(-1)[:nl], Yhost.view(-1)[:nl]
+        ydst.copy_(ysrc, non_blocking=True)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        ydst.copy_(ysrc, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        link_gbs = nl * 4 / (l0.elapsed_time(l1) * 1e-3) / 1e9
         te = torch.tensor([a.elapsed_time(b) / args.e2e_steps], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": world * ops_per_step(w) / (float(te.item()) * 1e-3) / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": int(gw.Xh.nbytes), "d2h_bytes_per_step": int(gw.Y.numel() * 4),
                "ms_per_step": float(te.item()),
-               "how": "pinned host X -> device, pack, beamform, Y -> pinned host, one stream"}
+               "how": "tcbf_beamform_host on pinned host X and Y: chunks of batches, "
+                      "host-to-device copy, pack + beamform and device-to-host copy of "
+                      "neighbouring chunks overlapped on separate streams",
+               "chunk": args.e2e_chunk or "auto (about batch / 16)",
+               "d2h_link_gbs": link_gbs,
+               "d2h_floor_ms": gw.Y.numel() * 4 / link_gbs / 1e6,
+               "frac_of_d2h_floor": gw.Y.numel() * 4 / link_gbs / 1e6 / float(te.item())}
         del Xhost, Yhost
 
     # ---- roofline of the dominant kernel (the GEMM)

@@ -250,6 +250,39 @@ tcbf_status tcbf_graph_capture(tcbf_plan_t plan, const void *X_src, int src_type
                                const void *Wp, void *Y);
 tcbf_status tcbf_graph_launch(tcbf_plan_t plan, tcbf_stream_t stream);
 
+/*
+ * The whole step for HOST-resident data: Y_host[b] = W[b / per_w] X_host[b]
+ * (Eq. 3) for every batch b, in every mode.  The paper's library sits inside
+ * an instrument's processing pipeline (Sec. V); this is the call such a
+ * pipeline makes when its samples arrive in host memory.  The data movement
+ * around the kernels is this library's own: the batches go through in
+ * chunks, each chunk's X copied host-to-device on one stream, packed and
+ * beamformed on a second, and its Y copied device-to-host on two more, so
+ * the copies of one chunk overlap the compute of its neighbours.
+ *   X_host: HOST [batch][K][N] interleaved complex of type src_type
+ *           (tcbf_src_type), as for tcbf_transpose_pack(which = 1).
+ *   Wp:     DEVICE packed weights of the plan's mode (tcbf_transpose_pack
+ *           which = 0 or tcbf_weights_from_geometry), all w_batches.
+ *   Y_host: HOST [batch][M][N] interleaved complex, 8 bytes per value:
+ *           FP32 (FP16 and split-FP8 plans) or int32 (1-bit plans).
+ *   chunk:  batches per chunk, a positive multiple of batch / w_batches (the
+ *           last chunk may be shorter); 0 picks about batch / 16.
+ * Device staging for three chunks (source X, packed X, Y) is allocated at
+ * the first call, or when `chunk` grows, and kept by the plan until
+ * tcbf_plan_destroy; TCBF_ERR_OOM if it cannot be had.  The work starts
+ * after everything already enqueued on `stream`, and `stream` waits for the
+ * last copy, so work enqueued on it later sees Y_host complete; the call
+ * itself does not block the host.  Host buffers must stay valid and X_host
+ * unmodified until then; page-locked host memory is needed for the copies to
+ * overlap (pageable memory gives the same result, serialised).  Calls on one
+ * plan share its staging, so they must be ordered (enqueue them on one
+ * stream).  Uneven batches (tcbf_plan_set_batch_rows) are not supported:
+ * TCBF_ERR_UNSUPPORTED.  Device errors surface through
+ * tcbf_last_device_error as for the other calls.
+ */
+tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host, int src_type, const void *Wp,
+                               void *Y_host, int64_t chunk, tcbf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

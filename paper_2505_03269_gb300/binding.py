@@ -29,6 +29,7 @@ EXPORTED = [
     "tcbf_status_string", "tcbf_plan_num_configs", "tcbf_plan_get_config",
     "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
     "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
+    "tcbf_beamform_host",
 ]
 
 
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_autotune": [vp, vp, vp, vp, i32, vp, ctypes.POINTER(i32), vp],
         "tcbf_graph_capture": [vp, vp, i32, vp, vp, vp],
         "tcbf_graph_launch": [vp, vp],
+        "tcbf_beamform_host": [vp, vp, i32, vp, vp, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -228,6 +230,14 @@ class Plan:
 
     def graph_launch(self, stream=None):
         _check(self._lib.tcbf_graph_launch(self.handle, _stream(stream)), "tcbf_graph_launch")
+
+    # ------------------------------------------------------- host-resident data
+    def beamform_host(self, X_host, Wp, Y_host, chunk=0, src_type=SRC_CF16, stream=None):
+        """tcbf_beamform_host: X_host and Y_host are CPU tensors (pinned for
+        overlap), Wp the packed weights on the device; stream-ordered."""
+        _check(self._lib.tcbf_beamform_host(self.handle, _ptr(X_host), int(src_type), _ptr(Wp),
+                                            _ptr(Y_host), int(chunk), _stream(stream)),
+               "tcbf_beamform_host")
 
 
 def beamform_fp16_noalloc(batch, M, N, K, Wp, X, Y, w_batches=0, device=0,

@@ -166,6 +166,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_destroy(tcbf_plan_t plan) {
     if (!plan) return TCBF_OK;
     {
         DeviceGuard g(plan->device);
+        host_pipe_destroy(*plan);
         if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
         if (plan->m_prefix) cudaFree(plan->m_prefix);
         if (plan->status) cudaFree(plan->status);

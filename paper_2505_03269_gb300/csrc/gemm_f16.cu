@@ -848,9 +848,10 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     }
     GemmArgs a;
     a.Y = Y;
-    a.w_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) +
-                                                        p.w_batches * 2 * p.M * row)
-                     : nullptr;
+    a.w_exps = !SPLIT ? nullptr
+               : pl.w_exps ? pl.w_exps
+                           : reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) +
+                                                               p.w_batches * 2 * p.M * row);
     a.x_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Xp) +
                                                         p.batch * 2 * p.N * row)
                      : nullptr;
@@ -959,9 +960,10 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
     }
     GemmArgs a;
     a.Y = Y;
-    a.w_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) +
-                                                        p.w_batches * 2 * p.M * row)
-                     : nullptr;
+    a.w_exps = !SPLIT ? nullptr
+               : pl.w_exps ? pl.w_exps
+                           : reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) +
+                                                               p.w_batches * 2 * p.M * row);
     a.x_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Xp) +
                                                         p.batch * 2 * p.N * row)
                      : nullptr;

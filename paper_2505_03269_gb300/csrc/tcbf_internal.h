@@ -25,6 +25,11 @@ struct tcbf_plan_s {
     int64_t m_tiles_sum = 0;
     // captured step (tcbf_graph_capture)
     cudaGraphExec_t graph_exec = nullptr;
+    // split-FP8 W scale exponents when Wp is a sub-range of a larger packed W
+    // (chunks of tcbf_beamform_host); nullptr: they follow Wp's planes
+    const int32_t *w_exps = nullptr;
+    // staging, streams and events of tcbf_beamform_host, made at its first call
+    struct tcbf_host_pipe *pipe = nullptr;
 };
 
 namespace tcbf {
@@ -67,6 +72,9 @@ int gemm_1bit_num_configs();
 const char *gemm_1bit_config_name(int config);
 cudaError_t launch_gemm_1bit(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,
                              int32_t *Y, cudaStream_t s);
+
+// Releases the staging of tcbf_beamform_host (plan destruction).
+void host_pipe_destroy(tcbf_plan_s &pl);
 
 cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double *tg,
                            int near_field, const double *freqs, double c, void *Wp,
