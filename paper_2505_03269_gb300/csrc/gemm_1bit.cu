@@ -10,14 +10,17 @@
 // FP32 accumulators.  Every partial sum is an integer of magnitude <= 2K,
 // exact in FP32 for K < 2^23, so the result equals K - 2 Hamming exactly.
 //
-// Warp roles (416 threads, one CTA per SM, persistent over tiles):
+// Warp roles (544 threads, one CTA per SM, persistent over tiles):
 //   warp 0      TMEM owner and single-thread MMA issuer (4 real MMAs per
 //               K step, negate-A for -Im(W) Im(X), as in the FP16 kernel)
-//   warps 1-8   converters (4 for W rows, 4 for X rows): 16-byte loads of
-//               packed words (L2-resident), expansion to E4M3 in the
-//               128-byte-swizzled K-major layout the MMA reads, one stage of
-//               128 K per ring slot
-//   warps 9-12  epilogue: TMEM -> int32 pairs -> staged TMA stores
+//   warps 1-12  converters: each thread takes every 384th row-plane of the
+//               stage (the W planes' rows, then the X planes' rows), a 16-byte
+//               load of its packed words (L2-resident) and its expansion to
+//               E4M3 in the 128-byte-swizzled K-major layout the MMA reads,
+//               one stage of 128 K per ring slot.  The expansion is latency-
+//               bound per thread, so the row-planes are spread evenly (two per
+//               thread for 128 x 256 tiles) rather than split by operand.
+//   warps 13-16 epilogue: TMEM -> int32 pairs -> staged TMA stores
 #include <algorithm>
 #include <cstring>
 
@@ -32,9 +35,7 @@ using namespace dev;
 
 constexpr int BM = 128;
 constexpr int BKE = 128;             // K elements per stage (one 128-byte E4M3 row)
-constexpr int kConvW = 128;          // converter threads for W rows
-constexpr int kConvX = 128;          // converter threads for X rows
-constexpr int kConv = kConvW + kConvX;
+constexpr int kConv = 384;           // converter threads
 constexpr int kThreads = 32 + kConv + 128;
 
 struct Args1 {
@@ -124,24 +125,25 @@ __device__ __forceinline__ void expand_row(uint32_t row_base, int r, uint4 words
     }
 }
 
-// Packed words one converter thread needs for one stage: a W row (both
-// planes) for the first kConvW threads, BN/128 X rows for the others, with
-// the number of valid K elements (0 for rows beyond M or N: zeros).
+// Row-planes of one stage: 2 x BM of W (Wr rows, then Wi rows) and 2 x BN
+// of X; converter thread ct takes ct, ct + kConv, ...  Each holds its packed
+// words and the number of valid K elements (0 for rows beyond M or N, which
+// are written as zeros).
 template <int BN>
 struct StageWords {
-    uint4 re[BN / 128], im[BN / 128];
-    int valid[BN / 128];
+    static constexpr int RP = (2 * (BM + BN) + kConv - 1) / kConv;   // row-planes per thread
+    uint4 w[RP];
+    int valid[RP];
 };
 
 // Load stage `i` of this CTA's flattened (tile, stage) sequence.
 template <int BN>
 __device__ __forceinline__ void load_stage(const Args1 &args, int ct, int i, int iters,
                                            StageWords<BN> &w) {
-    const uint4 zero = make_uint4(0, 0, 0, 0);
 #pragma unroll
-    for (int h = 0; h < BN / 128; ++h) {
-        w.re[h] = w.im[h] = zero;
-        w.valid[h] = 0;
+    for (int j = 0; j < StageWords<BN>::RP; ++j) {
+        w.w[j] = make_uint4(0, 0, 0, 0);
+        w.valid[j] = 0;
     }
     if (i >= iters) return;
     const int t = blockIdx.x + (i / args.num_kb) * gridDim.x;
@@ -149,26 +151,24 @@ __device__ __forceinline__ void load_stage(const Args1 &args, int ct, int i, int
     int b, mt, nt;
     decode_tile(t, args, b, mt, nt);
     const int valid = args.K - kb * BKE;
-    if (ct < kConvW) {
-        const int mrow = mt * BM + ct;
-        if (mrow < args.M) {
-            const uint32_t *wr = args.Wb +
-                (static_cast<size_t>((b / args.per_w) * 2) * args.M + mrow) * args.Kw + kb * 4;
-            w.re[0] = __ldg(reinterpret_cast<const uint4 *>(wr));
-            w.im[0] = __ldg(reinterpret_cast<const uint4 *>(wr + static_cast<size_t>(args.M) * args.Kw));
-            w.valid[0] = valid;
-        }
-        return;
-    }
 #pragma unroll
-    for (int h = 0; h < BN / 128; ++h) {
-        const int nrow = nt * BN + (ct - kConvW) + 128 * h;
-        if (nrow < args.N) {
-            const uint32_t *xr =
-                args.Xb + (static_cast<size_t>(b * 2) * args.N + nrow) * args.Kw + kb * 4;
-            w.re[h] = __ldg(reinterpret_cast<const uint4 *>(xr));
-            w.im[h] = __ldg(reinterpret_cast<const uint4 *>(xr + static_cast<size_t>(args.N) * args.Kw));
-            w.valid[h] = valid;
+    for (int j = 0; j < StageWords<BN>::RP; ++j) {
+        const int rp = ct + j * kConv;
+        const uint32_t *src = nullptr;
+        if (rp < 2 * BM) {
+            const int plane = rp / BM, mrow = mt * BM + rp % BM;
+            if (mrow < args.M)
+                src = args.Wb + (static_cast<size_t>((b / args.per_w) * 2 + plane) * args.M + mrow) *
+                                    args.Kw + kb * 4;
+        } else if (rp < 2 * (BM + BN)) {
+            const int x = rp - 2 * BM;
+            const int plane = x / BN, nrow = nt * BN + x % BN;
+            if (nrow < args.N)
+                src = args.Xb + (static_cast<size_t>(b * 2 + plane) * args.N + nrow) * args.Kw + kb * 4;
+        }
+        if (src) {
+            w.w[j] = __ldg(reinterpret_cast<const uint4 *>(src));
+            w.valid[j] = valid;
         }
     }
 }
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // The (tile, stage) sequence of this CTA is flattened and the packed
         // words of stage i + 2 are loaded while stage i is expanded, so the
         // L2 latency of the 16-byte loads is covered.
-        const int ct = threadIdx.x - 32;               // 0..255: W rows, then X rows
+        const int ct = threadIdx.x - 32;               // 0..kConv-1
         const int my_tiles = (args.total_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
         const int iters = my_tiles * args.num_kb;
         StageWords<BN> cur, nxt;
@@ -295,15 +295,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             const uint32_t a = s0 + stage * C::STAGE_BYTES;
-            if (ct < kConvW) {
-                expand_row(a + ct * 128, ct, cur.re[0], cur.valid[0]);
-                expand_row(a + C::A_PLANE + ct * 128, ct, cur.im[0], cur.valid[0]);
-            } else {
 #pragma unroll
-                for (int h = 0; h < BN / 128; ++h) {
-                    const int r = ct - kConvW + 128 * h;
-                    expand_row(a + C::A_BYTES + r * 128, r, cur.re[h], cur.valid[h]);
-                    expand_row(a + C::A_BYTES + C::B_PLANE + r * 128, r, cur.im[h], cur.valid[h]);
+            for (int j = 0; j < StageWords<BN>::RP; ++j) {
+                const int rp = ct + j * kConv;
+                if (rp < 2 * BM) {
+                    const int r = rp % BM;
+                    expand_row(a + (rp / BM) * C::A_PLANE + r * 128, r, cur.w[j], cur.valid[j]);
+                } else if (rp < 2 * (BM + BN)) {
+                    const int x = rp - 2 * BM, r = x % BN;
+                    expand_row(a + C::A_BYTES + (x / BN) * C::B_PLANE + r * 128, r, cur.w[j],
+                               cur.valid[j]);
                 }
             }
             fence_async_smem();                        // generic writes -> tensor core reads
