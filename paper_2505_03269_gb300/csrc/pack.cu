@@ -30,6 +30,18 @@ struct CF16 {
         re = __low2half(v);
         im = __high2half(v);
     }
+    // value i as one word: re in the low half, im in the high half
+    static __device__ __forceinline__ uint32_t load_word(const void *src, size_t i) {
+        return reinterpret_cast<const uint32_t *>(src)[i];
+    }
+    // values i .. i + 3 (i a multiple of 4, 16-byte aligned)
+    static __device__ __forceinline__ void load4(const void *src, size_t i, uint32_t (&w)[4]) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src) + i / 4);
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+    }
 };
 
 struct CF32 {
@@ -43,6 +55,23 @@ struct CF32 {
         const float2 v = reinterpret_cast<const float2 *>(src)[i];
         re = __float2half_rn(v.x);
         im = __float2half_rn(v.y);
+    }
+    static __device__ __forceinline__ uint32_t to_word(float re, float im) {
+        const __half2 h = __halves2half2(__float2half_rn(re), __float2half_rn(im));
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    static __device__ __forceinline__ uint32_t load_word(const void *src, size_t i) {
+        const float2 v = reinterpret_cast<const float2 *>(src)[i];
+        return to_word(v.x, v.y);
+    }
+    // values i .. i + 3 (i a multiple of 4, 32-byte aligned)
+    static __device__ __forceinline__ void load4(const void *src, size_t i, uint32_t (&w)[4]) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(src) + i / 2);
+        const float4 c = __ldg(reinterpret_cast<const float4 *>(src) + i / 2 + 1);
+        w[0] = to_word(a.x, a.y);
+        w[1] = to_word(a.z, a.w);
+        w[2] = to_word(c.x, c.y);
+        w[3] = to_word(c.z, c.w);
     }
 };
 
@@ -81,18 +110,22 @@ __global__ void pack_f16_w_kernel(const void *__restrict__ src, __half *__restri
     }
 }
 
-// X: 64 (k) x 64 (n) tiles through shared memory.  Loads read rows of X
-// (n contiguous); stores write rows of the packed planes (k contiguous),
-// eight threads per 128-byte row.
+// X: 64 (k) x 64 (n) tiles through shared memory, one 32-bit word (re, im
+// halves) per complex value.  Loads read rows of X (n contiguous), four
+// values per thread as one 16-byte access (FP16 source; FP32 sources are
+// rounded while loading); stores write rows of the packed planes (k
+// contiguous), eight threads per 128-byte row, each splitting 8 words into
+// 8 re and 8 im halves with byte permutes.  The word of (k, n) sits at
+// column n ^ 4 (k / 8) of row k: the 16-byte row writes stay contiguous and
+// the column reads of a warp (4 n x 8 k-chunks) hit 32 distinct banks.
 constexpr int TT = 64;
-constexpr int TPITCH = TT + 2;   // halves; odd word pitch spreads banks
+constexpr int TPITCH = TT + 2;   // halves; odd word pitch spreads banks (split-FP8 X pack)
 
-template <typename S>
+template <typename S, bool VEC>
 __global__ void __launch_bounds__(256) pack_f16_x_kernel(const void *__restrict__ src,
                                                         __half *__restrict__ dst, int K, int N,
                                                         int Kp, int k_tiles, int n_tiles) {
-    __shared__ __half sre[TT][TPITCH];
-    __shared__ __half sim[TT][TPITCH];
+    __shared__ __align__(16) uint32_t tile[TT * TT];
     const int tid = threadIdx.x;
     const int64_t tiles_per_b = int64_t(k_tiles) * n_tiles;
     const int64_t b = blockIdx.y;
@@ -100,24 +133,29 @@ __global__ void __launch_bounds__(256) pack_f16_x_kernel(const void *__restrict_
         const int kt = static_cast<int>(t / n_tiles);
         const int nt = static_cast<int>(t % n_tiles);
         const int k0 = kt * TT, n0 = nt * TT;
-        // load: thread (ty, tx) reads 4 consecutive n at rows ty + 16 i
+        // load: thread (ty, tx) takes n = 4 tx .. 4 tx + 3 of rows ty + 16 i
         const int tx = tid & 15, ty = tid >> 4;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int kk = ty + 16 * i;
             const int k = k0 + kk;
+            const int n = n0 + 4 * tx;
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (k < K) {
+                const size_t e = (static_cast<size_t>(b) * K + k) * N + n;
+                if (VEC && n + 3 < N) {
+                    S::load4(src, e, w);
+                } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int nn = tx * 4 + q;
-                const int n = n0 + nn;
-                __half re = __float2half_rn(0.f), im = __float2half_rn(0.f);
-                if (k < K && n < N) S::load_h(src, (static_cast<size_t>(b) * K + k) * N + n, re, im);
-                sre[nn][kk] = re;
-                sim[nn][kk] = im;
+                    for (int q = 0; q < 4; ++q)
+                        if (n + q < N) w[q] = S::load_word(src, e + q);
+                }
             }
+            const int col = (4 * tx) ^ (4 * (kk >> 3));
+            *reinterpret_cast<uint4 *>(&tile[kk * TT + col]) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         __syncthreads();
-        // store: thread -> (row n, 16-byte chunk c); two rows per thread
+        // store: thread -> (row n, k-chunk c of 8); two rows per thread
         const int c = tid & 7;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -125,16 +163,22 @@ __global__ void __launch_bounds__(256) pack_f16_x_kernel(const void *__restrict_
             const int n = n0 + nn;
             const int k = k0 + 8 * c;
             if (n < N && k < Kp) {
-                __align__(16) __half re[8], im[8];
+                uint32_t v[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    re[j] = sre[nn][8 * c + j];
-                    im[j] = sim[nn][8 * c + j];
-                }
+                for (int j = 0; j < 8; ++j) v[j] = tile[(8 * c + j) * TT + (nn ^ (4 * c))];
+                uint4 re, im;
+                re.x = __byte_perm(v[0], v[1], 0x5410);
+                re.y = __byte_perm(v[2], v[3], 0x5410);
+                re.z = __byte_perm(v[4], v[5], 0x5410);
+                re.w = __byte_perm(v[6], v[7], 0x5410);
+                im.x = __byte_perm(v[0], v[1], 0x7632);
+                im.y = __byte_perm(v[2], v[3], 0x7632);
+                im.z = __byte_perm(v[4], v[5], 0x7632);
+                im.w = __byte_perm(v[6], v[7], 0x7632);
                 const size_t o_re = (static_cast<size_t>(b * 2 + 0) * N + n) * Kp + k;
                 const size_t o_im = (static_cast<size_t>(b * 2 + 1) * N + n) * Kp + k;
-                *reinterpret_cast<uint4 *>(dst + o_re) = *reinterpret_cast<const uint4 *>(re);
-                *reinterpret_cast<uint4 *>(dst + o_im) = *reinterpret_cast<const uint4 *>(im);
+                *reinterpret_cast<uint4 *>(dst + o_re) = re;
+                *reinterpret_cast<uint4 *>(dst + o_im) = im;
             }
         }
         __syncthreads();
@@ -221,10 +265,20 @@ cudaError_t launch_pack_f16_x(const tcbf_plan_s &pl, int src_type, const void *s
     const int bx = static_cast<int>(std::min<int64_t>(per_b, std::max<int64_t>(1, int64_t(pl.num_sms) * 8 / std::max<int64_t>(1, std::min<int64_t>(pl.p.batch, 8)))));
     dim3 grid(bx, static_cast<unsigned>(pl.p.batch));
     auto *d = static_cast<__half *>(dst);
-    if (src_type == TCBF_SRC_CF16)
-        pack_f16_x_kernel<CF16><<<grid, 256, 0, s>>>(src, d, int(pl.p.K), int(pl.p.N), int(pl.Kp), k_tiles, n_tiles);
-    else
-        pack_f16_x_kernel<CF32><<<grid, 256, 0, s>>>(src, d, int(pl.p.K), int(pl.p.N), int(pl.Kp), k_tiles, n_tiles);
+    // 16-byte loads of four values need every row of X to start 16-byte aligned
+    const bool vec = pl.p.N % 4 == 0;
+    const int K = int(pl.p.K), N = int(pl.p.N), Kp = int(pl.Kp);
+    if (src_type == TCBF_SRC_CF16) {
+        if (vec)
+            pack_f16_x_kernel<CF16, true><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+        else
+            pack_f16_x_kernel<CF16, false><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+    } else {
+        if (vec)
+            pack_f16_x_kernel<CF32, true><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+        else
+            pack_f16_x_kernel<CF32, false><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+    }
     return cudaGetLastError();
 }
 

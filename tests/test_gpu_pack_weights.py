@@ -49,7 +49,8 @@ def _expected_planes(V16, k_axis_last):
     return out
 
 
-@pytest.mark.parametrize("B,M,N,K", [(1, 5, 7, 3), (3, 70, 130, 77), (2, 64, 256, 288)])
+@pytest.mark.parametrize("B,M,N,K", [(1, 5, 7, 3), (3, 70, 130, 77), (2, 64, 256, 288),
+                                     (2, 40, 132, 77), (1, 16, 4096, 288)])
 def test_pack_fp16_layout_bit_exact(B, M, N, K):
     from paper_2505_03269_gb300 import MODE_FP16
     W, X = ti.small_fp16(seed=B + M, M=M, K=K, N=N, B=B)
@@ -60,13 +61,14 @@ def test_pack_fp16_layout_bit_exact(B, M, N, K):
     assert np.array_equal(Xp.view(np.uint16), _expected_planes(X, False).ravel().view(np.uint16))
 
 
-def test_pack_fp32_source_rounds_to_nearest_even():
+@pytest.mark.parametrize("N", [66, 68])          # row starts unaligned / 16-byte aligned
+def test_pack_fp32_source_rounds_to_nearest_even(N):
     from paper_2505_03269_gb300 import MODE_FP16, SRC_CF32
     g = np.random.default_rng(3)
-    X32 = (g.standard_normal((2, 40, 66, 2)) * 1000).astype(np.float32)
+    X32 = (g.standard_normal((2, 40, N, 2)) * 1000).astype(np.float32)
     # values exactly between two FP16 numbers must round to even
     X32[0, 0, :4, 0] = np.array([1 + 2**-11, 1 + 3 * 2**-11, -(1 + 2**-11), 2049.0], np.float32)
-    with _plan(2, 4, 66, 40, MODE_FP16) as plan:
+    with _plan(2, 4, N, 40, MODE_FP16) as plan:
         Xp = _packed(plan, 1, X32, SRC_CF32).view(np.float16)
     assert np.array_equal(Xp.view(np.uint16),
                           _expected_planes(X32.astype(np.float16), False).ravel().view(np.uint16))
