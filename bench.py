@@ -98,6 +98,24 @@ def ops_per_step(w):
     return 8.0 * w["B"] * w["M"] * w["N"] * w["K"]
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every rank's measured ms, reduced with MAX
+    over the default process group (NCCL on the GPUs, gloo in the host
+    tests) when there is more than one rank."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, ops_per_rank, ms_per_step):
+    """TeraOps/s of the whole job: every rank processes its own replica of the
+    workload (weak scaling), all finish within the slowest rank's time."""
+    return world * ops_per_rank / (ms_per_step * 1e-3) / 1e12
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -489,11 +507,8 @@ def main():
     # ---- timed region: K steps (tuned configuration), clocks sampled
     total_ms, pack_ms, gemm_ms, clocks = timed(args.steps, sample_clocks=True)
     status = plan.last_device_error()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
-    value = world * ops_per_step(w) / (ms_per_step * 1e-3) / 1e12
+    ms_per_step = max_over_ranks(total_ms, world, "cuda") / args.steps
+    value = whole_job_value(world, ops_per_step(w), ms_per_step)
     if tuning is not None:
         tuning["tuned"]["gemm_ms"] = gemm_ms
         tuning["speedup_gemm"] = tuning["default"]["gemm_ms"] / gemm_ms
@@ -508,7 +523,7 @@ def main():
         plan.graph_launch()
     g1.record(stream)
     barrier()
-    graph_ms = g0.elapsed_time(g1) / args.steps
+    graph_ms = max_over_ranks(g0.elapsed_time(g1) / args.steps, world, "cuda")
 
     parity = gw.parity()
 
@@ -541,19 +556,17 @@ def main():
         l1.record(stream)
         torch.cuda.synchronize()
         link_gbs = nl * 4 / (l0.elapsed_time(l1) * 1e-3) / 1e9
-        te = torch.tensor([a.elapsed_time(b) / args.e2e_steps], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * ops_per_step(w) / (float(te.item()) * 1e-3) / 1e12, "unit": UNIT,
+        te_ms = max_over_ranks(a.elapsed_time(b) / args.e2e_steps, world, "cuda")
+        e2e = {"value": whole_job_value(world, ops_per_step(w), te_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(gw.Xh.nbytes), "d2h_bytes_per_step": int(gw.Y.numel() * 4),
-               "ms_per_step": float(te.item()),
+               "ms_per_step": te_ms,
                "how": "tcbf_beamform_host on pinned host X and Y: chunks of batches, "
                       "host-to-device copy, pack + beamform and device-to-host copy of "
                       "neighbouring chunks overlapped on separate streams",
                "chunk": args.e2e_chunk or "auto (about batch / 16)",
                "d2h_link_gbs": link_gbs,
                "d2h_floor_ms": gw.Y.numel() * 4 / link_gbs / 1e6,
-               "frac_of_d2h_floor": gw.Y.numel() * 4 / link_gbs / 1e6 / float(te.item())}
+               "frac_of_d2h_floor": gw.Y.numel() * 4 / link_gbs / 1e6 / te_ms}
         del Xhost, Yhost
 
     # ---- roofline of the dominant kernel (the GEMM)
@@ -617,7 +630,7 @@ def main():
         "clocks": clocks,
         "autotune": tuning,
         "graph_step": {"ms_per_step": graph_ms,
-                       "value": world * ops / (graph_ms * 1e-3) / 1e12,
+                       "value": whole_job_value(world, ops, graph_ms),
                        "how": "tcbf_graph_capture of pack + beamform, replayed K times"},
         "device_status": status,
         "parity_sampled": parity,
