@@ -348,6 +348,16 @@ __device__ __forceinline__ void split_value(float v, uint8_t &hi, uint8_t &lo) {
     lo = e4m3(v - e4m3_to_float(hi));
 }
 
+// The same for two values at once (paired conversions): hi and lo hold
+// the bytes of (a, b) in their low and high byte.
+__device__ __forceinline__ void split_pair(float a, float b, uint16_t &hi, uint16_t &lo) {
+    const __nv_fp8x2_storage_t h = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const __half2 hb = __half2(__nv_cvt_fp8x2_to_halfraw2(h, __NV_E4M3));
+    const float2 back = __half22float2(hb);
+    hi = h;
+    lo = __nv_cvt_float2_to_fp8x2(make_float2(a - back.x, b - back.y), __NV_SATFINITE, __NV_E4M3);
+}
+
 template <typename S>
 __device__ __forceinline__ float2 load_f16_value(const void *src, size_t i) {
     __half re, im;
@@ -488,6 +498,128 @@ __global__ void __launch_bounds__(256) split8_pack_x_kernel(const void *__restri
     }
 }
 
+// X transpose + split in one pass when all of K fits on chip (K <= 320):
+// a CTA of 8 TN threads takes TN samples of one batch, loads every K row of
+// them (16-byte loads of four values into a word tile, column
+// n ^ 4 ((k / 8) % (TN / 4))), takes each sample's largest magnitude over K
+// and both planes, splits every value once into its hi and lo bytes into a
+// staged output tile (rows of 2 x Kb2 bytes, padded by 16 so the row writes
+// of a warp hit distinct banks), and writes the packed rows out
+// contiguously.  Small tiles keep several CTAs per SM, so one CTA's loads
+// overlap another's split and stores.
+constexpr int kSplitFusedMaxK = 320;
+
+template <int TN>
+struct SplitFusedSmem {
+    static __host__ __device__ int rows(int K) { return (K + 63) / 64 * 64; }
+    static __host__ __device__ int out_pitch(int Kb2) { return 2 * Kb2 + 16; }
+    static __host__ __device__ int bytes(int K, int Kb2) {
+        return rows(K) * TN * 4 + TN * out_pitch(Kb2) + 8 * TN * 4 + TN * 4;
+    }
+};
+
+template <typename S, bool VEC, int TN>
+__global__ void __launch_bounds__(8 * TN) split8_pack_x_fused_kernel(const void *__restrict__ src,
+                                                                     uint8_t *__restrict__ dst,
+                                                                     int32_t *__restrict__ exps,
+                                                                     int64_t B, int K, int N,
+                                                                     int Kb2) {
+    using L = SplitFusedSmem<TN>;
+    constexpr int SW = TN / 4 - 1;                        // column swizzle mask (in 4-word units)
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int R = L::rows(K);                             // K rows incl. zero pad to 64
+    const int pitch = L::out_pitch(Kb2);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(sm);                 // [R][TN] words
+    uint8_t *out = sm + R * TN * 4;                                     // [TN][pitch]
+    float *red = reinterpret_cast<float *>(out + TN * pitch);           // [8][TN]
+    int *es = reinterpret_cast<int *>(red + 8 * TN);                    // [TN]
+    const int tid = threadIdx.x;
+    const int n_tiles = (N + TN - 1) / TN;
+    const int64_t total = B * n_tiles;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        const int64_t b = t / n_tiles;
+        const int n0 = static_cast<int>(t % n_tiles) * TN;
+        // load: TN / 4 threads per row, 32 rows per round
+        const int q = tid % (TN / 4);
+        for (int k = tid / (TN / 4); k < R; k += 32) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            const int n = n0 + 4 * q;
+            if (k < K) {
+                const size_t e = (static_cast<size_t>(b) * K + k) * N + n;
+                if (VEC && n + 3 < N) {
+                    S::load4(src, e, w);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (n + j < N) w[j] = S::load_word(src, e + j);
+                }
+            }
+            const int col = (4 * q) ^ (4 * ((k >> 3) & SW));
+            *reinterpret_cast<uint4 *>(&tile[k * TN + col]) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        __syncthreads();
+        // largest magnitude per sample: 8 threads per sample, then combined
+        {
+            const int n = tid % TN, part = tid / TN;
+            float amax = 0.f;
+            for (int k = part; k < R; k += 8) {
+                const uint32_t v = tile[k * TN + (n ^ (4 * ((k >> 3) & SW)))];
+                const __half2 h = *reinterpret_cast<const __half2 *>(&v);
+                amax = fmaxf(amax, fmaxf(fabsf(__low2float(h)), fabsf(__high2float(h))));
+            }
+            red[part * TN + n] = amax;
+        }
+        __syncthreads();
+        if (tid < TN) {
+            float amax = 0.f;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) amax = fmaxf(amax, red[p * TN + tid]);
+            const int e = split_exponent(amax);
+            es[tid] = e;
+            if (n0 + tid < N) exps[b * N + n0 + tid] = e;
+        }
+        __syncthreads();
+        // split: item -> (sample n fastest, plane, 16-element chunk c); hi and lo of
+        // every value once
+        const int chunks = R / 16;
+        for (int i = tid; i < TN * 2 * chunks; i += 8 * TN) {
+            const int n = i % TN;
+            const int p = (i / TN) & 1;
+            const int c = i / (2 * TN);
+            const float s = pow2f(es[n]);
+            __align__(16) uint16_t hi[8], lo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = 16 * c + 2 * j;
+                const uint32_t v0 = tile[k * TN + (n ^ (4 * ((k >> 3) & SW)))];
+                const uint32_t v1 = tile[(k + 1) * TN + (n ^ (4 * (((k + 1) >> 3) & SW)))];
+                const __half2 h0 = *reinterpret_cast<const __half2 *>(&v0);
+                const __half2 h1 = *reinterpret_cast<const __half2 *>(&v1);
+                const float a = (p == 0 ? __low2float(h0) : __high2float(h0)) * s;
+                const float b = (p == 0 ? __low2float(h1) : __high2float(h1)) * s;
+                split_pair(a, b, hi[j], lo[j]);
+            }
+            uint8_t *row = out + n * pitch + p * Kb2 + (c >> 2) * 128 + (c & 3) * 16;
+            *reinterpret_cast<uint4 *>(row) = *reinterpret_cast<const uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(row + 64) = *reinterpret_cast<const uint4 *>(lo);
+        }
+        __syncthreads();
+        // write the packed rows: 16-byte chunks, consecutive threads along a row
+        const int row_chunks = Kb2 / 16;
+        for (int i = tid; i < TN * 2 * row_chunks; i += 8 * TN) {
+            const int j = i % row_chunks;
+            const int rp = i / row_chunks;               // sample-major: (n, p)
+            const int n = rp >> 1, p = rp & 1;
+            if (n0 + n < N) {
+                uint8_t *grow = dst + (static_cast<size_t>(b * 2 + p) * N + n0 + n) * Kb2;
+                *reinterpret_cast<uint4 *>(grow + 16 * j) =
+                    *reinterpret_cast<const uint4 *>(out + n * pitch + p * Kb2 + 16 * j);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_pack_split8_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
@@ -518,6 +650,28 @@ cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void
     dim3 grid(bx, static_cast<unsigned>(B));
     const int k_chunks = static_cast<int>(ceil_div(pl.p.K, 256));
     const int g_amax = grid_for(B * N * k_chunks, 256, pl.num_sms);
+    if (pl.p.K <= kSplitFusedMaxK) {
+        constexpr int TN = 16;
+        const int smem = SplitFusedSmem<TN>::bytes(int(pl.p.K), Kb2);
+        const bool vec = N % 4 == 0;
+        const int K = int(pl.p.K), Ni = int(N);
+        auto launch = [&](auto kern) -> cudaError_t {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 8 * TN, smem);
+            if (e != cudaSuccess) return e;
+            const int64_t tiles = B * ceil_div(N, TN);
+            const int g = static_cast<int>(std::min<int64_t>(tiles, int64_t(pl.num_sms) * std::max(1, per_sm)));
+            kern<<<g, 8 * TN, smem, s>>>(src, d, ex, B, K, Ni, Kb2);
+            return cudaGetLastError();
+        };
+        if (src_type == TCBF_SRC_CF16)
+            return vec ? launch(split8_pack_x_fused_kernel<CF16, true, TN>)
+                       : launch(split8_pack_x_fused_kernel<CF16, false, TN>);
+        return vec ? launch(split8_pack_x_fused_kernel<CF32, true, TN>)
+                   : launch(split8_pack_x_fused_kernel<CF32, false, TN>);
+    }
     cudaError_t e = cudaMemsetAsync(ex, 0, sizeof(int32_t) * B * N, s);
     if (e != cudaSuccess) return e;
     if (src_type == TCBF_SRC_CF16) {

@@ -42,7 +42,7 @@ def _decode_split(raw, nb, rows, K):
     return hi, lo, ex
 
 
-def _run(W, X, config=None):
+def _run(W, X, config=None, src_type=0):
     import torch
     from gpu_util import dev
     Bw, M, K, _ = W.shape
@@ -53,8 +53,8 @@ def _run(W, X, config=None):
         Wp = torch.empty(plan.packed_size(0), dtype=torch.uint8, device="cuda")
         Xp = torch.empty(plan.packed_size(1), dtype=torch.uint8, device="cuda")
         Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
-        plan.transpose_pack(0, dev(W), Wp)
-        plan.transpose_pack(1, dev(X), Xp)
+        plan.transpose_pack(0, dev(W), Wp, src_type)
+        plan.transpose_pack(1, dev(X), Xp, src_type)
         plan.beamform_fp8split(Wp, Xp, Y)
         torch.cuda.synchronize()
         assert plan.last_device_error() == 0
@@ -62,11 +62,17 @@ def _run(W, X, config=None):
         return Yh[..., 0] + 1j * Yh[..., 1], Wp.cpu().numpy(), Xp.cpu().numpy()
 
 
-@pytest.mark.parametrize("B,M,N,K", [(1, 3, 5, 7), (2, 70, 130, 100), (2, 128, 256, 288)])
-def test_split_pack_matches_oracle_exactly(B, M, N, K):
+# K <= 320 packs X in one on-chip pass, longer K in two; N % 4 picks 16-byte loads
+@pytest.mark.parametrize("B,M,N,K,src", [(1, 3, 5, 7, 0), (2, 70, 130, 100, 0), (2, 128, 256, 288, 0),
+                                         (2, 40, 96, 320, 0), (1, 64, 68, 400, 0),
+                                         (2, 33, 72, 150, 1), (1, 20, 66, 77, 1)])
+def test_split_pack_matches_oracle_exactly(B, M, N, K, src):
     W, X = ti.small_fp16(seed=M + K, M=M, K=K, N=N, B=B)
     X[0, 0, :3, 0] = np.array([0.0, -0.0, 6e-8], np.float16)
-    _, Wraw, Xraw = _run(W, X)
+    if src == 1:            # FP32 sources holding FP16 values: the same packed bytes
+        _, Wraw, Xraw = _run(W.astype(np.float32), X.astype(np.float32), src_type=1)
+    else:
+        _, Wraw, Xraw = _run(W, X)
     (Wh, Wl, eW), (Xh, Xl, eX) = oracle.split_operands(W, X)
     hi, lo, ex = _decode_split(Wraw, B, M, K)
     assert np.array_equal(ex, eW)
