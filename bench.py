@@ -48,6 +48,7 @@ WORKLOADS = {
              "(110-190 MHz, 3 km disk, beams within 5 deg of zenith)"),
     "ultrasound": dict(
         mode="fp16", B=1, M=65536, N=256, K=16384, w_batches=1, geometry="ultrasound",
+        stacked=True,
         desc="computational ultrasound FP16: 65536 voxels x 16384 (128 elements x 128 "
              "frequency bins) x 256 frames, near-field model matrix"),
     "onebit": dict(
@@ -341,7 +342,10 @@ class GpuWorkload:
         self.Xh = host_x(w)
         self.Xd = torch.from_numpy(self.Xh).cuda()
         mode = {"1bit": tcbf.MODE_1BIT, "fp8split": tcbf.MODE_FP8SPLIT}.get(w["mode"], tcbf.MODE_FP16)
-        self.plan = tcbf.Plan(B, M, N, K, mode, w_batches=Bw, device=local)
+        # compute-bound FP16 shapes pack X with a third, negated plane (two N = 256
+        # MMAs per K step); plain FP16 elsewhere
+        flags = tcbf.FLAG_STACKED_X if (w.get("stacked") and mode == tcbf.MODE_FP16) else 0
+        self.plan = tcbf.Plan(B, M, N, K, mode, w_batches=Bw, device=local, flags=flags)
         if config is not None:
             self.plan.set_config(config)
         self.Wp = torch.empty(self.plan.packed_size(0), dtype=torch.uint8, device="cuda")

@@ -69,8 +69,19 @@ typedef struct {
     int64_t w_batches;  /* distinct weight matrices; batch b uses W[b / (batch / w_batches)].
                            0 means batch. Must divide batch. */
     int32_t mode;       /* tcbf_mode */
-    uint32_t flags;     /* reserved, must be 0 */
+    uint32_t flags;     /* tcbf_flag bits; others reserved, must be 0 */
 } tcbf_problem;
+
+/* Problem flags. */
+typedef enum {
+    /* FP16 only: packed X carries a third, negated plane ([-Xi, Xr, Xi],
+     * see the layouts below) so that the GEMM issues the complex product of
+     * Sec. III-B as two N = 256 MMAs per K step (Wr [Xr; Xi] + Wi [-Xi; Xr]
+     * = [Re | Im]) instead of four N = 128 ones.  For compute-bound shapes
+     * (large K and M, small N); it costs 1.5 x the packed X bytes.  Selects
+     * the stacked kernel configurations. */
+    TCBF_FLAG_STACKED_X = 1u
+} tcbf_flag;
 
 /*
  * Packed operand layouts (produced by tcbf_transpose_pack or
@@ -78,7 +89,9 @@ typedef struct {
  * needs its inputs split into real and imaginary planes (Sec. VI) and tiled
  * in device memory (Sec. III); here both operands are stored K-contiguous:
  *   FP16 W : [w_batches][2][M][Kp] binary16, Kp = K rounded up to 8, zero pad
- *   FP16 X : [batch][2][N][Kp]     binary16 (X transposed: samples are rows)
+ *   FP16 X : [batch][2][N][Kp]     binary16 (X transposed: samples are rows);
+ *            with TCBF_FLAG_STACKED_X [batch][3][N][Kp], planes -Xi, Xr, Xi
+ *            (-Xi: the Xi plane with every sign bit flipped, its pad -0.0)
  *   1-bit W: [w_batches][2][M][Kw] uint32,   Kw = 4 * ceil(K / 128)
  *   1-bit X: [batch][2][N][Kw]     uint32
  * Plane 0 is the real part, plane 1 the imaginary part.  1-bit element k

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "TCBF_OK", 1: "TCBF_ERR_INVALID_ARG", 2: "TCBF_ERR_UNSUPPORTE
                 6: "TCBF_ERR_TIMEOUT", 7: "TCBF_ERR_DEVICE"}
 MODE_FP16, MODE_FP8SPLIT, MODE_1BIT = 0, 1, 2
 SRC_CF16, SRC_CF32 = 0, 1
+FLAG_STACKED_X = 1
 
 # every symbol include/tcbf.h declares
 EXPORTED = [
@@ -117,10 +118,10 @@ def _stream(stream):
 class Plan:
     """A tcbf plan: one problem shape, mode and device."""
 
-    def __init__(self, batch, M, N, K, mode=MODE_FP16, w_batches=0, device=0):
+    def __init__(self, batch, M, N, K, mode=MODE_FP16, w_batches=0, device=0, flags=0):
         lib = load()
         self._lib = lib
-        self.problem = Problem(batch, M, N, K, w_batches, mode, 0)
+        self.problem = Problem(batch, M, N, K, w_batches, mode, flags)
         h = ctypes.c_void_p()
         _check(lib.tcbf_plan_create(ctypes.byref(h), ctypes.byref(self.problem), device),
                "tcbf_plan_create")
@@ -129,6 +130,7 @@ class Plan:
         self.w_batches = w_batches or batch
         self.mode = mode
         self.device = device
+        self.flags = flags
 
     def close(self):
         if getattr(self, "handle", None):

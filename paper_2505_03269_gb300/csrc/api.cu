@@ -67,7 +67,7 @@ size_t packed_bytes(const tcbf_plan_s &pl, int which) {
     const int64_t rows = which == 0 ? p.M : p.N;
     switch (p.mode) {
         case TCBF_MODE_FP16:
-            return static_cast<size_t>(nb * 2 * rows * pl.Kp * 2);
+            return static_cast<size_t>(nb * (which == 0 ? 2 : x_planes(pl)) * rows * pl.Kp * 2);
         case TCBF_MODE_1BIT:
             return static_cast<size_t>(nb * 2 * rows * pl.Kw * 4);
         case TCBF_MODE_FP8SPLIT:   // hi/lo bytes, then one int32 scale exponent per row
@@ -119,7 +119,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     if (q.batch % q.w_batches != 0) return TCBF_ERR_INVALID_ARG;
     if (q.mode != TCBF_MODE_FP16 && q.mode != TCBF_MODE_FP8SPLIT && q.mode != TCBF_MODE_1BIT)
         return TCBF_ERR_INVALID_ARG;
-    if (q.flags != 0) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & ~uint32_t(TCBF_FLAG_STACKED_X)) != 0) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & TCBF_FLAG_STACKED_X) && q.mode != TCBF_MODE_FP16) return TCBF_ERR_INVALID_ARG;
     if (q.M > kMaxDim || q.N > kMaxDim || q.K > kMaxDim || q.batch > 65535)
         return TCBF_ERR_UNSUPPORTED;
     // 1-bit sums are exact integers in the FP32 accumulators while 2K < 2^24
@@ -277,7 +278,9 @@ TCBF_EXPORT tcbf_status tcbf_last_device_error(tcbf_plan_t plan) {
 
 TCBF_EXPORT tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count) {
     if (!plan || !count) return TCBF_ERR_INVALID_ARG;
-    *count = plan->p.mode == TCBF_MODE_1BIT ? gemm_1bit_num_configs() : gemm_f16_num_configs();
+    *count = plan->p.mode == TCBF_MODE_1BIT              ? gemm_1bit_num_configs()
+             : (plan->p.flags & TCBF_FLAG_STACKED_X) ? gemm_f16_stacked_num_configs()
+                                                     : gemm_f16_num_configs();
     return TCBF_OK;
 }
 
@@ -292,7 +295,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
     int n = 0;
     tcbf_plan_num_configs(plan, &n);
     if (config < 0 || config >= n) return TCBF_ERR_INVALID_ARG;
-    if (plan->p.mode != TCBF_MODE_1BIT && !gemm_f16_config_valid(config, plan->p.K))
+    if (plan->p.mode != TCBF_MODE_1BIT && !(plan->p.flags & TCBF_FLAG_STACKED_X) &&
+        !gemm_f16_config_valid(config, plan->p.K))
         return TCBF_ERR_INVALID_ARG;
     plan->config = config;   // a captured graph keeps the configuration it was captured with
     return TCBF_OK;
@@ -300,6 +304,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
 
 TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
     if (!plan) return "invalid";
+    if (plan->p.flags & TCBF_FLAG_STACKED_X) return gemm_f16_stacked_config_name(config);
     if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
     if (plan->p.mode == TCBF_MODE_1BIT) return gemm_1bit_config_name(config);
     return gemm_split8_config_name(config);
@@ -329,6 +334,7 @@ cudaError_t launch_pack_x(const tcbf_plan_s &pl, int src_type, const void *src, 
 
 bool config_ok(const tcbf_plan_s &pl, int c) {
     if (pl.p.mode == TCBF_MODE_1BIT) return c >= 0 && c < gemm_1bit_num_configs();
+    if (pl.p.flags & TCBF_FLAG_STACKED_X) return c >= 0 && c < gemm_f16_stacked_num_configs();
     return gemm_f16_config_valid(c, pl.p.K);
 }
 

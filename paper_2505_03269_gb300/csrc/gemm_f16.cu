@@ -1077,6 +1077,7 @@ cudaError_t launch_gemm_split8(const tcbf_plan_s &pl, const void *Wp, const void
 
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s) {
+    if (pl.p.flags & TCBF_FLAG_STACKED_X) return launch_gemm_f16_stacked(pl, Wp, Xp, Y, s);
     const int c = (pl.config >= 0 && pl.config < gemm_f16_num_configs()) ? pl.config : 0;
     return kConfigs[c].fn(pl, Wp, Xp, Y, s, kConfigs[c].raster);
 }

@@ -100,7 +100,7 @@ int64_t src_bytes(int src_type) { return src_type == TCBF_SRC_CF16 ? 4 : 8; }
 int64_t packed_x_bytes(const tcbf_plan_s &pl, int64_t nb) {
     const int64_t N = pl.p.N;
     switch (pl.p.mode) {
-        case TCBF_MODE_FP16: return nb * 2 * N * pl.Kp * 2;
+        case TCBF_MODE_FP16: return nb * x_planes(pl) * N * pl.Kp * 2;
         case TCBF_MODE_1BIT: return nb * 2 * N * pl.Kw * 4;
         default: return nb * 2 * N * pl.Kb2 + nb * N * 4;
     }

@@ -121,7 +121,9 @@ __global__ void pack_f16_w_kernel(const void *__restrict__ src, __half *__restri
 constexpr int TT = 64;
 constexpr int TPITCH = TT + 2;   // halves; odd word pitch spreads banks (split-FP8 X pack)
 
-template <typename S, bool VEC>
+// PL = 3 writes the stacked layout: planes -Xi, Xr, Xi (the sign bits of
+// the imaginary halves flipped for the first).
+template <typename S, bool VEC, int PL>
 __global__ void __launch_bounds__(256) pack_f16_x_kernel(const void *__restrict__ src,
                                                         __half *__restrict__ dst, int K, int N,
                                                         int Kp, int k_tiles, int n_tiles) {
@@ -175,10 +177,16 @@ __global__ void __launch_bounds__(256) pack_f16_x_kernel(const void *__restrict_
                 im.y = __byte_perm(v[2], v[3], 0x7632);
                 im.z = __byte_perm(v[4], v[5], 0x7632);
                 im.w = __byte_perm(v[6], v[7], 0x7632);
-                const size_t o_re = (static_cast<size_t>(b * 2 + 0) * N + n) * Kp + k;
-                const size_t o_im = (static_cast<size_t>(b * 2 + 1) * N + n) * Kp + k;
+                const size_t o_re = (static_cast<size_t>(b * PL + PL - 2) * N + n) * Kp + k;
+                const size_t o_im = (static_cast<size_t>(b * PL + PL - 1) * N + n) * Kp + k;
                 *reinterpret_cast<uint4 *>(dst + o_re) = re;
                 *reinterpret_cast<uint4 *>(dst + o_im) = im;
+                if (PL == 3) {
+                    const size_t o_neg = (static_cast<size_t>(b * PL) * N + n) * Kp + k;
+                    *reinterpret_cast<uint4 *>(dst + o_neg) =
+                        make_uint4(im.x ^ 0x80008000u, im.y ^ 0x80008000u, im.z ^ 0x80008000u,
+                                   im.w ^ 0x80008000u);
+                }
             }
         }
         __syncthreads();
@@ -268,16 +276,18 @@ cudaError_t launch_pack_f16_x(const tcbf_plan_s &pl, int src_type, const void *s
     // 16-byte loads of four values need every row of X to start 16-byte aligned
     const bool vec = pl.p.N % 4 == 0;
     const int K = int(pl.p.K), N = int(pl.p.N), Kp = int(pl.Kp);
+    auto run = [&](auto kern) { kern<<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles); };
+    const bool stacked = x_planes(pl) == 3;
     if (src_type == TCBF_SRC_CF16) {
-        if (vec)
-            pack_f16_x_kernel<CF16, true><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+        if (stacked)
+            vec ? run(pack_f16_x_kernel<CF16, true, 3>) : run(pack_f16_x_kernel<CF16, false, 3>);
         else
-            pack_f16_x_kernel<CF16, false><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+            vec ? run(pack_f16_x_kernel<CF16, true, 2>) : run(pack_f16_x_kernel<CF16, false, 2>);
     } else {
-        if (vec)
-            pack_f16_x_kernel<CF32, true><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+        if (stacked)
+            vec ? run(pack_f16_x_kernel<CF32, true, 3>) : run(pack_f16_x_kernel<CF32, false, 3>);
         else
-            pack_f16_x_kernel<CF32, false><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+            vec ? run(pack_f16_x_kernel<CF32, true, 2>) : run(pack_f16_x_kernel<CF32, false, 2>);
     }
     return cudaGetLastError();
 }

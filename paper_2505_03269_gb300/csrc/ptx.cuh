@@ -347,6 +347,19 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
     return d;
 }
 
+// The same for a K-major operand with 64-byte swizzle: 64-byte rows (32
+// FP16 of K), 8-row atoms of 512 bytes stacked at stride 512.  The tile base
+// must be 512-byte aligned; the second K16 step of a row starts 32 bytes in.
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);   // start address >> 4, bits 0-13
+    d |= static_cast<uint64_t>(1) << 16;                    // leading byte offset (unused here)
+    d |= static_cast<uint64_t>(512 >> 4) << 32;             // stride byte offset >> 4
+    d |= static_cast<uint64_t>(1) << 46;                    // descriptor version for tcgen05
+    d |= static_cast<uint64_t>(4) << 61;                    // swizzle mode: 64-byte
+    return d;
+}
+
 // Instruction descriptor, dense MMA with FP32 accumulator, K-major A and B.
 // ab_format: kind::f16 -> 0 = f16, 1 = bf16; kind::f8f6f4 -> 0 = e4m3,
 // 1 = e5m2, 3 = e2m3, 4 = e3m2, 5 = e2m1.

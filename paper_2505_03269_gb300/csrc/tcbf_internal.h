@@ -68,6 +68,17 @@ const char *gemm_split8_config_name(int config);   // split-FP8 uses the FP16 ti
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s);
 
+// Stacked-plane FP16 GEMM (plans with TCBF_FLAG_STACKED_X).
+int gemm_f16_stacked_num_configs();
+const char *gemm_f16_stacked_config_name(int config);
+cudaError_t launch_gemm_f16_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                                    cudaStream_t s);
+
+// Planes of packed FP16 X: 3 with TCBF_FLAG_STACKED_X, else 2.
+inline int64_t x_planes(const tcbf_plan_s &pl) {
+    return (pl.p.flags & TCBF_FLAG_STACKED_X) ? 3 : 2;
+}
+
 int gemm_1bit_num_configs();
 const char *gemm_1bit_config_name(int config);
 cudaError_t launch_gemm_1bit(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,

@@ -1,0 +1,143 @@
+"""FP16 plans with stacked sample planes (TCBF_FLAG_STACKED_X).
+
+The packed X holds [-Xi, Xr, Xi]; the GEMM issues Wr [Xr; Xi] + Wi [-Xi; Xr]
+as two N = 256 MMAs per K step.  Bars: the packed bytes are the plain
+planes plus the sign-flipped imaginary plane, bit for bit; the product is
+within the FP16 parity bar of the FP64 oracle; and because every output
+element is summed in the same order as in the four-MMA kernel (Wr Xr then
+-Wi Xi, Wr Xi then Wi Xr, promoted every 2048 K in both), the two paths
+agree bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import tcbf_inputs as ti
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import ensure_lib
+    return ensure_lib()
+
+
+def _run(W, X, stacked=True, config=None, src_type=0, rows=None, packed=False):
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_STACKED_X, MODE_FP16, Plan
+    Bw, M, K, _ = W.shape
+    B, _, N, _ = X.shape
+    with Plan(B, M, N, K, MODE_FP16, w_batches=Bw, flags=FLAG_STACKED_X if stacked else 0) as plan:
+        if config is not None:
+            plan.set_config(config)
+        if rows is not None:
+            plan.set_batch_rows(rows)
+        Wp = empty_bytes(plan.packed_size(0))
+        Xp = empty_bytes(plan.packed_size(1))
+        Y = torch.full((B, M, N, 2), float("nan"), dtype=torch.float32, device="cuda")
+        plan.transpose_pack(0, dev(W), Wp, src_type)
+        plan.transpose_pack(1, dev(X), Xp, src_type)
+        plan.beamform_fp16(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        Yh = Y.cpu().numpy().astype(np.float64)
+        out = Yh[..., 0] + 1j * Yh[..., 1]
+        if packed:
+            return out, Xp.cpu().numpy(), (K + 7) // 8 * 8
+        return out
+
+
+@pytest.mark.parametrize("B,N,K,src", [(2, 130, 77, 0), (1, 256, 288, 0), (2, 68, 40, 1),
+                                       (1, 7, 3, 0)])
+def test_stacked_pack_layout_bit_exact(B, N, K, src):
+    W, X = ti.small_fp16(seed=N + K, M=16, K=K, N=N, B=B)
+    if src == 1:
+        _, Xp, Kp = _run(W.astype(np.float32), X.astype(np.float32), src_type=1, packed=True)
+    else:
+        _, Xp, Kp = _run(W, X, packed=True)
+    Xp = Xp[: B * 3 * N * Kp * 2].view(np.uint16).reshape(B, 3, N, Kp)
+    Xt = np.ascontiguousarray(X.transpose(0, 2, 1, 3))          # [B][N][K][2]
+    want = np.zeros((B, 3, N, Kp), np.uint16)
+    want[:, 1, :, :K] = Xt[..., 0].view(np.uint16)
+    want[:, 2, :, :K] = Xt[..., 1].view(np.uint16)
+    want[:, 0] = want[:, 2] ^ 0x8000     # -Xi: every sign bit flipped, zero pad included
+    assert np.array_equal(Xp, want)
+
+
+@pytest.mark.parametrize("config", [0, 1, 2])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (3, 5, 7), (129, 130, 288), (127, 257, 129),
+                                   (200, 96, 64), (64, 1024, 200)])
+def test_stacked_ragged_shapes(config, M, N, K):
+    W, X = ti.small_fp16(seed=M * 7 + N + K, M=M, K=K, N=N, B=2)
+    Y = _run(W, X, config=config)
+    assert oracle.rel_frobenius(Y, oracle.cgemm(W, X)) <= TOL
+
+
+@pytest.mark.parametrize("K", [300, 5000])
+def test_stacked_equals_four_mma_kernel_bit_for_bit(K):
+    W, _ = ti.small_fp16(seed=K, M=260, K=K, N=8, B=2)
+    X = ti.complex_gaussian_fp16(ti.rng(K + 1), (4, K, 300))
+    Ys = _run(W, X, stacked=True)
+    Y0 = _run(W, X, stacked=False)
+    assert np.array_equal(Ys, Y0)
+    assert oracle.rel_frobenius(Ys, oracle.cgemm(W, X)) <= TOL
+
+
+def test_stacked_integer_inputs_bit_exact():
+    g = ti.rng(1)
+    W = ti.integer_complex_fp16(g, (2, 150, 300))
+    X = ti.integer_complex_fp16(g, (4, 300, 270))
+    assert np.array_equal(_run(W, X), oracle.cgemm(W, X))
+
+
+def test_stacked_identity_and_imaginary_identity():
+    K, N = 96, 200
+    _, X = ti.small_fp16(seed=5, M=1, K=K, N=N)
+    Xc = X[..., 0].astype(np.float64) + 1j * X[..., 1].astype(np.float64)
+    for part, factor in ((0, 1.0), (1, 1j)):
+        W = np.zeros((1, K, K, 2), np.float16)
+        W[0, np.arange(K), np.arange(K), part] = 1.0
+        assert np.array_equal(_run(W, X), factor * Xc)
+
+
+@pytest.mark.parametrize("K", [8192, 16384])
+def test_stacked_long_k_within_tolerance(K):
+    W, _ = ti.small_fp16(seed=K, M=256, K=K, N=8)
+    X = ti.complex_gaussian_fp16(ti.rng(K), (1, K, 256))
+    assert oracle.rel_frobenius(_run(W, X), oracle.cgemm(W, X)) <= TOL
+
+
+def test_stacked_uneven_beam_counts():
+    rows = [300, 1, 129]
+    W, _ = ti.small_fp16(seed=21, M=300, K=100, N=8, B=3)
+    X = ti.complex_gaussian_fp16(ti.rng(22), (3, 100, 200))
+    Y = _run(W, X, rows=rows)
+    Yref = oracle.cgemm(W, X)
+    for b, r in enumerate(rows):
+        assert oracle.rel_frobenius(Y[b, :r], Yref[b, :r]) <= TOL
+
+
+def test_stacked_host_pipeline():
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_STACKED_X, MODE_FP16, Plan
+    W, X = ti.small_fp16(seed=9, M=130, K=150, N=260, B=6)
+    W = np.ascontiguousarray(W[:3])
+    Yd = _run(W, X)
+    with Plan(6, 130, 260, 150, MODE_FP16, w_batches=3, flags=FLAG_STACKED_X) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        plan.transpose_pack(0, dev(W), Wp)
+        Xh = torch.from_numpy(X).pin_memory()
+        Yh = torch.empty((6, 130, 260, 2), dtype=torch.float32).pin_memory()
+        s = torch.cuda.Stream()
+        plan.beamform_host(Xh, Wp, Yh, chunk=2, stream=s)
+        s.synchronize()
+        assert plan.last_device_error() == 0
+    Yn = Yh.numpy().astype(np.float64)
+    assert np.array_equal(Yn[..., 0] + 1j * Yn[..., 1], Yd)
