@@ -136,42 +136,69 @@ struct StageWords {
     int valid[RP];
 };
 
-// Load stage `i` of this CTA's flattened (tile, stage) sequence.
+// Walks this CTA's flattened (tile, stage) sequence for one converter
+// thread, two stages ahead of the expansion.  The tile decode and the row
+// addresses of the thread's row-planes are computed once per tile; a stage
+// then only advances K by 128 (4 words).
 template <int BN>
-__device__ __forceinline__ void load_stage(const Args1 &args, int ct, int i, int iters,
-                                           StageWords<BN> &w) {
+struct StageCursor {
+    static constexpr int RP = StageWords<BN>::RP;
+    const uint32_t *row[RP];     // packed words of the current tile's row-planes (nullptr: zero row)
+    int t, kb, num_kb, total, step;
+
+    __device__ void start_tile(const Args1 &args, int ct) {
+        if (t >= total) return;
+        int b, mt, nt;
+        decode_tile(t, args, b, mt, nt);
 #pragma unroll
-    for (int j = 0; j < StageWords<BN>::RP; ++j) {
-        w.w[j] = make_uint4(0, 0, 0, 0);
-        w.valid[j] = 0;
-    }
-    if (i >= iters) return;
-    const int t = blockIdx.x + (i / args.num_kb) * gridDim.x;
-    const int kb = i % args.num_kb;
-    int b, mt, nt;
-    decode_tile(t, args, b, mt, nt);
-    const int valid = args.K - kb * BKE;
-#pragma unroll
-    for (int j = 0; j < StageWords<BN>::RP; ++j) {
-        const int rp = ct + j * kConv;
-        const uint32_t *src = nullptr;
-        if (rp < 2 * BM) {
-            const int plane = rp / BM, mrow = mt * BM + rp % BM;
-            if (mrow < args.M)
-                src = args.Wb + (static_cast<size_t>((b / args.per_w) * 2 + plane) * args.M + mrow) *
-                                    args.Kw + kb * 4;
-        } else if (rp < 2 * (BM + BN)) {
-            const int x = rp - 2 * BM;
-            const int plane = x / BN, nrow = nt * BN + x % BN;
-            if (nrow < args.N)
-                src = args.Xb + (static_cast<size_t>(b * 2 + plane) * args.N + nrow) * args.Kw + kb * 4;
-        }
-        if (src) {
-            w.w[j] = __ldg(reinterpret_cast<const uint4 *>(src));
-            w.valid[j] = valid;
+        for (int j = 0; j < RP; ++j) {
+            const int rp = ct + j * kConv;
+            row[j] = nullptr;
+            if (rp < 2 * BM) {
+                const int plane = rp / BM, mrow = mt * BM + rp % BM;
+                if (mrow < args.M)
+                    row[j] = args.Wb +
+                             (static_cast<size_t>((b / args.per_w) * 2 + plane) * args.M + mrow) * args.Kw;
+            } else if (rp < 2 * (BM + BN)) {
+                const int x = rp - 2 * BM;
+                const int plane = x / BN, nrow = nt * BN + x % BN;
+                if (nrow < args.N)
+                    row[j] = args.Xb + (static_cast<size_t>(b * 2 + plane) * args.N + nrow) * args.Kw;
+            }
         }
     }
-}
+
+    __device__ void init(const Args1 &args, int ct) {
+        t = blockIdx.x;
+        kb = 0;
+        num_kb = args.num_kb;
+        total = args.total_tiles;
+        step = gridDim.x;
+        start_tile(args, ct);
+    }
+
+    // the words of the cursor's stage, then advance to the next stage
+    __device__ void load(const Args1 &args, int ct, StageWords<BN> &w) {
+#pragma unroll
+        for (int j = 0; j < RP; ++j) {
+            w.w[j] = make_uint4(0, 0, 0, 0);
+            w.valid[j] = 0;
+        }
+        if (t >= total) return;
+        const int valid = args.K - kb * BKE;
+#pragma unroll
+        for (int j = 0; j < RP; ++j)
+            if (row[j]) {
+                w.w[j] = __ldg(reinterpret_cast<const uint4 *>(row[j] + kb * 4));
+                w.valid[j] = valid;
+            }
+        if (++kb == num_kb) {
+            kb = 0;
+            t += step;
+            start_tile(args, ct);
+        }
+    }
+};
 
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -281,15 +308,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ct = threadIdx.x - 32;               // 0..kConv-1
         const int my_tiles = (args.total_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
         const int iters = my_tiles * args.num_kb;
+        StageCursor<BN> cursor;
+        cursor.init(args, ct);
         StageWords<BN> cur, nxt;
-        load_stage<BN>(args, ct, 0, iters, cur);
-        load_stage<BN>(args, ct, 1, iters, nxt);
+        cursor.load(args, ct, cur);
+        cursor.load(args, ct, nxt);
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
         for (int i = 0; i < iters; ++i) {
             StageWords<BN> ahead;
-            load_stage<BN>(args, ct, i + 2, iters, ahead);
+            cursor.load(args, ct, ahead);
             if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
                 ok = false;
                 break;
