@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full0 + 8 * s, kConv);
+            mbar_init(full0 + 8 * s, kConv / 32);       // one arrival per converter warp
             mbar_init(empty0 + 8 * s, 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             fence_async_smem();                        // generic writes -> tensor core reads
-            mbar_arrive(full0 + 8 * stage);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(full0 + 8 * stage);
             if (++stage == STAGES) {
                 stage = 0;
                 phase ^= 1u;
