@@ -50,12 +50,16 @@ struct Args1 {
     int num_kb, total_tiles;
 };
 
-template <int BN, int STAGES>
+// STK: stacked sample planes [-Xi, Xr, Xi] (the converters write the first
+// with flipped signs) so that Wr [Xr; Xi] + Wi [-Xi; Xr] = [Re | Im] is two
+// N = 2 BN MMAs per 32-K step into one 2 BN-column accumulator.
+template <int BN, int STAGES, bool STK = false>
 struct Cfg1 {
+    static constexpr int XPL = STK ? 3 : 2;                   // X planes per stage
     static constexpr int A_PLANE = BM * BKE;
     static constexpr int B_PLANE = BN * BKE;
     static constexpr int A_BYTES = 2 * A_PLANE;
-    static constexpr int STAGE_BYTES = A_BYTES + 2 * B_PLANE;
+    static constexpr int STAGE_BYTES = A_BYTES + XPL * B_PLANE;
     static constexpr int ACC_BUFS = (4 * BN <= 512) ? 2 : 1;
     static constexpr int TMEM_COLS = ACC_BUFS * 2 * BN <= 256 ? 256 : 512;
     static constexpr int STAGING_BYTES = 4 * 2 * 4096;
@@ -67,20 +71,22 @@ __device__ __forceinline__ void decode_tile(int t, const Args1 &a, int &b, int &
     tile_decode(a.tiles, t, b, mt, nt);
 }
 
-// 4 sign bits -> 4 E4M3 bytes: bit 1 -> 0x38 (+1.0), bit 0 -> 0xB8 (-1.0).
-// The multiply places bit j at bit 8j + 7 (copies at offsets 7, 14, 21, 28
-// do not overlap for a 4-bit value).
+// 4 sign bits -> 4 E4M3 bytes: bit 1 -> 0x38 (+1.0), bit 0 -> 0xB8 (-1.0);
+// NEG gives the negated values.  The multiply places bit j at bit 8j + 7
+// (copies at offsets 7, 14, 21, 28 do not overlap for a 4-bit value).
+template <bool NEG = false>
 __device__ __forceinline__ uint32_t expand4(uint32_t nib) {
-    return 0xB8B8B8B8u ^ ((nib * 0x10204080u) & 0x80808080u);
+    return (NEG ? 0x38383838u : 0xB8B8B8B8u) ^ ((nib * 0x10204080u) & 0x80808080u);
 }
 
 // 16 sign bits -> 16 E4M3 bytes; bytes whose element index is >= valid are 0.
+template <bool NEG = false>
 __device__ __forceinline__ uint4 expand16(uint32_t bits, int valid) {
     uint4 v;
-    v.x = expand4(bits & 15u);
-    v.y = expand4((bits >> 4) & 15u);
-    v.z = expand4((bits >> 8) & 15u);
-    v.w = expand4((bits >> 12) & 15u);
+    v.x = expand4<NEG>(bits & 15u);
+    v.y = expand4<NEG>((bits >> 4) & 15u);
+    v.z = expand4<NEG>((bits >> 8) & 15u);
+    v.w = expand4<NEG>((bits >> 12) & 15u);
     if (valid < 16) {
         uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -100,8 +106,9 @@ __device__ __forceinline__ void st_shared_u4(uint32_t addr, uint4 v) {
                  : "memory");
 }
 
-// Expand one row's 128 K (4 words) of one plane into the swizzled slot.
-// Full stages (valid >= 128) take the unmasked path.
+// Expand one row's 128 K (4 words) of one plane (negated if NEG) into the
+// swizzled slot.  Full stages (valid >= 128) take the unmasked path.
+template <bool NEG = false>
 __device__ __forceinline__ void expand_row(uint32_t row_base, int r, uint4 words, int valid) {
     const uint32_t w[4] = {words.x, words.y, words.z, words.w};
     const uint32_t sw = static_cast<uint32_t>(r & 7);
@@ -110,17 +117,17 @@ __device__ __forceinline__ void expand_row(uint32_t row_base, int r, uint4 words
         for (int c = 0; c < 8; ++c) {
             const uint32_t bits = w[c >> 1] >> (16 * (c & 1));
             uint4 v;
-            v.x = expand4(bits & 15u);
-            v.y = expand4((bits >> 4) & 15u);
-            v.z = expand4((bits >> 8) & 15u);
-            v.w = expand4((bits >> 12) & 15u);
+            v.x = expand4<NEG>(bits & 15u);
+            v.y = expand4<NEG>((bits >> 4) & 15u);
+            v.z = expand4<NEG>((bits >> 8) & 15u);
+            v.w = expand4<NEG>((bits >> 12) & 15u);
             st_shared_u4(row_base + ((c ^ sw) << 4), v);
         }
     } else {
 #pragma unroll 1
         for (int c = 0; c < 8; ++c) {
             const uint32_t bits = (w[c >> 1] >> (16 * (c & 1))) & 0xFFFFu;
-            st_shared_u4(row_base + ((c ^ sw) << 4), expand16(bits, valid - 16 * c));
+            st_shared_u4(row_base + ((c ^ sw) << 4), expand16<NEG>(bits, valid - 16 * c));
         }
     }
 }
@@ -129,9 +136,10 @@ __device__ __forceinline__ void expand_row(uint32_t row_base, int r, uint4 words
 // of X; converter thread ct takes ct, ct + kConv, ...  Each holds its packed
 // words and the number of valid K elements (0 for rows beyond M or N, which
 // are written as zeros).
-template <int BN>
+template <int BN, bool STK = false>
 struct StageWords {
-    static constexpr int RP = (2 * (BM + BN) + kConv - 1) / kConv;   // row-planes per thread
+    static constexpr int XPL = STK ? 3 : 2;
+    static constexpr int RP = (2 * BM + XPL * BN + kConv - 1) / kConv;   // row-planes per thread
     uint4 w[RP];
     int valid[RP];
 };
@@ -140,9 +148,10 @@ struct StageWords {
 // thread, two stages ahead of the expansion.  The tile decode and the row
 // addresses of the thread's row-planes are computed once per tile; a stage
 // then only advances K by 128 (4 words).
-template <int BN>
+template <int BN, bool STK = false>
 struct StageCursor {
-    static constexpr int RP = StageWords<BN>::RP;
+    static constexpr int RP = StageWords<BN, STK>::RP;
+    static constexpr int XPL = StageWords<BN, STK>::XPL;
     const uint32_t *row[RP];     // packed words of the current tile's row-planes (nullptr: zero row)
     int t, kb, num_kb, total, step;
 
@@ -159,9 +168,11 @@ struct StageCursor {
                 if (mrow < args.M)
                     row[j] = args.Wb +
                              (static_cast<size_t>((b / args.per_w) * 2 + plane) * args.M + mrow) * args.Kw;
-            } else if (rp < 2 * (BM + BN)) {
+            } else if (rp < 2 * BM + XPL * BN) {
                 const int x = rp - 2 * BM;
-                const int plane = x / BN, nrow = nt * BN + x % BN;
+                // stacked slots -Xi, Xr, Xi read the imaginary, real, imaginary bits
+                const int slot = x / BN, nrow = nt * BN + x % BN;
+                const int plane = STK ? (slot == 1 ? 0 : 1) : slot;
                 if (nrow < args.N)
                     row[j] = args.Xb + (static_cast<size_t>(b * 2 + plane) * args.N + nrow) * args.Kw;
             }
@@ -178,7 +189,7 @@ struct StageCursor {
     }
 
     // the words of the cursor's stage, then advance to the next stage
-    __device__ void load(const Args1 &args, int ct, StageWords<BN> &w) {
+    __device__ void load(const Args1 &args, int ct, StageWords<BN, STK> &w) {
 #pragma unroll
         for (int j = 0; j < RP; ++j) {
             w.w[j] = make_uint4(0, 0, 0, 0);
@@ -200,10 +211,10 @@ struct StageCursor {
     }
 };
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool STK>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_1bit_kernel(const __grid_constant__ CUtensorMap tmY, const Args1 args) {
-    using C = Cfg1<BN, STAGES>;
+    using C = Cfg1<BN, STAGES, STK>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -273,6 +284,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t a = s0 + stage * C::STAGE_BYTES;
                     const uint32_t bx = a + C::A_BYTES;
                     const int ksteps = min(BKE / 32, (args.K - kb * BKE + 31) / 32);
+                    if (STK) {
+                        // Wr [Xr; Xi] + Wi [-Xi; Xr] -> [Re | Im] (slots -Xi, Xr, Xi)
+                        constexpr uint32_t kIdesc2 = idesc_f32acc(BM, 2 * BN, 0, false);
+                        for (int j = 0; j < ksteps; ++j) {
+                            const uint32_t accum = (kb > 0 || j > 0) ? 1u : 0u;
+                            mma_f8f6f4(d_re, sdesc_kmajor_sw128(a + 32 * j),
+                                       sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j), kIdesc2, accum);
+                            mma_f8f6f4(d_re, sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j),
+                                       sdesc_kmajor_sw128(bx + 32 * j), kIdesc2, 1u);
+                        }
+                    } else
                     for (int j = 0; j < ksteps; ++j) {
                         const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
                         const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
@@ -308,16 +330,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ct = threadIdx.x - 32;               // 0..kConv-1
         const int my_tiles = (args.total_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
         const int iters = my_tiles * args.num_kb;
-        StageCursor<BN> cursor;
+        StageCursor<BN, STK> cursor;
         cursor.init(args, ct);
-        StageWords<BN> cur, nxt;
+        StageWords<BN, STK> cur, nxt;
         cursor.load(args, ct, cur);
         cursor.load(args, ct, nxt);
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
         for (int i = 0; i < iters; ++i) {
-            StageWords<BN> ahead;
+            StageWords<BN, STK> ahead;
             cursor.load(args, ct, ahead);
             if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
                 ok = false;
@@ -325,15 +347,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const uint32_t a = s0 + stage * C::STAGE_BYTES;
 #pragma unroll
-            for (int j = 0; j < StageWords<BN>::RP; ++j) {
+            for (int j = 0; j < StageWords<BN, STK>::RP; ++j) {
                 const int rp = ct + j * kConv;
                 if (rp < 2 * BM) {
                     const int r = rp % BM;
                     expand_row(a + (rp / BM) * C::A_PLANE + r * 128, r, cur.w[j], cur.valid[j]);
-                } else if (rp < 2 * (BM + BN)) {
+                } else if (rp < 2 * BM + C::XPL * BN) {
                     const int x = rp - 2 * BM, r = x % BN;
-                    expand_row(a + C::A_BYTES + (x / BN) * C::B_PLANE + r * 128, r, cur.w[j],
-                               cur.valid[j]);
+                    const uint32_t dst = a + C::A_BYTES + (x / BN) * C::B_PLANE + r * 128;
+                    if (STK && x < BN)                     // slot 0 holds -Xi
+                        expand_row<true>(dst, r, cur.w[j], cur.valid[j]);
+                    else
+                        expand_row(dst, r, cur.w[j], cur.valid[j]);
                 }
             }
             fence_async_smem();                        // generic writes -> tensor core reads
@@ -426,10 +451,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool STK = false>
 cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb, int32_t *Y,
                     cudaStream_t s, int raster) {
-    using C = Cfg1<BN, STAGES>;
+    using C = Cfg1<BN, STAGES, STK>;
     const tcbf_problem &p = pl.p;
     CUtensorMap tmY;
     const int tma_store = (p.N % 2 == 0) ? 1 : 0;
@@ -466,7 +491,7 @@ cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *X
                           a.tiles.n_tiles;
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
-    auto kern = cgemm_1bit_kernel<BN, STAGES>;
+    auto kern = cgemm_1bit_kernel<BN, STAGES, STK>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -487,6 +512,8 @@ const Config1 kConfigs1[] = {
     {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double n-fastest", 0, launch1<128, 3>},
     {"1bit->e4m3 BM128 BN256 BK128 stages2 tmem-single m-fastest", 1, launch1<256, 2>},
     {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double m-fastest", 1, launch1<128, 3>},
+    {"1bit->e4m3 stacked [-Xi,Xr,Xi] N256 BM128 BN128 BK128 stages2 tmem-double n-fastest", 0,
+     launch1<128, 2, true>},
 };
 
 }  // namespace

@@ -40,7 +40,7 @@ def run_1bit(Wb, Xb, K, config=None):
         return Y.cpu().numpy().astype(np.int64)
 
 
-@pytest.mark.parametrize("config", [0, 1])
+@pytest.mark.parametrize("config", [0, 1, 4])
 @pytest.mark.parametrize("B,M,N,K", [(1, 1, 1, 1), (2, 3, 5, 7), (2, 33, 70, 45),
                                      (1, 128, 256, 1024), (3, 130, 300, 200),
                                      (2, 200, 64, 129), (1, 64, 1000, 640)])
@@ -50,12 +50,13 @@ def test_random_bits_bit_exact(config, B, M, N, K):
     assert np.array_equal(Y, oracle.bgemm(Wb, Xb, K))
 
 
-def test_shared_weights_bit_exact():
+@pytest.mark.parametrize("config", [0, 4])
+def test_shared_weights_bit_exact(config):
     g = ti.rng(4)
     K = 300
     Wb = ti.random_sign_words(g, (2, 2, 96, ti.words_per_row(K)))
     Xb = ti.random_sign_words(g, (6, 2, 150, ti.words_per_row(K)))
-    Y = run_1bit(Wb, Xb, K)
+    Y = run_1bit(Wb, Xb, K, config)
     assert np.array_equal(Y, oracle.bgemm(Wb, Xb, K))
 
 
@@ -114,3 +115,15 @@ def test_full_size_radio_1bit_sampled():
             ref = oracle.bgemm(Wb[b:b + 1][:, :, ms], Xb[b:b + 1][:, :, ns], K)[0]
             got = Y[b][torch.from_numpy(ms).cuda()][:, torch.from_numpy(ns).cuda()]
             assert np.array_equal(got.cpu().numpy().astype(np.int64), ref)
+
+
+def test_all_configurations_bit_identical():
+    """Every 1-bit configuration, including stacked planes, gives the same
+    exact integers on a ragged shape (partial tiles, a partial last K stage)."""
+    Wb, Xb = ti.onebit_block(seed=31, B=3, M=389, K=333, N=270)
+    ref = oracle.bgemm(Wb, Xb, 333)
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    with Plan(3, 389, 270, 333, MODE_1BIT) as plan:
+        n = plan.num_configs()
+    for c in range(n):
+        assert np.array_equal(run_1bit(Wb, Xb, 333, c), ref), c

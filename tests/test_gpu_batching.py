@@ -64,7 +64,8 @@ def test_uneven_beam_counts_one_launch(config):
         assert np.all(np.isnan(untouched.real))
 
 
-def test_uneven_beam_counts_1bit():
+@pytest.mark.parametrize("config", [0, 4])
+def test_uneven_beam_counts_1bit(config):
     import torch
     from gpu_util import dev
     from paper_2505_03269_gb300 import MODE_1BIT, Plan
@@ -72,6 +73,7 @@ def test_uneven_beam_counts_1bit():
     B, M, N, K = 3, 256, 300, 200
     Wb, Xb = ti.onebit_block(seed=23, B=B, M=M, K=K, N=N)
     with Plan(B, M, N, K, MODE_1BIT) as plan:
+        plan.set_config(config)
         plan.set_batch_rows(rows)
         Y = torch.full((B, M, N, 2), -999, dtype=torch.int32, device="cuda")
         plan.beamform_1bit(dev(Wb), dev(Xb), Y)
