@@ -26,8 +26,9 @@ def device_name(device: int) -> str:
 
 
 def cache_key(plan) -> str:
-    return (f"{device_name(plan.device)}|mode={plan.mode}|batch={plan.batch}|M={plan.M}|"
-            f"N={plan.N}|K={plan.K}|w_batches={plan.w_batches}")
+    # the flags select the configuration table (stacked sample planes have their own)
+    return (f"{device_name(plan.device)}|mode={plan.mode}|flags={getattr(plan, 'flags', 0)}|"
+            f"batch={plan.batch}|M={plan.M}|N={plan.N}|K={plan.K}|w_batches={plan.w_batches}")
 
 
 def _read(path):
