@@ -76,6 +76,8 @@ def parse_args():
                     help="arithmetic of the FP workloads (default fp16)")
     ap.add_argument("--batches", type=int, default=None,
                     help="override the number of products (small profiling cases)")
+    ap.add_argument("--m-rows", type=int, default=None,
+                    help="override the beams / voxels per product (small profiling cases)")
     return ap.parse_args()
 
 
@@ -92,6 +94,9 @@ def workload(args):
         else:
             w["w_batches"] = min(w["w_batches"], args.batches)
         w["desc"] += f" [{args.batches} products]"
+    if getattr(args, "m_rows", None) is not None:
+        w["M"] = args.m_rows
+        w["desc"] += f" [{args.m_rows} rows]"
     return w
 
 
@@ -215,11 +220,16 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- inputs
 def geometry_of(w):
+    import numpy as np
     import tcbf_inputs as ti
     if w["geometry"] == "radio":
         return ti.radio_geometry(0, w["M"], w["K"], max(1, w["B"] // 2))
     if w["geometry"] == "ultrasound":
-        return ti.ultrasound_geometry()
+        g = ti.ultrasound_geometry()
+        if w["M"] < len(g.targets):          # reduced profiling case: the first M voxels
+            g = ti.Geometry(g.rx_pos, np.ascontiguousarray(g.targets[: w["M"]]), g.freqs,
+                            g.near_field, g.c)
+        return g
     return None
 
 
@@ -603,7 +613,8 @@ def main():
     else:
         roof = {"bound": "tensor", "achieved": gemm_tops, "peak": tensor_peak,
                 "unit": "TFLOP/s", "frac": gemm_tops / tensor_peak}
-    roof.update({"traffic": recorded_traffic(kname, args.workload if args.batches is None else None),
+    full_size = args.batches is None and args.m_rows is None
+    roof.update({"traffic": recorded_traffic(kname, args.workload if full_size else None),
                  "kernel": kname, "algorithmic_bytes": gbytes,
                  "peak_source": peaks["source"], "tensor_peak_note": peak_note,
                  "ceiling_tops": min(tensor_peak, ai * peaks["hbm_gbs"] / 1e3),
