@@ -1,0 +1,95 @@
+"""Full-size FP16 blocks through the path the benchmark times, checked on
+sampled outputs against the FP64 oracle.
+
+  radio block:      512 products (256 channels x 2 polarisations) of
+                    1024 beams x 288 receivers x 4096 samples, weights from
+                    the station geometry on the GPU, one persistent launch
+  ultrasound block: 65536 voxels x 16384 (128 elements x 128 bins) x 256
+                    frames, near-field model matrix from geometry, stacked
+                    sample planes
+
+The oracle computes its own weights from the same geometry (FP64, rounded
+once to FP16) and the complex sum at each sampled output.  Bar: relative
+Frobenius error over the samples <= 2e-5."""
+import numpy as np
+import pytest
+
+import oracle
+import tcbf_inputs as ti
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from gpu_util import ensure_lib
+    return ensure_lib()
+
+
+def _sampled_error(Y, Xh, geom, B, Bw, M, N, npts=96, seed=7):
+    import torch
+    g = np.random.default_rng(seed)
+    pts = np.stack([g.integers(0, B, npts), g.integers(0, M, npts), g.integers(0, N, npts)], 1)
+    ref = np.empty(npts, np.complex128)
+    for i, (b, m, n) in enumerate(pts):
+        bw = b // (B // Bw)
+        Wrow = oracle.weights_fp16(geom.rx_pos, geom.targets[m:m + 1], geom.freqs[bw:bw + 1],
+                                   geom.near_field, geom.c)
+        ref[i] = oracle.cgemm_points(Wrow, Xh[b:b + 1], np.array([[0, 0, n]]))[0]
+    t = torch.from_numpy(pts).cuda()
+    Yh = Y[t[:, 0], t[:, 1], t[:, 2]].double().cpu().numpy()
+    got = Yh[:, 0] + 1j * Yh[:, 1]
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def _run_block(B, Bw, M, N, K, geom, Xh, flags=0, configs=(None,)):
+    import torch
+    from gpu_util import empty_bytes
+    from paper_2505_03269_gb300 import MODE_FP16, Plan
+    errs = []
+    with Plan(B, M, N, K, MODE_FP16, w_batches=Bw, flags=flags) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        Xp = empty_bytes(plan.packed_size(1))
+        rx = torch.from_numpy(geom.rx_pos).cuda()
+        tg = torch.from_numpy(geom.targets).cuda()
+        fr = torch.from_numpy(np.ascontiguousarray(geom.freqs[:Bw])).cuda()
+        plan.weights_from_geometry(rx, tg, geom.near_field, fr, geom.c, Wp)
+        Xd = torch.from_numpy(Xh).cuda()
+        plan.transpose_pack(1, Xd, Xp)
+        del Xd
+        Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
+        for c in configs:
+            if c is not None:
+                plan.set_config(c)
+            Y.fill_(float("nan"))
+            plan.beamform_fp16(Wp, Xp, Y)
+            torch.cuda.synchronize()
+            assert plan.last_device_error() == 0
+            assert not torch.isnan(Y).any()
+            errs.append(_sampled_error(Y, Xh, geom, B, Bw, M, N))
+        del Y
+    torch.cuda.empty_cache()
+    return errs
+
+
+def test_full_size_radio_block_sampled():
+    B, Bw, M, K, N = 512, 256, 1024, 288, 4096
+    geom = ti.radio_geometry(0, M, K, Bw)
+    Xh = ti.radio_x(1, B, K, N)
+    # the default tile shape and the cluster-multicast shape the autotuner picks most often
+    for err in _run_block(B, Bw, M, N, K, geom, Xh, configs=(0, 6)):
+        assert err <= TOL
+
+
+def test_full_size_ultrasound_block_sampled():
+    from paper_2505_03269_gb300 import FLAG_STACKED_X
+    M, K, N = 65536, 16384, 256
+    geom = ti.ultrasound_geometry()
+    Xh = ti.ultrasound_frames(1, K, N)
+    for err in _run_block(1, 1, M, N, K, geom, Xh, flags=FLAG_STACKED_X, configs=(0, 1)):
+        assert err <= TOL
