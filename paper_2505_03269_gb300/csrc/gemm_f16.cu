@@ -32,6 +32,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "ptx.cuh"
 #include "tiles.cuh"
@@ -900,13 +901,15 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     // persistent grid: as many clusters as can be resident at once
-    static int max_clusters[64] = {};
-    int &mc = max_clusters[pl.device & 63];
+    // resident clusters per device, measured once (benign if two threads both measure)
+    static std::atomic<int> max_clusters[64];
+    int mc = max_clusters[pl.device & 63].load(std::memory_order_relaxed);
     if (mc == 0) {
         cfg.gridDim = dim3(pl.num_sms / CL * CL);
         e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
         if (e != cudaSuccess) return e;
         if (mc < 1) return cudaErrorInvalidConfiguration;
+        max_clusters[pl.device & 63].store(mc, std::memory_order_relaxed);
     }
     cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(total, mc)) * CL);
     e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);
@@ -1004,13 +1007,15 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int max_clusters[64] = {};
-    int &mc = max_clusters[pl.device & 63];
+    // resident clusters per device, measured once (benign if two threads both measure)
+    static std::atomic<int> max_clusters[64];
+    int mc = max_clusters[pl.device & 63].load(std::memory_order_relaxed);
     if (mc == 0) {
         cfg.gridDim = dim3(pl.num_sms / 2 * 2);
         e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
         if (e != cudaSuccess) return e;
         if (mc < 1) return cudaErrorInvalidConfiguration;
+        max_clusters[pl.device & 63].store(mc, std::memory_order_relaxed);
     }
     cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(total, mc)) * 2);
     e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);

@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "ptx.cuh"
 #include "tiles.cuh"
@@ -460,13 +461,15 @@ cudaError_t launch_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     // persistent grid: as many clusters as can be resident at once
-    static int max_clusters[64] = {};
-    int &mc = max_clusters[pl.device & 63];
+    // resident clusters per device, measured once (benign if two threads both measure)
+    static std::atomic<int> max_clusters[64];
+    int mc = max_clusters[pl.device & 63].load(std::memory_order_relaxed);
     if (mc == 0) {
         cfg.gridDim = dim3(pl.num_sms / CL * CL);
         e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
         if (e != cudaSuccess) return e;
         if (mc < 1) return cudaErrorInvalidConfiguration;
+        max_clusters[pl.device & 63].store(mc, std::memory_order_relaxed);
     }
     cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(total, mc)) * CL);
     e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);
