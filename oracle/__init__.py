@@ -251,9 +251,14 @@ def split_operands(W16: np.ndarray, X16: np.ndarray):
 
 def cgemm_split(W16: np.ndarray, X16: np.ndarray, products: int = 3) -> np.ndarray:
     """Split-FP8 beamforming in FP64: Y = 2^-(eW+eX) (Wh Xh + Wh Xl + Wl Xh)
-    (products=3) or with Wl Xl added (products=4); complex128 [B, M, N]."""
+    (products=3), with Wl Xl added (products=4), or the plain per-row-scaled
+    E4M3 product Y = 2^-(eW+eX) Wh Xh (products=1); complex128 [B, M, N]."""
+    if products not in (1, 3, 4):
+        raise ValueError("products must be 1, 3 or 4")
     (Wh, Wl, eW), (Xh, Xl, eX) = split_operands(W16, X16)
-    Y = cgemm(Wh, Xh) + cgemm(Wh, Xl) + cgemm(Wl, Xh)
+    Y = cgemm(Wh, Xh)
+    if products >= 3:
+        Y = Y + cgemm(Wh, Xl) + cgemm(Wl, Xh)
     if products == 4:
         Y = Y + cgemm(Wl, Xl)
     B = X16.shape[0]

@@ -372,3 +372,31 @@ def test_split_error_level_on_gaussian_data():
     W, X = ti.small_fp16(seed=32, M=32, K=256, N=64)
     err = oracle.rel_frobenius(oracle.cgemm_split(W, X), oracle.cgemm(W, X))
     assert 1e-4 < err < 5e-3
+
+
+def test_plain_fp8_product_exact_on_four_bit_integers():
+    """Integers in [-8, 8] have at most four significant bits, so after the
+    per-row power-of-two scale they are exact E4M3 values: the lo parts are
+    zero and the one-product (plain FP8) form equals the exact product."""
+    g = ti.rng(33)
+    W = ti.integer_complex_fp16(g, (2, 12, 40))
+    X = ti.integer_complex_fp16(g, (2, 40, 10))
+    (_, Wl, _), (_, Xl, _) = oracle.split_operands(W, X)
+    assert not Wl.any() and not Xl.any()
+    exact = oracle.cgemm(W, X)
+    for products in (1, 3, 4):
+        assert np.array_equal(oracle.cgemm_split(W, X, products=products), exact)
+
+
+def test_plain_fp8_error_level_on_gaussian_data():
+    """The one-product form keeps E4M3's 3 fraction bits per operand: on
+    Gaussian data its error sits at the few-percent level, well above the
+    three-product split's (no paper value exists for either)."""
+    W, X = ti.small_fp16(seed=34, M=32, K=256, N=64)
+    exact = oracle.cgemm(W, X)
+    e1 = oracle.rel_frobenius(oracle.cgemm_split(W, X, products=1), exact)
+    e3 = oracle.rel_frobenius(oracle.cgemm_split(W, X, products=3), exact)
+    assert 5e-3 < e1 < 1e-1
+    assert e3 < e1 / 5
+    with pytest.raises(ValueError):
+        oracle.cgemm_split(W, X, products=2)
