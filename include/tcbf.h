@@ -80,7 +80,16 @@ typedef enum {
      * = [Re | Im]) instead of four N = 128 ones.  For compute-bound shapes
      * (large K and M, small N); it costs 1.5 x the packed X bytes.  Selects
      * the stacked kernel configurations. */
-    TCBF_FLAG_STACKED_X = 1u
+    TCBF_FLAG_STACKED_X = 1u,
+    /* FP8-split only: the number of E4M3 products per complex K step.  By
+     * default three (Wh Xh + Wh Xl + Wl Xh, the hi+lo split that wins back
+     * accuracy); TCBF_FLAG_FP8_HI_ONLY keeps only Wh Xh, the plain E4M3
+     * product with the same per-row power-of-two scales (a third of the MMA
+     * work, E4M3 accuracy: a few percent on Gaussian data);
+     * TCBF_FLAG_FP8_FOUR_PRODUCTS adds Wl Xl.  The packed layouts are the
+     * same.  The paper names 8-bit floats only as future work (Sec. VI). */
+    TCBF_FLAG_FP8_HI_ONLY = 2u,
+    TCBF_FLAG_FP8_FOUR_PRODUCTS = 4u
 } tcbf_flag;
 
 /*

@@ -21,6 +21,8 @@ STATUS_NAMES = {0: "TCBF_OK", 1: "TCBF_ERR_INVALID_ARG", 2: "TCBF_ERR_UNSUPPORTE
 MODE_FP16, MODE_FP8SPLIT, MODE_1BIT = 0, 1, 2
 SRC_CF16, SRC_CF32 = 0, 1
 FLAG_STACKED_X = 1
+FLAG_FP8_HI_ONLY = 2
+FLAG_FP8_FOUR_PRODUCTS = 4
 
 # every symbol include/tcbf.h declares
 EXPORTED = [

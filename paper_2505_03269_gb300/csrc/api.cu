@@ -119,8 +119,11 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     if (q.batch % q.w_batches != 0) return TCBF_ERR_INVALID_ARG;
     if (q.mode != TCBF_MODE_FP16 && q.mode != TCBF_MODE_FP8SPLIT && q.mode != TCBF_MODE_1BIT)
         return TCBF_ERR_INVALID_ARG;
-    if ((q.flags & ~uint32_t(TCBF_FLAG_STACKED_X)) != 0) return TCBF_ERR_INVALID_ARG;
+    const uint32_t fp8_flags = TCBF_FLAG_FP8_HI_ONLY | TCBF_FLAG_FP8_FOUR_PRODUCTS;
+    if ((q.flags & ~(uint32_t(TCBF_FLAG_STACKED_X) | fp8_flags)) != 0) return TCBF_ERR_INVALID_ARG;
     if ((q.flags & TCBF_FLAG_STACKED_X) && q.mode != TCBF_MODE_FP16) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & fp8_flags) && q.mode != TCBF_MODE_FP8SPLIT) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & fp8_flags) == fp8_flags) return TCBF_ERR_INVALID_ARG;   // one or the other
     if (q.M > kMaxDim || q.N > kMaxDim || q.K > kMaxDim || q.batch > 65535)
         return TCBF_ERR_UNSUPPORTED;
     // 1-bit sums are exact integers in the FP32 accumulators while 2K < 2^24

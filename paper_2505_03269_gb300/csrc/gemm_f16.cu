@@ -62,6 +62,7 @@ struct GemmArgs {
     int kc_blocks;             // stages per accumulation chunk (num_kb when not promoting)
     int chunks;                // accumulation chunks per tile
     int total_tiles;
+    int products;              // split-FP8: 1 (hi hi), 3 (+ hi lo, lo hi) or 4 (+ lo lo)
 };
 
 constexpr int pow2_cols(int c) {
@@ -88,6 +89,36 @@ __device__ __forceinline__ float pow2_neg(int e) { return __int_as_float((127 - 
 
 __device__ __forceinline__ void decode_tile(int t, const GemmArgs &a, int &b, int &mt, int &nt) {
     tile_decode(a.tiles, t, b, mt, nt);
+}
+
+// Split-FP8 MMAs of one 32-K step j: (W part, X part) byte offsets (hi, hi),
+// (hi, lo), (lo, hi), (lo, lo), the first NP of them; the lo bytes sit 64
+// bytes into each 128-byte row.  One-SM (PAIR false) or two-SM MMAs.
+template <int NP, bool PAIR>
+__device__ __forceinline__ void split_step(uint32_t d_re, uint32_t d_im, uint32_t a, uint32_t bx,
+                                           int a_plane, int b_plane, int j, bool first,
+                                           uint32_t idesc, uint32_t idesc_neg) {
+#pragma unroll
+    for (int pr = 0; pr < NP; ++pr) {
+        const uint32_t wo = (pr >= 2 ? 64u : 0u) + 32u * j;
+        const uint32_t xo = ((pr & 1) ? 64u : 0u) + 32u * j;
+        const uint64_t ar = sdesc_kmajor_sw128(a + wo);
+        const uint64_t ai = sdesc_kmajor_sw128(a + a_plane + wo);
+        const uint64_t br = sdesc_kmajor_sw128(bx + xo);
+        const uint64_t bi = sdesc_kmajor_sw128(bx + b_plane + xo);
+        const uint32_t accum = (first && pr == 0) ? 0u : 1u;
+        if (PAIR) {
+            mma_f8f6f4_pair(d_re, ar, br, idesc, accum);
+            mma_f8f6f4_pair(d_re, ai, bi, idesc_neg, 1u);
+            mma_f8f6f4_pair(d_im, ar, bi, idesc, accum);
+            mma_f8f6f4_pair(d_im, ai, br, idesc, 1u);
+        } else {
+            mma_f8f6f4(d_re, ar, br, idesc, accum);
+            mma_f8f6f4(d_re, ai, bi, idesc_neg, 1u);
+            mma_f8f6f4(d_im, ar, bi, idesc, accum);
+            mma_f8f6f4(d_im, ai, br, idesc, 1u);
+        }
+    }
 }
 
 template <int BN, int STAGES, bool SPLIT, int CL>
@@ -270,23 +301,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         } else {
                             // 32 E4M3 per step; (W part, X part) byte offsets:
-                            // (hi, hi), (hi, lo), (lo, hi)
+                            // (hi, hi), (hi, lo), (lo, hi), (lo, lo), the first
+                            // args.products of them
                             const int ksteps = min(2, (args.K - kb * 64 + 31) / 32);
                             for (int j = 0; j < ksteps; ++j) {
-#pragma unroll
-                                for (int pr = 0; pr < 3; ++pr) {
-                                    const uint32_t wo = (pr == 2 ? 64u : 0u) + 32u * j;
-                                    const uint32_t xo = (pr == 1 ? 64u : 0u) + 32u * j;
-                                    const uint64_t ar = sdesc_kmajor_sw128(a + wo);
-                                    const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + wo);
-                                    const uint64_t br = sdesc_kmajor_sw128(bx + xo);
-                                    const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + xo);
-                                    const uint32_t accum = (kb > kb0 || j > 0 || pr > 0) ? 1u : 0u;
-                                    mma_f8f6f4(d_re, ar, br, kIdesc, accum);
-                                    mma_f8f6f4(d_re, ai, bi, kIdescNeg, 1u);
-                                    mma_f8f6f4(d_im, ar, bi, kIdesc, accum);
-                                    mma_f8f6f4(d_im, ai, br, kIdesc, 1u);
-                                }
+                                const bool first = kb == kb0 && j == 0;
+                                if (args.products == 3)
+                                    split_step<3, false>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                         first, kIdesc, kIdescNeg);
+                                else if (args.products == 1)
+                                    split_step<1, false>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                         first, kIdesc, kIdescNeg);
+                                else
+                                    split_step<4, false>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                         first, kIdesc, kIdescNeg);
                             }
                         }
                         if (CL == 1)
@@ -636,20 +664,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         } else {
                             const int ksteps = min(2, (args.K - kb * 64 + 31) / 32);
                             for (int j = 0; j < ksteps; ++j) {
-#pragma unroll
-                                for (int pr = 0; pr < 3; ++pr) {
-                                    const uint32_t wo = (pr == 2 ? 64u : 0u) + 32u * j;
-                                    const uint32_t xo = (pr == 1 ? 64u : 0u) + 32u * j;
-                                    const uint64_t ar = sdesc_kmajor_sw128(a + wo);
-                                    const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + wo);
-                                    const uint64_t br = sdesc_kmajor_sw128(bx + xo);
-                                    const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + xo);
-                                    const uint32_t accum = (kb > kb0 || j > 0 || pr > 0) ? 1u : 0u;
-                                    mma_f8f6f4_pair(d_re, ar, br, kIdesc, accum);
-                                    mma_f8f6f4_pair(d_re, ai, bi, kIdescNeg, 1u);
-                                    mma_f8f6f4_pair(d_im, ar, bi, kIdesc, accum);
-                                    mma_f8f6f4_pair(d_im, ai, br, kIdesc, 1u);
-                                }
+                                const bool first = kb == kb0 && j == 0;
+                                if (args.products == 3)
+                                    split_step<3, true>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                        first, kIdesc, kIdescNeg);
+                                else if (args.products == 1)
+                                    split_step<1, true>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                        first, kIdesc, kIdescNeg);
+                                else
+                                    split_step<4, true>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                        first, kIdesc, kIdescNeg);
                             }
                         }
                         mma_commit_pair(empty0 + 8 * stage, kBoth);
@@ -857,6 +881,7 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
                                                         p.batch * 2 * p.N * row)
                      : nullptr;
     a.tma_store = tma_store;
+    a.products = split_products(pl);
     a.status = pl.status;
     a.M = static_cast<int>(p.M);
     a.N = static_cast<int>(p.N);
@@ -971,6 +996,7 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
                                                         p.batch * 2 * p.N * row)
                      : nullptr;
     a.tma_store = tma_store;
+    a.products = split_products(pl);
     a.status = pl.status;
     a.M = static_cast<int>(p.M);
     a.N = static_cast<int>(p.N);

@@ -74,6 +74,13 @@ const char *gemm_f16_stacked_config_name(int config);
 cudaError_t launch_gemm_f16_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                                     cudaStream_t s);
 
+// Split-FP8 products per 32-K step: 1 (plain FP8), 3 (hi+lo split) or 4.
+inline int split_products(const tcbf_plan_s &pl) {
+    if (pl.p.flags & TCBF_FLAG_FP8_HI_ONLY) return 1;
+    if (pl.p.flags & TCBF_FLAG_FP8_FOUR_PRODUCTS) return 4;
+    return 3;
+}
+
 // Planes of packed FP16 X: 3 with TCBF_FLAG_STACKED_X, else 2.
 inline int64_t x_planes(const tcbf_plan_s &pl) {
     return (pl.p.flags & TCBF_FLAG_STACKED_X) ? 3 : 2;

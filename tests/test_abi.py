@@ -57,7 +57,9 @@ def _create(lib, **kw):
 
 @pytest.mark.parametrize("bad", [dict(M=0), dict(N=0), dict(K=0), dict(batch=0),
                                  dict(batch=4, w_batches=3), dict(mode=7), dict(flags=2),
-                                 dict(flags=1, mode=1), dict(flags=1, mode=2), dict(M=-5)])
+                                 dict(flags=1, mode=1), dict(flags=1, mode=2), dict(flags=8),
+                                 dict(flags=4, mode=0), dict(flags=2, mode=2),
+                                 dict(flags=6, mode=1), dict(M=-5)])
 def test_plan_create_rejects_bad_shapes(lib, bad):
     st, h = _create(lib, **bad)
     assert st == 1          # TCBF_ERR_INVALID_ARG, before any device query

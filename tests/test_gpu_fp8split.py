@@ -25,9 +25,9 @@ def lib():
     return ensure_lib()
 
 
-def _plan(B, M, N, K, Bw=0):
+def _plan(B, M, N, K, Bw=0, flags=0):
     from paper_2505_03269_gb300 import MODE_FP8SPLIT, Plan
-    return Plan(B, M, N, K, MODE_FP8SPLIT, w_batches=Bw)
+    return Plan(B, M, N, K, MODE_FP8SPLIT, w_batches=Bw, flags=flags)
 
 
 def _decode_split(raw, nb, rows, K):
@@ -42,12 +42,12 @@ def _decode_split(raw, nb, rows, K):
     return hi, lo, ex
 
 
-def _run(W, X, config=None, src_type=0):
+def _run(W, X, config=None, src_type=0, flags=0):
     import torch
     from gpu_util import dev
     Bw, M, K, _ = W.shape
     B, _, N, _ = X.shape
-    with _plan(B, M, N, K, Bw) as plan:
+    with _plan(B, M, N, K, Bw, flags) as plan:
         if config is not None:
             plan.set_config(config)
         Wp = torch.empty(plan.packed_size(0), dtype=torch.uint8, device="cuda")
@@ -120,3 +120,23 @@ def test_split_weights_from_geometry():
     assert np.mean(ex[0] == eW) >= 0.99
     same = (hi[0].transpose(1, 2, 0) == Wh) & (lo[0].transpose(1, 2, 0) == Wl)
     assert np.mean(same) >= 0.999
+
+
+# products per complex K step: 1 = plain E4M3 (TCBF_FLAG_FP8_HI_ONLY), 3 = hi+lo split,
+# 4 = split with Wl Xl (TCBF_FLAG_FP8_FOUR_PRODUCTS)
+@pytest.mark.parametrize("products,flags,ceiling", [(1, 2, 1e-1), (3, 0, 5e-3), (4, 4, 5e-3)])
+@pytest.mark.parametrize("config", [0, 8])
+def test_split_product_count_matches_oracle(products, flags, ceiling, config):
+    W, _ = ti.small_fp16(seed=50 + products, M=130, K=300, N=8, B=2)
+    X = ti.complex_gaussian_fp16(ti.rng(51), (4, 300, 260))
+    Y, _, _ = _run(W, X, config, flags=flags)
+    assert oracle.rel_frobenius(Y, oracle.cgemm_split(W, X, products=products)) <= TOL
+    assert oracle.rel_frobenius(Y, oracle.cgemm(W, X)) < ceiling
+
+
+def test_plain_fp8_exact_on_four_bit_integers():
+    g = ti.rng(52)
+    W = ti.integer_complex_fp16(g, (1, 100, 200))
+    X = ti.integer_complex_fp16(g, (2, 200, 96))
+    Y, _, _ = _run(W, X, flags=2)
+    assert np.array_equal(Y, oracle.cgemm(W, X))
