@@ -155,20 +155,24 @@ def kernel_sources_sha(files):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload_name):
-    """DRAM bytes per launch from a committed ncu summary, only if the
-    kernel's sources are unchanged since that capture."""
+def recorded_traffic(kernel, workload_name, config_name):
+    """DRAM bytes per launch from a committed ncu summary of this kernel, this
+    workload and this tile configuration, only if the kernel's sources are
+    unchanged since that capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
-            rec = json.load(fh)[kernel]
+            records = json.load(fh)["records"]
     except Exception:
         return None
-    if rec.get("workload") != workload_name:
-        return None
-    if rec.get("sources_sha") != kernel_sources_sha(rec.get("sources", [])):
-        return None
-    return rec.get("bytes_per_launch")
+    for rec in records:
+        if (rec.get("kernel"), rec.get("workload"), rec.get("config")) != (
+                kernel, workload_name, config_name):
+            continue
+        if rec.get("sources_sha") != kernel_sources_sha(rec.get("sources", [])):
+            return None
+        return rec.get("bytes_per_launch")
+    return None
 
 
 # ----------------------------------------------------------------- clocks
@@ -625,7 +629,7 @@ def main():
     else:
         tensor_peak = peaks["bf16_tflops"]
         peak_note = "FP16 tensor peak = measured bf16 burst (same dense rate)"
-        kname = "cgemm_f16_kernel"
+        kname = "cgemm_stacked_kernel" if w.get("stacked") else "cgemm_f16_kernel"
     ai = mma_factor * ops / gbytes
     ridge = tensor_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
     gemm_tops = mma_factor * ops / (gemm_ms * 1e-3) / 1e12
@@ -637,7 +641,9 @@ def main():
         roof = {"bound": "tensor", "achieved": gemm_tops, "peak": tensor_peak,
                 "unit": "TFLOP/s", "frac": gemm_tops / tensor_peak}
     full_size = args.batches is None and args.m_rows is None
-    roof.update({"traffic": recorded_traffic(kname, args.workload if full_size else None),
+    traffic_key = f"{args.workload}/{w['mode']}" if full_size else None
+    roof.update({"traffic": recorded_traffic(kname, traffic_key,
+                                             plan.config_name(plan.get_config())),
                  "kernel": kname, "algorithmic_bytes": gbytes,
                  "peak_source": peaks["source"], "tensor_peak_note": peak_note,
                  "ceiling_tops": min(tensor_peak, ai * peaks["hbm_gbs"] / 1e3),
