@@ -85,9 +85,10 @@ typedef enum {
      * default three (Wh Xh + Wh Xl + Wl Xh, the hi+lo split that wins back
      * accuracy); TCBF_FLAG_FP8_HI_ONLY keeps only Wh Xh, the plain E4M3
      * product with the same per-row power-of-two scales (a third of the MMA
-     * work, E4M3 accuracy: a few percent on Gaussian data);
-     * TCBF_FLAG_FP8_FOUR_PRODUCTS adds Wl Xl.  The packed layouts are the
-     * same.  The paper names 8-bit floats only as future work (Sec. VI). */
+     * work, E4M3 accuracy: a few percent on Gaussian data) and packs one
+     * byte per element (the hi bytes alone, see the layouts below);
+     * TCBF_FLAG_FP8_FOUR_PRODUCTS adds Wl Xl on the hi+lo layout.  The paper
+     * names 8-bit floats only as future work (Sec. VI). */
     TCBF_FLAG_FP8_HI_ONLY = 2u,
     TCBF_FLAG_FP8_FOUR_PRODUCTS = 4u
 } tcbf_flag;
@@ -114,7 +115,9 @@ typedef enum {
  *   amax * 2^e <= 448 (amax over the row's K elements of both planes, after
  *   rounding to FP16), hi = RN_e4m3(v 2^e), lo = RN_e4m3(v 2^e - hi), both
  *   saturating, so v ~ (hi + lo) 2^-e.  tcbf_packed_size includes the
- *   exponents.
+ *   exponents.  With TCBF_FLAG_FP8_HI_ONLY the rows hold the hi bytes alone,
+ *   Kb2 = K rounded up to 64 (hi byte of element k at offset k), followed by
+ *   the same exponents.
  */
 
 /* Create a plan for problem *p on CUDA device `device`.  Validates the

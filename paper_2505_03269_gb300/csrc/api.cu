@@ -144,7 +144,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     pl->per_w = q.batch / q.w_batches;
     pl->Kp = round_up(q.K, 8);
     pl->Kw = round_up(q.K, 128) / 32;
-    pl->Kb2 = 2 * round_up(q.K, 64);
+    pl->Kb2 = fp8_row_bytes(q.K, q.flags);
     pl->config = 0;
     {
         DeviceGuard g(device);

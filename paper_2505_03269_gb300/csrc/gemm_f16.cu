@@ -59,6 +59,7 @@ struct GemmArgs {
     int per_w;
     TileMap tiles;
     int num_kb;
+    int kps;                   // K elements per stage: 64, or 128 for hi-only FP8 rows
     int kc_blocks;             // stages per accumulation chunk (num_kb when not promoting)
     int chunks;                // accumulation chunks per tile
     int total_tiles;
@@ -93,7 +94,8 @@ __device__ __forceinline__ void decode_tile(int t, const GemmArgs &a, int &b, in
 
 // Split-FP8 MMAs of one 32-K step j: (W part, X part) byte offsets (hi, hi),
 // (hi, lo), (lo, hi), (lo, lo), the first NP of them; the lo bytes sit 64
-// bytes into each 128-byte row.  One-SM (PAIR false) or two-SM MMAs.
+// bytes into each 128-byte row.  Hi-only rows (NP = 1) hold 128 hi bytes per
+// stage row, j = 0..3.  One-SM (PAIR false) or two-SM MMAs.
 template <int NP, bool PAIR>
 __device__ __forceinline__ void split_step(uint32_t d_re, uint32_t d_im, uint32_t a, uint32_t bx,
                                            int a_plane, int b_plane, int j, bool first,
@@ -302,8 +304,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         } else {
                             // 32 E4M3 per step; (W part, X part) byte offsets:
                             // (hi, hi), (hi, lo), (lo, hi), (lo, lo), the first
-                            // args.products of them
-                            const int ksteps = min(2, (args.K - kb * 64 + 31) / 32);
+                            // args.products of them (hi-only rows: 4 steps)
+                            const int ksteps = min(args.kps / 32, (args.K - kb * args.kps + 31) / 32);
                             for (int j = 0; j < ksteps; ++j) {
                                 const bool first = kb == kb0 && j == 0;
                                 if (args.products == 3)
@@ -662,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 mma_f16_pair(d_im, ai, br, kIdesc, 1u);
                             }
                         } else {
-                            const int ksteps = min(2, (args.K - kb * 64 + 31) / 32);
+                            const int ksteps = min(args.kps / 32, (args.K - kb * args.kps + 31) / 32);
                             for (int j = 0; j < ksteps; ++j) {
                                 const bool first = kb == kb0 && j == 0;
                                 if (args.products == 3)
@@ -892,10 +894,13 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, BM));
     a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, BN));
     a.tiles.raster = raster;
-    a.num_kb = static_cast<int>(ceil_div(p.K, BK));
+    // hi-only FP8 rows carry 128 K in each 128-byte stage row, the other
+    // formats 64 (FP16, or 64 hi + 64 lo bytes); chunks stay 2048 K
+    a.kps = (SPLIT && fp8_hi_only(p.flags)) ? 2 * BK : BK;
+    a.num_kb = static_cast<int>(ceil_div(p.K, a.kps));
     if (p.K > kPromoteK) {
         if (4 * BN > 512) return cudaErrorInvalidConfiguration;   // no TMEM room for the sum
-        a.kc_blocks = kChunkBlocks;
+        a.kc_blocks = kChunkBlocks * BK / a.kps;
     } else {
         a.kc_blocks = a.num_kb;
     }
@@ -1007,10 +1012,13 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
     a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, BM));
     a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, BN));
     a.tiles.raster = 0;
-    a.num_kb = static_cast<int>(ceil_div(p.K, BK));
+    // hi-only FP8 rows carry 128 K in each 128-byte stage row, the other
+    // formats 64 (FP16, or 64 hi + 64 lo bytes); chunks stay 2048 K
+    a.kps = (SPLIT && fp8_hi_only(p.flags)) ? 2 * BK : BK;
+    a.num_kb = static_cast<int>(ceil_div(p.K, a.kps));
     if (p.K > kPromoteK) {
         if (4 * BN > 512) return cudaErrorInvalidConfiguration;
-        a.kc_blocks = kChunkBlocks;
+        a.kc_blocks = kChunkBlocks * BK / a.kps;
     } else {
         a.kc_blocks = a.num_kb;
     }

@@ -323,8 +323,9 @@ cudaError_t launch_pack_bits_x(const tcbf_plan_s &pl, int src_type, const void *
 // ===========================================================================
 // Split-FP8 packing.  Each packed row (one beam of W, one sample of X, one
 // plane) holds K in 64-element blocks of 64 E4M3 "hi" bytes then 64 E4M3
-// "lo" bytes; int32 scale exponents follow the data, one per row (shared by
-// both planes).  With e the largest integer such that amax * 2^e <= 448
+// "lo" bytes (HI: hi bytes only, 64 per block, for plans that keep the hi
+// product alone); int32 scale exponents follow the data, one per row (shared
+// by both planes).  With e the largest integer such that amax * 2^e <= 448
 // (amax over the row's K elements and both planes), hi = RN(v 2^e) and
 // lo = RN(v 2^e - hi), both saturating.  FP32 sources are first rounded to
 // FP16, so every mode sees the same input values.
@@ -376,7 +377,7 @@ __device__ __forceinline__ float2 load_f16_value(const void *src, size_t i) {
 }
 
 // W rows (no transpose): one warp per row.
-template <typename S>
+template <typename S, bool HI>
 __global__ void split8_rows_kernel(const void *__restrict__ src, uint8_t *__restrict__ dst,
                                    int32_t *__restrict__ exps, int64_t rows, int64_t M, int K,
                                    int Kb2) {
@@ -396,7 +397,8 @@ __global__ void split8_rows_kernel(const void *__restrict__ src, uint8_t *__rest
         const int64_t bw = r / M, m = r % M;
         uint8_t *row_re = dst + (static_cast<size_t>(bw * 2 + 0) * M + m) * Kb2;
         uint8_t *row_im = dst + (static_cast<size_t>(bw * 2 + 1) * M + m) * Kb2;
-        for (int j = 0; j < Kb2 / 128; ++j) {
+        constexpr int kBlk = HI ? 64 : 128;
+        for (int j = 0; j < Kb2 / kBlk; ++j) {
             uint8_t h[2][2], l[2][2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -406,10 +408,12 @@ __global__ void split8_rows_kernel(const void *__restrict__ src, uint8_t *__rest
                 split_value(v.x * s, h[0][q], l[0][q]);
                 split_value(v.y * s, h[1][q], l[1][q]);
             }
-            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 2 * lane) = h[0][0] | (h[0][1] << 8);
-            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
-            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 2 * lane) = h[1][0] | (h[1][1] << 8);
-            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_re + kBlk * j + 2 * lane) = h[0][0] | (h[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + kBlk * j + 2 * lane) = h[1][0] | (h[1][1] << 8);
+            if (!HI) {
+                *reinterpret_cast<uint16_t *>(row_re + kBlk * j + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
+                *reinterpret_cast<uint16_t *>(row_im + kBlk * j + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+            }
         }
         if (lane == 0) exps[r] = e;
     }
@@ -447,8 +451,8 @@ __global__ void split8_exps_kernel(int32_t *__restrict__ slot, int64_t rows) {
 }
 
 // X transpose + split: 64 (k) x 64 (n) tiles; each output row of a tile is
-// one K block: 64 hi bytes and 64 lo bytes per plane.
-template <typename S>
+// one K block: 64 hi bytes and 64 lo bytes per plane (HI: 64 hi bytes).
+template <typename S, bool HI>
 __global__ void __launch_bounds__(256) split8_pack_x_kernel(const void *__restrict__ src,
                                                            uint8_t *__restrict__ dst,
                                                            const int32_t *__restrict__ exps,
@@ -481,11 +485,12 @@ __global__ void __launch_bounds__(256) split8_pack_x_kernel(const void *__restri
         __syncthreads();
         // thread -> (row nn, 16-byte chunk c of 8: 4 hi chunks then 4 lo chunks)
         const int c = tid & 7;
+        constexpr int kBlk = HI ? 64 : 128;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int nn = (tid >> 3) + 32 * h;
             const int n = n0 + nn;
-            if (n < N) {
+            if (n < N && !(HI && c >= 4)) {
                 const float s = pow2f(split_exponent(__int_as_float(exps[b * N + n])));
                 const int kc = 16 * (c & 3);
                 const bool want_lo = c >= 4;
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(256) split8_pack_x_kernel(const void *__restri
                         split_value(v, hi, lo);
                         out[j] = want_lo ? lo : hi;
                     }
-                    uint8_t *row = dst + (static_cast<size_t>(b * 2 + p) * N + n) * Kb2 + kt * 128;
+                    uint8_t *row = dst + (static_cast<size_t>(b * 2 + p) * N + n) * Kb2 + kt * kBlk;
                     *reinterpret_cast<uint4 *>(row + 16 * c) = *reinterpret_cast<const uint4 *>(out);
                 }
             }
@@ -528,7 +533,7 @@ struct SplitFusedSmem {
     }
 };
 
-template <typename S, bool VEC, int TN>
+template <typename S, bool VEC, int TN, bool HI>
 __global__ void __launch_bounds__(8 * TN) split8_pack_x_fused_kernel(const void *__restrict__ src,
                                                                      uint8_t *__restrict__ dst,
                                                                      int32_t *__restrict__ exps,
@@ -609,9 +614,9 @@ __global__ void __launch_bounds__(8 * TN) split8_pack_x_fused_kernel(const void 
                 const float b = (p == 0 ? __low2float(h1) : __high2float(h1)) * s;
                 split_pair(a, b, hi[j], lo[j]);
             }
-            uint8_t *row = out + n * pitch + p * Kb2 + (c >> 2) * 128 + (c & 3) * 16;
+            uint8_t *row = out + n * pitch + p * Kb2 + (c >> 2) * (HI ? 64 : 128) + (c & 3) * 16;
             *reinterpret_cast<uint4 *>(row) = *reinterpret_cast<const uint4 *>(hi);
-            *reinterpret_cast<uint4 *>(row + 64) = *reinterpret_cast<const uint4 *>(lo);
+            if (!HI) *reinterpret_cast<uint4 *>(row + 64) = *reinterpret_cast<const uint4 *>(lo);
         }
         __syncthreads();
         // write the packed rows: 16-byte chunks, consecutive threads along a row
@@ -639,10 +644,15 @@ cudaError_t launch_pack_split8_w(const tcbf_plan_s &pl, int src_type, const void
     auto *d = static_cast<uint8_t *>(dst);
     auto *ex = reinterpret_cast<int32_t *>(d + rows * 2 * Kb2);
     const int grid = grid_for(rows * 32, 256, pl.num_sms);
-    if (src_type == TCBF_SRC_CF16)
-        split8_rows_kernel<CF16><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, int(pl.p.K), Kb2);
-    else
-        split8_rows_kernel<CF32><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, int(pl.p.K), Kb2);
+    const bool hi = fp8_hi_only(pl.p.flags);
+    const int K = static_cast<int>(pl.p.K);
+    if (src_type == TCBF_SRC_CF16) {
+        if (hi) split8_rows_kernel<CF16, true><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, K, Kb2);
+        else split8_rows_kernel<CF16, false><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, K, Kb2);
+    } else {
+        if (hi) split8_rows_kernel<CF32, true><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, K, Kb2);
+        else split8_rows_kernel<CF32, false><<<grid, 256, 0, s>>>(src, d, ex, rows, pl.p.M, K, Kb2);
+    }
     return cudaGetLastError();
 }
 
@@ -653,7 +663,8 @@ cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void
     auto *d = static_cast<uint8_t *>(dst);
     auto *ex = reinterpret_cast<int32_t *>(d + B * 2 * N * Kb2);
     const int g1 = grid_for(B * N, 256, pl.num_sms);
-    const int k_tiles = Kb2 / 128;
+    const bool hi = fp8_hi_only(pl.p.flags);
+    const int k_tiles = static_cast<int>(ceil_div(pl.p.K, 64));
     const int n_tiles = static_cast<int>(ceil_div(N, TT));
     const int64_t per_b = int64_t(k_tiles) * n_tiles;
     const int bx = static_cast<int>(std::min<int64_t>(per_b, std::max<int64_t>(1, int64_t(pl.num_sms) * 8 / std::max<int64_t>(1, std::min<int64_t>(B, 8)))));
@@ -676,20 +687,30 @@ cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void
             kern<<<g, 8 * TN, smem, s>>>(src, d, ex, B, K, Ni, Kb2);
             return cudaGetLastError();
         };
-        if (src_type == TCBF_SRC_CF16)
-            return vec ? launch(split8_pack_x_fused_kernel<CF16, true, TN>)
-                       : launch(split8_pack_x_fused_kernel<CF16, false, TN>);
-        return vec ? launch(split8_pack_x_fused_kernel<CF32, true, TN>)
-                   : launch(split8_pack_x_fused_kernel<CF32, false, TN>);
+        if (src_type == TCBF_SRC_CF16) {
+            if (hi)
+                return vec ? launch(split8_pack_x_fused_kernel<CF16, true, TN, true>)
+                           : launch(split8_pack_x_fused_kernel<CF16, false, TN, true>);
+            return vec ? launch(split8_pack_x_fused_kernel<CF16, true, TN, false>)
+                       : launch(split8_pack_x_fused_kernel<CF16, false, TN, false>);
+        }
+        if (hi)
+            return vec ? launch(split8_pack_x_fused_kernel<CF32, true, TN, true>)
+                       : launch(split8_pack_x_fused_kernel<CF32, false, TN, true>);
+        return vec ? launch(split8_pack_x_fused_kernel<CF32, true, TN, false>)
+                   : launch(split8_pack_x_fused_kernel<CF32, false, TN, false>);
     }
     cudaError_t e = cudaMemsetAsync(ex, 0, sizeof(int32_t) * B * N, s);
     if (e != cudaSuccess) return e;
+    const int K = static_cast<int>(pl.p.K), Ni = static_cast<int>(N);
     if (src_type == TCBF_SRC_CF16) {
-        split8_amax_x_kernel<CF16><<<g_amax, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N), k_chunks);
-        split8_pack_x_kernel<CF16><<<grid, 256, 0, s>>>(src, d, ex, int(pl.p.K), int(N), Kb2, k_tiles, n_tiles);
+        split8_amax_x_kernel<CF16><<<g_amax, 256, 0, s>>>(src, ex, B, K, Ni, k_chunks);
+        if (hi) split8_pack_x_kernel<CF16, true><<<grid, 256, 0, s>>>(src, d, ex, K, Ni, Kb2, k_tiles, n_tiles);
+        else split8_pack_x_kernel<CF16, false><<<grid, 256, 0, s>>>(src, d, ex, K, Ni, Kb2, k_tiles, n_tiles);
     } else {
-        split8_amax_x_kernel<CF32><<<g_amax, 256, 0, s>>>(src, ex, B, int(pl.p.K), int(N), k_chunks);
-        split8_pack_x_kernel<CF32><<<grid, 256, 0, s>>>(src, d, ex, int(pl.p.K), int(N), Kb2, k_tiles, n_tiles);
+        split8_amax_x_kernel<CF32><<<g_amax, 256, 0, s>>>(src, ex, B, K, Ni, k_chunks);
+        if (hi) split8_pack_x_kernel<CF32, true><<<grid, 256, 0, s>>>(src, d, ex, K, Ni, Kb2, k_tiles, n_tiles);
+        else split8_pack_x_kernel<CF32, false><<<grid, 256, 0, s>>>(src, d, ex, K, Ni, Kb2, k_tiles, n_tiles);
     }
     split8_exps_kernel<<<g1, 256, 0, s>>>(ex, B * N);
     return cudaGetLastError();

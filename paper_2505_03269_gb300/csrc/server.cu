@@ -169,7 +169,7 @@ tcbf_plan_s request_plan(const tcbf_server_s *s, const Req &q) {
     pl.per_w = 1;
     pl.Kp = round_up(q.K, 8);
     pl.Kw = round_up(q.K, 128) / 32;
-    pl.Kb2 = 2 * round_up(q.K, 64);
+    pl.Kb2 = fp8_row_bytes(q.K, pl.p.flags);
     pl.config = 0;
     pl.status = s->status + 64 * q.stream;
     return pl;

@@ -17,7 +17,7 @@ struct tcbf_plan_s {
     int64_t per_w = 1;       // batch / w_batches
     int64_t Kp = 0;          // K rounded up to 8 (FP16 / FP8 row length, elements)
     int64_t Kw = 0;          // 1-bit row length in 32-bit words (multiple of 4)
-    int64_t Kb2 = 0;         // split-FP8 row length in bytes: 2 * K rounded up to 64
+    int64_t Kb2 = 0;         // FP8 row length in bytes (fp8_row_bytes)
     int config = 0;          // kernel configuration (tile shape) in use
     uint32_t *status = nullptr;   // device status word (256 bytes)
     // uneven batches: per-batch row counts and the device m-tile prefix
@@ -79,6 +79,15 @@ inline int split_products(const tcbf_plan_s &pl) {
     if (pl.p.flags & TCBF_FLAG_FP8_HI_ONLY) return 1;
     if (pl.p.flags & TCBF_FLAG_FP8_FOUR_PRODUCTS) return 4;
     return 3;
+}
+
+// FP8 packed rows hold K in 64-element blocks: 64 E4M3 hi bytes, then 64
+// lo bytes unless the plan keeps the hi product only (TCBF_FLAG_FP8_HI_ONLY:
+// one byte per element, hi byte k at offset k).
+inline bool fp8_hi_only(uint32_t flags) { return (flags & TCBF_FLAG_FP8_HI_ONLY) != 0; }
+inline int64_t fp8_block_bytes(uint32_t flags) { return fp8_hi_only(flags) ? 64 : 128; }
+inline int64_t fp8_row_bytes(int64_t K, uint32_t flags) {
+    return round_up(K, 64) / 64 * fp8_block_bytes(flags);
 }
 
 // Planes of packed FP16 X: 3 with TCBF_FLAG_STACKED_X, else 2.

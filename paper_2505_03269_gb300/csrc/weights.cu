@@ -109,13 +109,15 @@ __global__ void weights_bits_kernel(Geo g, uint32_t *__restrict__ dst, int64_t B
 
 // Split-FP8: one warp per (weight batch, beam) row; the weights are computed
 // twice, first for the row's largest magnitude (the scale exponent), then
-// for the hi/lo bytes, in the packed layout of the transpose/pack kernel.
+// for the hi/lo bytes, in the packed layout of the transpose/pack kernel
+// (HI: the hi bytes only, for plans that keep the hi product alone).
 __device__ __forceinline__ void split_bytes(float v, uint8_t &hi, uint8_t &lo) {
     hi = static_cast<uint8_t>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
     const float h = __half2float(__half(__nv_cvt_fp8_to_halfraw(hi, __NV_E4M3)));
     lo = static_cast<uint8_t>(__nv_cvt_float_to_fp8(v - h, __NV_SATFINITE, __NV_E4M3));
 }
 
+template <bool HI>
 __global__ void weights_split8_kernel(Geo g, uint8_t *__restrict__ dst, int32_t *__restrict__ exps,
                                       int64_t Bw, int Kb2) {
     const int lane = threadIdx.x & 31;
@@ -144,7 +146,8 @@ __global__ void weights_split8_kernel(Geo g, uint8_t *__restrict__ dst, int32_t 
         const float s = __int_as_float((127 + e) << 23);
         uint8_t *row_re = dst + (static_cast<size_t>(bw * 2 + 0) * g.M + m) * Kb2;
         uint8_t *row_im = dst + (static_cast<size_t>(bw * 2 + 1) * g.M + m) * Kb2;
-        for (int j = 0; j < Kb2 / 128; ++j) {
+        constexpr int kBlk = HI ? 64 : 128;
+        for (int j = 0; j < Kb2 / kBlk; ++j) {
             uint8_t h[2][2], l[2][2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -158,10 +161,12 @@ __global__ void weights_split8_kernel(Geo g, uint8_t *__restrict__ dst, int32_t 
                 split_bytes(wr * s, h[0][q], l[0][q]);
                 split_bytes(wi * s, h[1][q], l[1][q]);
             }
-            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 2 * lane) = h[0][0] | (h[0][1] << 8);
-            *reinterpret_cast<uint16_t *>(row_re + 128 * j + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
-            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 2 * lane) = h[1][0] | (h[1][1] << 8);
-            *reinterpret_cast<uint16_t *>(row_im + 128 * j + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_re + kBlk * j + 2 * lane) = h[0][0] | (h[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + kBlk * j + 2 * lane) = h[1][0] | (h[1][1] << 8);
+            if (!HI) {
+                *reinterpret_cast<uint16_t *>(row_re + kBlk * j + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
+                *reinterpret_cast<uint16_t *>(row_im + kBlk * j + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+            }
         }
         if (lane == 0) exps[r] = e;
     }
@@ -195,7 +200,10 @@ cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double
         auto *d = static_cast<uint8_t *>(Wp);
         auto *ex = reinterpret_cast<int32_t *>(d + rows * 2 * Kb2);
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, int64_t(pl.num_sms) * 32)));
-        weights_split8_kernel<<<grid, 256, 0, s>>>(g, d, ex, Bw, Kb2);
+        if (fp8_hi_only(pl.p.flags))
+            weights_split8_kernel<true><<<grid, 256, 0, s>>>(g, d, ex, Bw, Kb2);
+        else
+            weights_split8_kernel<false><<<grid, 256, 0, s>>>(g, d, ex, Bw, Kb2);
     }
     return cudaGetLastError();
 }

@@ -75,6 +75,26 @@ def small_fp16(seed=0, M=64, K=128, N=1024, B=1):
     return W, X
 
 
+def random_phase_rows(seed, M, K, block_rows=1024, threads=None):
+    """W = exp(i phi), phi ~ U[0, 2 pi) -> FP16, [1, M, K, 2], drawn in
+    blocks of rows from independent streams in parallel (full-size model
+    matrices with the value distribution of the small FP16 workload)."""
+    import concurrent.futures as cf
+    import os
+    out = np.empty((1, M, K, 2), np.float16)
+
+    def one(blk):
+        r0 = blk * block_rows
+        r1 = min(M, r0 + block_rows)
+        phi = batch_rng(seed, blk).uniform(0.0, 2.0 * math.pi, size=(r1 - r0, K))
+        out[0, r0:r1, :, 0] = np.cos(phi)
+        out[0, r0:r1, :, 1] = np.sin(phi)
+
+    with cf.ThreadPoolExecutor(threads or min(32, os.cpu_count() or 4)) as ex:
+        list(ex.map(one, range((M + block_rows - 1) // block_rows)))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Radio-astronomy geometry (Sec. V-B): stations in a disk, beams near zenith.
 # ---------------------------------------------------------------------------

@@ -134,3 +134,45 @@ def test_full_size_ultrasound_split_fp8_sampled():
             got[i] = v[0] + 1j * v[1]
     assert np.linalg.norm(got - ref_split) / np.linalg.norm(ref_split) <= TOL
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 5e-3
+
+
+def test_full_size_ultrasound_plain_fp8_sampled():
+    """Plain E4M3 (one byte per element, hi product only) on the full ultrasound
+    shape.  W is drawn on the host (unit-magnitude random phases, FP16) so both
+    sides see the same FP16 values: the GPU packs and multiplies them, the
+    oracle splits the same rows and takes the one-product sum.  Parity bar 2e-5;
+    the method's accuracy against the exact product (a few percent) is stated
+    with a loose ceiling."""
+    import torch
+    from gpu_util import empty_bytes
+    from paper_2505_03269_gb300 import FLAG_FP8_HI_ONLY, MODE_FP8SPLIT, Plan
+    M, K, N = 65536, 16384, 256
+    W = ti.random_phase_rows(3, M, K)
+    Xh = ti.ultrasound_frames(1, K, N)
+    with Plan(1, M, N, K, MODE_FP8SPLIT, flags=FLAG_FP8_HI_ONLY) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        Xp = empty_bytes(plan.packed_size(1))
+        Wd = torch.from_numpy(W).cuda()
+        plan.transpose_pack(0, Wd, Wp)
+        del Wd
+        plan.transpose_pack(1, torch.from_numpy(Xh).cuda(), Xp)
+        Y = torch.full((1, M, N, 2), float("nan"), dtype=torch.float32, device="cuda")
+        plan.beamform_fp8split(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        g = np.random.default_rng(13)
+        ms, ns = g.integers(0, M, 48), g.integers(0, N, 48)
+        got = np.empty(48, np.complex128)
+        ref_fp8 = np.empty(48, np.complex128)
+        ref = np.empty(48, np.complex128)
+        for i, (m, n) in enumerate(zip(ms, ns)):
+            Wrow = np.ascontiguousarray(W[:, m:m + 1])
+            Xcol = np.ascontiguousarray(Xh[:, :, n:n + 1])
+            ref_fp8[i] = oracle.cgemm_split(Wrow, Xcol, products=1)[0, 0, 0]
+            ref[i] = oracle.cgemm(Wrow, Xcol)[0, 0, 0]
+            v = Y[0, int(m), int(n)].double().cpu().numpy()
+            got[i] = v[0] + 1j * v[1]
+        del Y
+    torch.cuda.empty_cache()
+    assert np.linalg.norm(got - ref_fp8) / np.linalg.norm(ref_fp8) <= TOL
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-1
