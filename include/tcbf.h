@@ -197,6 +197,22 @@ tcbf_status tcbf_weights_from_geometry(tcbf_plan_t plan, const double *rx_pos,
  * Returns TCBF_OK, TCBF_ERR_TIMEOUT or TCBF_ERR_DEVICE. */
 tcbf_status tcbf_last_device_error(tcbf_plan_t plan);
 
+/* Test hook for the device-side failure path (every wait in the GEMM
+ * kernels gives up after 2 s and records it in the status word).  The next
+ * tcbf_beamform_fp16 / tcbf_beamform_fp8split call on this plan launches
+ * with the operand load number `fill` (0-based, in the first CTA's order of
+ * stages) left out: its shared-memory slot is never marked full, so the
+ * MMA issuer's wait runs out, the CTA records the timeout, lets its other
+ * copies land, releases tensor memory and returns (after about 4 s); other
+ * CTAs finish normally and that CTA's tiles of Y are left unwritten.
+ * tcbf_last_device_error then returns TCBF_ERR_TIMEOUT and the device
+ * context stays usable.  Applies to one call, then clears; fill < 0 clears
+ * it at once.  Supported on plans running a one-SM, non-cluster tile
+ * configuration of the FP16 or FP8 GEMM (configurations 0-5, no stacked
+ * planes, even batches), else TCBF_ERR_UNSUPPORTED.  Nothing faults, traps
+ * or spins without a limit. */
+tcbf_status tcbf_debug_drop_fill(tcbf_plan_t plan, int64_t fill);
+
 /* Static text for a status code. */
 const char *tcbf_status_string(tcbf_status s);
 

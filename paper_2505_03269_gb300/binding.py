@@ -32,7 +32,7 @@ EXPORTED = [
     "tcbf_status_string", "tcbf_plan_num_configs", "tcbf_plan_get_config",
     "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
     "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
-    "tcbf_beamform_host",
+    "tcbf_beamform_host", "tcbf_debug_drop_fill",
 ]
 
 
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_beamform_1bit": [vp, vp, vp, vp, vp],
         "tcbf_weights_from_geometry": [vp, vp, vp, i32, vp, ctypes.c_double, vp, vp],
         "tcbf_last_device_error": [vp],
+        "tcbf_debug_drop_fill": [vp, ctypes.c_int64],
         "tcbf_plan_num_configs": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_get_config": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_set_config": [vp, i32],
@@ -189,6 +190,12 @@ class Plan:
 
     def last_device_error(self) -> int:
         return self._lib.tcbf_last_device_error(self.handle)
+
+    def debug_drop_fill(self, fill: int):
+        """Test hook of the device failure path: the next beamform call leaves
+        out operand load `fill` of the first CTA, so its bounded waits run out
+        (TCBF_ERR_TIMEOUT from last_device_error).  fill < 0 clears it."""
+        _check(self._lib.tcbf_debug_drop_fill(self.handle, int(fill)), "debug_drop_fill")
 
     # ------------------------------------------------------------- configs
     def num_configs(self) -> int:

@@ -226,7 +226,9 @@ TCBF_EXPORT tcbf_status tcbf_beamform_fp16(tcbf_plan_t plan, const void *Wp, con
     if (!aligned16(Wp) || !aligned16(Xp) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     if (!g.ok()) return TCBF_ERR_CUDA;
-    return from_cuda(launch_gemm_f16(*plan, Wp, Xp, Y, static_cast<cudaStream_t>(stream)));
+    const cudaError_t e = launch_gemm_f16(*plan, Wp, Xp, Y, static_cast<cudaStream_t>(stream));
+    plan->debug_drop_fill = -1;          // the test hook applies to one call
+    return from_cuda(e);
 }
 
 TCBF_EXPORT tcbf_status tcbf_beamform_fp8split(tcbf_plan_t plan, const void *Wp, const void *Xp,
@@ -236,7 +238,26 @@ TCBF_EXPORT tcbf_status tcbf_beamform_fp8split(tcbf_plan_t plan, const void *Wp,
     if (!aligned16(Wp) || !aligned16(Xp) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     if (!g.ok()) return TCBF_ERR_CUDA;
-    return from_cuda(launch_gemm_split8(*plan, Wp, Xp, Y, static_cast<cudaStream_t>(stream)));
+    const cudaError_t e = launch_gemm_split8(*plan, Wp, Xp, Y, static_cast<cudaStream_t>(stream));
+    plan->debug_drop_fill = -1;          // the test hook applies to one call
+    return from_cuda(e);
+}
+
+TCBF_EXPORT tcbf_status tcbf_debug_drop_fill(tcbf_plan_t plan, int64_t fill) {
+    if (!plan) return TCBF_ERR_INVALID_ARG;
+    if (fill < 0) {
+        plan->debug_drop_fill = -1;
+        return TCBF_OK;
+    }
+    if (plan->p.mode != TCBF_MODE_FP16 && plan->p.mode != TCBF_MODE_FP8SPLIT)
+        return TCBF_ERR_UNSUPPORTED;
+    // one-SM, non-cluster tile configurations only (the cluster and pair
+    // kernels share barriers across CTAs)
+    if ((plan->p.flags & TCBF_FLAG_STACKED_X) || plan->config < 0 || plan->config > 5)
+        return TCBF_ERR_UNSUPPORTED;
+    if (fill > 0x7fffffff) return TCBF_ERR_INVALID_ARG;
+    plan->debug_drop_fill = fill;
+    return TCBF_OK;
 }
 
 TCBF_EXPORT tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbits,
@@ -391,6 +412,7 @@ TCBF_EXPORT tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const vo
     DeviceGuard g(plan->device);
     if (!g.ok()) return TCBF_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    plan->debug_drop_fill = -1;
     int n = 0;
     tcbf_plan_num_configs(plan, &n);
     cudaEvent_t e0, e1;
@@ -440,6 +462,7 @@ TCBF_EXPORT tcbf_status tcbf_graph_capture(tcbf_plan_t plan, const void *X_src, 
         return TCBF_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     if (!g.ok()) return TCBF_ERR_CUDA;
+    plan->debug_drop_fill = -1;
     if (plan->graph_exec) {
         cudaGraphExecDestroy(plan->graph_exec);
         plan->graph_exec = nullptr;

@@ -64,6 +64,7 @@ struct GemmArgs {
     int chunks;                // accumulation chunks per tile
     int total_tiles;
     int products;              // split-FP8: 1 (hi hi), 3 (+ hi lo, lo hi) or 4 (+ lo lo)
+    int drop_fill;             // test hook: CTA 0 leaves out this operand load (-1: none)
 };
 
 constexpr int pow2_cols(int c) {
@@ -214,13 +215,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     const uint32_t fb = full0 + 8 * stage;
                     const uint32_t dst = s0 + stage * C::STAGE_BYTES;
-                    mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
                     // x: 128 bytes per stage in both formats (64 FP16, or 64 hi + 64 lo bytes)
                     const int x = kb * (SPLIT ? 128 : BK);
-                    tma_load_3d(dst, &tmW, fb, x, mt * BM, 2 * bw);
                     if (CL == 1) {
-                        tma_load_3d(dst + C::A_BYTES, &tmX, fb, x, nt * BN, 2 * b);
+                        // the failure-path test hook leaves one load (and its arrival) out
+                        if (blockIdx.x != 0 || static_cast<int>(issued) != args.drop_fill) {
+                            mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
+                            tma_load_3d(dst, &tmW, fb, x, mt * BM, 2 * bw);
+                            tma_load_3d(dst + C::A_BYTES, &tmX, fb, x, nt * BN, 2 * b);
+                        }
                     } else {
+                        mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
+                        tma_load_3d(dst, &tmW, fb, x, mt * BM, 2 * bw);
                         constexpr int kRows = BN / CL;
 #pragma unroll
                         for (int pl = 0; pl < 2; ++pl)
@@ -884,6 +890,7 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
                      : nullptr;
     a.tma_store = tma_store;
     a.products = split_products(pl);
+    a.drop_fill = (CL == 1 && pl.debug_drop_fill >= 0) ? static_cast<int>(pl.debug_drop_fill) : -1;
     a.status = pl.status;
     a.M = static_cast<int>(p.M);
     a.N = static_cast<int>(p.N);
@@ -1002,6 +1009,7 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
                      : nullptr;
     a.tma_store = tma_store;
     a.products = split_products(pl);
+    a.drop_fill = -1;
     a.status = pl.status;
     a.M = static_cast<int>(p.M);
     a.N = static_cast<int>(p.N);

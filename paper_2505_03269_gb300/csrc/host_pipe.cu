@@ -234,6 +234,7 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
         sub.p.w_batches = nb / per_w;
         sub.graph_exec = nullptr;
         sub.pipe = nullptr;
+        sub.debug_drop_fill = -1;
         sub.w_exps = w_exps_all ? w_exps_all + wb0 * p.M : nullptr;
         const void *w_sub = static_cast<const uint8_t *>(Wp) + wb0 * wb;
 

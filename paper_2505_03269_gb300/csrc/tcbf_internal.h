@@ -30,6 +30,8 @@ struct tcbf_plan_s {
     const int32_t *w_exps = nullptr;
     // staging, streams and events of tcbf_beamform_host, made at its first call
     struct tcbf_host_pipe *pipe = nullptr;
+    // tcbf_debug_drop_fill: operand load left out by the next GEMM launch (-1: none)
+    int64_t debug_drop_fill = -1;
 };
 
 namespace tcbf {
