@@ -600,13 +600,21 @@ def main():
         e2e = {"value": whole_job_value(world, ops_per_step(w), te_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(gw.Xh.nbytes), "d2h_bytes_per_step": int(gw.Y.numel() * 4),
                "ms_per_step": te_ms,
-               "how": "tcbf_beamform_host on pinned host X and Y: chunks of batches, "
-                      "host-to-device copy, pack + beamform and device-to-host copy of "
-                      "neighbouring chunks overlapped on separate streams",
-               "chunk": args.e2e_chunk or "auto (about batch / 16)",
+               "how": "tcbf_beamform_host on pinned host X and Y: "
+                      + ("ranges of W rows of the one product (X in and packed once), "
+                         "beamform of one range overlapped with the device-to-host copy of "
+                         "the previous on separate streams" if w["B"] == 1 else
+                         "chunks of batches, host-to-device copy, pack + beamform and "
+                         "device-to-host copy of neighbouring chunks overlapped on separate "
+                         "streams"),
+               "chunk": ("about M / 4 rows, whole waves of 128-row tiles" if w["B"] == 1
+                         else args.e2e_chunk or "auto (about batch / 16)"),
                "d2h_link_gbs": link_gbs,
                "d2h_floor_ms": gw.Y.numel() * 4 / link_gbs / 1e6,
-               "frac_of_d2h_floor": gw.Y.numel() * 4 / link_gbs / 1e6 / te_ms}
+               "frac_of_d2h_floor": gw.Y.numel() * 4 / link_gbs / 1e6 / te_ms,
+               # the larger of the two limits: the device-resident step and the Y copy-out
+               "floor_ms": max(ms_per_step, gw.Y.numel() * 4 / link_gbs / 1e6),
+               "frac_of_floor": max(ms_per_step, gw.Y.numel() * 4 / link_gbs / 1e6) / te_ms}
         del Xhost, Yhost
 
     # ---- roofline of the dominant kernel (the GEMM)

@@ -308,6 +308,10 @@ tcbf_status tcbf_graph_launch(tcbf_plan_t plan, tcbf_stream_t stream);
  *           FP32 (FP16 and split-FP8 plans) or int32 (1-bit plans).
  *   chunk:  batches per chunk, a positive multiple of batch / w_batches (the
  *           last chunk may be shorter); 0 picks about batch / 16.
+ * A single-batch problem (batch = 1) is cut into ranges of W rows instead:
+ * X is copied in and packed once, then each range of about M / 4 rows
+ * (whole waves of 128-row tiles over the SMs) is beamformed and its rows of
+ * Y copied out while the next range computes; chunk must be 0 or 1.
  * Device staging for three chunks (source X, packed X, Y) is allocated at
  * the first call, or when `chunk` grows, and kept by the plan until
  * tcbf_plan_destroy; TCBF_ERR_OOM if it cannot be had.  The work starts

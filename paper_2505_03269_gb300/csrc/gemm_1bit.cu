@@ -45,6 +45,7 @@ struct Args1 {
     uint32_t *status;
     int tma_store;
     int M, N, K, Kw;
+    int w_rows;            // rows between packed W planes (M, or more for a row range)
     int per_w;
     TileMap tiles;
     int num_kb, total_tiles;
@@ -167,7 +168,7 @@ struct StageCursor {
                 const int plane = rp / BM, mrow = mt * BM + rp % BM;
                 if (mrow < args.M)
                     row[j] = args.Wb +
-                             (static_cast<size_t>((b / args.per_w) * 2 + plane) * args.M + mrow) * args.Kw;
+                             (static_cast<size_t>((b / args.per_w) * 2 + plane) * args.w_rows + mrow) * args.Kw;
             } else if (rp < 2 * BM + XPL * BN) {
                 const int x = rp - 2 * BM;
                 // stacked slots -Xi, Xr, Xi read the imaginary, real, imaginary bits
@@ -477,6 +478,7 @@ cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *X
     a.status = pl.status;
     a.tma_store = tma_store;
     a.M = static_cast<int>(p.M);
+    a.w_rows = static_cast<int>(w_plane_rows(pl));
     a.N = static_cast<int>(p.N);
     a.K = static_cast<int>(p.K);
     a.Kw = static_cast<int>(pl.Kw);

@@ -847,7 +847,7 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
         const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.M),
                                   static_cast<uint64_t>(2 * p.w_batches)};
         const uint64_t strides[2] = {static_cast<uint64_t>(row * esz),
-                                     static_cast<uint64_t>(p.M * row * esz)};
+                                     static_cast<uint64_t>(w_plane_rows(pl) * row * esz)};
         const uint32_t box[3] = {static_cast<uint32_t>(128 / esz), BM, 2};
         if (encode_tiled(&tmW, dt, 3, const_cast<void *>(Wp), dims,
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
@@ -969,7 +969,7 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
         const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.M),
                                   static_cast<uint64_t>(2 * p.w_batches)};
         const uint64_t strides[2] = {static_cast<uint64_t>(row * esz),
-                                     static_cast<uint64_t>(p.M * row * esz)};
+                                     static_cast<uint64_t>(w_plane_rows(pl) * row * esz)};
         const uint32_t box[3] = {static_cast<uint32_t>(128 / esz), BM, 2};
         if (encode_tiled(&tmW, dt, 3, const_cast<void *>(Wp), dims, strides, box,
                          CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)

@@ -389,7 +389,7 @@ cudaError_t launch_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp
         const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.M),
                                   static_cast<uint64_t>(2 * p.w_batches)};
         const uint64_t strides[2] = {static_cast<uint64_t>(row * 2),
-                                     static_cast<uint64_t>(p.M * row * 2)};
+                                     static_cast<uint64_t>(w_plane_rows(pl) * row * 2)};
         const uint32_t box[3] = {SBK, SBM, 2};
         if (encode_tiled(&tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Wp), dims,
                          strides, box, CU_TENSOR_MAP_SWIZZLE_64B) != CUDA_SUCCESS)

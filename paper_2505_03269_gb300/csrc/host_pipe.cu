@@ -10,8 +10,16 @@
 //   d2h streams:    wait comp[s]; Yd[s] -> Y_host, split over kD2h streams   -> d2h[s]
 // The chunk's work goes to a sub-plan (batch = nb, w_batches = nb / per_w)
 // whose W is the matching sub-range of the packed weights.
+//
+// A single-batch problem has nothing to overlap across batches, so it is cut
+// into ranges of W rows instead: X is copied in and packed once, then each
+// range's GEMM (a sub-plan over rows [m0, m0 + rows) of the same packed W)
+// writes slot s and its rows of Y are copied out while the next range
+// computes.  Ranges are whole waves of 128-row tiles over all SMs, so the
+// persistent grid stays full.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <new>
 
@@ -22,6 +30,7 @@ namespace {
 
 constexpr int kSlots = 3;   // chunks in flight: one copying in, one computing, one copying out
 constexpr int kD2h = 2;     // device-to-host streams per chunk (Y is the large direction)
+constexpr int kRowRanges = 4;   // row ranges of a single-batch problem (about)
 
 }  // namespace
 }  // namespace tcbf
@@ -103,6 +112,15 @@ int64_t packed_x_bytes(const tcbf_plan_s &pl, int64_t nb) {
         case TCBF_MODE_FP16: return nb * x_planes(pl) * N * pl.Kp * 2;
         case TCBF_MODE_1BIT: return nb * 2 * N * pl.Kw * 4;
         default: return nb * 2 * N * pl.Kb2 + nb * N * 4;
+    }
+}
+
+// Bytes of one packed W row in one plane.
+int64_t packed_w_row_bytes(const tcbf_plan_s &pl) {
+    switch (pl.p.mode) {
+        case TCBF_MODE_FP16: return pl.Kp * 2;
+        case TCBF_MODE_1BIT: return pl.Kw * 4;
+        default: return pl.Kb2;
     }
 }
 
@@ -223,48 +241,95 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
     const auto *xh = static_cast<const uint8_t *>(X_host);
     auto *yh = static_cast<uint8_t *>(Y_host);
 
-    int64_t c = 0;
-    for (int64_t b0 = 0; b0 < p.batch && e == cudaSuccess; b0 += chunk, ++c) {
-        const int s = static_cast<int>(c % kSlots);
-        const int64_t nb = b0 + chunk <= p.batch ? chunk : p.batch - b0;
-        const int64_t wb0 = b0 / per_w;
-        // the chunk's sub-plan: its batches, their weights
-        tcbf_plan_s sub = *plan;
-        sub.p.batch = nb;
-        sub.p.w_batches = nb / per_w;
-        sub.graph_exec = nullptr;
-        sub.pipe = nullptr;
-        sub.debug_drop_fill = -1;
-        sub.w_exps = w_exps_all ? w_exps_all + wb0 * p.M : nullptr;
-        const void *w_sub = static_cast<const uint8_t *>(Wp) + wb0 * wb;
-
-        // copy in (the slot's source buffer is free once its last pack ran)
-        if (hp.used[s]) e = cudaStreamWaitEvent(hp.h2d, hp.ev_comp[s], 0);
+    if (p.batch == 1) {
+        // ---- one batch: X in and packed once, then ranges of W rows
+        const int64_t n_tiles = ceil_div(p.N, 128);
+        const int64_t rows_wave = 128 * std::max<int64_t>(1, plan->num_sms / n_tiles);
+        const int64_t rows = round_up(ceil_div(p.M, kRowRanges), rows_wave);
+        const int64_t wrow = packed_w_row_bytes(*plan);
+        for (int s = 0; s < kSlots && e == cudaSuccess; ++s)
+            if (hp.used[s]) e = cudaStreamWaitEvent(hp.h2d, hp.ev_comp[s], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hp.xsrc[s], xh + b0 * xsrc_per_b, static_cast<size_t>(nb * xsrc_per_b),
-                                cudaMemcpyHostToDevice, hp.h2d);
-        if (e == cudaSuccess) e = cudaEventRecord(hp.ev_h2d[s], hp.h2d);
-        // compute (the slot's Y is free once its last copy-out ran)
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.comp, hp.ev_h2d[s], 0);
-        for (int i = 0; i < kD2h && e == cudaSuccess && hp.used[s]; ++i)
-            e = cudaStreamWaitEvent(hp.comp, hp.ev_d2h[s][i], 0);
-        if (e == cudaSuccess) e = pack_x(sub, src_type, hp.xsrc[s], hp.xp[s], hp.comp);
-        if (e == cudaSuccess) e = beamform(sub, w_sub, hp.xp[s], hp.yd[s], hp.comp);
-        if (e == cudaSuccess) e = cudaEventRecord(hp.ev_comp[s], hp.comp);
-        // copy out, split by batches (or by bytes for one batch) over the d2h streams
-        const int64_t ybytes = nb * y_per_b;
-        int64_t off = 0;
-        for (int i = 0; i < kD2h && e == cudaSuccess; ++i) {
-            int64_t part = (ybytes / kD2h + 15) / 16 * 16;
-            if (i == kD2h - 1 || off + part > ybytes) part = ybytes - off;
-            e = cudaStreamWaitEvent(hp.d2h[i], hp.ev_comp[s], 0);
-            if (e == cudaSuccess && part > 0)
-                e = cudaMemcpyAsync(yh + b0 * y_per_b + off, static_cast<uint8_t *>(hp.yd[s]) + off,
-                                    static_cast<size_t>(part), cudaMemcpyDeviceToHost, hp.d2h[i]);
-            if (e == cudaSuccess) e = cudaEventRecord(hp.ev_d2h[s][i], hp.d2h[i]);
-            off += part;
+            e = cudaMemcpyAsync(hp.xsrc[0], xh, static_cast<size_t>(xsrc_per_b), cudaMemcpyHostToDevice,
+                                hp.h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(hp.ev_h2d[0], hp.h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.comp, hp.ev_h2d[0], 0);
+        if (e == cudaSuccess) e = pack_x(*plan, src_type, hp.xsrc[0], hp.xp[0], hp.comp);
+        int64_t c = 0;
+        for (int64_t m0 = 0; m0 < p.M && e == cudaSuccess; m0 += rows, ++c) {
+            const int s = static_cast<int>(c % kSlots);
+            const int64_t nr = std::min(rows, p.M - m0);
+            tcbf_plan_s sub = *plan;
+            sub.p.M = nr;
+            sub.w_rows = p.M;
+            sub.graph_exec = nullptr;
+            sub.pipe = nullptr;
+            sub.debug_drop_fill = -1;
+            sub.w_exps = w_exps_all ? w_exps_all + m0 : nullptr;
+            const void *w_sub = static_cast<const uint8_t *>(Wp) + m0 * wrow;
+            // the slot's Y is free once its last copy-out ran
+            for (int i = 0; i < kD2h && e == cudaSuccess && hp.used[s]; ++i)
+                e = cudaStreamWaitEvent(hp.comp, hp.ev_d2h[s][i], 0);
+            if (e == cudaSuccess) e = beamform(sub, w_sub, hp.xp[0], hp.yd[s], hp.comp);
+            if (e == cudaSuccess) e = cudaEventRecord(hp.ev_comp[s], hp.comp);
+            const int64_t ybytes = nr * p.N * 8;
+            int64_t off = 0;
+            for (int i = 0; i < kD2h && e == cudaSuccess; ++i) {
+                int64_t part = (ybytes / kD2h + 15) / 16 * 16;
+                if (i == kD2h - 1 || off + part > ybytes) part = ybytes - off;
+                e = cudaStreamWaitEvent(hp.d2h[i], hp.ev_comp[s], 0);
+                if (e == cudaSuccess && part > 0)
+                    e = cudaMemcpyAsync(yh + m0 * p.N * 8 + off, static_cast<uint8_t *>(hp.yd[s]) + off,
+                                        static_cast<size_t>(part), cudaMemcpyDeviceToHost, hp.d2h[i]);
+                if (e == cudaSuccess) e = cudaEventRecord(hp.ev_d2h[s][i], hp.d2h[i]);
+                off += part;
+            }
+            if (e == cudaSuccess) hp.used[s] = true;
         }
-        if (e == cudaSuccess) hp.used[s] = true;
+    } else {
+        int64_t c = 0;
+        for (int64_t b0 = 0; b0 < p.batch && e == cudaSuccess; b0 += chunk, ++c) {
+            const int s = static_cast<int>(c % kSlots);
+            const int64_t nb = b0 + chunk <= p.batch ? chunk : p.batch - b0;
+            const int64_t wb0 = b0 / per_w;
+            // the chunk's sub-plan: its batches, their weights
+            tcbf_plan_s sub = *plan;
+            sub.p.batch = nb;
+            sub.p.w_batches = nb / per_w;
+            sub.graph_exec = nullptr;
+            sub.pipe = nullptr;
+            sub.debug_drop_fill = -1;
+            sub.w_exps = w_exps_all ? w_exps_all + wb0 * p.M : nullptr;
+            const void *w_sub = static_cast<const uint8_t *>(Wp) + wb0 * wb;
+
+            // copy in (the slot's source buffer is free once its last pack ran)
+            if (hp.used[s]) e = cudaStreamWaitEvent(hp.h2d, hp.ev_comp[s], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hp.xsrc[s], xh + b0 * xsrc_per_b, static_cast<size_t>(nb * xsrc_per_b),
+                                    cudaMemcpyHostToDevice, hp.h2d);
+            if (e == cudaSuccess) e = cudaEventRecord(hp.ev_h2d[s], hp.h2d);
+            // compute (the slot's Y is free once its last copy-out ran)
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.comp, hp.ev_h2d[s], 0);
+            for (int i = 0; i < kD2h && e == cudaSuccess && hp.used[s]; ++i)
+                e = cudaStreamWaitEvent(hp.comp, hp.ev_d2h[s][i], 0);
+            if (e == cudaSuccess) e = pack_x(sub, src_type, hp.xsrc[s], hp.xp[s], hp.comp);
+            if (e == cudaSuccess) e = beamform(sub, w_sub, hp.xp[s], hp.yd[s], hp.comp);
+            if (e == cudaSuccess) e = cudaEventRecord(hp.ev_comp[s], hp.comp);
+            // copy out, split by batches (or by bytes for one batch) over the d2h streams
+            const int64_t ybytes = nb * y_per_b;
+            int64_t off = 0;
+            for (int i = 0; i < kD2h && e == cudaSuccess; ++i) {
+                int64_t part = (ybytes / kD2h + 15) / 16 * 16;
+                if (i == kD2h - 1 || off + part > ybytes) part = ybytes - off;
+                e = cudaStreamWaitEvent(hp.d2h[i], hp.ev_comp[s], 0);
+                if (e == cudaSuccess && part > 0)
+                    e = cudaMemcpyAsync(yh + b0 * y_per_b + off, static_cast<uint8_t *>(hp.yd[s]) + off,
+                                        static_cast<size_t>(part), cudaMemcpyDeviceToHost, hp.d2h[i]);
+                if (e == cudaSuccess) e = cudaEventRecord(hp.ev_d2h[s][i], hp.d2h[i]);
+                off += part;
+            }
+            if (e == cudaSuccess) hp.used[s] = true;
+        }
     }
     // the caller's stream waits for every copy-out
     for (int i = 0; i < kD2h && e == cudaSuccess; ++i) {

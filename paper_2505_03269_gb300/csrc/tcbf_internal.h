@@ -32,6 +32,9 @@ struct tcbf_plan_s {
     struct tcbf_host_pipe *pipe = nullptr;
     // tcbf_debug_drop_fill: operand load left out by the next GEMM launch (-1: none)
     int64_t debug_drop_fill = -1;
+    // rows between the planes of packed W (0: M).  Row-range sub-plans of
+    // tcbf_beamform_host point into a larger packed W.
+    int64_t w_rows = 0;
 };
 
 namespace tcbf {
@@ -91,6 +94,9 @@ inline int64_t fp8_block_bytes(uint32_t flags) { return fp8_hi_only(flags) ? 64 
 inline int64_t fp8_row_bytes(int64_t K, uint32_t flags) {
     return round_up(K, 64) / 64 * fp8_block_bytes(flags);
 }
+
+// Rows between the planes of the packed W a GEMM launch reads.
+inline int64_t w_plane_rows(const tcbf_plan_s &pl) { return pl.w_rows ? pl.w_rows : pl.p.M; }
 
 // Planes of packed FP16 X: 3 with TCBF_FLAG_STACKED_X, else 2.
 inline int64_t x_planes(const tcbf_plan_s &pl) {

@@ -1,5 +1,6 @@
 """tcbf_beamform_host: the step for host-resident X and Y, chunked over the
-batches with the copies overlapped with the kernels.
+batches (a single batch: over ranges of W rows) with the copies overlapped
+with the kernels.
 
 Bars: bit-exact against the device-buffer path of the same plan (the same
 kernels on the same batches; only the data movement differs) for every
@@ -128,3 +129,34 @@ def test_invalid_arguments():
         plan.set_batch_rows([64, 10, 64, 1])
         with pytest.raises(TcbfError, match="UNSUPPORTED"):
             plan.beamform_host(Xh, Wp, Yh, chunk=2)
+
+
+# One batch: X in and packed once, then ranges of W rows, each copied out while the
+# next computes.  M = 20000 with N = 300 gives ranges of 6400 rows (whole waves of
+# 128-row tiles on 152 SMs) and a ragged last range of 800; M = 100 is one range.
+@pytest.mark.parametrize("mode,flags", [(0, 0), (0, 1), (1, 0), (1, 2), (2, 0)])
+@pytest.mark.parametrize("M", [20000, 100])
+def test_single_batch_row_ranges_equal_device_path(mode, flags, M):
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import Plan
+    N, K = 300, 64
+    W, X = _inputs(M + flags, 1, 1, M, N, K, 0)
+    with Plan(1, M, N, K, mode, flags=flags) as plan:
+        Wp, Yref = _device_path(plan, mode, dev(W), dev(X), 0, 1, M, N)
+        Yh = _host_path(plan, Wp, _pinned(X), Yref, 0, 0, calls=2)
+    assert np.array_equal(Yh.numpy(), Yref.numpy())
+
+
+def test_single_batch_fp32_source_against_oracle():
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_FP16, Plan
+    M, N, K = 13000, 256, 96
+    W, X = _inputs(5, 1, 1, M, N, K, 1)
+    with Plan(1, M, N, K, MODE_FP16) as plan:
+        Wp, Yref = _device_path(plan, MODE_FP16, dev(W), dev(X), 1, 1, M, N)
+        Yh = _host_path(plan, Wp, _pinned(X), Yref, 0, 1).numpy()
+    assert np.array_equal(Yh, Yref.numpy())
+    rows = np.arange(0, M, 37)
+    Y = Yh[0, rows, :, 0].astype(np.float64) + 1j * Yh[0, rows, :, 1]
+    ref = oracle.cgemm(np.ascontiguousarray(W[:, rows].astype(np.float16)), X.astype(np.float16))[0]
+    assert oracle.rel_frobenius(Y, ref) <= TOL
