@@ -55,6 +55,16 @@ WORKLOADS = {
         mode="1bit", B=64, M=2048, N=8192, K=1024, w_batches=64, geometry=None,
         desc="radio-astronomy 1-bit block: 64 channels x 2048 beams x 1024 receivers x "
              "8192 samples, +-1+-i values, exact int32 output"),
+    # the paper's kernel-tuning shapes (Sec. IV, Table III), for comparison with its
+    # TeraOps/s and TeraOps/J; the 1-bit one with K cut from 524288 so a step takes seconds
+    "paper_fp16": dict(
+        mode="fp16", B=1, M=8192, N=8192, K=8192, w_batches=1, geometry="random", stacked=True,
+        desc="paper tuning shape FP16: M = N = K = 8192, W = exp(i phi) random phases, "
+             "X complex Gaussian"),
+    "paper_int1": dict(
+        mode="1bit", B=1, M=32768, N=8192, K=65536, w_batches=1, geometry=None, x_phase=True,
+        desc="paper tuning shape 1-bit with K reduced: 32768 x 8192 x 65536 (the paper's K is "
+             "524288), +-1+-i values, exact int32 output"),
 }
 
 
@@ -70,6 +80,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-energy", action="store_true", help="skip the power-sampled loops")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="batches per chunk of the end-to-end host pipeline (0: about batch / 16)")
     ap.add_argument("--mode", choices=["fp16", "fp8split", "fp8"], default=None,
@@ -238,6 +249,8 @@ class ClockSampler:
 def geometry_of(w):
     import numpy as np
     import tcbf_inputs as ti
+    if w["geometry"] == "random":
+        return None
     if w["geometry"] == "radio":
         return ti.radio_geometry(0, w["M"], w["K"], max(1, w["B"] // 2))
     if w["geometry"] == "ultrasound":
@@ -251,6 +264,10 @@ def geometry_of(w):
 
 def host_x(w):
     import tcbf_inputs as ti
+    if w.get("x_phase"):       # unit-magnitude random phases, drawn in parallel (large K)
+        return ti.random_phase_rows(1, w["K"], w["N"])
+    if w["geometry"] == "random":
+        return ti.complex_gaussian_fp16(ti.rng(1), (w["B"], w["K"], w["N"]))
     if w["geometry"] == "ultrasound":
         return ti.ultrasound_frames(1, w["K"], w["N"])
     return ti.radio_x(1, w["B"], w["K"], w["N"])
@@ -270,7 +287,7 @@ def oracle_sample(w, seconds_target):
 
     if w["mode"] == "1bit":
         Wb = onebit_weights(w)[:1]
-        X = ti.radio_x_batch(1, 0, w["K"], w["N"])[None]
+        X = host_x(w) if w.get("x_phase") else ti.radio_x_batch(1, 0, w["K"], w["N"])[None]
         Xb = oracle.pack_signs(X, k_is_row=True, Kw=Wb.shape[-1])
 
         def run(rows):
@@ -285,6 +302,19 @@ def oracle_sample(w, seconds_target):
             f"{rows} of {w['M']} beam rows of one product (int64 loops)"
 
     geom = geometry_of(w)
+    if w["geometry"] == "random":
+        X = host_x(w)
+        Wr = ti.random_phase_rows(0, 256, w["K"])
+
+        def run(rows):
+            t0 = time.perf_counter()
+            oracle.cgemm(Wr[:, :rows], X)
+            return time.perf_counter() - t0
+        rows = 4
+        dt = run(rows)
+        rows = max(4, min(256, int(rows * seconds_target / max(dt, 1e-3))))
+        dt = run(rows)
+        return 8.0 * rows * w["N"] * w["K"], dt, f"{rows} of {w['M']} beam rows of the product"
     if w["geometry"] == "ultrasound":
         X = host_x(w)
 
@@ -385,6 +415,10 @@ class GpuWorkload:
         if w["mode"] == "1bit":
             self.Wbits = onebit_weights(w)
             self.Wp.copy_(torch.from_numpy(self.Wbits.view(np.uint8).ravel()).cuda())
+        elif w["geometry"] == "random":
+            import tcbf_inputs as ti
+            self.Wh = ti.random_phase_rows(0, M, K)
+            self.plan.transpose_pack(0, torch.from_numpy(self.Wh).cuda(), self.Wp)
         else:
             self.geom = geometry_of(w)
             rx = torch.from_numpy(self.geom.rx_pos).cuda()
@@ -442,11 +476,14 @@ class GpuWorkload:
         pts = np.stack([g.integers(0, B, npts), g.integers(0, M, npts), g.integers(0, N, npts)], 1)
         ref = np.empty(npts, np.complex128)
         ref_split = np.empty(npts, np.complex128)
-        geom = self.geom
+        geom = getattr(self, "geom", None)
         for i, (b, m, n) in enumerate(pts):
             bw = b // (B // Bw)
-            Wrow = oracle.weights_fp16(geom.rx_pos, geom.targets[m:m + 1], geom.freqs[bw:bw + 1],
-                                       geom.near_field, geom.c)
+            if geom is None:        # host-drawn weights: the same FP16 rows the GPU packed
+                Wrow = np.ascontiguousarray(self.Wh[bw:bw + 1, m:m + 1])
+            else:
+                Wrow = oracle.weights_fp16(geom.rx_pos, geom.targets[m:m + 1],
+                                           geom.freqs[bw:bw + 1], geom.near_field, geom.c)
             ref[i] = oracle.cgemm_points(Wrow, self.Xh[b:b + 1], np.array([[0, 0, n]]))[0]
             if is_fp8(w):
                 Xcol = np.ascontiguousarray(self.Xh[b:b + 1, :, n:n + 1])
@@ -458,7 +495,8 @@ class GpuWorkload:
         def rel(a, r):
             return float(np.linalg.norm(a - r) / np.linalg.norm(r))
         out = {"points": npts, "rel_err": rel(got, ref),
-               "reference": "FP64 oracle, its own weights from the same geometry"}
+               "reference": ("FP64 oracle on the same host-drawn FP16 weights" if geom is None
+                             else "FP64 oracle, its own weights from the same geometry")}
         if is_fp8(w):
             out["rel_err_vs_split_oracle"] = rel(got, ref_split)
             out["note"] = ("rel_err is the split method's accuracy against the exact product; "
@@ -566,6 +604,38 @@ def main():
     graph_ms = max_over_ranks(g0.elapsed_time(g1) / args.steps, world, "cuda")
 
     parity = gw.parity()
+
+    # ---- energy efficiency (Sec. IV: useful TeraOps/s over the GPU's mean power while the
+    # kernels run): the step, then the GEMM alone, each looped for about a second and a
+    # half with the board power sampled by nvidia-smi every 100 ms
+    energy = None
+    if not args.no_energy:
+        def power_loop(unit, unit_ms):
+            n = max(3, int(1500.0 / max(unit_ms, 1e-3)))
+            sampler = ClockSampler(local)
+            sampler.start()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for _ in range(n):
+                unit()
+            p1.record(stream)
+            torch.cuda.synchronize()
+            clk = sampler.stop()
+            ms = p0.elapsed_time(p1) / n
+            tops = ops_per_step(w) / (ms * 1e-3) / 1e12
+            pw = clk["power_w_median"] if clk else None
+            return {"tops": tops, "ms": ms, "iterations": n,
+                    "power_w_median": pw, "samples": clk["samples"] if clk else 0,
+                    "sm_mhz": clk["sm_mhz"] if clk else None,
+                    "reasons": clk["reasons"] if clk else None,
+                    "tops_per_joule": tops / pw if pw else None}
+        energy = {"step": power_loop(gw.step, ms_per_step),
+                  "gemm": power_loop(gw.gemm, gemm_ms),
+                  "unit": "TeraOps/J",
+                  "how": "useful TeraOps/s of a ~1.5 s loop divided by the median board power "
+                         "nvidia-smi reports during it (every 100 ms); a sustained rate under "
+                         "the board's power limit, below the short timed region's"}
+        barrier()
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -687,6 +757,7 @@ def main():
         "device_status": status,
         "parity_sampled": parity,
         "e2e": e2e,
+        "energy": energy,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
