@@ -269,12 +269,15 @@ tcbf_status tcbf_plan_set_batch_rows(tcbf_plan_t plan, const int64_t *rows);
 /*
  * Autotuner (Sec. IV-A: the work per block and the number of buffers are
  * tuned per GPU and shape).  Times every valid configuration of the plan's
- * mode with CUDA events on `stream` (one warm-up launch, then `reps`
- * launches) on the caller's packed operands and output, selects the fastest
- * and leaves it set on the plan.  Synchronises the stream.  *best receives
- * the chosen configuration; ms_per_config (nullable, tcbf_plan_num_configs
- * entries) the mean milliseconds per launch, -1 for configurations not
- * valid for this shape.  Y is overwritten.  All modes.
+ * mode with CUDA events on `stream` on the caller's packed operands and
+ * output: each is warmed up and sized into a group of launches lasting at
+ * least 0.2 ms, then the configurations are timed round-robin for `reps`
+ * rounds (so a slow drift of the clocks affects them alike) and each keeps
+ * its fastest group.  Selects the fastest and leaves it set on the plan.
+ * Synchronises the stream.  *best receives the chosen configuration;
+ * ms_per_config (nullable, tcbf_plan_num_configs entries) the milliseconds
+ * per launch of each one's fastest group, -1 for configurations not valid
+ * for this shape.  Y is overwritten.  All modes.
  */
 tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const void *Xp, void *Y, int reps,
                           tcbf_stream_t stream, int *best, float *ms_per_config);

@@ -3,9 +3,11 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "tcbf_internal.h"
 
@@ -422,30 +424,50 @@ TCBF_EXPORT tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const vo
         return TCBF_ERR_CUDA;
     }
     const int saved = plan->config;
-    int best_c = -1;
-    float best_ms = 0.f;
     tcbf_status st = TCBF_OK;
-    for (int c = 0; c < n && st == TCBF_OK; ++c) {
-        if (ms_per_config) ms_per_config[c] = -1.f;
-        if (!config_ok(*plan, c)) continue;
+    // Every valid configuration is warmed up and sized into groups of launches
+    // of at least 0.2 ms; then the configurations are timed round-robin, `reps`
+    // rounds, keeping each one's fastest group.  Interleaving the rounds keeps
+    // a slow drift of the clocks (power, temperature) from favouring whichever
+    // configuration happened to run first.
+    std::vector<int> group(static_cast<size_t>(n), 0);
+    std::vector<float> best_ms(static_cast<size_t>(n), -1.f);
+    auto timed = [&](int c, int launches, float &ms) -> cudaError_t {
         plan->config = c;
-        cudaError_t e = launch_beamform(*plan, Wp, Xp, Y, s);        // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_beamform(*plan, Wp, Xp, Y, s);
+        cudaError_t e = cudaEventRecord(e0, s);
+        for (int r = 0; r < launches && e == cudaSuccess; ++r) e = launch_beamform(*plan, Wp, Xp, Y, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        return e;
+    };
+    for (int c = 0; c < n && st == TCBF_OK; ++c) {
+        if (!config_ok(*plan, c)) continue;
+        float ms = 0.f;
+        cudaError_t e = timed(c, 1, ms);                               // warm-up
+        if (e == cudaSuccess) e = timed(c, 1, ms);
         if (e != cudaSuccess) {
             st = from_cuda(e);
             break;
         }
-        ms /= reps;
-        if (ms_per_config) ms_per_config[c] = ms;
-        if (best_c < 0 || ms < best_ms) {
-            best_c = c;
-            best_ms = ms;
+        group[c] = std::max(1, std::min(1000, static_cast<int>(0.2f / std::max(ms, 1e-4f)) + 1));
+    }
+    for (int r = 0; r < reps && st == TCBF_OK; ++r)
+        for (int c = 0; c < n && st == TCBF_OK; ++c) {
+            if (group[c] == 0) continue;
+            float ms = 0.f;
+            const cudaError_t e = timed(c, group[c], ms);
+            if (e != cudaSuccess) {
+                st = from_cuda(e);
+                break;
+            }
+            ms /= group[c];
+            if (best_ms[c] < 0.f || ms < best_ms[c]) best_ms[c] = ms;
         }
+    int best_c = -1;
+    for (int c = 0; c < n; ++c) {
+        if (ms_per_config) ms_per_config[c] = best_ms[c];
+        if (best_ms[c] >= 0.f && (best_c < 0 || best_ms[c] < best_ms[best_c])) best_c = c;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
