@@ -151,6 +151,22 @@ tcbf_status tcbf_transpose_pack(tcbf_plan_t plan, int which, int src_type, const
                                 void *dst, tcbf_stream_t stream);
 
 /*
+ * 1-bit unpacking (Sec. III: the library provides packing and unpacking for
+ * 1-bit data), the inverse of tcbf_transpose_pack on a 1-bit plan: packed
+ * bit planes back to interleaved complex values, bit 1 -> +1 and bit 0 -> -1
+ * (Fig. 1), exactly.
+ *   which = 0: src = packed W [w_batches][2][M][Kw] uint32,
+ *              dst = [w_batches][M][K] interleaved complex
+ *   which = 1: src = packed X [batch][2][N][Kw] uint32,
+ *              dst = [batch][K][N] interleaved complex (un-transposed)
+ *   dst_type:  TCBF_SRC_CF16 (4 bytes per value) or TCBF_SRC_CF32 (8 bytes)
+ * Bits at k >= K are ignored.  Both pointers DEVICE, 16-byte aligned.
+ * TCBF_ERR_INVALID_ARG for another mode or a bad which / dst_type.
+ */
+tcbf_status tcbf_unpack_bits(tcbf_plan_t plan, int which, const uint32_t *src, void *dst,
+                             int dst_type, tcbf_stream_t stream);
+
+/*
  * FP16 complex GEMM, Y[b] = W[b'] X[b] (Eq. 3), four real tensor-core MMAs
  * per complex tile (Sec. III-B) accumulated in FP32.
  *   Wp, Xp: FP16 packed operands of this plan (mode TCBF_MODE_FP16).

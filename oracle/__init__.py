@@ -167,6 +167,21 @@ def pack_signs(V: np.ndarray, k_is_row: bool, Kw: int) -> np.ndarray:
     return out
 
 
+def unpack_signs(P: np.ndarray, K: int, k_is_row: bool) -> np.ndarray:
+    """Packed planes [B, 2, rows, Kw] back to interleaved complex +-1 values
+    (Fig. 1: bit 1 is +1, bit 0 is -1; element k is bit k % 32 of word
+    k / 32): [B, rows, K, 2] (weights), or transposed to [B, K, rows, 2]
+    when k_is_row (data, rows = samples).  Float64."""
+    P = np.ascontiguousarray(P, dtype=np.uint32)
+    k = np.arange(K)
+    bits = (P[..., k // 32] >> (k % 32).astype(np.uint32)) & 1          # [B, 2, rows, K]
+    vals = np.where(bits == 1, 1.0, -1.0)
+    out = np.moveaxis(vals, 1, -1)                                       # [B, rows, K, 2]
+    if k_is_row:
+        out = out.transpose(0, 2, 1, 3)
+    return np.ascontiguousarray(out)
+
+
 def weights(rx_pos, targets, freqs, near_field: bool, c: float) -> np.ndarray:
     """w[b,m,k] = A exp(-2 pi i f[b,k] tau[m,k]) in FP64 -> complex128 [Bw, M, K]."""
     lib = _load()

@@ -32,7 +32,7 @@ EXPORTED = [
     "tcbf_status_string", "tcbf_plan_num_configs", "tcbf_plan_get_config",
     "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
     "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
-    "tcbf_beamform_host", "tcbf_debug_drop_fill",
+    "tcbf_beamform_host", "tcbf_debug_drop_fill", "tcbf_unpack_bits",
 ]
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_weights_from_geometry": [vp, vp, vp, i32, vp, ctypes.c_double, vp, vp],
         "tcbf_last_device_error": [vp],
         "tcbf_debug_drop_fill": [vp, ctypes.c_int64],
+        "tcbf_unpack_bits": [vp, i32, vp, vp, i32, vp],
         "tcbf_plan_num_configs": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_get_config": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_set_config": [vp, i32],
@@ -170,6 +171,12 @@ class Plan:
     def transpose_pack(self, which, src, dst, src_type=SRC_CF16, stream=None):
         _check(self._lib.tcbf_transpose_pack(self.handle, which, src_type, _ptr(src), _ptr(dst),
                                              _stream(stream)), "tcbf_transpose_pack")
+
+    def unpack_bits(self, which, src, dst, dst_type=SRC_CF16, stream=None):
+        """Packed 1-bit planes back to interleaved complex +-1 values (the
+        inverse of transpose_pack on a 1-bit plan)."""
+        _check(self._lib.tcbf_unpack_bits(self.handle, int(which), _ptr(src), _ptr(dst),
+                                          int(dst_type), _stream(stream)), "tcbf_unpack_bits")
 
     def beamform_fp16(self, Wp, Xp, Y, stream=None):
         _check(self._lib.tcbf_beamform_fp16(self.handle, _ptr(Wp), _ptr(Xp), _ptr(Y),

@@ -221,6 +221,18 @@ TCBF_EXPORT tcbf_status tcbf_transpose_pack(tcbf_plan_t plan, int which, int src
     return from_cuda(e);
 }
 
+TCBF_EXPORT tcbf_status tcbf_unpack_bits(tcbf_plan_t plan, int which, const uint32_t *src,
+                                         void *dst, int dst_type, tcbf_stream_t stream) {
+    if (!plan || !src || !dst || (which != 0 && which != 1)) return TCBF_ERR_INVALID_ARG;
+    if (dst_type != TCBF_SRC_CF16 && dst_type != TCBF_SRC_CF32) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_1BIT) return TCBF_ERR_INVALID_ARG;
+    if (!aligned16(src) || !aligned16(dst)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(launch_unpack_bits(*plan, which, src, dst_type, dst,
+                                        static_cast<cudaStream_t>(stream)));
+}
+
 TCBF_EXPORT tcbf_status tcbf_beamform_fp16(tcbf_plan_t plan, const void *Wp, const void *Xp,
                                            float *Y, tcbf_stream_t stream) {
     if (!plan || !Wp || !Xp || !Y) return TCBF_ERR_INVALID_ARG;

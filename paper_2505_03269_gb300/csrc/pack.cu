@@ -251,7 +251,89 @@ __global__ void pack_bits_x_kernel(const void *__restrict__ src, uint32_t *__res
     }
 }
 
+// Unpacking (the inverse of the two kernels above): bits back to interleaved
+// complex +-1 values (Fig. 1: bit 1 is +1, bit 0 is -1), one (re, im) pair
+// per store.  W: one warp per (row, word), lane l writes element 32 w + l.
+// X: lane l owns column n0 + l of one word and walks its 32 rows k, so each
+// store instruction writes 32 consecutive samples of one row.
+__device__ __forceinline__ void store_pm1(__half *p, uint32_t re, uint32_t im) {
+    *reinterpret_cast<__half2 *>(p) = __halves2half2(__float2half_rn(re ? 1.f : -1.f),
+                                                     __float2half_rn(im ? 1.f : -1.f));
+}
+__device__ __forceinline__ void store_pm1(float *p, uint32_t re, uint32_t im) {
+    *reinterpret_cast<float2 *>(p) = make_float2(re ? 1.f : -1.f, im ? 1.f : -1.f);
+}
+
+template <typename T>
+__global__ void unpack_bits_w_kernel(const uint32_t *__restrict__ src, T *__restrict__ dst,
+                                     int64_t rows, int64_t M, int K, int Kw) {
+    const int lane = threadIdx.x & 31;
+    const int words = (K + 31) / 32;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const int64_t total = rows * words;
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < total;
+         i += warps_total) {
+        const int64_t r = i / words;
+        const int w = static_cast<int>(i % words);
+        const int k = 32 * w + lane;
+        const int64_t bw = r / M, m = r % M;
+        const uint32_t wr = __ldg(src + (static_cast<size_t>(bw * 2 + 0) * M + m) * Kw + w);
+        const uint32_t wi = __ldg(src + (static_cast<size_t>(bw * 2 + 1) * M + m) * Kw + w);
+        if (k < K) store_pm1(dst + (static_cast<size_t>(r) * K + k) * 2, (wr >> lane) & 1u, (wi >> lane) & 1u);
+    }
+}
+
+template <typename T>
+__global__ void unpack_bits_x_kernel(const uint32_t *__restrict__ src, T *__restrict__ dst,
+                                     int K, int N, int Kw, int n_groups) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.y;
+    const int words = (K + 31) / 32;
+    const int64_t total = int64_t(words) * n_groups;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < total;
+         i += warps_total) {
+        const int w = static_cast<int>(i / n_groups);
+        const int n = static_cast<int>(i % n_groups) * 32 + lane;
+        if (n >= N) continue;
+        const uint32_t wr = __ldg(src + (static_cast<size_t>(b * 2 + 0) * N + n) * Kw + w);
+        const uint32_t wi = __ldg(src + (static_cast<size_t>(b * 2 + 1) * N + n) * Kw + w);
+        const int kend = min(32, K - 32 * w);
+        for (int j = 0; j < kend; ++j)
+            store_pm1(dst + ((static_cast<size_t>(b) * K + 32 * w + j) * N + n) * 2, (wr >> j) & 1u,
+                      (wi >> j) & 1u);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_unpack_bits(const tcbf_plan_s &pl, int which, const uint32_t *src, int dst_type,
+                               void *dst, cudaStream_t s) {
+    const int K = static_cast<int>(pl.p.K), Kw = static_cast<int>(pl.Kw);
+    const int words = (K + 31) / 32;
+    if (which == 0) {
+        const int64_t rows = pl.p.w_batches * pl.p.M;
+        const int grid = grid_for(rows * words * 32, 256, pl.num_sms);
+        if (dst_type == TCBF_SRC_CF16)
+            unpack_bits_w_kernel<__half><<<grid, 256, 0, s>>>(src, static_cast<__half *>(dst), rows,
+                                                               pl.p.M, K, Kw);
+        else
+            unpack_bits_w_kernel<float><<<grid, 256, 0, s>>>(src, static_cast<float *>(dst), rows,
+                                                              pl.p.M, K, Kw);
+    } else {
+        const int n_groups = static_cast<int>(ceil_div(pl.p.N, 32));
+        const int64_t per_b = int64_t(words) * n_groups * 32;
+        const int bx = std::max(1, std::min(grid_for(per_b, 256, pl.num_sms), 4096));
+        dim3 grid(bx, static_cast<unsigned>(pl.p.batch));
+        if (dst_type == TCBF_SRC_CF16)
+            unpack_bits_x_kernel<__half><<<grid, 256, 0, s>>>(src, static_cast<__half *>(dst), K,
+                                                               int(pl.p.N), Kw, n_groups);
+        else
+            unpack_bits_x_kernel<float><<<grid, 256, 0, s>>>(src, static_cast<float *>(dst), K,
+                                                              int(pl.p.N), Kw, n_groups);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack_f16_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
                               cudaStream_t s) {

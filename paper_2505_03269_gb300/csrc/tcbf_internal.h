@@ -59,6 +59,10 @@ cudaError_t launch_pack_bits_w(const tcbf_plan_s &pl, int src_type, const void *
 cudaError_t launch_pack_bits_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
                                cudaStream_t s);
 
+// 1-bit planes back to interleaved complex +-1 values (FP16 or FP32).
+cudaError_t launch_unpack_bits(const tcbf_plan_s &pl, int which, const uint32_t *src, int dst_type,
+                               void *dst, cudaStream_t s);
+
 cudaError_t launch_pack_split8_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
                                  cudaStream_t s);
 cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,

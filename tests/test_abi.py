@@ -80,6 +80,7 @@ def test_null_arguments(lib):
     assert lib.tcbf_weights_from_geometry(None, None, None, 0, None, 1.0, None, None) == 1
     assert lib.tcbf_last_device_error(None) == 1
     assert lib.tcbf_debug_drop_fill(None, ctypes.c_int64(0)) == 1
+    assert lib.tcbf_unpack_bits(None, 0, None, None, 0, None) == 1
     assert lib.tcbf_plan_destroy(None) == 0
 
 

@@ -167,3 +167,31 @@ def test_weights_then_gemm_pipeline():
     Yg = Yh[..., 0] + 1j * Yh[..., 1]
     Wref = oracle.weights_fp16(geom.rx_pos, geom.targets, geom.freqs[:Bw], False, geom.c)
     assert oracle.rel_frobenius(Yg, oracle.cgemm(Wref, X)) <= 2e-5
+
+
+@pytest.mark.parametrize("which,dst_type", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("B,M,N,K", [(1, 3, 5, 1), (2, 33, 70, 45), (2, 64, 96, 300)])
+def test_unpack_1bit_inverts_pack_exactly(which, dst_type, B, M, N, K):
+    """tcbf_unpack_bits on the GPU's own packed signs gives back sign(v) as +-1,
+    and on random words (junk beyond K included) equals the oracle's unpacking."""
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT
+    W, X = ti.small_fp16(seed=K + 3, M=M, K=K, N=N, B=B)
+    X.reshape(-1)[:2] = np.array([0.0, -0.0], np.float16)
+    V = W if which == 0 else X
+    rows = M if which == 0 else N
+    dt = torch.float16 if dst_type == 0 else torch.float32
+    with _plan(B, M, N, K, MODE_1BIT) as plan:
+        kw = plan.Kw
+        packed = _packed(plan, which, V).view(np.uint32).reshape(B, 2, rows, kw)
+        words = ti.random_sign_words(ti.rng(K + 4), (B, 2, rows, kw))
+        outs = []
+        for src in (packed, words):
+            out = torch.full(V.shape, 7.0, dtype=dt, device="cuda")
+            plan.unpack_bits(which, dev(np.ascontiguousarray(src)), out, dst_type)
+            torch.cuda.synchronize()
+            assert plan.last_device_error() == 0
+            outs.append(out.cpu().numpy().astype(np.float64))
+    assert np.array_equal(outs[0], np.where(V.astype(np.float64) >= 0, 1.0, -1.0))
+    assert np.array_equal(outs[1], oracle.unpack_signs(words, K, k_is_row=(which == 1)))

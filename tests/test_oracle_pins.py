@@ -400,3 +400,26 @@ def test_plain_fp8_error_level_on_gaussian_data():
     assert e3 < e1 / 5
     with pytest.raises(ValueError):
         oracle.cgemm_split(W, X, products=2)
+
+
+def test_unpack_signs_table2_and_round_trip():
+    """Unpacking follows Fig. 1: Table II's binary columns read back as its
+    decimal columns; and unpack(pack(v)) is the sign quantisation of v
+    (v >= 0 -> +1, so -0 -> +1), for ragged K on both layouts."""
+    rows, _ = _read_table2()
+    a_bits = sum(int(r[4]) << i for i, r in enumerate(rows))
+    b_bits = sum(int(r[5]) << i for i, r in enumerate(rows))
+    P = np.array([a_bits, b_bits], np.uint32).reshape(1, 2, 1, 1)     # re plane = A, im plane = B
+    U = oracle.unpack_signs(np.concatenate([P, np.zeros((1, 2, 1, 3), np.uint32)], -1), 4, False)
+    assert U[0, 0, :, 0].tolist() == [float(r[1]) for r in rows]
+    assert U[0, 0, :, 1].tolist() == [float(r[2]) for r in rows]
+    g = ti.rng(8)
+    for K in (1, 31, 33, 130):
+        V = ti.complex_gaussian_fp16(g, (2, 5, K))
+        V.reshape(-1)[:2] = np.array([0.0, -0.0], np.float16)
+        want = np.where(V.astype(np.float64) >= 0, 1.0, -1.0)
+        kw = ti.words_per_row(K)
+        assert np.array_equal(oracle.unpack_signs(oracle.pack_signs(V, False, kw), K, False), want)
+        X = ti.complex_gaussian_fp16(g, (2, K, 7))
+        wantx = np.where(X.astype(np.float64) >= 0, 1.0, -1.0)
+        assert np.array_equal(oracle.unpack_signs(oracle.pack_signs(X, True, kw), K, True), wantx)
