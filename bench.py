@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Beamforming TeraOps/s (8 ops/cMAC), % tensor peak; served p50/p99 latency"
 UNIT = "TeraOps/s"
 FP8_OVER_BF16 = 4.5 / 2.25     # nominal dense-rate ratio used to scale the measured bf16 peak
+TF32_OVER_BF16 = 1.1 / 2.25    # the same for TF32
 
 WORKLOADS = {
     "radio": dict(
@@ -83,7 +84,7 @@ def parse_args():
     ap.add_argument("--no-energy", action="store_true", help="skip the power-sampled loops")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="batches per chunk of the end-to-end host pipeline (0: about batch / 16)")
-    ap.add_argument("--mode", choices=["fp16", "fp8split", "fp8"], default=None,
+    ap.add_argument("--mode", choices=["fp16", "fp8split", "fp8", "tf32"], default=None,
                     help="arithmetic of the FP workloads (default fp16); fp8split: E4M3 hi+lo, "
                          "three products; fp8: the plain E4M3 product (hi only)")
     ap.add_argument("--batches", type=int, default=None,
@@ -99,6 +100,8 @@ def workload(args):
         w["mode"] = args.mode
         if args.mode == "fp8split":
             w["desc"] = w["desc"].replace("FP16", "split-FP8 (E4M3 hi+lo)")
+        elif args.mode == "tf32":
+            w["desc"] = w["desc"].replace("FP16", "TF32 (FP32 data)")
         elif args.mode == "fp8":
             w["desc"] = w["desc"].replace("FP16", "FP8 (E4M3, per-row scales)")
     if args.batches is not None:
@@ -396,9 +399,13 @@ class GpuWorkload:
         self.w = w
         B, M, N, K, Bw = w["B"], w["M"], w["N"], w["K"], w["w_batches"]
         self.Xh = host_x(w)
+        if w["mode"] == "tf32":              # the TF32 path is for data that arrives in FP32
+            self.Xh = self.Xh.astype(np.float32)
+        self.src_type = tcbf.SRC_CF32 if self.Xh.dtype == np.float32 else tcbf.SRC_CF16
         self.Xd = torch.from_numpy(self.Xh).cuda()
         mode = (tcbf.MODE_1BIT if w["mode"] == "1bit" else
-                tcbf.MODE_FP8SPLIT if is_fp8(w) else tcbf.MODE_FP16)
+                tcbf.MODE_FP8SPLIT if is_fp8(w) else
+                tcbf.MODE_TF32 if w["mode"] == "tf32" else tcbf.MODE_FP16)
         # compute-bound FP16 shapes pack X with a third, negated plane (two N = 256
         # MMAs per K step); plain FP16 elsewhere
         flags = tcbf.FLAG_STACKED_X if (w.get("stacked") and mode == tcbf.MODE_FP16) else 0
@@ -434,13 +441,15 @@ class GpuWorkload:
             self.weights_ms = e0.elapsed_time(e1)
 
     def pack(self):
-        self.plan.transpose_pack(1, self.Xd, self.Xp)
+        self.plan.transpose_pack(1, self.Xd, self.Xp, self.src_type)
 
     def gemm(self):
         if self.w["mode"] == "1bit":
             self.plan.beamform_1bit(self.Wp, self.Xp, self.Y)
         elif is_fp8(self.w):
             self.plan.beamform_fp8split(self.Wp, self.Xp, self.Y)
+        elif self.w["mode"] == "tf32":
+            self.plan.beamform_tf32(self.Wp, self.Xp, self.Y)
         else:
             self.plan.beamform_fp16(self.Wp, self.Xp, self.Y)
 
@@ -481,10 +490,20 @@ class GpuWorkload:
             bw = b // (B // Bw)
             if geom is None:        # host-drawn weights: the same FP16 rows the GPU packed
                 Wrow = np.ascontiguousarray(self.Wh[bw:bw + 1, m:m + 1])
+            elif w["mode"] == "tf32":
+                # the oracle's FP64 weights rounded as the GPU stores them: FP32, then TF32
+                wc = oracle.weights(geom.rx_pos, geom.targets[m:m + 1], geom.freqs[bw:bw + 1],
+                                    geom.near_field, geom.c)
+                Wrow = np.stack([oracle.round_tf32(wc.real.astype(np.float32)),
+                                 oracle.round_tf32(wc.imag.astype(np.float32))], -1)
             else:
                 Wrow = oracle.weights_fp16(geom.rx_pos, geom.targets[m:m + 1],
                                            geom.freqs[bw:bw + 1], geom.near_field, geom.c)
-            ref[i] = oracle.cgemm_points(Wrow, self.Xh[b:b + 1], np.array([[0, 0, n]]))[0]
+            if w["mode"] == "tf32":
+                Xcol = oracle.round_tf32(self.Xh[b:b + 1, :, n:n + 1])
+                ref[i] = oracle.cgemm(Wrow, Xcol)[0, 0, 0]
+            else:
+                ref[i] = oracle.cgemm_points(Wrow, self.Xh[b:b + 1], np.array([[0, 0, n]]))[0]
             if is_fp8(w):
                 Xcol = np.ascontiguousarray(self.Xh[b:b + 1, :, n:n + 1])
                 ref_split[i] = oracle.cgemm_split(Wrow, Xcol, products=fp8_products(w))[0, 0, 0]
@@ -592,7 +611,7 @@ def main():
         tuning["speedup_gemm"] = tuning["default"]["gemm_ms"] / gemm_ms
 
     # ---- the same step replayed as one captured CUDA graph
-    plan.graph_capture(gw.Xd, gw.Xp, gw.Wp, gw.Y)
+    plan.graph_capture(gw.Xd, gw.Xp, gw.Wp, gw.Y, gw.src_type)
     plan.graph_launch()
     barrier()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -697,6 +716,10 @@ def main():
         tensor_peak = peaks["bf16_tflops"] * FP8_OVER_BF16
         peak_note = "E4M3 tensor peak = measured bf16 burst x nominal fp8/bf16 ratio 2"
         kname = "cgemm_1bit_kernel"
+    elif w["mode"] == "tf32":
+        tensor_peak = peaks["bf16_tflops"] * TF32_OVER_BF16
+        peak_note = "TF32 tensor peak = measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"
+        kname = "cgemm_tc_kernel<tf32>"
     elif is_fp8(w):
         tensor_peak = peaks["bf16_tflops"] * FP8_OVER_BF16
         mma_factor = float(fp8_products(w))
@@ -730,7 +753,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"1bit": "u1", "fp8split": "e4m3x2", "fp8": "e4m3"}.get(w["mode"], "f16"),
+        "dtype": {"1bit": "u1", "fp8split": "e4m3x2", "fp8": "e4m3", "tf32": "tf32"}.get(
+            w["mode"], "f16"),
         "data": "synthetic",
         "config": {"workload": w["desc"], "batch": w["B"], "M": w["M"], "N": w["N"], "K": w["K"],
                    "w_batches": w["w_batches"],

@@ -52,7 +52,9 @@ typedef enum {
 typedef enum {
     TCBF_MODE_FP16 = 0,        /* FP16 planar re/im inputs, FP32 accumulate (Sec. III) */
     TCBF_MODE_FP8SPLIT = 1,    /* e4m3 hi+lo split of each operand, FP32 accumulate (FP8: Sec. VI) */
-    TCBF_MODE_1BIT = 2         /* +-1+-i values, one bit per component, exact int32 (Sec. III-D) */
+    TCBF_MODE_1BIT = 2,        /* +-1+-i values, one bit per component, exact int32 (Sec. III-D) */
+    TCBF_MODE_TF32 = 3         /* FP32 planar inputs rounded to TF32, FP32 accumulate (formats
+                                  beyond 16 bits: Sec. VI) */
 } tcbf_mode;
 
 /* Source element types accepted by tcbf_transpose_pack. */
@@ -118,6 +120,10 @@ typedef enum {
  *   exponents.  With TCBF_FLAG_FP8_HI_ONLY the rows hold the hi bytes alone,
  *   Kb2 = K rounded up to 64 (hi byte of element k at offset k), followed by
  *   the same exponents.
+ *   TF32 W : [w_batches][2][M][Kp] FP32, X : [batch][2][N][Kp] FP32, each
+ *            value rounded to TF32 (nearest, ties to even, to 10 mantissa
+ *            bits; the low 13 bits zero), zero pad.  FP16 sources convert
+ *            exactly; FP32 sources are rounded.
  */
 
 /* Create a plan for problem *p on CUDA device `device`.  Validates the
@@ -183,6 +189,15 @@ tcbf_status tcbf_beamform_fp16(tcbf_plan_t plan, const void *Wp, const void *Xp,
  */
 tcbf_status tcbf_beamform_fp8split(tcbf_plan_t plan, const void *Wp, const void *Xp, float *Y,
                                    tcbf_stream_t stream);
+
+/*
+ * TF32 complex GEMM for data that arrives in FP32: the FP16 product of
+ * Sec. III-B with kind::tf32 MMAs (10 mantissa bits like FP16, FP32's
+ * exponent range, half the FP16 tensor rate).  Wp, Xp: TF32 packed operands
+ * of this plan (mode TCBF_MODE_TF32).  Y as for FP16.
+ */
+tcbf_status tcbf_beamform_tf32(tcbf_plan_t plan, const void *Wp, const void *Xp, float *Y,
+                               tcbf_stream_t stream);
 
 /*
  * 1-bit complex GEMM (Sec. III-D, Eq. 4-6), exact.  Wbits, Xbits: 1-bit

@@ -167,6 +167,27 @@ def pack_signs(V: np.ndarray, k_is_row: bool, Kw: int) -> np.ndarray:
     return out
 
 
+TF32_MAX = (2.0 - 2.0 ** -10) * 2.0 ** 127
+
+
+def round_tf32(x: np.ndarray) -> np.ndarray:
+    """FP32 values rounded to TF32 (an implicit bit and 10 stored mantissa
+    bits over FP32's exponent range): to nearest, ties to the even
+    neighbour; beyond the largest TF32 value to +-inf.  Float64 result.
+    A value with leading bit 2^e (e >= -126, else the subnormal step) has
+    the quantum 2^(e - 10); x / quantum is exact in FP64 and rint rounds it
+    half to even."""
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    out = x.copy()
+    fin = np.isfinite(x) & (x != 0)
+    _, e2 = np.frexp(x[fin])                    # x = f 2^e2, 0.5 <= |f| < 1
+    q = np.ldexp(1.0, np.maximum(e2 - 1, -126) - 10)
+    r = np.rint(x[fin] / q) * q
+    r = np.where(np.abs(r) > TF32_MAX, np.copysign(np.inf, r), r)
+    out[fin] = r
+    return out
+
+
 def unpack_signs(P: np.ndarray, K: int, k_is_row: bool) -> np.ndarray:
     """Packed planes [B, 2, rows, Kw] back to interleaved complex +-1 values
     (Fig. 1: bit 1 is +1, bit 0 is -1; element k is bit k % 32 of word

@@ -18,7 +18,7 @@ TCBF_OK = 0
 STATUS_NAMES = {0: "TCBF_OK", 1: "TCBF_ERR_INVALID_ARG", 2: "TCBF_ERR_UNSUPPORTED",
                 3: "TCBF_ERR_OOM", 4: "TCBF_ERR_BUDGET", 5: "TCBF_ERR_CUDA",
                 6: "TCBF_ERR_TIMEOUT", 7: "TCBF_ERR_DEVICE"}
-MODE_FP16, MODE_FP8SPLIT, MODE_1BIT = 0, 1, 2
+MODE_FP16, MODE_FP8SPLIT, MODE_1BIT, MODE_TF32 = 0, 1, 2, 3
 SRC_CF16, SRC_CF32 = 0, 1
 FLAG_STACKED_X = 1
 FLAG_FP8_HI_ONLY = 2
@@ -32,7 +32,7 @@ EXPORTED = [
     "tcbf_status_string", "tcbf_plan_num_configs", "tcbf_plan_get_config",
     "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
     "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
-    "tcbf_beamform_host", "tcbf_debug_drop_fill", "tcbf_unpack_bits",
+    "tcbf_beamform_host", "tcbf_debug_drop_fill", "tcbf_unpack_bits", "tcbf_beamform_tf32",
 ]
 
 
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_last_device_error": [vp],
         "tcbf_debug_drop_fill": [vp, ctypes.c_int64],
         "tcbf_unpack_bits": [vp, i32, vp, vp, i32, vp],
+        "tcbf_beamform_tf32": [vp, vp, vp, vp, vp],
         "tcbf_plan_num_configs": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_get_config": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_set_config": [vp, i32],
@@ -171,6 +172,10 @@ class Plan:
     def transpose_pack(self, which, src, dst, src_type=SRC_CF16, stream=None):
         _check(self._lib.tcbf_transpose_pack(self.handle, which, src_type, _ptr(src), _ptr(dst),
                                              _stream(stream)), "tcbf_transpose_pack")
+
+    def beamform_tf32(self, Wp, Xp, Y, stream=None):
+        _check(self._lib.tcbf_beamform_tf32(self.handle, _ptr(Wp), _ptr(Xp), _ptr(Y),
+                                            _stream(stream)), "tcbf_beamform_tf32")
 
     def unpack_bits(self, which, src, dst, dst_type=SRC_CF16, stream=None):
         """Packed 1-bit planes back to interleaved complex +-1 values (the

@@ -74,6 +74,8 @@ size_t packed_bytes(const tcbf_plan_s &pl, int which) {
             return static_cast<size_t>(nb * 2 * rows * pl.Kw * 4);
         case TCBF_MODE_FP8SPLIT:   // hi/lo bytes, then one int32 scale exponent per row
             return static_cast<size_t>(nb * 2 * rows * pl.Kb2 + nb * rows * 4);
+        case TCBF_MODE_TF32:       // FP32 planes holding TF32 values
+            return static_cast<size_t>(nb * 2 * rows * pl.Kp * 4);
         default:
             return 0;
     }
@@ -119,7 +121,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     if (q.w_batches == 0) q.w_batches = q.batch;
     if (q.batch < 1 || q.M < 1 || q.N < 1 || q.K < 1 || q.w_batches < 1) return TCBF_ERR_INVALID_ARG;
     if (q.batch % q.w_batches != 0) return TCBF_ERR_INVALID_ARG;
-    if (q.mode != TCBF_MODE_FP16 && q.mode != TCBF_MODE_FP8SPLIT && q.mode != TCBF_MODE_1BIT)
+    if (q.mode != TCBF_MODE_FP16 && q.mode != TCBF_MODE_FP8SPLIT && q.mode != TCBF_MODE_1BIT &&
+        q.mode != TCBF_MODE_TF32)
         return TCBF_ERR_INVALID_ARG;
     const uint32_t fp8_flags = TCBF_FLAG_FP8_HI_ONLY | TCBF_FLAG_FP8_FOUR_PRODUCTS;
     if ((q.flags & ~(uint32_t(TCBF_FLAG_STACKED_X) | fp8_flags)) != 0) return TCBF_ERR_INVALID_ARG;
@@ -215,6 +218,10 @@ TCBF_EXPORT tcbf_status tcbf_transpose_pack(tcbf_plan_t plan, int which, int src
             e = which == 0 ? launch_pack_split8_w(*plan, src_type, src, dst, s)
                            : launch_pack_split8_x(*plan, src_type, src, dst, s);
             break;
+        case TCBF_MODE_TF32:
+            e = which == 0 ? launch_pack_tf32_w(*plan, src_type, src, dst, s)
+                           : launch_pack_tf32_x(*plan, src_type, src, dst, s);
+            break;
         default:
             return TCBF_ERR_UNSUPPORTED;
     }
@@ -257,13 +264,26 @@ TCBF_EXPORT tcbf_status tcbf_beamform_fp8split(tcbf_plan_t plan, const void *Wp,
     return from_cuda(e);
 }
 
+TCBF_EXPORT tcbf_status tcbf_beamform_tf32(tcbf_plan_t plan, const void *Wp, const void *Xp,
+                                           float *Y, tcbf_stream_t stream) {
+    if (!plan || !Wp || !Xp || !Y) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_TF32) return TCBF_ERR_INVALID_ARG;
+    if (!aligned16(Wp) || !aligned16(Xp) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    const cudaError_t e = launch_gemm_tf32(*plan, Wp, Xp, Y, static_cast<cudaStream_t>(stream));
+    plan->debug_drop_fill = -1;          // the test hook applies to one call
+    return from_cuda(e);
+}
+
 TCBF_EXPORT tcbf_status tcbf_debug_drop_fill(tcbf_plan_t plan, int64_t fill) {
     if (!plan) return TCBF_ERR_INVALID_ARG;
     if (fill < 0) {
         plan->debug_drop_fill = -1;
         return TCBF_OK;
     }
-    if (plan->p.mode != TCBF_MODE_FP16 && plan->p.mode != TCBF_MODE_FP8SPLIT)
+    if (plan->p.mode != TCBF_MODE_FP16 && plan->p.mode != TCBF_MODE_FP8SPLIT &&
+        plan->p.mode != TCBF_MODE_TF32)
         return TCBF_ERR_UNSUPPORTED;
     // one-SM, non-cluster tile configurations only (the cluster and pair
     // kernels share barriers across CTAs)
@@ -345,6 +365,7 @@ TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
     if (plan->p.flags & TCBF_FLAG_STACKED_X) return gemm_f16_stacked_config_name(config);
     if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
     if (plan->p.mode == TCBF_MODE_1BIT) return gemm_1bit_config_name(config);
+    if (plan->p.mode == TCBF_MODE_TF32) return gemm_tf32_config_name(config);
     return gemm_split8_config_name(config);
 }
 
@@ -360,6 +381,7 @@ cudaError_t launch_beamform(const tcbf_plan_s &pl, const void *Wp, const void *X
     if (pl.p.mode == TCBF_MODE_1BIT)
         return launch_gemm_1bit(pl, static_cast<const uint32_t *>(Wp),
                                 static_cast<const uint32_t *>(Xp), static_cast<int32_t *>(Y), s);
+    if (pl.p.mode == TCBF_MODE_TF32) return launch_gemm_tf32(pl, Wp, Xp, static_cast<float *>(Y), s);
     return launch_gemm_split8(pl, Wp, Xp, static_cast<float *>(Y), s);
 }
 
@@ -367,6 +389,7 @@ cudaError_t launch_pack_x(const tcbf_plan_s &pl, int src_type, const void *src, 
                           cudaStream_t s) {
     if (pl.p.mode == TCBF_MODE_FP16) return launch_pack_f16_x(pl, src_type, src, dst, s);
     if (pl.p.mode == TCBF_MODE_1BIT) return launch_pack_bits_x(pl, src_type, src, dst, s);
+    if (pl.p.mode == TCBF_MODE_TF32) return launch_pack_tf32_x(pl, src_type, src, dst, s);
     return launch_pack_split8_x(pl, src_type, src, dst, s);
 }
 

@@ -7,11 +7,16 @@
 // descriptor's negate-A bit does it, so no operand is modified.
 //
 // Split-FP8 (8-bit float formats are the paper's future work, Sec. VI): the
-// same kernel with SPLIT = true reads packed rows of 64-element K blocks of
+// same kernel with FMT = kFmtSplit8 reads packed rows of 64-element K blocks of
 // 64 E4M3 "hi" bytes then 64 "lo" bytes (the same 128-byte swizzled rows and
 // TMA boxes as FP16), issues Wh Xh + Wh Xl + Wl Xh as 12 kind::f8f6f4 MMAs
 // per 32-element K step, and rescales each output by 2^-(eW[m] + eX[n]),
 // the per-row power-of-two scales of the split.
+//
+// TF32 (for callers whose data arrives in FP32; the paper names more input
+// formats as future work, Sec. VI): FMT = kFmtTf32 reads planes of FP32
+// values already rounded to TF32, 32 per 128-byte row, and issues the same
+// four real products as kind::tf32 MMAs of K = 8.
 //
 // Persistent, warp-specialised kernel (one CTA per SM, 192 threads):
 //   warp 0      TMA producer: both planes of a W tile (128 x 64) and of an
@@ -48,6 +53,12 @@ constexpr int BK = 64;         // K elements per stage: one 128-byte swizzled ro
 constexpr int kThreads = 192;
 constexpr int kPromoteK = 4096;     // K above this is accumulated in promoted chunks
 constexpr int kChunkBlocks = 32;    // stages (x 64 K) per promoted chunk
+
+// Operand formats of the kernel template: FP16 planes, E4M3 hi/lo rows, or
+// TF32 planes (FP32 storage).  Every format fills 128-byte rows per stage.
+constexpr int kFmtF16 = 0;
+constexpr int kFmtSplit8 = 1;
+constexpr int kFmtTf32 = 2;
 
 struct GemmArgs {
     float *Y;
@@ -124,12 +135,14 @@ __device__ __forceinline__ void split_step(uint32_t d_re, uint32_t d_im, uint32_
     }
 }
 
-template <int BN, int STAGES, bool SPLIT, int CL>
+template <int BN, int STAGES, int FMT, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmW,
                      const __grid_constant__ CUtensorMap tmX,
                      const __grid_constant__ CUtensorMap tmY, const GemmArgs args) {
     using C = Cfg<BN, STAGES>;
+    constexpr bool SPLIT = FMT == kFmtSplit8;
+    constexpr bool TF32 = FMT == kFmtTf32;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -216,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t fb = full0 + 8 * stage;
                     const uint32_t dst = s0 + stage * C::STAGE_BYTES;
                     // x: 128 bytes per stage in both formats (64 FP16, or 64 hi + 64 lo bytes)
-                    const int x = kb * (SPLIT ? 128 : BK);
+                    const int x = kb * (SPLIT ? 128 : args.kps);
                     if (CL == 1) {
                         // the failure-path test hook leaves one load (and its arrival) out
                         if (blockIdx.x != 0 || static_cast<int>(issued) != args.drop_fill) {
@@ -266,8 +279,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t kIdesc = idesc_f32acc(BM, BN, 0, false);
-            constexpr uint32_t kIdescNeg = idesc_f32acc(BM, BN, 0, true);
+            // A / B format: F16 and E4M3 are 0 in their kinds, TF32 is 2
+            constexpr uint32_t kIdesc = idesc_f32acc(BM, BN, TF32 ? 2u : 0u, false);
+            constexpr uint32_t kIdescNeg = idesc_f32acc(BM, BN, TF32 ? 2u : 0u, true);
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;                                  // accumulator hand-offs so far
@@ -295,17 +309,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t a = s0 + stage * C::STAGE_BYTES;
                         const uint32_t bx = a + C::A_BYTES;
                         if (!SPLIT) {
-                            const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
+                            // 32 bytes per MMA step: 16 FP16 or 8 TF32 elements
+                            constexpr int kStep = TF32 ? 8 : 16;
+                            const int ksteps = min(4, (args.K - kb * args.kps + kStep - 1) / kStep);
                             for (int j = 0; j < ksteps; ++j) {
                                 const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
                                 const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
                                 const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
                                 const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
                                 const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
-                                mma_f16(d_re, ar, br, kIdesc, accum);
-                                mma_f16(d_re, ai, bi, kIdescNeg, 1u);
-                                mma_f16(d_im, ar, bi, kIdesc, accum);
-                                mma_f16(d_im, ai, br, kIdesc, 1u);
+                                if (TF32) {
+                                    mma_tf32(d_re, ar, br, kIdesc, accum);
+                                    mma_tf32(d_re, ai, bi, kIdescNeg, 1u);
+                                    mma_tf32(d_im, ar, bi, kIdesc, accum);
+                                    mma_tf32(d_im, ai, br, kIdesc, 1u);
+                                } else {
+                                    mma_f16(d_re, ar, br, kIdesc, accum);
+                                    mma_f16(d_re, ai, bi, kIdescNeg, 1u);
+                                    mma_f16(d_im, ar, bi, kIdesc, accum);
+                                    mma_f16(d_im, ai, br, kIdesc, 1u);
+                                }
                             }
                         } else {
                             // 32 E4M3 per step; (W part, X part) byte offsets:
@@ -507,12 +530,14 @@ struct CfgPair {
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_pair_kernel(const __grid_constant__ CUtensorMap tmW,
                       const __grid_constant__ CUtensorMap tmX,
                       const __grid_constant__ CUtensorMap tmY, const GemmArgs args) {
     using C = CfgPair<BN, STAGES>;
+    constexpr bool SPLIT = FMT == kFmtSplit8;
+    constexpr bool TF32 = FMT == kFmtTf32;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -592,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t fb = full0_lead + 8 * stage;
                     if (leader) mbar_arrive_expect_tx(full0 + 8 * stage, 2 * C::STAGE_BYTES);
                     const uint32_t dst = s0 + stage * C::STAGE_BYTES;
-                    const int x = kb * (SPLIT ? 128 : BK);
+                    const int x = kb * (SPLIT ? 128 : args.kps);
                     tma_load_3d_pair(dst, &tmW, fb, x, mp * 256 + 128 * rank, 2 * bw);
                     tma_load_3d_pair(dst + C::A_BYTES, &tmX, fb, x, nt * BN + rank * (BN / 2), 2 * b);
                     ++issued;
@@ -628,8 +653,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ------------------------------------------ MMA issuer, even CTA only
         if (lane == 0 && leader) {
-            constexpr uint32_t kIdesc = idesc_f32acc(256, BN, 0, false);
-            constexpr uint32_t kIdescNeg = idesc_f32acc(256, BN, 0, true);
+            constexpr uint32_t kIdesc = idesc_f32acc(256, BN, TF32 ? 2u : 0u, false);
+            constexpr uint32_t kIdescNeg = idesc_f32acc(256, BN, TF32 ? 2u : 0u, true);
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;
@@ -657,17 +682,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint32_t a = s0 + stage * C::STAGE_BYTES;
                         const uint32_t bx = a + C::A_BYTES;
                         if (!SPLIT) {
-                            const int ksteps = min(BK / 16, (args.K - kb * BK + 15) / 16);
+                            constexpr int kStep = TF32 ? 8 : 16;
+                            const int ksteps = min(4, (args.K - kb * args.kps + kStep - 1) / kStep);
                             for (int j = 0; j < ksteps; ++j) {
                                 const uint64_t ar = sdesc_kmajor_sw128(a + 32 * j);
                                 const uint64_t ai = sdesc_kmajor_sw128(a + C::A_PLANE + 32 * j);
                                 const uint64_t br = sdesc_kmajor_sw128(bx + 32 * j);
                                 const uint64_t bi = sdesc_kmajor_sw128(bx + C::B_PLANE + 32 * j);
                                 const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
-                                mma_f16_pair(d_re, ar, br, kIdesc, accum);
-                                mma_f16_pair(d_re, ai, bi, kIdescNeg, 1u);
-                                mma_f16_pair(d_im, ar, bi, kIdesc, accum);
-                                mma_f16_pair(d_im, ai, br, kIdesc, 1u);
+                                if (TF32) {
+                                    mma_tf32_pair(d_re, ar, br, kIdesc, accum);
+                                    mma_tf32_pair(d_re, ai, bi, kIdescNeg, 1u);
+                                    mma_tf32_pair(d_im, ar, bi, kIdesc, accum);
+                                    mma_tf32_pair(d_im, ai, br, kIdesc, 1u);
+                                } else {
+                                    mma_f16_pair(d_re, ar, br, kIdesc, accum);
+                                    mma_f16_pair(d_re, ai, bi, kIdescNeg, 1u);
+                                    mma_f16_pair(d_im, ar, bi, kIdesc, accum);
+                                    mma_f16_pair(d_im, ai, br, kIdesc, 1u);
+                                }
                             }
                         } else {
                             const int ksteps = min(args.kps / 32, (args.K - kb * args.kps + 31) / 32);
@@ -831,15 +864,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int BN, int STAGES, bool SPLIT, int CL>
+template <int BN, int STAGES, int FMT, int CL>
 cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                        cudaStream_t s, int raster) {
     if (CL > 1 && pl.m_prefix)   // uneven batches walk per-batch m-tiles: no clusters
-        return launch_cfg<BN, STAGES, SPLIT, 1>(pl, Wp, Xp, Y, s, raster);
+        return launch_cfg<BN, STAGES, FMT, 1>(pl, Wp, Xp, Y, s, raster);
     // row length in elements of the tensor map: FP16 elements or split-FP8 bytes
+    constexpr bool SPLIT = FMT == kFmtSplit8;
+    constexpr bool TF32 = FMT == kFmtTf32;
     const int64_t row = SPLIT ? pl.Kb2 : pl.Kp;
-    const CUtensorMapDataType dt = SPLIT ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const int64_t esz = SPLIT ? 1 : 2;
+    const CUtensorMapDataType dt = SPLIT  ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const int64_t esz = SPLIT ? 1 : TF32 ? 4 : 2;
     using C = Cfg<BN, STAGES>;
     const tcbf_problem &p = pl.p;
     CUtensorMap tmW, tmX;
@@ -903,7 +940,7 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     a.tiles.raster = raster;
     // hi-only FP8 rows carry 128 K in each 128-byte stage row, the other
     // formats 64 (FP16, or 64 hi + 64 lo bytes); chunks stay 2048 K
-    a.kps = (SPLIT && fp8_hi_only(p.flags)) ? 2 * BK : BK;
+    a.kps = (SPLIT && fp8_hi_only(p.flags)) ? 2 * BK : TF32 ? BK / 2 : BK;
     a.num_kb = static_cast<int>(ceil_div(p.K, a.kps));
     if (p.K > kPromoteK) {
         if (4 * BN > 512) return cudaErrorInvalidConfiguration;   // no TMEM room for the sum
@@ -917,7 +954,7 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     const int64_t total = m_units * a.tiles.n_tiles;     // tiles, or cluster tiles
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
-    auto kern = cgemm_tc_kernel<BN, STAGES, SPLIT, CL>;
+    auto kern = cgemm_tc_kernel<BN, STAGES, FMT, CL>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -954,15 +991,19 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     return cudaGetLastError();
 }
 
-template <int BN, int STAGES, bool SPLIT>
+template <int BN, int STAGES, int FMT>
 cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                         cudaStream_t s, int raster) {
     if (pl.m_prefix)   // uneven batches walk per-batch m-tiles: one-SM tiles
-        return launch_cfg<BN, 3, SPLIT, 1>(pl, Wp, Xp, Y, s, raster);
+        return launch_cfg<BN, 3, FMT, 1>(pl, Wp, Xp, Y, s, raster);
     using C = CfgPair<BN, STAGES>;
+    constexpr bool SPLIT = FMT == kFmtSplit8;
+    constexpr bool TF32 = FMT == kFmtTf32;
     const int64_t row = SPLIT ? pl.Kb2 : pl.Kp;
-    const CUtensorMapDataType dt = SPLIT ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    const int64_t esz = SPLIT ? 1 : 2;
+    const CUtensorMapDataType dt = SPLIT  ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const int64_t esz = SPLIT ? 1 : TF32 ? 4 : 2;
     const tcbf_problem &p = pl.p;
     CUtensorMap tmW, tmX, tmY;
     {
@@ -1022,7 +1063,7 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
     a.tiles.raster = 0;
     // hi-only FP8 rows carry 128 K in each 128-byte stage row, the other
     // formats 64 (FP16, or 64 hi + 64 lo bytes); chunks stay 2048 K
-    a.kps = (SPLIT && fp8_hi_only(p.flags)) ? 2 * BK : BK;
+    a.kps = (SPLIT && fp8_hi_only(p.flags)) ? 2 * BK : TF32 ? BK / 2 : BK;
     a.num_kb = static_cast<int>(ceil_div(p.K, a.kps));
     if (p.K > kPromoteK) {
         if (4 * BN > 512) return cudaErrorInvalidConfiguration;
@@ -1034,7 +1075,7 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
     const int64_t total = ceil_div(a.tiles.m_tiles, 2) * p.batch * a.tiles.n_tiles;
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
-    auto kern = cgemm_pair_kernel<BN, STAGES, SPLIT>;
+    auto kern = cgemm_pair_kernel<BN, STAGES, FMT>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -1073,28 +1114,41 @@ struct ConfigEntry {
 };
 
 const ConfigEntry kConfigs[] = {
-    {"f16 BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, false, 1>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, false, 1>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, false, 1>},
-    {"f16 BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, false, 1>},
-    {"f16 BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, false, 1>},
-    {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, false, 1>},
-    {"f16 BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, false, 2>},
-    {"f16 BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, false, 4>},
-    {"f16 2-SM pair BM256 BN128 BK64 stages4 tmem-double", 128, 0, launch_pair<128, 4, false>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, kFmtF16, 1>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, kFmtF16, 1>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, kFmtF16, 1>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, kFmtF16, 1>},
+    {"f16 BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, kFmtF16, 1>},
+    {"f16 BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, kFmtF16, 1>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, kFmtF16, 2>},
+    {"f16 BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, kFmtF16, 4>},
+    {"f16 2-SM pair BM256 BN128 BK64 stages4 tmem-double", 128, 0, launch_pair<128, 4, kFmtF16>},
 };
 
 // split-FP8: the same tile shapes, index for index
 const ConfigEntry kConfigsSplit[] = {
-    {"fp8split BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, true, 1>},
-    {"fp8split BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, true, 1>},
-    {"fp8split BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, true, 1>},
-    {"fp8split BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, true, 1>},
-    {"fp8split BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, true, 1>},
-    {"fp8split BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, true, 1>},
-    {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, true, 2>},
-    {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, true, 4>},
-    {"fp8split 2-SM pair BM256 BN128 BK64 stages4 tmem-double", 128, 0, launch_pair<128, 4, true>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, kFmtSplit8, 1>},
+    {"fp8split BM128 BN256 BK64 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, kFmtSplit8, 1>},
+    {"fp8split BM128 BN64 BK64 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, kFmtSplit8, 1>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, kFmtSplit8, 1>},
+    {"fp8split BM128 BN256 BK64 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, kFmtSplit8, 1>},
+    {"fp8split BM128 BN64 BK64 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, kFmtSplit8, 1>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, kFmtSplit8, 2>},
+    {"fp8split BM128 BN128 BK64 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, kFmtSplit8, 4>},
+    {"fp8split 2-SM pair BM256 BN128 BK64 stages4 tmem-double", 128, 0, launch_pair<128, 4, kFmtSplit8>},
+};
+
+// TF32: the same tile shapes, index for index (32 K per 128-byte stage row)
+const ConfigEntry kConfigsTf32[] = {
+    {"tf32 BM128 BN128 BK32 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, kFmtTf32, 1>},
+    {"tf32 BM128 BN256 BK32 stages2 tmem-single n-fastest", 256, 0, launch_cfg<256, 2, kFmtTf32, 1>},
+    {"tf32 BM128 BN64 BK32 stages4 tmem-double n-fastest", 64, 0, launch_cfg<64, 4, kFmtTf32, 1>},
+    {"tf32 BM128 BN128 BK32 stages3 tmem-double m-fastest", 128, 1, launch_cfg<128, 3, kFmtTf32, 1>},
+    {"tf32 BM128 BN256 BK32 stages2 tmem-single m-fastest", 256, 1, launch_cfg<256, 2, kFmtTf32, 1>},
+    {"tf32 BM128 BN64 BK32 stages4 tmem-double m-fastest", 64, 1, launch_cfg<64, 4, kFmtTf32, 1>},
+    {"tf32 BM128 BN128 BK32 stages3 tmem-double cluster2 X-multicast", 128, 0, launch_cfg<128, 3, kFmtTf32, 2>},
+    {"tf32 BM128 BN128 BK32 stages3 tmem-double cluster4 X-multicast", 128, 0, launch_cfg<128, 3, kFmtTf32, 4>},
+    {"tf32 2-SM pair BM256 BN128 BK32 stages4 tmem-double", 128, 0, launch_pair<128, 4, kFmtTf32>},
 };
 
 }  // namespace
@@ -1114,6 +1168,17 @@ bool gemm_f16_config_valid(int config, int64_t K) {
 const char *gemm_split8_config_name(int config) {
     if (config < 0 || config >= gemm_f16_num_configs()) return "invalid";
     return kConfigsSplit[config].name;
+}
+
+const char *gemm_tf32_config_name(int config) {
+    if (config < 0 || config >= gemm_f16_num_configs()) return "invalid";
+    return kConfigsTf32[config].name;
+}
+
+cudaError_t launch_gemm_tf32(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                             cudaStream_t s) {
+    const int c = (pl.config >= 0 && pl.config < gemm_f16_num_configs()) ? pl.config : 0;
+    return kConfigsTf32[c].fn(pl, Wp, Xp, Y, s, kConfigsTf32[c].raster);
 }
 
 cudaError_t launch_gemm_split8(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,

@@ -111,6 +111,7 @@ int64_t packed_x_bytes(const tcbf_plan_s &pl, int64_t nb) {
     switch (pl.p.mode) {
         case TCBF_MODE_FP16: return nb * x_planes(pl) * N * pl.Kp * 2;
         case TCBF_MODE_1BIT: return nb * 2 * N * pl.Kw * 4;
+        case TCBF_MODE_TF32: return nb * 2 * N * pl.Kp * 4;
         default: return nb * 2 * N * pl.Kb2 + nb * N * 4;
     }
 }
@@ -120,6 +121,7 @@ int64_t packed_w_row_bytes(const tcbf_plan_s &pl) {
     switch (pl.p.mode) {
         case TCBF_MODE_FP16: return pl.Kp * 2;
         case TCBF_MODE_1BIT: return pl.Kw * 4;
+        case TCBF_MODE_TF32: return pl.Kp * 4;
         default: return pl.Kb2;
     }
 }
@@ -131,6 +133,7 @@ int64_t packed_w_batch_bytes(const tcbf_plan_s &pl) {
     switch (pl.p.mode) {
         case TCBF_MODE_FP16: return 2 * M * pl.Kp * 2;
         case TCBF_MODE_1BIT: return 2 * M * pl.Kw * 4;
+        case TCBF_MODE_TF32: return 2 * M * pl.Kp * 4;
         default: return 2 * M * pl.Kb2;
     }
 }
@@ -138,6 +141,7 @@ int64_t packed_w_batch_bytes(const tcbf_plan_s &pl) {
 cudaError_t pack_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst, cudaStream_t s) {
     if (pl.p.mode == TCBF_MODE_FP16) return launch_pack_f16_x(pl, src_type, src, dst, s);
     if (pl.p.mode == TCBF_MODE_1BIT) return launch_pack_bits_x(pl, src_type, src, dst, s);
+    if (pl.p.mode == TCBF_MODE_TF32) return launch_pack_tf32_x(pl, src_type, src, dst, s);
     return launch_pack_split8_x(pl, src_type, src, dst, s);
 }
 
@@ -146,6 +150,7 @@ cudaError_t beamform(const tcbf_plan_s &pl, const void *Wp, const void *Xp, void
     if (pl.p.mode == TCBF_MODE_1BIT)
         return launch_gemm_1bit(pl, static_cast<const uint32_t *>(Wp),
                                 static_cast<const uint32_t *>(Xp), static_cast<int32_t *>(Y), s);
+    if (pl.p.mode == TCBF_MODE_TF32) return launch_gemm_tf32(pl, Wp, Xp, static_cast<float *>(Y), s);
     return launch_gemm_split8(pl, Wp, Xp, static_cast<float *>(Y), s);
 }
 

@@ -8,6 +8,7 @@
 //                                      is contiguous for the GEMM's TMA)
 //   1-bit: the same two shapes, keeping only the sign of each component,
 //   32 signs per uint32 along K (bit k % 32 of word k / 32, 1 = +1).
+//   TF32: the FP16 shapes with FP32 storage, each value rounded to TF32.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -193,6 +194,80 @@ __global__ void __launch_bounds__(256) pack_f16_x_kernel(const void *__restrict_
     }
 }
 
+// ------------------------------------------------------------ TF32 planes
+// Rounding to TF32 (10 stored mantissa bits) to nearest, ties to even, kept
+// in FP32 storage with the 13 low bits zero: adding 0xFFF plus the lowest
+// kept bit and clearing the dropped bits rounds the magnitude (a carry into
+// the exponent is the correct step to the next binade, or to infinity).
+// Infinities pass unchanged; NaNs stay NaN (quiet bit set).
+__device__ __forceinline__ float tf32_rne(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u)
+        return __uint_as_float((u & 0x007fffffu) ? ((u | 0x00400000u) & 0xffffe000u) : u);
+    u += 0x0fffu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xffffe000u);
+}
+
+// W: one thread writes 4 consecutive K elements (16 bytes) of both planes.
+template <typename S>
+__global__ void pack_tf32_w_kernel(const void *__restrict__ src, float *__restrict__ dst,
+                                   int64_t rows, int64_t M, int K, int Kp) {
+    const int64_t chunks = Kp / 4;
+    const int64_t total = rows * chunks;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = i / chunks;
+        const int k0 = static_cast<int>(i % chunks) * 4;
+        const int64_t bw = r / M, m = r % M;
+        float re[4], im[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            re[j] = im[j] = 0.f;
+            if (k0 + j < K) S::load(src, static_cast<size_t>(r) * K + k0 + j, re[j], im[j]);
+        }
+        *reinterpret_cast<float4 *>(dst + (static_cast<size_t>(bw * 2 + 0) * M + m) * Kp + k0) =
+            make_float4(tf32_rne(re[0]), tf32_rne(re[1]), tf32_rne(re[2]), tf32_rne(re[3]));
+        *reinterpret_cast<float4 *>(dst + (static_cast<size_t>(bw * 2 + 1) * M + m) * Kp + k0) =
+            make_float4(tf32_rne(im[0]), tf32_rne(im[1]), tf32_rne(im[2]), tf32_rne(im[3]));
+    }
+}
+
+// X: 32 (k) x 32 (n) tiles through shared memory: warps read rows of X (n
+// contiguous) and write rows of the packed planes (k contiguous).
+template <typename S>
+__global__ void __launch_bounds__(256) pack_tf32_x_kernel(const void *__restrict__ src,
+                                                         float *__restrict__ dst, int K, int N,
+                                                         int Kp, int k_tiles, int n_tiles) {
+    __shared__ float2 tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t b = blockIdx.y;
+    const int64_t tiles_per_b = int64_t(k_tiles) * n_tiles;
+    for (int64_t t = blockIdx.x; t < tiles_per_b; t += gridDim.x) {
+        const int k0 = static_cast<int>(t / n_tiles) * 32;
+        const int n0 = static_cast<int>(t % n_tiles) * 32;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kk = ty + 8 * i;
+            float re = 0.f, im = 0.f;
+            if (k0 + kk < K && n0 + tx < N)
+                S::load(src, (static_cast<size_t>(b) * K + k0 + kk) * N + n0 + tx, re, im);
+            tile[kk][tx] = make_float2(tf32_rne(re), tf32_rne(im));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int nn = ty + 8 * i;
+            const int n = n0 + nn, k = k0 + tx;
+            if (n < N && k < Kp) {
+                const float2 v = tile[tx][nn];
+                dst[(static_cast<size_t>(b * 2 + 0) * N + n) * Kp + k] = v.x;
+                dst[(static_cast<size_t>(b * 2 + 1) * N + n) * Kp + k] = v.y;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // --------------------------------------------------------------- sign bits
 // Sign of one component: v >= 0 gives bit 1 (+1), so -0 gives +1; negative
 // values and NaN give bit 0 (-1).
@@ -371,6 +446,34 @@ cudaError_t launch_pack_f16_x(const tcbf_plan_s &pl, int src_type, const void *s
         else
             vec ? run(pack_f16_x_kernel<CF32, true, 2>) : run(pack_f16_x_kernel<CF32, false, 2>);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_tf32_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s) {
+    const int64_t rows = pl.p.w_batches * pl.p.M;
+    const int grid = grid_for(rows * (pl.Kp / 4), 256, pl.num_sms);
+    auto *d = static_cast<float *>(dst);
+    if (src_type == TCBF_SRC_CF16)
+        pack_tf32_w_kernel<CF16><<<grid, 256, 0, s>>>(src, d, rows, pl.p.M, int(pl.p.K), int(pl.Kp));
+    else
+        pack_tf32_w_kernel<CF32><<<grid, 256, 0, s>>>(src, d, rows, pl.p.M, int(pl.p.K), int(pl.Kp));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_tf32_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s) {
+    const int k_tiles = static_cast<int>(ceil_div(pl.Kp, 32));
+    const int n_tiles = static_cast<int>(ceil_div(pl.p.N, 32));
+    const int64_t per_b = int64_t(k_tiles) * n_tiles;
+    const int bx = static_cast<int>(std::min<int64_t>(per_b, std::max<int64_t>(1, int64_t(pl.num_sms) * 8 / std::max<int64_t>(1, std::min<int64_t>(pl.p.batch, 8)))));
+    dim3 grid(bx, static_cast<unsigned>(pl.p.batch));
+    auto *d = static_cast<float *>(dst);
+    const int K = int(pl.p.K), N = int(pl.p.N), Kp = int(pl.Kp);
+    if (src_type == TCBF_SRC_CF16)
+        pack_tf32_x_kernel<CF16><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
+    else
+        pack_tf32_x_kernel<CF32><<<grid, 256, 0, s>>>(src, d, K, N, Kp, k_tiles, n_tiles);
     return cudaGetLastError();
 }
 

@@ -59,6 +59,15 @@ cudaError_t launch_pack_bits_w(const tcbf_plan_s &pl, int src_type, const void *
 cudaError_t launch_pack_bits_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
                                cudaStream_t s);
 
+// TF32 planes (FP32 storage, values rounded to TF32).
+cudaError_t launch_pack_tf32_w(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s);
+cudaError_t launch_pack_tf32_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s);
+cudaError_t launch_gemm_tf32(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                             cudaStream_t s);
+const char *gemm_tf32_config_name(int config);    // TF32 uses the FP16 tile table
+
 // 1-bit planes back to interleaved complex +-1 values (FP16 or FP32).
 cudaError_t launch_unpack_bits(const tcbf_plan_s &pl, int which, const uint32_t *src, int dst_type,
                                void *dst, cudaStream_t s);

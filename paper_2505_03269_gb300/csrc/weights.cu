@@ -10,6 +10,7 @@
 // Output goes straight into the GEMM's packed W layout, so W needs no
 // separate transpose/pack pass:
 //   FP16 mode : planes [Bw][2][M][Kp], one thread per 8 consecutive k
+//   TF32 mode : FP32 planes [Bw][2][M][Kp] rounded to TF32, 4 k per thread
 //   1-bit mode: sign planes [Bw][2][M][Kw], one warp per 32 consecutive k
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -83,6 +84,36 @@ __global__ void weights_f16_kernel(Geo g, __half *__restrict__ dst, int64_t Bw, 
             *reinterpret_cast<const uint4 *>(re);
         *reinterpret_cast<uint4 *>(dst + (static_cast<size_t>(bw * 2 + 1) * g.M + m) * Kp + k0) =
             *reinterpret_cast<const uint4 *>(im);
+    }
+}
+
+// TF32: the FP32 weight rounded to TF32 (nearest, ties to even; see the
+// pack kernels), one thread per 4 consecutive k.
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;
+    u += 0x0fffu + ((u >> 13) & 1u);
+    return __uint_as_float(u & 0xffffe000u);
+}
+
+__global__ void weights_tf32_kernel(Geo g, float *__restrict__ dst, int64_t Bw, int Kp) {
+    const int64_t chunks = Kp / 4;
+    const int64_t total = Bw * g.M * chunks;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int k0 = static_cast<int>(i % chunks) * 4;
+        const int64_t r = i / chunks;
+        const int64_t m = r % g.M, bw = r / g.M;
+        float re[4], im[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            re[j] = im[j] = 0.f;
+            if (k0 + j < g.K) weight(g, bw, m, k0 + j, re[j], im[j]);
+        }
+        *reinterpret_cast<float4 *>(dst + (static_cast<size_t>(bw * 2 + 0) * g.M + m) * Kp + k0) =
+            make_float4(to_tf32(re[0]), to_tf32(re[1]), to_tf32(re[2]), to_tf32(re[3]));
+        *reinterpret_cast<float4 *>(dst + (static_cast<size_t>(bw * 2 + 1) * g.M + m) * Kp + k0) =
+            make_float4(to_tf32(im[0]), to_tf32(im[1]), to_tf32(im[2]), to_tf32(im[3]));
     }
 }
 
@@ -190,6 +221,10 @@ cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double
         const int64_t work = Bw * pl.p.M * pl.Kw * 32;
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(pl.num_sms) * 32)));
         weights_bits_kernel<<<grid, 256, 0, s>>>(g, static_cast<uint32_t *>(Wp), Bw, int(pl.Kw));
+    } else if (pl.p.mode == TCBF_MODE_TF32) {
+        const int64_t work = Bw * pl.p.M * (pl.Kp / 4);
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(pl.num_sms) * 32)));
+        weights_tf32_kernel<<<grid, 256, 0, s>>>(g, static_cast<float *>(Wp), Bw, int(pl.Kp));
     } else if (pl.p.mode == TCBF_MODE_FP16) {
         const int64_t work = Bw * pl.p.M * (pl.Kp / 8);
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(pl.num_sms) * 32)));

@@ -46,6 +46,8 @@ def _device_path(plan, mode, Wd, Xd, src_type, B, M, N):
     Y = torch.empty((B, M, N, 2), dtype=dt, device="cuda")
     if mode == MODE_FP16:
         plan.beamform_fp16(Wp, Xp, Y)
+    elif mode == 3:
+        plan.beamform_tf32(Wp, Xp, Y)
     elif mode == MODE_1BIT:
         plan.beamform_1bit(Wp, Xp, Y)
     else:
@@ -74,7 +76,7 @@ def _inputs(seed, Bw, B, M, N, K, src_type):
     return W, X
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("B,Bw,M,N,K,chunk", [(6, 3, 130, 300, 200, 4), (4, 2, 64, 256, 96, 2),
                                               (5, 5, 200, 136, 72, 0), (3, 1, 96, 64, 40, 3)])
 def test_host_path_equals_device_path(mode, B, Bw, M, N, K, chunk):

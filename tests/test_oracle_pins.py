@@ -423,3 +423,56 @@ def test_unpack_signs_table2_and_round_trip():
         X = ti.complex_gaussian_fp16(g, (2, K, 7))
         wantx = np.where(X.astype(np.float64) >= 0, 1.0, -1.0)
         assert np.array_equal(oracle.unpack_signs(oracle.pack_signs(X, True, kw), K, True), wantx)
+
+
+def _tf32_exact(v: float) -> float:
+    """Brute force with exact rationals: the TF32 neighbours of v (the grid of
+    11 significant bits, subnormal step 2^-136) and the nearer one, ties to the
+    even significand, overflow past the largest TF32 value to infinity."""
+    from fractions import Fraction
+    import math
+    if not math.isfinite(v) or v == 0.0:
+        return v
+    f = Fraction(v)
+    a = abs(f)
+    e = math.floor(math.log2(a))
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    q = Fraction(2) ** (max(e, -126) - 10)
+    lo = (a // q) * q
+    hi = lo + q
+    if a - lo < hi - a:
+        r = lo
+    elif hi - a < a - lo:
+        r = hi
+    else:
+        r = lo if (lo / q) % 2 == 0 else hi
+    if r > Fraction(oracle.TF32_MAX):
+        return math.copysign(math.inf, v)
+    return math.copysign(float(r), v)
+
+
+def test_round_tf32_against_exact_rationals():
+    g = np.random.default_rng(12)
+    bits = g.integers(0, 2 ** 32, 3000, dtype=np.uint64).astype(np.uint32)
+    # ties (dropped bits exactly 0x1000) with both kept-bit parities, values just
+    # off the tie, subnormals, the largest finite values and zero
+    ties = (g.integers(0, 2 ** 19, 200, dtype=np.uint64).astype(np.uint32) << 13) | 0x1000
+    near = ties ^ 1
+    sub = g.integers(1, 2 ** 23, 100, dtype=np.uint64).astype(np.uint32)
+    big = np.array([0x7f7fffff, 0x7f7ff000, 0x7f7fefff, 0xff7fffff, 0x00000000, 0x80000000],
+                   np.uint32)
+    x = np.concatenate([bits, ties, near, sub, big]).view(np.float32)
+    x = x[np.isfinite(x)]
+    got = oracle.round_tf32(x)
+    want = np.array([_tf32_exact(float(v)) for v in x.astype(np.float64)])
+    assert np.array_equal(got, want)
+    # every result is representable: its FP32 pattern has the 13 low bits zero
+    fin = np.isfinite(got)
+    assert not np.any(got[fin].astype(np.float32).view(np.uint32) & 0x1fff)
+    # FP16 values are TF32 values
+    h = g.standard_normal(1000).astype(np.float16).astype(np.float32)
+    assert np.array_equal(oracle.round_tf32(h), h.astype(np.float64))
+    assert oracle.round_tf32(np.array([np.inf, -np.inf], np.float32)).tolist() == [np.inf, -np.inf]
