@@ -19,6 +19,8 @@
 // fit beside the output staging.  Long K is accumulated in promoted chunks
 // exactly as in the one-SM kernel (Sec. III-B's FP32 accumulation, here
 // with the partial in TMEM columns 0-255 and the running sum in 256-511).
+// The default configuration runs the same product on SM pairs (M = 256,
+// cta_group::2), see cgemm_stacked_pair_kernel.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -477,6 +479,420 @@ cudaError_t launch_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp
     return cudaGetLastError();
 }
 
+// ===========================================================================
+// Two-SM stacked tiles (cta_group::2): a cluster of two CTAs computes a
+// 256-row x 128-sample tile with M = 256, N = 256 MMAs issued by the even
+// CTA.  Each B operand is split across the pair by rows (samples): of
+// B1 = [Xr; Xi] the even CTA holds Xr and the odd one Xi, of B2 = [-Xi; Xr]
+// the even CTA holds -Xi and the odd one Xr, each at the same shared-memory
+// offset, so every CTA loads two of the three packed planes and each SM's
+// tensor core takes 128 rows of W and 128 of X per MMA, a third less than a
+// one-SM N = 256 tile.  Stages hold 64 K in 128-byte swizzled rows.  Both
+// CTAs' loads complete on the even CTA's full barrier, its MMA completions
+// are committed to both CTAs, and both CTAs' epilogues release an
+// accumulator on the even CTA's barrier.  Promotion as in the one-SM kernel.
+// ===========================================================================
+constexpr int PBK = 64;                  // K per stage: one 128-byte row
+constexpr int kStkPairChunkBlocks = 32;  // stages (x 64 K) per promoted chunk
+
+template <int STAGES>
+struct CfgStkPair {
+    static constexpr int PLANE = 128 * PBK * 2;               // 16 KB: 128 rows x 128 B
+    static constexpr int W_BYTES = 2 * PLANE;                 // Wr, Wi (this CTA's 128 rows)
+    static constexpr int STAGE_BYTES = W_BYTES + 2 * PLANE;   // + the CTA's halves of B1, B2
+    static constexpr int TMEM_COLS = 512;                     // 2 x [Re 128 | Im 128]
+    static constexpr int STAGING_BYTES = 4 * 4096;
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(kStkThreads, 1)
+    cgemm_stacked_pair_kernel(const __grid_constant__ CUtensorMap tmW,
+                              const __grid_constant__ CUtensorMap tmX,
+                              const __grid_constant__ CUtensorMap tmY, const StkArgs args) {
+    using C = CfgStkPair<STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+    const uint32_t s0 = smem_u32(smem);
+    const uint32_t staging0 = s0 + STAGES * C::STAGE_BYTES;
+    const uint32_t bar0 = staging0 + C::STAGING_BYTES;
+    const uint32_t full0 = bar0;
+    const uint32_t empty0 = full0 + 8 * STAGES;
+    const uint32_t tfull0 = empty0 + 8 * STAGES;
+    const uint32_t tempty0 = tfull0 + 16;
+    const uint32_t done_bar = tempty0 + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + STAGES * C::STAGE_BYTES +
+                                                       C::STAGING_BYTES + 16 * STAGES + 40);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int rank = static_cast<int>(cluster_ctarank());
+    const bool leader = rank == 0;
+    const int t_first = static_cast<int>(cluster_id_x());
+    const int t_step = static_cast<int>(nclusters_x());
+    constexpr uint16_t kBoth = 3;
+    // packed planes -Xi (0), Xr (1), Xi (2): this CTA's rows of B1 and of B2
+    const int plane_b1 = leader ? 1 : 2;
+    const int plane_b2 = leader ? 0 : 1;
+    // (batch, 256-row pair tile, sample tile) of pair tile t, samples fastest
+    auto decode = [&](int t, int &b, int &mp, int &nt) {
+        const int groups = (args.tiles.m_tiles + 1) / 2;
+        const int per_b = groups * args.tiles.n_tiles;
+        b = t / per_b;
+        const int local = t - b * per_b;
+        nt = local % args.tiles.n_tiles;
+        mp = local / args.tiles.n_tiles;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);          // used in the even CTA
+            mbar_init(empty0 + 8 * s, 1);         // the even CTA's commit, both CTAs
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 8);        // 4 epilogue warps x 2 CTAs (even CTA)
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmW);
+        tma_prefetch_desc(&tmX);
+        if (args.tma_store) tma_prefetch_desc(&tmY);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t full0_lead = mapa_shared(full0, 0);
+    const uint32_t tempty0_lead = mapa_shared(tempty0, 0);
+
+    if (warp == 0) {
+        // --------------------------------------------- TMA producer, both CTAs
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0;
+            bool ok = true;
+            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
+                int b, mp, nt;
+                decode(t, b, mp, nt);
+                const int bw = b / args.per_w;
+                for (int kb = 0; kb < args.num_kb; ++kb) {
+                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = full0_lead + 8 * stage;
+                    if (leader) mbar_arrive_expect_tx(full0 + 8 * stage, 2 * C::STAGE_BYTES);
+                    const uint32_t dst = s0 + stage * C::STAGE_BYTES;
+                    const int x = kb * PBK;
+                    tma_load_3d_pair(dst, &tmW, fb, x, mp * 256 + 128 * rank, 2 * bw);
+                    tma_load_3d_pair(dst + C::W_BYTES, &tmX, fb, x, nt * SBN, 3 * b + plane_b1);
+                    tma_load_3d_pair(dst + C::W_BYTES + C::PLANE, &tmX, fb, x, nt * SBN,
+                                     3 * b + plane_b2);
+                    ++issued;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutProducer);
+                *abort_flag = 1;
+                if (leader) {
+                    for (int s = 0; s < STAGES; ++s) {
+                        if (issued > static_cast<uint32_t>(s)) {
+                            const uint32_t count = (issued - s + STAGES - 1) / STAGES;
+                            if (!mbar_wait(full0 + 8 * s, (count - 1) & 1u))
+                                atomicOr(args.status, kErrTimeoutDrain);
+                        }
+                    }
+                }
+            } else {
+                // the even CTA's release of every slot this CTA filled has arrived
+                for (int s = 0; s < STAGES; ++s) {
+                    if (issued > static_cast<uint32_t>(s)) {
+                        const uint32_t count = (issued - s + STAGES - 1) / STAGES;
+                        if (!mbar_wait(empty0 + 8 * s, (count - 1) & 1u))
+                            atomicOr(args.status, kErrTimeoutDrain);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------ MMA issuer, even CTA only
+        if (lane == 0 && leader) {
+            constexpr uint32_t kIdesc = idesc_f32acc(256, 2 * SBN, 0, false);
+            int stage = 0;
+            uint32_t phase = 0;
+            int ev = 0;
+            const int nbuf = args.chunks > 1 ? 1 : 2;
+            bool ok = true;
+            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
+                for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+                    const int acc = ev % nbuf;
+                    const uint32_t aphase = (ev / nbuf) & 1;
+                    if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + acc * 2 * SBN;
+                    const int kb0 = ch * args.kc_blocks;
+                    const int kb1 = min(args.num_kb, kb0 + args.kc_blocks);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a = s0 + stage * C::STAGE_BYTES;   // Wr, Wi
+                        const uint32_t x = a + C::W_BYTES;                 // B1 half, B2 half
+                        const int ksteps = min(PBK / 16, (args.K - kb * PBK + 15) / 16);
+                        for (int j = 0; j < ksteps; ++j) {
+                            const uint32_t accum = (kb > kb0 || j > 0) ? 1u : 0u;
+                            // Wr [Xr; Xi] -> [Wr Xr | Wr Xi]
+                            mma_f16_pair(d, sdesc_kmajor_sw128(a + 32 * j),
+                                         sdesc_kmajor_sw128(x + 32 * j), kIdesc, accum);
+                            // Wi [-Xi; Xr] -> [-Wi Xi | Wi Xr]
+                            mma_f16_pair(d, sdesc_kmajor_sw128(a + C::PLANE + 32 * j),
+                                         sdesc_kmajor_sw128(x + C::PLANE + 32 * j), kIdesc, 1u);
+                        }
+                        mma_commit_pair(empty0 + 8 * stage, kBoth);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit_pair(tfull0 + 8 * acc, kBoth);
+                }
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutMma);
+                *abort_flag = 1;
+            }
+            mma_commit_pair(done_bar, 1);
+            if (!mbar_wait(done_bar, 0)) atomicOr(args.status, kErrTimeoutDrain);
+        }
+    } else {
+        // ------------------------------------------------- epilogue, both CTAs
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t stage_buf = staging0 + (warp - 2) * 4096;
+        const bool vec_ok = (args.N & 1) == 0;
+        int ev = 0;
+        const int nbuf = args.chunks > 1 ? 1 : 2;
+        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
+        const uint32_t tS = tmem_base + lane_off + 2 * SBN;    // running sum (promotion only)
+        bool ok = true;
+        for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
+            int b, mp, nt;
+            decode(t, b, mp, nt);
+            const int mrow0 = mp * 256 + 128 * rank;           // this CTA's first row
+            const int m = mrow0 + row;
+            float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
+            for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+                const int acc = ev % nbuf;
+                const uint32_t aphase = (ev / nbuf) & 1;
+                if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tP = tmem_base + lane_off + acc * 2 * SBN;
+                if (ch + 1 < args.chunks) {
+                    // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
+#pragma unroll 1
+                    for (int g = 0; g < SBN / 16; ++g) {
+                        float pr[16], pi[16];
+                        tmem_ld_2x16(tP + g * 16, tP + SBN + g * 16, pr, pi);
+                        if (ch > 0) {
+                            float sr[16], si[16];
+                            tmem_ld_2x16(tS + g * 16, tS + SBN + g * 16, sr, si);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                pr[i] = __fadd_rn(sr[i], pr[i]);
+                                pi[i] = __fadd_rn(si[i], pi[i]);
+                            }
+                        }
+                        tmem_st_2x16(tS + g * 16, tS + SBN + g * 16, pr, pi);
+                    }
+                    tmem_st_wait();
+                } else {
+#pragma unroll 1
+                    for (int c = 0; c < SBN / 16; ++c) {
+                        float re[16], im[16];
+                        tmem_ld_2x16(tP + c * 16, tP + SBN + c * 16, re, im);
+                        if (args.chunks > 1) {
+                            float sr[16], si[16];
+                            tmem_ld_2x16(tS + c * 16, tS + SBN + c * 16, sr, si);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                re[i] = __fadd_rn(sr[i], re[i]);
+                                im[i] = __fadd_rn(si[i], im[i]);
+                            }
+                        }
+                        const int n0 = nt * SBN + c * 16;
+                        if (args.tma_store) {
+                            if (n0 < args.N) {
+                                if (lane == 0) bulk_wait_read<0>();
+                                __syncwarp();
+                                const uint32_t rbase = stage_buf + lane * 128;
+#pragma unroll
+                                for (int j = 0; j < 8; ++j)
+                                    st_shared_v4(rbase + ((j ^ (lane & 7)) << 4), re[2 * j], im[2 * j],
+                                                 re[2 * j + 1], im[2 * j + 1]);
+                                fence_async_smem();
+                                __syncwarp();
+                                if (lane == 0) {
+                                    tma_store_3d(&tmY, stage_buf, 2 * n0, mrow0 + quarter * 32, b);
+                                    bulk_commit();
+                                }
+                            }
+                        } else if (m < args.M && n0 < args.N) {
+                            if (vec_ok && n0 + 16 <= args.N) {
+                                float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
+#pragma unroll
+                                for (int i = 0; i < 8; ++i)
+                                    dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    if (n0 + i < args.N) {
+                                        yrow[2 * (n0 + i)] = re[i];
+                                        yrow[2 * (n0 + i) + 1] = im[i];
+                                    }
+                            }
+                        }
+                    }
+                }
+                // this warp is done with the accumulator: release it on the even CTA
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(tempty0_lead + 8 * acc);
+            }
+        }
+        if (args.tma_store && lane == 0) bulk_wait<0>();
+        __syncwarp();
+        if (!ok && lane == 0) {
+            atomicOr(args.status, kErrTimeoutEpilogue);
+            *abort_flag = 1;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();                       // no CTA leaves while its peer may signal it
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
+    }
+}
+
+template <int STAGES>
+cudaError_t launch_stacked_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
+                                cudaStream_t s, int raster) {
+    if (pl.m_prefix)   // uneven batches walk per-batch m-tiles: one-SM tiles
+        return launch_stacked<5, 1>(pl, Wp, Xp, Y, s, raster);
+    using C = CfgStkPair<STAGES>;
+    const tcbf_problem &p = pl.p;
+    const int64_t row = pl.Kp;
+    CUtensorMap tmW, tmX, tmY;
+    {
+        const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(2 * p.w_batches)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(row * 2),
+                                     static_cast<uint64_t>(w_plane_rows(pl) * row * 2)};
+        const uint32_t box[3] = {PBK, 128, 2};
+        if (encode_tiled(&tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Wp), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        const uint64_t dims[3] = {static_cast<uint64_t>(row), static_cast<uint64_t>(p.N),
+                                  static_cast<uint64_t>(3 * p.batch)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(row * 2),
+                                     static_cast<uint64_t>(p.N * row * 2)};
+        const uint32_t box[3] = {PBK, SBN, 1};              // one plane of 128 samples
+        if (encode_tiled(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Xp), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const int tma_store = (p.N % 2 == 0) ? 1 : 0;
+    if (tma_store) {
+        const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(p.batch)};
+        const uint64_t strides[2] = {static_cast<uint64_t>(p.N * 8),
+                                     static_cast<uint64_t>(p.M * p.N * 8)};
+        const uint32_t box[3] = {32, 32, 1};
+        if (encode_tiled(&tmY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Y, dims, strides, box,
+                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
+        tmY = tmX;   // unused
+    }
+    StkArgs a;
+    a.Y = Y;
+    a.status = pl.status;
+    a.tma_store = tma_store;
+    a.M = static_cast<int>(p.M);
+    a.N = static_cast<int>(p.N);
+    a.K = static_cast<int>(p.K);
+    a.per_w = static_cast<int>(pl.per_w);
+    a.tiles.prefix = nullptr;
+    a.tiles.batch = static_cast<int>(p.batch);
+    a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, 128));
+    a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, SBN));
+    a.tiles.raster = 0;
+    a.num_kb = static_cast<int>(ceil_div(p.K, PBK));
+    a.kc_blocks = p.K > kStkPromoteK ? kStkPairChunkBlocks : a.num_kb;
+    a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
+    const int64_t total = ceil_div(a.tiles.m_tiles, 2) * p.batch * a.tiles.n_tiles;   // pair tiles
+    if (total > 0x7fffffff) return cudaErrorInvalidValue;
+    a.total_tiles = static_cast<int>(total);
+    auto kern = cgemm_stacked_pair_kernel<STAGES>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kStkThreads);
+    cfg.dynamicSmemBytes = C::SMEM_BYTES;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // resident pairs per device, measured once (benign if two threads both measure)
+    static std::atomic<int> max_clusters[64];
+    int mc = max_clusters[pl.device & 63].load(std::memory_order_relaxed);
+    if (mc == 0) {
+        cfg.gridDim = dim3(pl.num_sms / 2 * 2);
+        e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (mc < 1) return cudaErrorInvalidConfiguration;
+        max_clusters[pl.device & 63].store(mc, std::memory_order_relaxed);
+    }
+    cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(total, mc)) * 2);
+    e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 struct StkConfig {
     const char *name;
     int raster;
@@ -484,6 +900,7 @@ struct StkConfig {
 };
 
 const StkConfig kStkConfigs[] = {
+    {"f16 stacked-X N256 2-SM pair BM256 BN128 BK64 stages3 tmem-double", 0, launch_stacked_pair<3>},
     {"f16 stacked-X N256 BM128 BN128 BK32-sw64 stages5 tmem-double cluster2 X-multicast", 0,
      launch_stacked<5, 2>},
     {"f16 stacked-X N256 BM128 BN128 BK32-sw64 stages5 tmem-double n-fastest", 0, launch_stacked<5, 1>},

@@ -91,7 +91,7 @@ def test_full_size_ultrasound_block_sampled():
     M, K, N = 65536, 16384, 256
     geom = ti.ultrasound_geometry()
     Xh = ti.ultrasound_frames(1, K, N)
-    for err in _run_block(1, 1, M, N, K, geom, Xh, flags=FLAG_STACKED_X, configs=(0, 1)):
+    for err in _run_block(1, 1, M, N, K, geom, Xh, flags=FLAG_STACKED_X, configs=(0, 1, 2)):
         assert err <= TOL
 
 

@@ -1,7 +1,8 @@
 """FP16 plans with stacked sample planes (TCBF_FLAG_STACKED_X).
 
 The packed X holds [-Xi, Xr, Xi]; the GEMM issues Wr [Xr; Xi] + Wi [-Xi; Xr]
-as two N = 256 MMAs per K step.  Bars: the packed bytes are the plain
+as two N = 256 MMAs per K step, on one SM (configurations 1-4) or on SM
+pairs with M = 256 (configuration 0, the default).  Bars: the packed bytes are the plain
 planes plus the sign-flipped imaginary plane, bit for bit; the product is
 within the FP16 parity bar of the FP64 oracle; and because every output
 element is summed in the same order as in the four-MMA kernel (Wr Xr then
@@ -70,30 +71,32 @@ def test_stacked_pack_layout_bit_exact(B, N, K, src):
     assert np.array_equal(Xp, want)
 
 
-@pytest.mark.parametrize("config", [0, 1, 2])
+@pytest.mark.parametrize("config", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (3, 5, 7), (129, 130, 288), (127, 257, 129),
-                                   (200, 96, 64), (64, 1024, 200)])
+                                   (200, 96, 64), (64, 1024, 200), (300, 260, 70)])
 def test_stacked_ragged_shapes(config, M, N, K):
     W, X = ti.small_fp16(seed=M * 7 + N + K, M=M, K=K, N=N, B=2)
     Y = _run(W, X, config=config)
     assert oracle.rel_frobenius(Y, oracle.cgemm(W, X)) <= TOL
 
 
+@pytest.mark.parametrize("config", [0, 1])
 @pytest.mark.parametrize("K", [300, 5000])
-def test_stacked_equals_four_mma_kernel_bit_for_bit(K):
+def test_stacked_equals_four_mma_kernel_bit_for_bit(K, config):
     W, _ = ti.small_fp16(seed=K, M=260, K=K, N=8, B=2)
     X = ti.complex_gaussian_fp16(ti.rng(K + 1), (4, K, 300))
-    Ys = _run(W, X, stacked=True)
+    Ys = _run(W, X, stacked=True, config=config)
     Y0 = _run(W, X, stacked=False)
     assert np.array_equal(Ys, Y0)
     assert oracle.rel_frobenius(Ys, oracle.cgemm(W, X)) <= TOL
 
 
-def test_stacked_integer_inputs_bit_exact():
+@pytest.mark.parametrize("config", [0, 1])
+def test_stacked_integer_inputs_bit_exact(config):
     g = ti.rng(1)
     W = ti.integer_complex_fp16(g, (2, 150, 300))
     X = ti.integer_complex_fp16(g, (4, 300, 270))
-    assert np.array_equal(_run(W, X), oracle.cgemm(W, X))
+    assert np.array_equal(_run(W, X, config=config), oracle.cgemm(W, X))
 
 
 def test_stacked_identity_and_imaginary_identity():
@@ -106,11 +109,12 @@ def test_stacked_identity_and_imaginary_identity():
         assert np.array_equal(_run(W, X), factor * Xc)
 
 
+@pytest.mark.parametrize("config", [0, 1])
 @pytest.mark.parametrize("K", [8192, 16384])
-def test_stacked_long_k_within_tolerance(K):
+def test_stacked_long_k_within_tolerance(K, config):
     W, _ = ti.small_fp16(seed=K, M=256, K=K, N=8)
     X = ti.complex_gaussian_fp16(ti.rng(K), (1, K, 256))
-    assert oracle.rel_frobenius(_run(W, X), oracle.cgemm(W, X)) <= TOL
+    assert oracle.rel_frobenius(_run(W, X, config=config), oracle.cgemm(W, X)) <= TOL
 
 
 def test_stacked_uneven_beam_counts():
