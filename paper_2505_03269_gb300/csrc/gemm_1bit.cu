@@ -10,7 +10,7 @@
 // FP32 accumulators.  Every partial sum is an integer of magnitude <= 2K,
 // exact in FP32 for K < 2^23, so the result equals K - 2 Hamming exactly.
 //
-// Warp roles (544 threads, one CTA per SM, persistent over tiles):
+// Warp roles (544 or 672 threads, one CTA per SM, persistent over tiles):
 //   warp 0      TMEM owner and single-thread MMA issuer (4 real MMAs per
 //               K step, negate-A for -Im(W) Im(X), as in the FP16 kernel)
 //   warps 1-12  converters: each thread takes every 384th row-plane of the
@@ -20,7 +20,10 @@
 //               one stage of 128 K per ring slot.  The expansion is latency-
 //               bound per thread, so the row-planes are spread evenly (two per
 //               thread for 128 x 256 tiles) rather than split by operand.
-//   warps 13-16 epilogue: TMEM -> int32 pairs -> staged TMA stores
+//   warps 13-   epilogue: TMEM -> int32 pairs -> staged TMA stores; eight
+//               warps (two per TMEM lane quarter, one 4 KB staging buffer
+//               each) when the accumulator is single-buffered, so that its
+//               drain holds up the next tile's MMAs for less time, else four
 #include <algorithm>
 #include <cstring>
 
@@ -36,7 +39,6 @@ using namespace dev;
 constexpr int BM = 128;
 constexpr int BKE = 128;             // K elements per stage (one 128-byte E4M3 row)
 constexpr int kConv = 384;           // converter threads
-constexpr int kThreads = 32 + kConv + 128;
 
 struct Args1 {
     int32_t *Y;
@@ -63,6 +65,8 @@ struct Cfg1 {
     static constexpr int STAGE_BYTES = A_BYTES + XPL * B_PLANE;
     static constexpr int ACC_BUFS = (4 * BN <= 512) ? 2 : 1;
     static constexpr int TMEM_COLS = ACC_BUFS * 2 * BN <= 256 ? 256 : 512;
+    static constexpr int EPI_WARPS = ACC_BUFS == 1 ? 8 : 4;
+    static constexpr int THREADS = 32 + kConv + 32 * EPI_WARPS;
     static constexpr int STAGING_BYTES = 4 * 2 * 4096;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
     static_assert(SMEM_BYTES <= 232448, "shared memory");
@@ -213,7 +217,7 @@ struct StageCursor {
 };
 
 template <int BN, int STAGES, bool STK>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Cfg1<BN, STAGES, STK>::THREADS, 1)
     cgemm_1bit_kernel(const __grid_constant__ CUtensorMap tmY, const Args1 args) {
     using C = Cfg1<BN, STAGES, STK>;
     extern __shared__ uint8_t smem_raw[];
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull0 + 8 * a, 1);
-            mbar_init(tempty0 + 8 * a, 128);
+            mbar_init(tempty0 + 8 * a, 32 * C::EPI_WARPS);
         }
         mbar_init(done_bar, 1);
         *abort_flag = 0;
@@ -380,7 +384,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // --------------------------------------------------------- epilogue
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const uint32_t stage_buf = staging0 + (warp - 1 - kConv / 32) * 8192;
+        const int ew = warp - 1 - kConv / 32;          // epilogue warp 0 .. EPI_WARPS - 1
+        constexpr int kChunks = BN / 16 / (C::EPI_WARPS / 4);
+        const int c0 = (ew >> 2) * kChunks;            // this warp's 16-column chunks
+        // eight warps: one 4 KB buffer each; four: two each
+        const uint32_t stage_buf = staging0 + ew * (C::EPI_WARPS == 8 ? 4096 : 8192);
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
         int local = 0;
         int chunk_count = 0;
@@ -399,14 +407,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t tP = tmem_base + lane_off + acc * 2 * BN;
             int32_t *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
 #pragma unroll 1
-            for (int c = 0; c < BN / 16; ++c) {
+            for (int c = c0; c < c0 + kChunks; ++c) {
                 float re[16], im[16];
                 tmem_ld_2x16(tP + c * 16, tP + BN + c * 16, re, im);
                 const int n0 = nt * BN + c * 16;
                 if (args.tma_store) {
                     if (n0 < args.N) {
-                        const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
-                        if (lane == 0) bulk_wait_read<1>();
+                        const uint32_t buf =
+                            stage_buf + (C::EPI_WARPS == 8 ? 0 : (chunk_count & 1) * 4096);
+                        if (lane == 0) {
+                            if (C::EPI_WARPS == 8)
+                                bulk_wait_read<0>();   // the buffer's last store has read it
+                            else
+                                bulk_wait_read<1>();
+                        }
                         __syncwarp();
                         const uint32_t rbase = buf + lane * 128;
 #pragma unroll
@@ -498,7 +512,7 @@ cudaError_t launch1(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *X
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int grid = static_cast<int>(std::min<int64_t>(total, pl.num_sms));
-    kern<<<grid, kThreads, C::SMEM_BYTES, s>>>(tmY, a);
+    kern<<<grid, C::THREADS, C::SMEM_BYTES, s>>>(tmY, a);
     return cudaGetLastError();
 }
 
