@@ -40,6 +40,7 @@ METRIC = "Beamforming TeraOps/s (8 ops/cMAC), % tensor peak; served p50/p99 late
 UNIT = "TeraOps/s"
 FP8_OVER_BF16 = 4.5 / 2.25     # nominal dense-rate ratio used to scale the measured bf16 peak
 TF32_OVER_BF16 = 1.1 / 2.25    # the same for TF32
+FP4_OVER_BF16 = 13.5 / 2.25    # and for the dense 4-bit (E2M1) rate
 
 WORKLOADS = {
     "radio": dict(
@@ -440,11 +441,28 @@ class GpuWorkload:
             torch.cuda.synchronize()
             self.weights_ms = e0.elapsed_time(e1)
 
+    def fp4(self):
+        """1-bit plan on the 4-bit tensor path: W is expanded to E2M1 once
+        (weights fixed over the block, as they are packed once on the FP16
+        path), and each step expands X before the GEMM."""
+        return (self.w["mode"] == "1bit" and
+                self.plan.config_name(self.plan.get_config()).startswith("1bit->e2m1"))
+
+    def prepare_weights(self):
+        if self.fp4():
+            self.plan.expand_1bit(0, self.Wp)
+
     def pack(self):
         self.plan.transpose_pack(1, self.Xd, self.Xp, self.src_type)
 
+    def prep(self):
+        if self.fp4():
+            self.plan.expand_1bit(1, self.Xp)
+
     def gemm(self):
-        if self.w["mode"] == "1bit":
+        if self.fp4():
+            self.plan.beamform_1bit_expanded(self.Y)
+        elif self.w["mode"] == "1bit":
             self.plan.beamform_1bit(self.Wp, self.Xp, self.Y)
         elif is_fp8(self.w):
             self.plan.beamform_fp8split(self.Wp, self.Xp, self.Y)
@@ -455,9 +473,14 @@ class GpuWorkload:
 
     def step(self):
         self.pack()
+        self.prep()
         self.gemm()
 
     def gemm_bytes(self):
+        if self.fp4():
+            # the E2M1 planes the GEMM reads: W (Wr, Wi) and X (-Xi, Xr, Xi), 16 bytes per word
+            w, kw = self.w, self.plan.Kw
+            return (w["w_batches"] * 2 * w["M"] + w["B"] * 3 * w["N"]) * kw * 16 + self.Y.numel() * 4
         return self.plan.packed_size(0) + self.plan.packed_size(1) + self.Y.numel() * 4
 
     def parity(self, npts=128):
@@ -563,6 +586,7 @@ def main():
 
     gw = GpuWorkload(w, local, args.config)
     plan = gw.plan
+    gw.prepare_weights()
     stream = torch.cuda.current_stream()
     warmup = max(args.warmup, 3)
     for _ in range(warmup):
@@ -571,8 +595,9 @@ def main():
     assert plan.last_device_error() == 0
 
     def timed(nsteps, sample_clocks=False):
-        """nsteps steps with events around each kernel on the launch stream."""
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nsteps)]
+        """nsteps steps with events around each kernel on the launch stream:
+        pack, then (4-bit 1-bit path) the expansion of X, then the GEMM."""
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nsteps)]
         sampler = ClockSampler(local) if sample_clocks else None
         if sampler:
             sampler.start()
@@ -581,13 +606,16 @@ def main():
             ev[i][0].record(stream)
             gw.pack()
             ev[i][1].record(stream)
-            gw.gemm()
+            gw.prep()
             ev[i][2].record(stream)
+            gw.gemm()
+            ev[i][3].record(stream)
         barrier()
         clk = sampler.stop() if sampler else None
-        total = ev[0][0].elapsed_time(ev[-1][2])
+        total = ev[0][0].elapsed_time(ev[-1][3])
+        timed.prep_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
         return (total, statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
-                statistics.mean(e[1].elapsed_time(e[2]) for e in ev), clk)
+                statistics.mean(e[2].elapsed_time(e[3]) for e in ev), clk)
 
     # ---- the fixed default configuration against the autotuned one
     tuning = None
@@ -597,7 +625,10 @@ def main():
         from paper_2505_03269_gb300 import tuner
         entry = tuner.tune(plan, gw.Wp, gw.Xp, gw.Y, reps=3, store=False)
         tuning = {"default": {"config": default_name, "gemm_ms": d_gemm},
-                  "tuned": {"config": entry["name"]}, "ms_per_config": entry["ms"]}
+                  "tuned": {"config": entry["name"]}, "ms_per_config": entry["ms"],
+                  "how": "every configuration's whole beamform call (4-bit 1-bit path: "
+                         "both expansions and the GEMM), timed round-robin"}
+        gw.prepare_weights()
         for _ in range(2):
             gw.step()
 
@@ -712,7 +743,12 @@ def main():
     pack_bytes = gw.Xh.nbytes + plan.packed_size(1)
     ops = ops_per_step(w)
     mma_factor = 1.0
-    if w["mode"] == "1bit":
+    if gw.fp4():
+        tensor_peak = peaks["bf16_tflops"] * FP4_OVER_BF16
+        peak_note = ("dense E2M1 tensor peak = measured bf16 burst x nominal fp4/bf16 ratio "
+                     "13.5/2.25; the GEMM alone (the expansion of X is timed beside it)")
+        kname = "cgemm_1bit_fp4_pair_kernel"
+    elif w["mode"] == "1bit":
         tensor_peak = peaks["bf16_tflops"] * FP8_OVER_BF16
         peak_note = "E4M3 tensor peak = measured bf16 burst x nominal fp8/bf16 ratio 2"
         kname = "cgemm_1bit_kernel"
@@ -753,21 +789,26 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"1bit": "u1", "fp8split": "e4m3x2", "fp8": "e4m3", "tf32": "tf32"}.get(
-            w["mode"], "f16"),
+        "dtype": ("e2m1" if gw.fp4() else
+                  {"1bit": "u1", "fp8split": "e4m3x2", "fp8": "e4m3", "tf32": "tf32"}.get(
+                      w["mode"], "f16")),
         "data": "synthetic",
         "config": {"workload": w["desc"], "batch": w["B"], "M": w["M"], "N": w["N"], "K": w["K"],
                    "w_batches": w["w_batches"],
-                   "step": "transpose_pack(X) + beamform (weights resident)",
+                   "step": ("transpose_pack(X) + expand_1bit(X) + beamform_1bit_expanded "
+                            "(weights expanded once, resident)" if gw.fp4() else
+                            "transpose_pack(X) + beamform (weights resident)"),
                    "l2": "inputs larger than L2 (X %.2f GB, Y %.1f GB per step)"
                          % (gw.Xh.nbytes / 1e9, gw.Y.numel() * 4 / 1e9),
                    "kernel_config": plan.config_name(plan.get_config()),
                    "parallelism": f"{world} independent replica(s), no collective"},
         # kernels per step: pack(X) + GEMM; split-FP8 packs X in three kernels
-        # (column maxima, pack, exponents) after a memset
-        "gpu_launches": (4 if is_fp8(w) else 2) * args.steps,
+        # (column maxima, pack, exponents) after a memset; the 4-bit 1-bit
+        # path adds the expansion of X
+        "gpu_launches": (4 if is_fp8(w) else 3 if gw.fp4() else 2) * args.steps,
         "roofline": roof,
         "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms, "weights_ms_once": gw.weights_ms,
+                    "expand_x_ms": timed.prep_ms if gw.fp4() else None,
                     "gemm_useful_tops": ops / (gemm_ms * 1e-3) / 1e12,
                     "gemm_tops": gemm_tops, "gemm_frac_of_tensor_peak": gemm_tops / tensor_peak,
                     "gemm_gbs": gemm_gbs, "gemm_ai_ops_per_byte": ai,
@@ -777,7 +818,8 @@ def main():
         "autotune": tuning,
         "graph_step": {"ms_per_step": graph_ms,
                        "value": whole_job_value(world, ops, graph_ms),
-                       "how": "tcbf_graph_capture of pack + beamform, replayed K times"},
+                       "how": "tcbf_graph_capture of pack + beamform, replayed K times (4-bit 1-bit "
+                              "path: the captured call also expands W)"},
         "device_status": status,
         "parity_sampled": parity,
         "e2e": e2e,

@@ -203,9 +203,47 @@ tcbf_status tcbf_beamform_tf32(tcbf_plan_t plan, const void *Wp, const void *Xp,
  * 1-bit complex GEMM (Sec. III-D, Eq. 4-6), exact.  Wbits, Xbits: 1-bit
  * packed operands (mode TCBF_MODE_1BIT).  Y: [batch][M][N] interleaved
  * int32 pairs (re, im), each |value| <= 2K.
+ *
+ * Two arithmetic paths, chosen by the plan's configuration: bits expanded
+ * on chip to E4M3 +-1 (FP8 MMAs; configurations "1bit->e4m3 ..."), or the
+ * 4-bit tensor path (configurations "1bit->e2m1 ..."): each call expands
+ * W and X into E2M1 +-1 planes held by the plan (tcbf_expand_1bit below),
+ * then runs block-scaled 4-bit MMAs with unit scales.  Both are exact for
+ * K <= 2^23 (every partial sum an integer of magnitude <= 2K in FP32).
+ * tcbf_plan_create gives a 1-bit plan the 4-bit path by default when
+ * K <= 2^23 and its planes fit in device memory: (w_batches x 2 x M +
+ * batch x 3 x N) rows of 16 x Kw bytes, owned by the plan and freed by
+ * tcbf_plan_destroy; otherwise configuration 0 (E4M3).  Selecting a 4-bit
+ * configuration with tcbf_plan_set_config allocates the planes if needed
+ * (TCBF_ERR_OOM when they do not fit).  Plans the 4-bit path cannot take
+ * (uneven batch rows, K > 2^23) run configuration 0 instead.
  */
 tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbits, const uint32_t *Xbits,
                                int32_t *Y, tcbf_stream_t stream);
+
+/*
+ * The two halves of tcbf_beamform_1bit on the 4-bit tensor path, for
+ * callers that keep W fixed over many blocks of samples (the beamformer's
+ * usual case: expand W once, then X and the GEMM per block).
+ *
+ * tcbf_expand_1bit: expand packed bits into the plan's E2M1 planes.
+ *   which = 0: bits = packed W [w_batches][2][M][Kw] uint32; which = 1:
+ *   packed X [batch][2][N][Kw] (the layouts of tcbf_beamform_1bit; bits at
+ *   k >= K are ignored).  W becomes the planes Wr, Wi and X the planes
+ *   -Xi, Xr, Xi, each element 0x2 (+1), 0xA (-1) or 0 (k >= K), two per
+ *   byte.  Asynchronous on `stream`; the planes stay until the next
+ *   expansion of the same operand or tcbf_plan_destroy.
+ * tcbf_beamform_1bit_expanded: Y = W X (Eq. 3) from the planes last
+ *   expanded; Y as for tcbf_beamform_1bit.  The configuration in use when
+ *   it is called chooses the tile shape.
+ * Errors: TCBF_ERR_INVALID_ARG (null plan or pointer, pointer not 16-byte
+ * aligned, which not 0 or 1, plan not TCBF_MODE_1BIT), TCBF_ERR_UNSUPPORTED
+ * (configuration not on the 4-bit path, or the plan cannot take it: uneven
+ * batch rows, K > 2^23), TCBF_ERR_CUDA (launch failure).
+ */
+tcbf_status tcbf_expand_1bit(tcbf_plan_t plan, int which, const uint32_t *bits,
+                             tcbf_stream_t stream);
+tcbf_status tcbf_beamform_1bit_expanded(tcbf_plan_t plan, int32_t *Y, tcbf_stream_t stream);
 
 /*
  * Steering weights from geometry (Eq. 1-2): for weight batch b, beam m and

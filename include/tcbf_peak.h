@@ -23,7 +23,11 @@ extern "C" {
  *   2 tcgen05 kind::i8 (not available on sm_103a: always TCBF_ERR_UNSUPPORTED),
  *   3 mma.sync m16n8k16 f16->f32,
  *   4 mma.sync m16n8k256 b1 AND-popc, 5 CUDA-core popc(xor) on 32-bit words,
- *   6 tcgen05 kind::f16 M128 N128 K16 (the beamformer's one-SM tile MMA).
+ *   6 tcgen05 kind::f16 M128 N128 K16 (the beamformer's one-SM tile MMA),
+ *   7 tcgen05 kind::mxf4 M128 N256 K64 (packed E2M1 with unit UE8M0 block
+ *     scales: the 1-bit GEMM's 4-bit path),
+ *   8 tcgen05 kind::mxf4nvf4 M128 N256 K64 with unit UE4M3 scales per 16 K,
+ *   9 tcgen05 kind::mxf4nvf4 M128 N256 K64 with unit UE8M0 scales per 32 K.
  * iters: MMAs (or loop trips) per issuing thread.  On success *seconds is the
  * timed launch's duration and *ops the operations it performed (2 per
  * multiply-accumulate).  Allocates and frees a 256-byte status word.

@@ -33,6 +33,7 @@ EXPORTED = [
     "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
     "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
     "tcbf_beamform_host", "tcbf_debug_drop_fill", "tcbf_unpack_bits", "tcbf_beamform_tf32",
+    "tcbf_expand_1bit", "tcbf_beamform_1bit_expanded",
 ]
 
 
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_beamform_fp16": [vp, vp, vp, vp, vp],
         "tcbf_beamform_fp8split": [vp, vp, vp, vp, vp],
         "tcbf_beamform_1bit": [vp, vp, vp, vp, vp],
+        "tcbf_expand_1bit": [vp, i32, vp, vp],
+        "tcbf_beamform_1bit_expanded": [vp, vp, vp],
         "tcbf_weights_from_geometry": [vp, vp, vp, i32, vp, ctypes.c_double, vp, vp],
         "tcbf_last_device_error": [vp],
         "tcbf_debug_drop_fill": [vp, ctypes.c_int64],
@@ -194,6 +197,17 @@ class Plan:
     def beamform_1bit(self, Wb, Xb, Y, stream=None):
         _check(self._lib.tcbf_beamform_1bit(self.handle, _ptr(Wb), _ptr(Xb), _ptr(Y),
                                             _stream(stream)), "tcbf_beamform_1bit")
+
+    def expand_1bit(self, which, bits, stream=None):
+        """4-bit tensor path: expand packed bits of W (0) or X (1) into the
+        plan's E2M1 planes."""
+        _check(self._lib.tcbf_expand_1bit(self.handle, int(which), _ptr(bits), _stream(stream)),
+               "tcbf_expand_1bit")
+
+    def beamform_1bit_expanded(self, Y, stream=None):
+        """4-bit tensor path: the GEMM on the planes last expanded."""
+        _check(self._lib.tcbf_beamform_1bit_expanded(self.handle, _ptr(Y), _stream(stream)),
+               "tcbf_beamform_1bit_expanded")
 
     def weights_from_geometry(self, rx_pos, targets, near_field, freqs, c, Wp, stream=None):
         _check(self._lib.tcbf_weights_from_geometry(

@@ -166,6 +166,10 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
             delete pl;
             return TCBF_ERR_CUDA;
         }
+        // 1-bit: the 4-bit tensor path by default when its planes fit
+        if (q.mode == TCBF_MODE_1BIT && gemm_1bit_fp4_reserve(*pl) == cudaSuccess &&
+            gemm_1bit_fp4_usable(*pl))
+            pl->config = gemm_1bit_fp4_default_config();
     }
     *out = pl;
     return TCBF_OK;
@@ -179,6 +183,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_destroy(tcbf_plan_t plan) {
         if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
         if (plan->m_prefix) cudaFree(plan->m_prefix);
         if (plan->status) cudaFree(plan->status);
+        gemm_1bit_fp4_release(*plan);
     }
     delete plan;
     return TCBF_OK;
@@ -305,6 +310,29 @@ TCBF_EXPORT tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbi
     return from_cuda(launch_gemm_1bit(*plan, Wbits, Xbits, Y, static_cast<cudaStream_t>(stream)));
 }
 
+TCBF_EXPORT tcbf_status tcbf_expand_1bit(tcbf_plan_t plan, int which, const uint32_t *bits,
+                                         tcbf_stream_t stream) {
+    if (!plan || !bits || (which != 0 && which != 1)) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_1BIT || !aligned16(bits)) return TCBF_ERR_INVALID_ARG;
+    if (!gemm_1bit_config_fp4(plan->config) || !gemm_1bit_fp4_usable(*plan))
+        return TCBF_ERR_UNSUPPORTED;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(launch_expand_1bit_fp4(*plan, which, bits, static_cast<cudaStream_t>(stream)));
+}
+
+TCBF_EXPORT tcbf_status tcbf_beamform_1bit_expanded(tcbf_plan_t plan, int32_t *Y,
+                                                    tcbf_stream_t stream) {
+    if (!plan || !Y) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_1BIT || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
+    if (!gemm_1bit_config_fp4(plan->config) || !gemm_1bit_fp4_usable(*plan))
+        return TCBF_ERR_UNSUPPORTED;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(launch_gemm_1bit_fp4_expanded(*plan, Y, static_cast<cudaStream_t>(stream),
+                                                   gemm_1bit_fp4_variant(plan->config)));
+}
+
 TCBF_EXPORT tcbf_status tcbf_weights_from_geometry(tcbf_plan_t plan, const double *rx_pos,
                                                    const double *targets, int near_field,
                                                    const double *freqs, double c, void *Wp_out,
@@ -356,6 +384,13 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
     if (plan->p.mode != TCBF_MODE_1BIT && !(plan->p.flags & TCBF_FLAG_STACKED_X) &&
         !gemm_f16_config_valid(config, plan->p.K))
         return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode == TCBF_MODE_1BIT && gemm_1bit_config_fp4(config)) {
+        // the E2M1 planes live in the plan; plans the path cannot take
+        // (uneven batches, K > 2^23) run configuration 0 instead
+        DeviceGuard g(plan->device);
+        if (!g.ok()) return TCBF_ERR_CUDA;
+        if (gemm_1bit_fp4_reserve(*plan) != cudaSuccess) return TCBF_ERR_OOM;
+    }
     plan->config = config;   // a captured graph keeps the configuration it was captured with
     return TCBF_OK;
 }
@@ -394,7 +429,9 @@ cudaError_t launch_pack_x(const tcbf_plan_s &pl, int src_type, const void *src, 
 }
 
 bool config_ok(const tcbf_plan_s &pl, int c) {
-    if (pl.p.mode == TCBF_MODE_1BIT) return c >= 0 && c < gemm_1bit_num_configs();
+    if (pl.p.mode == TCBF_MODE_1BIT)
+        return c >= 0 && c < gemm_1bit_num_configs() &&
+               (!gemm_1bit_config_fp4(c) || gemm_1bit_fp4_usable(pl));
     if (pl.p.flags & TCBF_FLAG_STACKED_X) return c >= 0 && c < gemm_f16_stacked_num_configs();
     return gemm_f16_config_valid(c, pl.p.K);
 }
@@ -460,6 +497,14 @@ TCBF_EXPORT tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const vo
     }
     const int saved = plan->config;
     tcbf_status st = TCBF_OK;
+    // 1-bit: the 4-bit configurations need the plan's E2M1 scratch; without
+    // device memory for it they are left out
+    if (plan->p.mode == TCBF_MODE_1BIT && !plan->m_prefix)
+        for (int c = 0; c < n; ++c)
+            if (gemm_1bit_config_fp4(c)) {
+                gemm_1bit_fp4_reserve(*plan);
+                break;
+            }
     // Every valid configuration is warmed up and sized into groups of launches
     // of at least 0.2 ms; then the configurations are timed round-robin, `reps`
     // rounds, keeping each one's fastest group.  Interleaving the rounds keeps

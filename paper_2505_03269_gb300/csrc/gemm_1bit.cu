@@ -523,6 +523,16 @@ struct Config1 {
                       cudaStream_t, int);
 };
 
+// The 4-bit tensor path (gemm_1bit_fp4.cu); plans it cannot take (no scratch,
+// K > 2^23, uneven batches) run configuration 0 instead.
+template <int V>
+cudaError_t launch_fp4_or_e4m3(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,
+                               int32_t *Y, cudaStream_t s, int) {
+    const cudaError_t e = launch_gemm_1bit_fp4(pl, Wb, Xb, Y, s, V);
+    if (e == cudaErrorNotSupported) return launch1<256, 2>(pl, Wb, Xb, Y, s, 0);
+    return e;
+}
+
 const Config1 kConfigs1[] = {
     {"1bit->e4m3 BM128 BN256 BK128 stages2 tmem-single n-fastest", 0, launch1<256, 2>},
     {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double n-fastest", 0, launch1<128, 3>},
@@ -530,11 +540,26 @@ const Config1 kConfigs1[] = {
     {"1bit->e4m3 BM128 BN128 BK128 stages3 tmem-double m-fastest", 1, launch1<128, 3>},
     {"1bit->e4m3 stacked [-Xi,Xr,Xi] N256 BM128 BN128 BK128 stages2 tmem-double n-fastest", 0,
      launch1<128, 2, true>},
+    {"1bit->e2m1 mxf4 stacked [-Xi,Xr,Xi] N256 2-SM pair BM256 BN128 BK256 stages3 tmem-single", 0,
+     launch_fp4_or_e4m3<0>},
+    {"1bit->e2m1 mxf4 stacked [-Xi,Xr,Xi] N128 2-SM pair BM256 BN64 BK256 stages4 tmem-double", 0,
+     launch_fp4_or_e4m3<1>},
 };
+constexpr int kFirstFp4Config = 5;
 
 }  // namespace
 
 int gemm_1bit_num_configs() { return static_cast<int>(sizeof(kConfigs1) / sizeof(kConfigs1[0])); }
+
+bool gemm_1bit_config_fp4(int config) {
+    return config >= kFirstFp4Config && config < gemm_1bit_num_configs();
+}
+
+int gemm_1bit_fp4_variant(int config) {
+    return gemm_1bit_config_fp4(config) ? config - kFirstFp4Config : -1;
+}
+
+int gemm_1bit_fp4_default_config() { return kFirstFp4Config; }
 
 const char *gemm_1bit_config_name(int config) {
     if (config < 0 || config >= gemm_1bit_num_configs()) return "invalid";

@@ -494,6 +494,11 @@ cudaError_t launch_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp
 // ===========================================================================
 constexpr int PBK = 64;                  // K per stage: one 128-byte row
 constexpr int kStkPairChunkBlocks = 32;  // stages (x 64 K) per promoted chunk
+// Pair tiles run in groups of kPairGroupM pair rows, samples fastest within
+// a group: the clusters running at one time then share their W rows and
+// their X columns in L2.  With samples fastest over all rows, a product
+// whose X does not fit in L2 streams all of X once per pair row.
+constexpr int kPairGroupM = 8;
 
 template <int STAGES>
 struct CfgStkPair {
@@ -537,14 +542,20 @@ __global__ void __launch_bounds__(kStkThreads, 1)
     // packed planes -Xi (0), Xr (1), Xi (2): this CTA's rows of B1 and of B2
     const int plane_b1 = leader ? 1 : 2;
     const int plane_b2 = leader ? 0 : 1;
-    // (batch, 256-row pair tile, sample tile) of pair tile t, samples fastest
+    // (batch, 256-row pair tile, sample tile) of pair tile t: groups of
+    // kPairGroupM pair rows (the last one possibly shorter), pair rows
+    // fastest inside a group, then sample tiles
     auto decode = [&](int t, int &b, int &mp, int &nt) {
-        const int groups = (args.tiles.m_tiles + 1) / 2;
-        const int per_b = groups * args.tiles.n_tiles;
+        const int m_pairs = (args.tiles.m_tiles + 1) / 2;
+        const int per_b = m_pairs * args.tiles.n_tiles;
         b = t / per_b;
         const int local = t - b * per_b;
-        nt = local % args.tiles.n_tiles;
-        mp = local / args.tiles.n_tiles;
+        const int group = local / (kPairGroupM * args.tiles.n_tiles);
+        const int first = group * kPairGroupM;
+        const int gm = min(kPairGroupM, m_pairs - first);
+        const int in = local - group * kPairGroupM * args.tiles.n_tiles;
+        mp = first + in % gm;
+        nt = in / gm;
     };
 
     if (threadIdx.x == 0) {

@@ -13,6 +13,10 @@
 //   kind 4: mma.sync m16n8k256 b1 AND-popc -> s32 (legacy warp MMA)
 //   kind 5: CUDA-core popc of XOR on 32-bit words
 //   kind 6: tcgen05.mma kind::f16   M128 N128 K16  (the beamformer's tile MMA)
+//   kind 7: tcgen05.mma kind::mxf4  M128 N256 K64  (packed E2M1, unit UE8M0
+//           scales in tensor memory: the 1-bit GEMM's 4-bit path)
+//   kind 8: tcgen05.mma kind::mxf4nvf4 M128 N256 K64, UE4M3 scale per 16 K
+//   kind 9: tcgen05.mma kind::mxf4nvf4 M128 N256 K64, UE8M0 scale per 32 K
 // Ops are counted as 2 per multiply-accumulate (b1: per bit product).
 #include <cuda_runtime.h>
 
@@ -31,6 +35,9 @@ using namespace dev;
 // 256x128B (B) swizzled tiles into a 256-column FP32/S32 accumulator.
 template <int KIND>
 __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *status) {
+    // the 4-bit kinds keep their scale factors in columns [256, 512)
+    constexpr bool kFp4 = KIND >= 7;
+    constexpr uint32_t kCols = kFp4 ? 512 : 256;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
@@ -39,12 +46,14 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *st
     const uint32_t bar = s0 + 49152;
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 49152 + 64);
     // operands: hashed values of magnitude in [0.5, 1) with random signs
-    // (FP16 pairs for kind 0, E4M3 bytes for kind 1), so the timed loop
-    // draws realistic power
+    // (FP16 pairs for kind 0, E4M3 bytes for kind 1; kind 7: +-1 E2M1
+    // nibbles), so the timed loop draws realistic power
     for (int i = threadIdx.x; i < 49152 / 4; i += blockDim.x) {
         const uint32_t h = (i + 1) * 0x9E3779B9u;
         reinterpret_cast<uint32_t *>(smem)[i] =
-            KIND == 1 ? ((h & 0x87878787u) | 0x30303030u) : ((h & 0x83FF83FFu) | 0x38003800u);
+            KIND == 1   ? ((h & 0x87878787u) | 0x30303030u)
+            : kFp4      ? ((h & 0x88888888u) | 0x22222222u)
+                        : ((h & 0x83FF83FFu) | 0x38003800u);
     }
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -52,13 +61,24 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *st
     }
     fence_async_smem();
     if (threadIdx.x < 32) {
-        tmem_alloc(smem_u32(slot), 256);
+        tmem_alloc(smem_u32(slot), kCols);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *slot;
+    if (kFp4) {
+        // every byte of the scale columns is 1.0: UE8M0 127, or UE4M3 0x38
+        // (kind 8); each warp writes its lanes
+        const uint32_t one = KIND == 8 ? 0x38383838u : 0x7F7F7F7Fu;
+        const uint32_t lane_off = static_cast<uint32_t>((threadIdx.x >> 5) * 32) << 16;
+        for (uint32_t c = 256; c < kCols; c += 4) tmem_st_fill4(tmem + lane_off + c, one);
+        tmem_st_wait();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
     if (threadIdx.x == 0) {
         const uint64_t ad = sdesc_kmajor_sw128(a_addr);
         const uint64_t bd = sdesc_kmajor_sw128(b_addr);
@@ -71,6 +91,10 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *st
         } else if (KIND == 1) {
             constexpr uint32_t id = idesc_f32acc(128, 256, 0, false);   // e4m3 x e4m3
             for (int i = 0; i < iters; ++i) mma_f8f6f4(tmem, ad, bd, id, i > 0);
+        } else if (kFp4) {
+            constexpr uint32_t id = idesc_mxf4(128, 256, KIND != 8);
+            for (int i = 0; i < iters; ++i)
+                mma_mxf4<KIND - 7>(tmem, ad, bd, id, tmem + 256, tmem + 384, i > 0);
         }
         mma_commit(bar);
         if (!mbar_wait(bar, 0)) atomicOr(status, kErrTimeoutMma);
@@ -79,7 +103,7 @@ __global__ void __launch_bounds__(128, 1) tc_peak_kernel(int iters, uint32_t *st
     __syncthreads();
     if (threadIdx.x < 32) {
         tc_fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, kCols);
     }
 }
 
@@ -139,7 +163,7 @@ using namespace tcbf;
 
 TCBF_EXPORT tcbf_status tcbf_peak_run(int kind, int device, int iters, double *seconds,
                                       double *ops) {
-    if (!seconds || !ops || kind < 0 || kind > 6 || iters < 1) return TCBF_ERR_INVALID_ARG;
+    if (!seconds || !ops || kind < 0 || kind > 9 || iters < 1) return TCBF_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TCBF_ERR_UNSUPPORTED;
     if (device < 0 || device >= ndev) return TCBF_ERR_INVALID_ARG;
@@ -178,6 +202,21 @@ TCBF_EXPORT tcbf_status tcbf_peak_run(int kind, int device, int iters, double *s
                     cudaFuncSetAttribute(tc_peak_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
                     tc_peak_kernel<6><<<sms, 128, smem>>>(iters, status);
                     per_launch = 2.0 * 128 * 128 * 16 * double(iters) * sms;
+                    break;
+                case 7:
+                    cudaFuncSetAttribute(tc_peak_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                    tc_peak_kernel<7><<<sms, 128, smem>>>(iters, status);
+                    per_launch = 2.0 * 128 * 256 * 64 * double(iters) * sms;
+                    break;
+                case 8:
+                    cudaFuncSetAttribute(tc_peak_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                    tc_peak_kernel<8><<<sms, 128, smem>>>(iters, status);
+                    per_launch = 2.0 * 128 * 256 * 64 * double(iters) * sms;
+                    break;
+                case 9:
+                    cudaFuncSetAttribute(tc_peak_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                    tc_peak_kernel<9><<<sms, 128, smem>>>(iters, status);
+                    per_launch = 2.0 * 128 * 256 * 64 * double(iters) * sms;
                     break;
                 case 3:
                     warp_peak_kernel<3><<<sms * 4, 256>>>(iters, 1, status);

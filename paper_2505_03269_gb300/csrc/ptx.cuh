@@ -293,6 +293,53 @@ __device__ __forceinline__ void mma_f8f6f4_pair(uint32_t d, uint64_t a, uint64_t
         : "memory");
 }
 
+// Block-scaled 4-bit MMA on one SM (see mma_mxf4_pair).  FP4K selects the
+// kind: 0 kind::mxf4 (UE8M0 scale per 32 K), 1 kind::mxf4nvf4 with UE4M3
+// scales per 16 K, 2 kind::mxf4nvf4 with UE8M0 scales per 32 K.
+template <int FP4K = 0>
+__device__ __forceinline__ void mma_mxf4(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    if (FP4K == 0)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, "
+            "[%4], [%5], p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+            : "memory");
+    else if (FP4K == 1)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4nvf4.block_scale.scale_vec::4X [%0], %1, %2, %3, "
+            "[%4], [%5], p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4nvf4.block_scale.scale_vec::2X [%0], %1, %2, %3, "
+            "[%4], [%5], p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+            : "memory");
+}
+
+// Block-scaled 4-bit MMA on an SM pair: A and B are E2M1 values packed two
+// per byte (K = 64 per instruction, 32 bytes of each row), every 32 K
+// elements of a row carry one UE8M0 scale read from tensor memory at sfa
+// (A) and sfb (B), and D is FP32.
+__device__ __forceinline__ void mma_mxf4_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                              uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], "
+        "[%5], p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
+}
+
 // arrive on the barrier at this offset in both CTAs of the pair (mask) once
 // all pair MMAs issued so far by this thread complete
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar, uint16_t cta_mask) {
@@ -348,6 +395,13 @@ __device__ __forceinline__ void tmem_st_2x16(uint32_t ta, uint32_t tb, const flo
         : "memory");
 }
 
+// The same 32-bit value into 4 consecutive columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_st_fill4(uint32_t ta, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta), "r"(v),
+                 "r"(v), "r"(v), "r"(v)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_st_wait() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -391,6 +445,19 @@ __host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N, uint32_t ab_fo
            | (ab_format << 10)                         // B format
            | ((negate_a ? 1u : 0u) << 13)              // negate A
            | (static_cast<uint32_t>(N >> 3) << 17)     // N >> 3
+           | (static_cast<uint32_t>(M >> 4) << 24);    // M >> 4
+}
+
+// Instruction descriptor of the block-scaled kinds for kind::mxf4: E2M1 A
+// and B (format 1 in that kind), UE8M0 scales (bit 23), scale-factor ids 0
+// (bits 4-5 for B, 29-30 for A), K-major, no negation (the kind has none),
+// FP32 D implied.
+// kind::mxf4nvf4 uses the same layout; ue8m0 = false selects UE4M3 scales.
+__host__ __device__ constexpr uint32_t idesc_mxf4(int M, int N, bool ue8m0 = true) {
+    return (1u << 7)                                   // A format: E2M1
+           | (1u << 10)                                // B format: E2M1
+           | (static_cast<uint32_t>(N >> 3) << 17)     // N >> 3
+           | ((ue8m0 ? 1u : 0u) << 23)                 // scale format: UE8M0 (1), UE4M3 (0)
            | (static_cast<uint32_t>(M >> 4) << 24);    // M >> 4
 }
 

@@ -35,6 +35,10 @@ struct tcbf_plan_s {
     // rows between the planes of packed W (0: M).  Row-range sub-plans of
     // tcbf_beamform_host point into a larger packed W.
     int64_t w_rows = 0;
+    // 1-bit plans on the 4-bit tensor path: E2M1 planes of W and X, made
+    // when such a configuration is first set (nullptr until then)
+    void *fp4_buf = nullptr;
+    size_t fp4_bytes = 0;
 };
 
 namespace tcbf {
@@ -120,6 +124,30 @@ int gemm_1bit_num_configs();
 const char *gemm_1bit_config_name(int config);
 cudaError_t launch_gemm_1bit(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,
                              int32_t *Y, cudaStream_t s);
+// Configurations of the 1-bit table that run on the 4-bit tensor path.
+bool gemm_1bit_config_fp4(int config);
+
+// 1-bit GEMM on the 4-bit tensor path (gemm_1bit_fp4.cu): device scratch for
+// the E2M1 planes (reserve: allocate once per plan; release: free), whether
+// a plan can take the path (scratch present, K <= 2^23, no uneven batches),
+// and the launch (variant 0: 256 x 128 pair tiles, one accumulator;
+// 1: 256 x 64, two).  cudaErrorNotSupported when the plan cannot take it.
+size_t gemm_1bit_fp4_scratch_bytes(const tcbf_plan_s &pl);
+cudaError_t gemm_1bit_fp4_reserve(tcbf_plan_s &pl);
+void gemm_1bit_fp4_release(tcbf_plan_s &pl);
+bool gemm_1bit_fp4_usable(const tcbf_plan_s &pl);
+cudaError_t launch_gemm_1bit_fp4(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,
+                                 int32_t *Y, cudaStream_t s, int variant);
+// Its two halves: expansion of one operand (which 0: W, 1: X) into the
+// scratch, and the GEMM on the planes there.
+cudaError_t launch_expand_1bit_fp4(const tcbf_plan_s &pl, int which, const uint32_t *bits,
+                                   cudaStream_t s);
+cudaError_t launch_gemm_1bit_fp4_expanded(const tcbf_plan_s &pl, int32_t *Y, cudaStream_t s,
+                                          int variant);
+// Variant (0 or 1) of a 4-bit configuration of the 1-bit table, -1 otherwise.
+int gemm_1bit_fp4_variant(int config);
+// The configuration a 1-bit plan starts with when it can take the 4-bit path.
+int gemm_1bit_fp4_default_config();
 
 // Releases the staging of tcbf_beamform_host (plan destruction).
 void host_pipe_destroy(tcbf_plan_s &pl);

@@ -21,6 +21,9 @@ KINDS = {
     4: ("mma_sync_b1_and_m16n8k256", 20000),
     5: ("cuda_core_popc_xor32", 20000),
     6: ("tcgen05_f16_m128n128k16", 80000),
+    7: ("tcgen05_mxf4_e2m1_m128n256k64", 40000),
+    8: ("tcgen05_mxf4nvf4_ue4m3x16_m128n256k64", 40000),
+    9: ("tcgen05_mxf4nvf4_ue8m0x32_m128n256k64", 40000),
 }
 
 

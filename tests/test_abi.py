@@ -77,6 +77,8 @@ def test_null_arguments(lib):
     assert lib.tcbf_beamform_fp16(None, None, None, None, None) == 1
     assert lib.tcbf_beamform_fp8split(None, None, None, None, None) == 1
     assert lib.tcbf_beamform_1bit(None, None, None, None, None) == 1
+    assert lib.tcbf_expand_1bit(None, 0, None, None) == 1
+    assert lib.tcbf_beamform_1bit_expanded(None, None, None) == 1
     assert lib.tcbf_weights_from_geometry(None, None, None, 0, None, 1.0, None, None) == 1
     assert lib.tcbf_last_device_error(None) == 1
     assert lib.tcbf_debug_drop_fill(None, ctypes.c_int64(0)) == 1

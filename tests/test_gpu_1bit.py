@@ -40,7 +40,9 @@ def run_1bit(Wb, Xb, K, config=None):
         return Y.cpu().numpy().astype(np.int64)
 
 
-@pytest.mark.parametrize("config", [0, 1, 4])
+# 5 and 6: the 4-bit tensor path (bits expanded to E2M1 planes in the plan's
+# scratch, block-scaled MMAs on SM pairs)
+@pytest.mark.parametrize("config", [0, 1, 4, 5, 6])
 @pytest.mark.parametrize("B,M,N,K", [(1, 1, 1, 1), (2, 3, 5, 7), (2, 33, 70, 45),
                                      (1, 128, 256, 1024), (3, 130, 300, 200),
                                      (2, 200, 64, 129), (1, 64, 1000, 640)])
@@ -50,7 +52,7 @@ def test_random_bits_bit_exact(config, B, M, N, K):
     assert np.array_equal(Y, oracle.bgemm(Wb, Xb, K))
 
 
-@pytest.mark.parametrize("config", [0, 4])
+@pytest.mark.parametrize("config", [0, 4, 5, 6])
 def test_shared_weights_bit_exact(config):
     g = ti.rng(4)
     K = 300
@@ -94,7 +96,8 @@ def test_pack_then_gemm_pipeline():
     assert np.array_equal(Yg, oracle.bgemm(Wb, Xb, K))
 
 
-def test_full_size_radio_1bit_sampled():
+@pytest.mark.parametrize("config", [0, 5, 6])
+def test_full_size_radio_1bit_sampled(config):
     """64 channels x 2048 beams x 1024 receivers x 8192 samples: the whole
     launch as timed, checked bit-exact on sampled row/column blocks."""
     import torch
@@ -103,6 +106,7 @@ def test_full_size_radio_1bit_sampled():
     B, M, K, N = 64, 2048, 1024, 8192
     Wb, Xb = ti.onebit_block(seed=0, B=B, M=M, K=K, N=N)
     with Plan(B, M, N, K, MODE_1BIT) as plan:
+        plan.set_config(config)
         Y = torch.empty((B, M, N, 2), dtype=torch.int32, device="cuda")
         plan.beamform_1bit(dev(Wb), dev(Xb), Y)
         torch.cuda.synchronize()
@@ -127,3 +131,57 @@ def test_all_configurations_bit_identical():
         n = plan.num_configs()
     for c in range(n):
         assert np.array_equal(run_1bit(Wb, Xb, 333, c), ref), c
+
+
+def test_default_configuration_is_the_4bit_path():
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    with Plan(2, 300, 200, 500, MODE_1BIT) as plan:
+        assert plan.config_name(plan.get_config()).startswith("1bit->e2m1")
+
+
+def test_expand_once_then_gemm_per_block():
+    """W expanded once, then X blocks expanded and multiplied in turn: each
+    block exact, and equal to the one-call path."""
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    B, M, N, K = 2, 260, 190, 700
+    g = ti.rng(41)
+    Wb = ti.random_sign_words(g, (1, 2, M, ti.words_per_row(K)))
+    with Plan(B, M, N, K, MODE_1BIT, w_batches=1) as plan:
+        for config in (5, 6):
+            plan.set_config(config)
+            plan.expand_1bit(0, dev(Wb))
+            for blk in range(3):
+                Xb = ti.random_sign_words(g, (B, 2, N, ti.words_per_row(K)))
+                Y = torch.full((B, M, N, 2), -7, dtype=torch.int32, device="cuda")
+                plan.expand_1bit(1, dev(Xb))
+                plan.beamform_1bit_expanded(Y)
+                Y1 = torch.full_like(Y, -9)
+                plan.beamform_1bit(dev(Wb), dev(Xb), Y1)
+                torch.cuda.synchronize()
+                assert plan.last_device_error() == 0
+                got = Y.cpu().numpy().astype(np.int64)
+                assert np.array_equal(got, oracle.bgemm(Wb, Xb, K)), (config, blk)
+                assert np.array_equal(got, Y1.cpu().numpy().astype(np.int64))
+
+
+def test_expand_needs_the_4bit_path():
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan, TcbfError
+    K = 64
+    Wb = ti.random_sign_words(ti.rng(42), (1, 2, 8, ti.words_per_row(K)))
+    with Plan(1, 8, 8, K, MODE_1BIT) as plan:
+        plan.set_config(0)
+        with pytest.raises(TcbfError, match="UNSUPPORTED"):
+            plan.expand_1bit(0, dev(Wb))
+        Y = torch.zeros((1, 8, 8, 2), dtype=torch.int32, device="cuda")
+        with pytest.raises(TcbfError, match="UNSUPPORTED"):
+            plan.beamform_1bit_expanded(Y)
+        plan.set_config(5)
+        with pytest.raises(TcbfError, match="INVALID_ARG"):
+            plan.expand_1bit(2, dev(Wb))
+        plan.set_batch_rows([3])          # uneven rows: not on the 4-bit path
+        with pytest.raises(TcbfError, match="UNSUPPORTED"):
+            plan.expand_1bit(0, dev(Wb))

@@ -149,6 +149,22 @@ def test_single_batch_row_ranges_equal_device_path(mode, flags, M):
     assert np.array_equal(Yh.numpy(), Yref.numpy())
 
 
+# The 4-bit tensor path of the 1-bit mode expands W and X into plan-owned
+# scratch; the batch chunks and the row ranges of one batch (sub-plans that
+# share it, one after another on one stream) equal the device path.
+@pytest.mark.parametrize("config", [5, 6])
+@pytest.mark.parametrize("B,Bw,M,N,K,chunk", [(6, 3, 130, 300, 200, 2), (1, 1, 20000, 300, 64, 0)])
+def test_1bit_fp4_host_path_equals_device_path(config, B, Bw, M, N, K, chunk):
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    W, X = _inputs(M + config, Bw, B, M, N, K, 0)
+    with Plan(B, M, N, K, MODE_1BIT, w_batches=Bw) as plan:
+        plan.set_config(config)
+        Wp, Yref = _device_path(plan, MODE_1BIT, dev(W), dev(X), 0, B, M, N)
+        Yh = _host_path(plan, Wp, _pinned(X), Yref, chunk, 0, calls=2)
+    assert np.array_equal(Yh.numpy(), Yref.numpy())
+
+
 def test_single_batch_fp32_source_against_oracle():
     from gpu_util import dev
     from paper_2505_03269_gb300 import MODE_FP16, Plan
