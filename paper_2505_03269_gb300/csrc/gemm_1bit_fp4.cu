@@ -21,8 +21,8 @@
 //               completing on the even CTA's full barrier
 //   warp 1      TMEM owner; in the even CTA the single-thread MMA issuer
 //   warps 2-5   scale-factor fill at start, then the epilogue: TMEM ->
-//               int32 pairs -> staged TMA stores, releasing an accumulator
-//               on the even CTA's barrier
+//               int32 pairs -> staged TMA stores (two buffers per warp),
+//               releasing an accumulator on the even CTA's barrier
 // Tensor memory: accumulators in columns [0, 256), scale factors in
 // [256, 512), every byte UE8M0 127, so any scale layout reads 1.0.
 #include <algorithm>
@@ -37,7 +37,6 @@ namespace {
 
 using namespace dev;
 
-constexpr int kFp4Threads = 192;
 constexpr int kRowBytes = 128;     // bytes of each row per stage: 256 E2M1 values
 constexpr int kStageK = 256;
 constexpr int kSfCol = 256;        // first tensor-memory column of the scale factors
@@ -131,6 +130,8 @@ __device__ __forceinline__ void fp4_decode(int t, const Fp4Args &a, int &b, int 
     nt = in / gm;
 }
 
+constexpr int kFp4Threads = 192;
+
 template <int SBN, int STAGES>
 struct CfgFp4 {
     static constexpr int W_PLANE = 128 * kRowBytes;            // 16 KB
@@ -140,7 +141,10 @@ struct CfgFp4 {
     static constexpr int ACC_COLS = 2 * SBN;                    // [Re | Im]
     static constexpr int ACC_BUFS = 2 * ACC_COLS <= kSfCol ? 2 : 1;
     static constexpr int TMEM_COLS = 512;
-    static constexpr int STAGING_BYTES = 4 * 4096;
+    // two 32 x 128-byte output buffers per epilogue warp: one store in
+    // flight while the next block is staged (the output stream of short-K
+    // products is bound by the stores a warp keeps in flight)
+    static constexpr int STAGING_BYTES = 4 * 2 * 4096;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
     static_assert(ACC_BUFS * ACC_COLS <= kSfCol, "accumulators below the scale columns");
     static_assert(SBN % 16 == 0 && SBN >= 32 && 2 * SBN <= 256, "pair N");
@@ -340,9 +344,10 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
         // ------------------------------------------------- epilogue, both CTAs
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        const uint32_t stage_buf = staging0 + (warp - 2) * 4096;
+        const uint32_t stage_buf = staging0 + (warp - 2) * 8192;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
         int ev = 0;
+        int chunk_count = 0;
         bool ok = true;
         for (int t = t_first; t < args.total_tiles && ok; t += t_step, ++ev) {
             int b, mp, nt;
@@ -365,9 +370,10 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
                 const int n0 = nt * SBN + c * 16;
                 if (args.tma_store) {
                     if (n0 < args.N) {
-                        if (lane == 0) bulk_wait_read<0>();   // the buffer's last store has read it
+                        const uint32_t buf = stage_buf + (chunk_count & 1) * 4096;
+                        if (lane == 0) bulk_wait_read<1>();   // the buffer's last store has read it
                         __syncwarp();
-                        const uint32_t rbase = stage_buf + lane * 128;
+                        const uint32_t rbase = buf + lane * 128;
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
                             st_shared_i4(rbase + ((j ^ (lane & 7)) << 4), __float2int_rn(re[2 * j]),
@@ -376,9 +382,10 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
                         fence_async_smem();
                         __syncwarp();
                         if (lane == 0) {
-                            tma_store_3d(&tmY, stage_buf, 2 * n0, mrow0 + quarter * 32, b);
+                            tma_store_3d(&tmY, buf, 2 * n0, mrow0 + quarter * 32, b);
                             bulk_commit();
                         }
+                        ++chunk_count;
                     }
                 } else if (m < args.M && n0 < args.N) {
 #pragma unroll
