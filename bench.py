@@ -777,6 +777,12 @@ def main():
     else:
         roof = {"bound": "tensor", "achieved": gemm_tops, "peak": tensor_peak,
                 "unit": "TFLOP/s", "frac": gemm_tops / tensor_peak}
+    fp4_micro = None
+    if gw.fp4():
+        # the 4-bit rate measured on chip by the library's microbenchmark
+        # (kind::mxf4, operands in shared memory), beside the nominal-ratio peak
+        from paper_2505_03269_gb300 import peaks as tcbf_peaks
+        fp4_micro = tcbf_peaks.measure(7, local)
     full_size = args.batches is None and args.m_rows is None
     traffic_key = f"{args.workload}/{w['mode']}" if full_size else None
     roof.update({"traffic": recorded_traffic(kname, traffic_key,
@@ -811,6 +817,8 @@ def main():
                     "expand_x_ms": timed.prep_ms if gw.fp4() else None,
                     "gemm_useful_tops": ops / (gemm_ms * 1e-3) / 1e12,
                     "gemm_tops": gemm_tops, "gemm_frac_of_tensor_peak": gemm_tops / tensor_peak,
+                    "fp4_microbench_tops": fp4_micro,
+                    "gemm_frac_of_fp4_microbench": gemm_tops / fp4_micro if fp4_micro else None,
                     "gemm_gbs": gemm_gbs, "gemm_ai_ops_per_byte": ai,
                     "pack_gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
                     "pack_frac_of_hbm": pack_bytes / (pack_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},

@@ -37,13 +37,27 @@ def sm_clock(device: int):
         return None
 
 
-def run(device: int = 0, scale: float = 1.0) -> dict:
-    tcbf_build.build()
+def _peak_fn():
     lib = binding.load()
     f = lib.tcbf_peak_run
     f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                   ctypes.POINTER(ctypes.c_double)]
     f.restype = ctypes.c_int
+    return f
+
+
+def measure(kind: int, device: int = 0) -> float:
+    """TeraOps/s of one microbenchmark kind (raises on a failed run)."""
+    sec, ops = ctypes.c_double(), ctypes.c_double()
+    st = _peak_fn()(kind, device, KINDS[kind][1], ctypes.byref(sec), ctypes.byref(ops))
+    if st != 0:
+        raise binding.TcbfError(st, f"tcbf_peak_run({kind})")
+    return ops.value / sec.value / 1e12
+
+
+def run(device: int = 0, scale: float = 1.0) -> dict:
+    tcbf_build.build()
+    f = _peak_fn()
     res = {}
     for kind, (name, iters) in KINDS.items():
         sec, ops = ctypes.c_double(), ctypes.c_double()
