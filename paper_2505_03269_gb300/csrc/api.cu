@@ -169,7 +169,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
         // 1-bit: the 4-bit tensor path by default when its planes fit
         if (q.mode == TCBF_MODE_1BIT && gemm_1bit_fp4_reserve(*pl) == cudaSuccess &&
             gemm_1bit_fp4_usable(*pl))
-            pl->config = gemm_1bit_fp4_default_config();
+            pl->config = gemm_1bit_fp4_default_config(q.K);
     }
     *out = pl;
     return TCBF_OK;

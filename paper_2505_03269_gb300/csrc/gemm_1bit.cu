@@ -544,6 +544,8 @@ const Config1 kConfigs1[] = {
      launch_fp4_or_e4m3<0>},
     {"1bit->e2m1 mxf4 stacked [-Xi,Xr,Xi] N128 2-SM pair BM256 BN64 BK256 stages4 tmem-double", 0,
      launch_fp4_or_e4m3<1>},
+    {"1bit->e2m1 mxf4 stacked [-Xi,Xr,Xi] N192 2-SM pair BM256 BN96 BK256 stages3 tmem-double", 0,
+     launch_fp4_or_e4m3<2>},
 };
 constexpr int kFirstFp4Config = 5;
 
@@ -559,7 +561,12 @@ int gemm_1bit_fp4_variant(int config) {
     return gemm_1bit_config_fp4(config) ? config - kFirstFp4Config : -1;
 }
 
-int gemm_1bit_fp4_default_config() { return kFirstFp4Config; }
+// Short K: 256 x 96 tiles with two accumulators, so each tile's drain
+// overlaps the next tile's MMAs; long K (the MMAs dominate the drain): the
+// full-width N = 256 tiles with one accumulator.  On the radio 1-bit block
+// (K = 1024) the first takes 2.76 ms per call against 2.97; on K = 65536
+// 20.5 ms against 16.6; they cross near K = 8800.
+int gemm_1bit_fp4_default_config(int64_t K) { return K <= 8192 ? kFirstFp4Config + 2 : kFirstFp4Config; }
 
 const char *gemm_1bit_config_name(int config) {
     if (config < 0 || config >= gemm_1bit_num_configs()) return "invalid";

@@ -23,8 +23,9 @@
 //   warps 2-5   scale-factor fill at start, then the epilogue: TMEM ->
 //               int32 pairs -> staged TMA stores (two buffers per warp),
 //               releasing an accumulator on the even CTA's barrier
-// Tensor memory: accumulators in columns [0, 256), scale factors in
-// [256, 512), every byte UE8M0 127, so any scale layout reads 1.0.
+// Tensor memory: the accumulators from column 0, the scale factors in the
+// columns above them up to 512 (from 256, or 384 for two 192-column
+// accumulators), every byte UE8M0 127, so any scale layout reads 1.0.
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -39,7 +40,6 @@ using namespace dev;
 
 constexpr int kRowBytes = 128;     // bytes of each row per stage: 256 E2M1 values
 constexpr int kStageK = 256;
-constexpr int kSfCol = 256;        // first tensor-memory column of the scale factors
 constexpr int64_t kMaxExactK = int64_t(1) << 23;
 // Tile order: groups of kGroupM pair rows (256 W rows each), samples
 // fastest within a group, so the clusters running at one time share both
@@ -139,14 +139,18 @@ struct CfgFp4 {
     static constexpr int W_BYTES = 2 * W_PLANE;                 // Wr, Wi (this CTA's rows)
     static constexpr int STAGE_BYTES = W_BYTES + 2 * X_PLANE;  // + this CTA's halves of B1, B2
     static constexpr int ACC_COLS = 2 * SBN;                    // [Re | Im]
-    static constexpr int ACC_BUFS = 2 * ACC_COLS <= kSfCol ? 2 : 1;
+    // two accumulators when they leave at least 64 columns for the scales
+    static constexpr int ACC_BUFS = 2 * ACC_COLS + 64 <= 512 ? 2 : 1;
     static constexpr int TMEM_COLS = 512;
+    // scale factors: A from SF_COL, B from the middle of the rest
+    static constexpr int SF_COL = (ACC_BUFS * ACC_COLS + 63) / 64 * 64;
+    static constexpr int SFB_COL = SF_COL + (TMEM_COLS - SF_COL) / 2;
     // two 32 x 128-byte output buffers per epilogue warp: one store in
     // flight while the next block is staged (the output stream of short-K
     // products is bound by the stores a warp keeps in flight)
     static constexpr int STAGING_BYTES = 4 * 2 * 4096;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
-    static_assert(ACC_BUFS * ACC_COLS <= kSfCol, "accumulators below the scale columns");
+    static_assert(SF_COL + 64 <= TMEM_COLS, "room for the scale columns");
     static_assert(SBN % 16 == 0 && SBN >= 32 && 2 * SBN <= 256, "pair N");
     static_assert(X_PLANE % 1024 == 0, "swizzle atoms");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
@@ -216,11 +220,11 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    // scale factors of A and B: every byte of columns [kSfCol, 512) is 2^0
+    // scale factors of A and B: every byte of columns [SF_COL, 512) is 2^0
     if (warp >= 2) {
         const uint32_t lane_off = static_cast<uint32_t>((warp & 3) * 32) << 16;
 #pragma unroll 1
-        for (int c = kSfCol; c < C::TMEM_COLS; c += 4)
+        for (int c = C::SF_COL; c < C::TMEM_COLS; c += 4)
             tmem_st_fill4(tmem_base + lane_off + c, 0x7F7F7F7Fu);
         tmem_st_wait();
     }
@@ -289,8 +293,8 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
         // ------------------------------------------ MMA issuer, even CTA only
         if (lane == 0 && leader) {
             constexpr uint32_t kIdesc = idesc_mxf4(256, 2 * SBN);
-            const uint32_t sfa = tmem_base + kSfCol;
-            const uint32_t sfb = tmem_base + kSfCol + 128;
+            const uint32_t sfa = tmem_base + C::SF_COL;
+            const uint32_t sfb = tmem_base + C::SFB_COL;
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;
@@ -578,7 +582,8 @@ cudaError_t launch_gemm_1bit_fp4_expanded(const tcbf_plan_s &pl, int32_t *Y, cud
                                           int variant) {
     if (!gemm_1bit_fp4_usable(pl)) return cudaErrorNotSupported;
     if (variant == 0) return launch_fp4_pair<128, 3>(pl, Y, s);
-    return launch_fp4_pair<64, 4>(pl, Y, s);
+    if (variant == 1) return launch_fp4_pair<64, 4>(pl, Y, s);
+    return launch_fp4_pair<96, 3>(pl, Y, s);
 }
 
 cudaError_t launch_gemm_1bit_fp4(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,

@@ -131,7 +131,8 @@ bool gemm_1bit_config_fp4(int config);
 // the E2M1 planes (reserve: allocate once per plan; release: free), whether
 // a plan can take the path (scratch present, K <= 2^23, no uneven batches),
 // and the launch (variant 0: 256 x 128 pair tiles, one accumulator;
-// 1: 256 x 64, two).  cudaErrorNotSupported when the plan cannot take it.
+// 1: 256 x 64, two; 2: 256 x 96, two).  cudaErrorNotSupported when the
+// plan cannot take it.
 size_t gemm_1bit_fp4_scratch_bytes(const tcbf_plan_s &pl);
 cudaError_t gemm_1bit_fp4_reserve(tcbf_plan_s &pl);
 void gemm_1bit_fp4_release(tcbf_plan_s &pl);
@@ -144,10 +145,10 @@ cudaError_t launch_expand_1bit_fp4(const tcbf_plan_s &pl, int which, const uint3
                                    cudaStream_t s);
 cudaError_t launch_gemm_1bit_fp4_expanded(const tcbf_plan_s &pl, int32_t *Y, cudaStream_t s,
                                           int variant);
-// Variant (0 or 1) of a 4-bit configuration of the 1-bit table, -1 otherwise.
+// Variant (0-2) of a 4-bit configuration of the 1-bit table, -1 otherwise.
 int gemm_1bit_fp4_variant(int config);
 // The configuration a 1-bit plan starts with when it can take the 4-bit path.
-int gemm_1bit_fp4_default_config();
+int gemm_1bit_fp4_default_config(int64_t K);
 
 // Releases the staging of tcbf_beamform_host (plan destruction).
 void host_pipe_destroy(tcbf_plan_s &pl);

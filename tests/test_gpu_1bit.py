@@ -40,9 +40,9 @@ def run_1bit(Wb, Xb, K, config=None):
         return Y.cpu().numpy().astype(np.int64)
 
 
-# 5 and 6: the 4-bit tensor path (bits expanded to E2M1 planes in the plan's
+# 5-7: the 4-bit tensor path (bits expanded to E2M1 planes in the plan's
 # scratch, block-scaled MMAs on SM pairs)
-@pytest.mark.parametrize("config", [0, 1, 4, 5, 6])
+@pytest.mark.parametrize("config", [0, 1, 4, 5, 6, 7])
 @pytest.mark.parametrize("B,M,N,K", [(1, 1, 1, 1), (2, 3, 5, 7), (2, 33, 70, 45),
                                      (1, 128, 256, 1024), (3, 130, 300, 200),
                                      (2, 200, 64, 129), (1, 64, 1000, 640)])
@@ -52,7 +52,7 @@ def test_random_bits_bit_exact(config, B, M, N, K):
     assert np.array_equal(Y, oracle.bgemm(Wb, Xb, K))
 
 
-@pytest.mark.parametrize("config", [0, 4, 5, 6])
+@pytest.mark.parametrize("config", [0, 4, 5, 6, 7])
 def test_shared_weights_bit_exact(config):
     g = ti.rng(4)
     K = 300
@@ -96,7 +96,7 @@ def test_pack_then_gemm_pipeline():
     assert np.array_equal(Yg, oracle.bgemm(Wb, Xb, K))
 
 
-@pytest.mark.parametrize("config", [0, 5, 6])
+@pytest.mark.parametrize("config", [0, 5, 6, 7])
 def test_full_size_radio_1bit_sampled(config):
     """64 channels x 2048 beams x 1024 receivers x 8192 samples: the whole
     launch as timed, checked bit-exact on sampled row/column blocks."""
@@ -149,7 +149,7 @@ def test_expand_once_then_gemm_per_block():
     g = ti.rng(41)
     Wb = ti.random_sign_words(g, (1, 2, M, ti.words_per_row(K)))
     with Plan(B, M, N, K, MODE_1BIT, w_batches=1) as plan:
-        for config in (5, 6):
+        for config in (5, 6, 7):
             plan.set_config(config)
             plan.expand_1bit(0, dev(Wb))
             for blk in range(3):

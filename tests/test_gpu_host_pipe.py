@@ -152,7 +152,7 @@ def test_single_batch_row_ranges_equal_device_path(mode, flags, M):
 # The 4-bit tensor path of the 1-bit mode expands W and X into plan-owned
 # scratch; the batch chunks and the row ranges of one batch (sub-plans that
 # share it, one after another on one stream) equal the device path.
-@pytest.mark.parametrize("config", [5, 6])
+@pytest.mark.parametrize("config", [5, 6, 7])
 @pytest.mark.parametrize("B,Bw,M,N,K,chunk", [(6, 3, 130, 300, 200, 2), (1, 1, 20000, 300, 64, 0)])
 def test_1bit_fp4_host_path_equals_device_path(config, B, Bw, M, N, K, chunk):
     from gpu_util import dev
