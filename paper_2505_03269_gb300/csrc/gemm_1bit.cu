@@ -562,11 +562,11 @@ int gemm_1bit_fp4_variant(int config) {
 }
 
 // Short K: 256 x 96 tiles with two accumulators, so each tile's drain
-// overlaps the next tile's MMAs; long K (the MMAs dominate the drain): the
-// full-width N = 256 tiles with one accumulator.  On the radio 1-bit block
-// (K = 1024) the first takes 2.76 ms per call against 2.97; on K = 65536
-// 20.5 ms against 16.6; they cross near K = 8800.
-int gemm_1bit_fp4_default_config(int64_t K) { return K <= 8192 ? kFirstFp4Config + 2 : kFirstFp4Config; }
+// overlaps the next tile's MMAs; longer K: the full-width N = 256 tiles with
+// one accumulator.  Measured: the radio 1-bit block (K = 1024, 64 batches)
+// 2.76 ms per call against 2.97; single products M = N = K = 2048 to 8192
+// 1-9% faster with the N = 256 tiles, and K = 65536 16.6 ms against 20.5.
+int gemm_1bit_fp4_default_config(int64_t K) { return K <= 1024 ? kFirstFp4Config + 2 : kFirstFp4Config; }
 
 const char *gemm_1bit_config_name(int config) {
     if (config < 0 || config >= gemm_1bit_num_configs()) return "invalid";
