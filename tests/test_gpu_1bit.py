@@ -1,10 +1,13 @@
 """1-bit complex beamforming on the GPU against the exact int64 oracle.
 
-Bar: bit-exact int32 output.  Inputs are iid fair bits, including random
-bits beyond K in the last word (they must be ignored), ragged shapes that
-leave partial tiles and partial stages, weight sharing across batches, the
-matched-conjugate closed form, and the full-size 1-bit radio block on
-sampled outputs."""
+Bar: bit-exact int32 output, on both arithmetic paths: bits expanded on
+chip to E4M3 (configurations 0-4) and the 4-bit tensor path (5-7: E2M1
+planes in the plan's scratch, block-scaled MMAs on SM pairs, the default),
+including its expand-once entry points.  Inputs are iid fair bits,
+including random bits beyond K in the last word (they must be ignored),
+ragged shapes that leave partial tiles and partial stages, weight sharing
+across batches, the matched-conjugate closed form, and the full-size 1-bit
+radio block on sampled outputs."""
 import numpy as np
 import pytest
 
