@@ -17,9 +17,10 @@ beams x 1024 receivers x 8192 samples, 1-bit; step = sign-pack X + 1-bit
 GEMM).
 
 Metric: TeraOps/s with 8 useful operations per complex multiply-accumulate
-(8 * batch * M * N * K per step).  Prints ONE JSON line on rank 0.
+(8 * batch * M * N * K per step).  Prints ONE JSON line.  One GPU only:
+--gpus other than 1 exits with an error before any CUDA call.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus 1] [--steps K] [--warmup W] [--impl ours|reference]
 """
 from __future__ import annotations
 
@@ -131,22 +132,9 @@ def ops_per_step(w):
     return 8.0 * w["B"] * w["M"] * w["N"] * w["K"]
 
 
-def max_over_ranks(ms, world, device):
-    """The slowest rank's time: every rank's measured ms, reduced with MAX
-    over the default process group (NCCL on the GPUs, gloo in the host
-    tests) when there is more than one rank."""
-    import torch
-    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def whole_job_value(world, ops_per_rank, ms_per_step):
-    """TeraOps/s of the whole job: every rank processes its own replica of the
-    workload (weak scaling), all finish within the slowest rank's time."""
-    return world * ops_per_rank / (ms_per_step * 1e-3) / 1e12
+def tops(ops, ms):
+    """TeraOps/s of `ops` useful operations done in `ms` milliseconds."""
+    return ops / (ms * 1e-3) / 1e12
 
 
 def load_peaks():
@@ -364,9 +352,6 @@ def cpu_baseline(w, seconds):
 def reference_arm(args, w):
     """The oracle as the reference arm: each step one bounded sample."""
     import oracle
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
     target = 0.4      # seconds of oracle work per step
     _, _, desc = oracle_sample(w, target)
     for _ in range(args.warmup):
@@ -555,6 +540,9 @@ class GpuWorkload:
 
 def main():
     args = parse_args()
+    if args.gpus != 1:
+        # every product fits one GB300; the library and this benchmark are one-GPU only
+        sys.exit(f"bench.py: --gpus {args.gpus} is not supported: this benchmark runs on one GPU")
     w = workload(args)
     if args.impl == "reference":
         reference_arm(args, w)
@@ -562,26 +550,16 @@ def main():
 
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     import paper_2505_03269_gb300 as tcbf
     from paper_2505_03269_gb300 import build as tcbf_build
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    local = 0
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0 or world == 1:
-        tcbf_build.build()
-    if world > 1:
-        dist.barrier()
+    tcbf_build.build()
     tcbf.load()
 
     def barrier():
-        if world > 1:
-            dist.barrier()
         torch.cuda.synchronize()
 
     gw = GpuWorkload(w, local, args.config)
@@ -635,8 +613,8 @@ def main():
     # ---- timed region: K steps (tuned configuration), clocks sampled
     total_ms, pack_ms, gemm_ms, clocks = timed(args.steps, sample_clocks=True)
     status = plan.last_device_error()
-    ms_per_step = max_over_ranks(total_ms, world, "cuda") / args.steps
-    value = whole_job_value(world, ops_per_step(w), ms_per_step)
+    ms_per_step = total_ms / args.steps
+    value = tops(ops_per_step(w), ms_per_step)
     if tuning is not None:
         tuning["tuned"]["gemm_ms"] = gemm_ms
         tuning["speedup_gemm"] = tuning["default"]["gemm_ms"] / gemm_ms
@@ -651,7 +629,7 @@ def main():
         plan.graph_launch()
     g1.record(stream)
     barrier()
-    graph_ms = max_over_ranks(g0.elapsed_time(g1) / args.steps, world, "cuda")
+    graph_ms = g0.elapsed_time(g1) / args.steps
 
     parity = gw.parity()
 
@@ -716,8 +694,8 @@ def main():
         l1.record(stream)
         torch.cuda.synchronize()
         link_gbs = nl * 4 / (l0.elapsed_time(l1) * 1e-3) / 1e9
-        te_ms = max_over_ranks(a.elapsed_time(b) / args.e2e_steps, world, "cuda")
-        e2e = {"value": whole_job_value(world, ops_per_step(w), te_ms), "unit": UNIT,
+        te_ms = a.elapsed_time(b) / args.e2e_steps
+        e2e = {"value": tops(ops_per_step(w), te_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(gw.Xh.nbytes), "d2h_bytes_per_step": int(gw.Y.numel() * 4),
                "ms_per_step": te_ms,
                "how": "tcbf_beamform_host on pinned host X and Y: "
@@ -792,7 +770,7 @@ def main():
                  "ceiling_tops": min(tensor_peak, ai * peaks["hbm_gbs"] / 1e3),
                  "algorithmic_flops_per_useful_op": mma_factor})
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": ("e2m1" if gw.fp4() else
@@ -807,7 +785,7 @@ def main():
                    "l2": "inputs larger than L2 (X %.2f GB, Y %.1f GB per step)"
                          % (gw.Xh.nbytes / 1e9, gw.Y.numel() * 4 / 1e9),
                    "kernel_config": plan.config_name(plan.get_config()),
-                   "parallelism": f"{world} independent replica(s), no collective"},
+                   "parallelism": "one GPU"},
         # kernels per step: pack(X) + GEMM; split-FP8 packs X in three kernels
         # (column maxima, pack, exponents) after a memset; the 4-bit 1-bit
         # path adds the expansion of X
@@ -825,7 +803,7 @@ def main():
         "clocks": clocks,
         "autotune": tuning,
         "graph_step": {"ms_per_step": graph_ms,
-                       "value": whole_job_value(world, ops, graph_ms),
+                       "value": tops(ops, graph_ms),
                        "how": "tcbf_graph_capture of pack + beamform, replayed K times (4-bit 1-bit "
                               "path: the captured call also expands W)"},
         "device_status": status,
@@ -833,14 +811,10 @@ def main():
         "e2e": e2e,
         "energy": energy,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    print(json.dumps(line), flush=True)
     plan.close()
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
