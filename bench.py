@@ -5,16 +5,23 @@ Default workload (the radio-astronomy block): 512 independent products
 (256 frequency channels x 2 polarisations, both polarisations of a channel
 sharing its weights), each 1024 beams x 288 receivers x 4096 samples,
 FP16 inputs, FP32 accumulation.  One step is one pass of the hot path over
-one block of samples that is already resident in HBM:
-    tcbf_transpose_pack(X)  (interleaved complex FP16 -> packed planes)
-    tcbf_beamform_fp16      (all 512 products in one persistent launch)
-The weights are computed once from geometry beforehand (they are constant
-over many blocks) and timed separately.
+one block of samples that is already resident in HBM: the plan reads X in
+its interleaved complex layout (TCBF_FLAG_INTERLEAVED_X), so the step is
+    tcbf_beamform_fp16      (all 512 products in one persistent launch,
+                             no transpose/pack pass over X)
+The planar path (tcbf_transpose_pack(X) into planes + the planar GEMM) is
+timed beside it (`planar_step`).  The weights are computed once from
+geometry beforehand (they are constant over many blocks) and timed
+separately.
 
-Other workloads (--workload): "ultrasound" (65536 voxels x 16384 x 256
-frames, FP16, near-field model matrix) and "onebit" (64 channels x 2048
-beams x 1024 receivers x 8192 samples, 1-bit; step = sign-pack X + 1-bit
-GEMM).
+The same JSON line carries the other configured workloads as sub-records
+(`workloads`): the ultrasound block (65536 voxels x 16384 x 256 frames) in
+FP16, split-FP8 (E4M3 hi+lo, three products) and plain FP8, the 1-bit radio
+block (64 channels x 2048 beams x 1024 receivers x 8192 samples, exact
+int32), and the serving stream (continuous batching, p50/p99 latency beside
+the one-request-per-launch FP16 baseline); each with its GEMM time, roofline,
+clocks and sampled parity against the oracle.  --workload runs one of them
+as the headline instead, --no-subs skips the sub-records.
 
 Metric: TeraOps/s with 8 useful operations per complex multiply-accumulate
 (8 * batch * M * N * K per step).  Prints ONE JSON line.  One GPU only:
@@ -46,6 +53,7 @@ FP4_OVER_BF16 = 13.5 / 2.25    # and for the dense 4-bit (E2M1) rate
 WORKLOADS = {
     "radio": dict(
         mode="fp16", B=512, M=1024, N=4096, K=288, w_batches=256, geometry="radio",
+        layout="interleaved",
         desc="radio-astronomy FP16 block: 256 channels x 2 pols = 512 products of "
              "1024 beams x 288 receivers x 4096 samples, weights from geometry "
              "(110-190 MHz, 3 km disk, beams within 5 deg of zenith)"),
@@ -89,6 +97,11 @@ def parse_args():
     ap.add_argument("--mode", choices=["fp16", "fp8split", "fp8", "tf32"], default=None,
                     help="arithmetic of the FP workloads (default fp16); fp8split: E4M3 hi+lo, "
                          "three products; fp8: the plain E4M3 product (hi only)")
+    ap.add_argument("--layout", choices=["interleaved", "planar", "stacked"], default=None,
+                    help="FP16 X layout: interleaved (no pack, the radio default), planar, stacked")
+    ap.add_argument("--no-subs", action="store_true", help="skip the sub-workload records")
+    ap.add_argument("--sub-steps", type=int, default=10)
+    ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--batches", type=int, default=None,
                     help="override the number of products (small profiling cases)")
     ap.add_argument("--m-rows", type=int, default=None,
@@ -116,7 +129,20 @@ def workload(args):
     if getattr(args, "m_rows", None) is not None:
         w["M"] = args.m_rows
         w["desc"] += f" [{args.m_rows} rows]"
+    if getattr(args, "layout", None) is not None and w["mode"] == "fp16":
+        w["layout"] = args.layout
+        w["stacked"] = args.layout == "stacked"
     return w
+
+
+def layout_of(w):
+    """FP16 X layout of the workload: interleaved (read as it lies), stacked
+    planes, or the default planar planes."""
+    if w["mode"] != "fp16":
+        return "planar"
+    if w.get("stacked"):
+        return "stacked"
+    return w.get("layout", "planar")
 
 
 def is_fp8(w):
@@ -378,13 +404,13 @@ def reference_arm(args, w):
 class GpuWorkload:
     """Device-resident inputs and the step of one workload."""
 
-    def __init__(self, w, local, config):
+    def __init__(self, w, local, config, xh=None):
         import numpy as np
         import torch
         import paper_2505_03269_gb300 as tcbf
         self.w = w
         B, M, N, K, Bw = w["B"], w["M"], w["N"], w["K"], w["w_batches"]
-        self.Xh = host_x(w)
+        self.Xh = host_x(w) if xh is None else xh
         if w["mode"] == "tf32":              # the TF32 path is for data that arrives in FP32
             self.Xh = self.Xh.astype(np.float32)
         self.src_type = tcbf.SRC_CF32 if self.Xh.dtype == np.float32 else tcbf.SRC_CF16
@@ -393,15 +419,20 @@ class GpuWorkload:
                 tcbf.MODE_FP8SPLIT if is_fp8(w) else
                 tcbf.MODE_TF32 if w["mode"] == "tf32" else tcbf.MODE_FP16)
         # compute-bound FP16 shapes pack X with a third, negated plane (two N = 256
-        # MMAs per K step); plain FP16 elsewhere
-        flags = tcbf.FLAG_STACKED_X if (w.get("stacked") and mode == tcbf.MODE_FP16) else 0
+        # MMAs per K step); the radio block reads X as it lies (no pack)
+        lay = layout_of(w)
+        flags = (tcbf.FLAG_STACKED_X if lay == "stacked" else
+                 tcbf.FLAG_INTERLEAVED_X if lay == "interleaved" else 0)
         if w["mode"] == "fp8":
             flags = tcbf.FLAG_FP8_HI_ONLY
+        self.layout = lay
         self.plan = tcbf.Plan(B, M, N, K, mode, w_batches=Bw, device=local, flags=flags)
         if config is not None:
             self.plan.set_config(config)
         self.Wp = torch.empty(self.plan.packed_size(0), dtype=torch.uint8, device="cuda")
-        self.Xp = torch.empty(self.plan.packed_size(1), dtype=torch.uint8, device="cuda")
+        # interleaved X: the GEMM reads the resident samples themselves
+        self.Xp = (self.Xd if lay == "interleaved" else
+                   torch.empty(self.plan.packed_size(1), dtype=torch.uint8, device="cuda"))
         ydt = torch.int32 if w["mode"] == "1bit" else torch.float32
         self.Y = torch.empty((B, M, N, 2), dtype=ydt, device="cuda")
         self.weights_ms = None
@@ -438,7 +469,8 @@ class GpuWorkload:
             self.plan.expand_1bit(0, self.Wp)
 
     def pack(self):
-        self.plan.transpose_pack(1, self.Xd, self.Xp, self.src_type)
+        if self.layout != "interleaved":     # interleaved X needs no pack
+            self.plan.transpose_pack(1, self.Xd, self.Xp, self.src_type)
 
     def prep(self):
         if self.fp4():
@@ -462,11 +494,17 @@ class GpuWorkload:
         self.gemm()
 
     def gemm_bytes(self):
-        if self.fp4():
-            # the E2M1 planes the GEMM reads: W (Wr, Wi) and X (-Xi, Xr, Xi), 16 bytes per word
-            w, kw = self.w, self.plan.Kw
-            return (w["w_batches"] * 2 * w["M"] + w["B"] * 3 * w["N"]) * kw * 16 + self.Y.numel() * 4
+        """Algorithmic bytes of the GEMM: its operands in the method's own
+        encoding (packed FP16 / FP8 / TF32 planes or the interleaved samples;
+        for 1-bit the packed sign bits, 2 bits per complex value) read once,
+        and Y written once."""
         return self.plan.packed_size(0) + self.plan.packed_size(1) + self.Y.numel() * 4
+
+    def fp4_plane_bytes(self):
+        """Bytes the 4-bit 1-bit GEMM actually reads: its E2M1 planes (W: Wr,
+        Wi; X: -Xi, Xr, Xi; 16 bytes per word of bits) and Y."""
+        w, kw = self.w, self.plan.Kw
+        return (w["w_batches"] * 2 * w["M"] + w["B"] * 3 * w["N"]) * kw * 16 + self.Y.numel() * 4
 
     def parity(self, npts=128):
         """Sampled outputs against the oracle, which derives everything
@@ -538,188 +576,12 @@ class GpuWorkload:
         return out
 
 
-def main():
-    args = parse_args()
-    if args.gpus != 1:
-        # every product fits one GB300; the library and this benchmark are one-GPU only
-        sys.exit(f"bench.py: --gpus {args.gpus} is not supported: this benchmark runs on one GPU")
-    w = workload(args)
-    if args.impl == "reference":
-        reference_arm(args, w)
-        return
-
-    import numpy as np
-    import torch
-
-    import paper_2505_03269_gb300 as tcbf
-    from paper_2505_03269_gb300 import build as tcbf_build
-
-    local = 0
-    torch.cuda.set_device(local)
-    tcbf_build.build()
-    tcbf.load()
-
-    def barrier():
-        torch.cuda.synchronize()
-
-    gw = GpuWorkload(w, local, args.config)
-    plan = gw.plan
-    gw.prepare_weights()
-    stream = torch.cuda.current_stream()
-    warmup = max(args.warmup, 3)
-    for _ in range(warmup):
-        gw.step()
-    barrier()
-    assert plan.last_device_error() == 0
-
-    def timed(nsteps, sample_clocks=False):
-        """nsteps steps with events around each kernel on the launch stream:
-        pack, then (4-bit 1-bit path) the expansion of X, then the GEMM."""
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nsteps)]
-        sampler = ClockSampler(local) if sample_clocks else None
-        if sampler:
-            sampler.start()
-        barrier()
-        for i in range(nsteps):
-            ev[i][0].record(stream)
-            gw.pack()
-            ev[i][1].record(stream)
-            gw.prep()
-            ev[i][2].record(stream)
-            gw.gemm()
-            ev[i][3].record(stream)
-        barrier()
-        clk = sampler.stop() if sampler else None
-        total = ev[0][0].elapsed_time(ev[-1][3])
-        timed.prep_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
-        return (total, statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
-                statistics.mean(e[2].elapsed_time(e[3]) for e in ev), clk)
-
-    # ---- the fixed default configuration against the autotuned one
-    tuning = None
-    if args.config is None:
-        d_total, _, d_gemm, _ = timed(max(3, args.steps // 4))
-        default_name = plan.config_name(plan.get_config())
-        from paper_2505_03269_gb300 import tuner
-        entry = tuner.tune(plan, gw.Wp, gw.Xp, gw.Y, reps=3, store=False)
-        tuning = {"default": {"config": default_name, "gemm_ms": d_gemm},
-                  "tuned": {"config": entry["name"]}, "ms_per_config": entry["ms"],
-                  "how": "every configuration's whole beamform call (4-bit 1-bit path: "
-                         "both expansions and the GEMM), timed round-robin"}
-        gw.prepare_weights()
-        for _ in range(2):
-            gw.step()
-
-    # ---- timed region: K steps (tuned configuration), clocks sampled
-    total_ms, pack_ms, gemm_ms, clocks = timed(args.steps, sample_clocks=True)
-    status = plan.last_device_error()
-    ms_per_step = total_ms / args.steps
-    value = tops(ops_per_step(w), ms_per_step)
-    if tuning is not None:
-        tuning["tuned"]["gemm_ms"] = gemm_ms
-        tuning["speedup_gemm"] = tuning["default"]["gemm_ms"] / gemm_ms
-
-    # ---- the same step replayed as one captured CUDA graph
-    plan.graph_capture(gw.Xd, gw.Xp, gw.Wp, gw.Y, gw.src_type)
-    plan.graph_launch()
-    barrier()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    for _ in range(args.steps):
-        plan.graph_launch()
-    g1.record(stream)
-    barrier()
-    graph_ms = g0.elapsed_time(g1) / args.steps
-
-    parity = gw.parity()
-
-    # ---- energy efficiency (Sec. IV: useful TeraOps/s over the GPU's mean power while the
-    # kernels run): the step, then the GEMM alone, each looped for about a second and a
-    # half with the board power sampled by nvidia-smi every 100 ms
-    energy = None
-    if not args.no_energy:
-        def power_loop(unit, unit_ms):
-            n = max(3, int(1500.0 / max(unit_ms, 1e-3)))
-            sampler = ClockSampler(local)
-            sampler.start()
-            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            p0.record(stream)
-            for _ in range(n):
-                unit()
-            p1.record(stream)
-            torch.cuda.synchronize()
-            clk = sampler.stop()
-            ms = p0.elapsed_time(p1) / n
-            tops = ops_per_step(w) / (ms * 1e-3) / 1e12
-            pw = clk["power_w_median"] if clk else None
-            return {"tops": tops, "ms": ms, "iterations": n,
-                    "power_w_median": pw, "samples": clk["samples"] if clk else 0,
-                    "sm_mhz": clk["sm_mhz"] if clk else None,
-                    "reasons": clk["reasons"] if clk else None,
-                    "tops_per_joule": tops / pw if pw else None}
-        energy = {"step": power_loop(gw.step, ms_per_step),
-                  "gemm": power_loop(gw.gemm, gemm_ms),
-                  "unit": "TeraOps/J",
-                  "how": "useful TeraOps/s of a ~1.5 s loop divided by the median board power "
-                         "nvidia-smi reports during it (every 100 ms); a sustained rate under "
-                         "the board's power limit, below the short timed region's"}
-        barrier()
-
-    # ---- end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        Xhost = torch.from_numpy(gw.Xh).pin_memory()
-        Yhost = torch.empty(gw.Y.shape, dtype=gw.Y.dtype, pin_memory=True)
-        src_type = 1 if gw.Xh.dtype == np.float32 else 0
-
-        def e2e_step():
-            gw.plan.beamform_host(Xhost, gw.Wp, Yhost, chunk=args.e2e_chunk, src_type=src_type,
-                                  stream=stream)
-        e2e_step()
-        barrier()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        b.record(stream)
-        barrier()
-        # the host link's own device-to-host rate (one plain copy of up to 4 GiB of Y),
-        # the floor the step's Y copy-out cannot beat
-        nl = min(gw.Y.numel(), 1 << 30)
-        ysrc, ydst = gw.Y.view(-1)[:nl], Yhost.view(-1)[:nl]
-        ydst.copy_(ysrc, non_blocking=True)
-        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0.record(stream)
-        ydst.copy_(ysrc, non_blocking=True)
-        l1.record(stream)
-        torch.cuda.synchronize()
-        link_gbs = nl * 4 / (l0.elapsed_time(l1) * 1e-3) / 1e9
-        te_ms = a.elapsed_time(b) / args.e2e_steps
-        e2e = {"value": tops(ops_per_step(w), te_ms), "unit": UNIT,
-               "h2d_bytes_per_step": int(gw.Xh.nbytes), "d2h_bytes_per_step": int(gw.Y.numel() * 4),
-               "ms_per_step": te_ms,
-               "how": "tcbf_beamform_host on pinned host X and Y: "
-                      + ("ranges of W rows of the one product (X in and packed once), "
-                         "beamform of one range overlapped with the device-to-host copy of "
-                         "the previous on separate streams" if w["B"] == 1 else
-                         "chunks of batches, host-to-device copy, pack + beamform and "
-                         "device-to-host copy of neighbouring chunks overlapped on separate "
-                         "streams"),
-               "chunk": ("about M / 4 rows, whole waves of 128-row tiles" if w["B"] == 1
-                         else args.e2e_chunk or "auto (about batch / 16)"),
-               "d2h_link_gbs": link_gbs,
-               "d2h_floor_ms": gw.Y.numel() * 4 / link_gbs / 1e6,
-               "frac_of_d2h_floor": gw.Y.numel() * 4 / link_gbs / 1e6 / te_ms,
-               # the larger of the two limits: the device-resident step and the Y copy-out
-               "floor_ms": max(ms_per_step, gw.Y.numel() * 4 / link_gbs / 1e6),
-               "frac_of_floor": max(ms_per_step, gw.Y.numel() * 4 / link_gbs / 1e6) / te_ms}
-        del Xhost, Yhost
-
-    # ---- roofline of the dominant kernel (the GEMM)
-    peaks = load_peaks()
-    gbytes = gw.gemm_bytes()
-    pack_bytes = gw.Xh.nbytes + plan.packed_size(1)
+def roofline_of(gw, peaks, gemm_ms):
+    """Roofline of the step's dominant kernel (the GEMM): bound, achieved,
+    peak, fraction, with the algorithmic bytes / flops it is measured on."""
+    w = gw.w
     ops = ops_per_step(w)
+    gbytes = gw.gemm_bytes()
     mma_factor = 1.0
     if gw.fp4():
         tensor_peak = peaks["bf16_tflops"] * FP4_OVER_BF16
@@ -744,7 +606,8 @@ def main():
     else:
         tensor_peak = peaks["bf16_tflops"]
         peak_note = "FP16 tensor peak = measured bf16 burst (same dense rate)"
-        kname = "cgemm_stacked_kernel" if w.get("stacked") else "cgemm_f16_kernel"
+        kname = {"stacked": "cgemm_stacked_pair_kernel", "interleaved": "cgemm_ix_kernel"}.get(
+            gw.layout, "cgemm_tc_kernel")
     ai = mma_factor * ops / gbytes
     ridge = tensor_peak * 1e12 / (peaks["hbm_gbs"] * 1e9)
     gemm_tops = mma_factor * ops / (gemm_ms * 1e-3) / 1e12
@@ -755,20 +618,280 @@ def main():
     else:
         roof = {"bound": "tensor", "achieved": gemm_tops, "peak": tensor_peak,
                 "unit": "TFLOP/s", "frac": gemm_tops / tensor_peak}
+    roof.update({"kernel": kname, "algorithmic_bytes": gbytes, "peak_source": peaks["source"],
+                 "tensor_peak_note": peak_note,
+                 "ceiling_tops": min(tensor_peak, ai * peaks["hbm_gbs"] / 1e3),
+                 "algorithmic_flops_per_useful_op": mma_factor,
+                 "gemm_tops": gemm_tops, "gemm_frac_of_tensor_peak": gemm_tops / tensor_peak})
+    if gw.fp4():
+        fb = gw.fp4_plane_bytes()
+        roof["kernel_plane_bytes"] = fb
+        roof["kernel_plane_gbs"] = fb / (gemm_ms * 1e-3) / 1e9
+        roof["algorithmic_bytes_note"] = ("packed sign bits of W and X (2 bits per complex "
+                                          "value) + int32 Y; the E2M1 planes the kernel reads "
+                                          "are an intermediate of this design (kernel_plane_bytes)")
+    return roof
+
+
+class Stepper:
+    """Timed steps of one GpuWorkload: events around each kernel on the
+    launch stream (pack, the 4-bit path's expansion of X, the GEMM)."""
+
+    def __init__(self, gw):
+        import torch
+        self.gw = gw
+        self.stream = torch.cuda.current_stream()
+
+    def run(self, nsteps, sample_clocks=False):
+        import torch
+        gw, stream = self.gw, self.stream
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nsteps)]
+        sampler = ClockSampler(0) if sample_clocks else None
+        if sampler:
+            sampler.start()
+        torch.cuda.synchronize()
+        for i in range(nsteps):
+            ev[i][0].record(stream)
+            gw.pack()
+            ev[i][1].record(stream)
+            gw.prep()
+            ev[i][2].record(stream)
+            gw.gemm()
+            ev[i][3].record(stream)
+        torch.cuda.synchronize()
+        clk = sampler.stop() if sampler else None
+        return {"total_ms": ev[0][0].elapsed_time(ev[-1][3]),
+                "pack_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                "prep_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in ev),
+                "gemm_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in ev),
+                "clocks": clk}
+
+
+def measure_sub(name, w, args, peaks):
+    """A configured workload as a sub-record: default configuration,
+    args.sub_steps timed steps, roofline, clocks and sampled parity."""
+    import torch
+    gw = GpuWorkload(w, 0, None)
+    try:
+        gw.prepare_weights()
+        st = Stepper(gw)
+        for _ in range(3):
+            gw.step()
+        torch.cuda.synchronize()
+        r = st.run(args.sub_steps, sample_clocks=True)
+        status = gw.plan.last_device_error()
+        ms = r["total_ms"] / args.sub_steps
+        out = {"workload": w["desc"], "batch": w["B"], "M": w["M"], "N": w["N"], "K": w["K"],
+               "value": tops(ops_per_step(w), ms), "unit": UNIT, "ms_per_step": ms,
+               "steps": args.sub_steps,
+               "dtype": ("e2m1" if gw.fp4() else
+                         {"1bit": "u1", "fp8split": "e4m3x2", "fp8": "e4m3"}.get(w["mode"], "f16")),
+               "kernel_config": gw.plan.config_name(gw.plan.get_config()),
+               "kernels": {"gemm_ms": r["gemm_ms"], "pack_ms": r["pack_ms"],
+                           "expand_x_ms": r["prep_ms"] if gw.fp4() else None,
+                           "gemm_useful_tops": tops(ops_per_step(w), r["gemm_ms"])},
+               "roofline": roofline_of(gw, peaks, r["gemm_ms"]),
+               "clocks": r["clocks"], "device_status": status,
+               "parity_sampled": gw.parity(64 if w["mode"] != "1bit" else 128)}
+        if is_fp8(w):
+            out["error_vs_fp64"] = {"rel_err": out["parity_sampled"]["rel_err"],
+                                    "note": "sampled outputs against the exact product of the "
+                                            "FP16 inputs (FP64 oracle)"}
+        return out
+    finally:
+        gw.plan.close()
+        del gw
+        torch.cuda.empty_cache()
+
+
+def measure_serving(args):
+    """Configured serving stream: the continuous-batching server against the
+    one-request-per-launch FP16 baseline at offered loads 0.8 and 0.95 of
+    the baseline's capacity."""
+    from paper_2505_03269_gb300 import serve
+    t0 = time.perf_counter()
+    r = serve.measure(n_requests=args.serving_requests, loads=(0.8, 0.95))
+    r["seconds"] = time.perf_counter() - t0
+    r["p99_ms_at_0.95"] = r["loads"][-1]["continuous_batching"]["p99_ms"]
+    r["p50_ms_at_0.95"] = r["loads"][-1]["continuous_batching"]["p50_ms"]
+    return r
+
+
+def main():
+    args = parse_args()
+    if args.gpus != 1:
+        # every product fits one GB300; the library and this benchmark are one-GPU only
+        sys.exit(f"bench.py: --gpus {args.gpus} is not supported: this benchmark runs on one GPU")
+    w = workload(args)
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2505_03269_gb300 as tcbf
+    from paper_2505_03269_gb300 import build as tcbf_build
+
+    torch.cuda.set_device(0)
+    tcbf_build.build()
+    tcbf.load()
+    peaks = load_peaks()
+
+    gw = GpuWorkload(w, 0, args.config)
+    plan = gw.plan
+    gw.prepare_weights()
+    stream = torch.cuda.current_stream()
+    st = Stepper(gw)
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
+        gw.step()
+    torch.cuda.synchronize()
+    assert plan.last_device_error() == 0
+
+    # ---- the fixed default configuration against the autotuned one
+    tuning = None
+    if args.config is None:
+        d = st.run(max(3, args.steps // 4))
+        default_name = plan.config_name(plan.get_config())
+        from paper_2505_03269_gb300 import tuner
+        entry = tuner.tune(plan, gw.Wp, gw.Xp, gw.Y, reps=3, store=False)
+        tuning = {"default": {"config": default_name, "gemm_ms": d["gemm_ms"]},
+                  "tuned": {"config": entry["name"]}, "ms_per_config": entry["ms"],
+                  "how": "every configuration's whole beamform call (4-bit 1-bit path: "
+                         "both expansions and the GEMM), timed round-robin"}
+        gw.prepare_weights()
+        for _ in range(2):
+            gw.step()
+
+    # ---- timed region: K steps (tuned configuration), clocks sampled
+    r = st.run(args.steps, sample_clocks=True)
+    total_ms, pack_ms, gemm_ms, clocks = r["total_ms"], r["pack_ms"], r["gemm_ms"], r["clocks"]
+    status = plan.last_device_error()
+    ms_per_step = total_ms / args.steps
+    value = tops(ops_per_step(w), ms_per_step)
+    if tuning is not None:
+        tuning["tuned"]["gemm_ms"] = gemm_ms
+        tuning["speedup_gemm"] = tuning["default"]["gemm_ms"] / gemm_ms
+
+    # ---- the same step replayed as one captured CUDA graph
+    plan.graph_capture(gw.Xd if gw.layout != "interleaved" else None, gw.Xp, gw.Wp, gw.Y,
+                       gw.src_type)
+    plan.graph_launch()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        plan.graph_launch()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / args.steps
+
+    parity = gw.parity()
+
+    # ---- energy efficiency (Sec. IV: useful TeraOps/s over the GPU's mean power while the
+    # kernels run): the step, then the GEMM alone, each looped for about a second and a
+    # half with the board power sampled by nvidia-smi every 100 ms
+    energy = None
+    if not args.no_energy:
+        def power_loop(unit, unit_ms):
+            n = max(3, int(1500.0 / max(unit_ms, 1e-3)))
+            sampler = ClockSampler(0)
+            sampler.start()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for _ in range(n):
+                unit()
+            p1.record(stream)
+            torch.cuda.synchronize()
+            clk = sampler.stop()
+            ms = p0.elapsed_time(p1) / n
+            t = tops(ops_per_step(w), ms)
+            pw = clk["power_w_median"] if clk else None
+            return {"tops": t, "ms": ms, "iterations": n,
+                    "power_w_median": pw, "samples": clk["samples"] if clk else 0,
+                    "sm_mhz": clk["sm_mhz"] if clk else None,
+                    "reasons": clk["reasons"] if clk else None,
+                    "tops_per_joule": t / pw if pw else None}
+        energy = {"step": power_loop(gw.step, ms_per_step),
+                  "gemm": power_loop(gw.gemm, gemm_ms),
+                  "unit": "TeraOps/J",
+                  "how": "useful TeraOps/s of a ~1.5 s loop divided by the median board power "
+                         "nvidia-smi reports during it (every 100 ms); a sustained rate under "
+                         "the board's power limit, below the short timed region's"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xhost = torch.from_numpy(gw.Xh).pin_memory()
+        Yhost = torch.empty(gw.Y.shape, dtype=gw.Y.dtype, pin_memory=True)
+        src_type = 1 if gw.Xh.dtype == np.float32 else 0
+
+        def e2e_step():
+            gw.plan.beamform_host(Xhost, gw.Wp, Yhost, chunk=args.e2e_chunk, src_type=src_type,
+                                  stream=stream)
+        e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        # the host link's own device-to-host rate (one plain copy of up to 4 GiB of Y),
+        # the floor the step's Y copy-out cannot beat
+        nl = min(gw.Y.numel(), 1 << 30)
+        ysrc, ydst = gw.Y.view(-1)[:nl], Yhost.view(-1)[:nl]
+        ydst.copy_(ysrc, non_blocking=True)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        ydst.copy_(ysrc, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        link_gbs = nl * 4 / (l0.elapsed_time(l1) * 1e-3) / 1e9
+        te_ms = a.elapsed_time(b) / args.e2e_steps
+        floor_ms = gw.Y.numel() * 4 / link_gbs / 1e6
+        e2e = {"value": tops(ops_per_step(w), te_ms), "unit": UNIT,
+               "h2d_bytes_per_step": int(gw.Xh.nbytes), "d2h_bytes_per_step": int(gw.Y.numel() * 4),
+               "ms_per_step": te_ms,
+               "how": "tcbf_beamform_host on pinned host X and Y: "
+                      + ("ranges of W rows of the one product (X in and packed once), "
+                         "beamform of one range overlapped with the device-to-host copy of "
+                         "the previous on separate streams" if w["B"] == 1 else
+                         "chunks of batches, host-to-device copy, "
+                         + ("beamform of the copied samples as they lie" if gw.layout == "interleaved"
+                            else "pack + beamform")
+                         + " and device-to-host copy of neighbouring chunks overlapped on "
+                           "separate streams"),
+               "chunk": ("about M / 4 rows, whole waves of 128-row tiles" if w["B"] == 1
+                         else args.e2e_chunk or "auto (about batch / 16)"),
+               "d2h_link_gbs": link_gbs, "d2h_floor_ms": floor_ms,
+               "frac_of_d2h_floor": floor_ms / te_ms,
+               # the larger of the two limits: the device-resident step and the Y copy-out
+               "floor_ms": max(ms_per_step, floor_ms),
+               "frac_of_floor": max(ms_per_step, floor_ms) / te_ms}
+        del Xhost, Yhost
+
+    # ---- roofline of the dominant kernel (the GEMM)
+    roof = roofline_of(gw, peaks, gemm_ms)
+    kname = roof["kernel"]
     fp4_micro = None
     if gw.fp4():
         # the 4-bit rate measured on chip by the library's microbenchmark
         # (kind::mxf4, operands in shared memory), beside the nominal-ratio peak
         from paper_2505_03269_gb300 import peaks as tcbf_peaks
-        fp4_micro = tcbf_peaks.measure(7, local)
+        fp4_micro = tcbf_peaks.measure(7, 0)
     full_size = args.batches is None and args.m_rows is None
     traffic_key = f"{args.workload}/{w['mode']}" if full_size else None
-    roof.update({"traffic": recorded_traffic(kname, traffic_key,
-                                             plan.config_name(plan.get_config())),
-                 "kernel": kname, "algorithmic_bytes": gbytes,
-                 "peak_source": peaks["source"], "tensor_peak_note": peak_note,
-                 "ceiling_tops": min(tensor_peak, ai * peaks["hbm_gbs"] / 1e3),
-                 "algorithmic_flops_per_useful_op": mma_factor})
+    roof["traffic"] = recorded_traffic(kname, traffic_key, plan.config_name(plan.get_config()))
+    gemm_tops = roof["gemm_tops"]
+    pack_bytes = gw.Xh.nbytes + plan.packed_size(1)
+    ops = ops_per_step(w)
+    step_desc = ("transpose_pack(X) + expand_1bit(X) + beamform_1bit_expanded "
+                 "(weights expanded once, resident)" if gw.fp4() else
+                 "beamform_fp16 reading the resident interleaved samples (no transpose/pack "
+                 "pass; weights resident)" if gw.layout == "interleaved" else
+                 "transpose_pack(X) + beamform (weights resident)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -778,43 +901,89 @@ def main():
                       w["mode"], "f16")),
         "data": "synthetic",
         "config": {"workload": w["desc"], "batch": w["B"], "M": w["M"], "N": w["N"], "K": w["K"],
-                   "w_batches": w["w_batches"],
-                   "step": ("transpose_pack(X) + expand_1bit(X) + beamform_1bit_expanded "
-                            "(weights expanded once, resident)" if gw.fp4() else
-                            "transpose_pack(X) + beamform (weights resident)"),
+                   "w_batches": w["w_batches"], "step": step_desc, "x_layout": gw.layout,
                    "l2": "inputs larger than L2 (X %.2f GB, Y %.1f GB per step)"
                          % (gw.Xh.nbytes / 1e9, gw.Y.numel() * 4 / 1e9),
                    "kernel_config": plan.config_name(plan.get_config()),
                    "parallelism": "one GPU"},
-        # kernels per step: pack(X) + GEMM; split-FP8 packs X in three kernels
-        # (column maxima, pack, exponents) after a memset; the 4-bit 1-bit
-        # path adds the expansion of X
-        "gpu_launches": (4 if is_fp8(w) else 3 if gw.fp4() else 2) * args.steps,
+        # kernels per step: the GEMM, plus pack(X) unless X is read interleaved;
+        # split-FP8 packs X in three kernels (column maxima, pack, exponents)
+        # after a memset; the 4-bit 1-bit path adds the expansion of X
+        "gpu_launches": ((4 if is_fp8(w) else 3 if gw.fp4() else
+                          1 if gw.layout == "interleaved" else 2) * args.steps),
         "roofline": roof,
-        "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms, "weights_ms_once": gw.weights_ms,
-                    "expand_x_ms": timed.prep_ms if gw.fp4() else None,
+        "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms if gw.layout != "interleaved" else 0.0,
+                    "weights_ms_once": gw.weights_ms,
+                    "expand_x_ms": r["prep_ms"] if gw.fp4() else None,
                     "gemm_useful_tops": ops / (gemm_ms * 1e-3) / 1e12,
-                    "gemm_tops": gemm_tops, "gemm_frac_of_tensor_peak": gemm_tops / tensor_peak,
+                    "gemm_tops": gemm_tops, "gemm_frac_of_tensor_peak": roof["gemm_frac_of_tensor_peak"],
                     "fp4_microbench_tops": fp4_micro,
                     "gemm_frac_of_fp4_microbench": gemm_tops / fp4_micro if fp4_micro else None,
-                    "gemm_gbs": gemm_gbs, "gemm_ai_ops_per_byte": ai,
-                    "pack_gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
-                    "pack_frac_of_hbm": pack_bytes / (pack_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+                    "gemm_gbs": gw.gemm_bytes() / (gemm_ms * 1e-3) / 1e9,
+                    "gemm_ai_ops_per_byte": ops / gw.gemm_bytes()},
         "clocks": clocks,
         "autotune": tuning,
-        "graph_step": {"ms_per_step": graph_ms,
-                       "value": tops(ops, graph_ms),
-                       "how": "tcbf_graph_capture of pack + beamform, replayed K times (4-bit 1-bit "
+        "graph_step": {"ms_per_step": graph_ms, "value": tops(ops, graph_ms),
+                       "how": "tcbf_graph_capture of the step, replayed K times (4-bit 1-bit "
                               "path: the captured call also expands W)"},
         "device_status": status,
         "parity_sampled": parity,
         "e2e": e2e,
         "energy": energy,
     }
+    if gw.layout != "interleaved" and not gw.fp4() and w["mode"] != "1bit":
+        line["kernels"]["pack_gbs"] = pack_bytes / (pack_ms * 1e-3) / 1e9
+        line["kernels"]["pack_frac_of_hbm"] = line["kernels"]["pack_gbs"] / peaks["hbm_gbs"]
+    Xh_keep = gw.Xh
+    plan.close()
+    del gw, plan, st
+    torch.cuda.empty_cache()
+
+    # ---- the planar path of the same workload: transpose/pack X + planar GEMM
+    if w.get("layout") == "interleaved" and args.config is None:
+        wp = dict(w, layout="planar")
+        gp = GpuWorkload(wp, 0, None, xh=Xh_keep)
+        try:
+            for _ in range(3):
+                gp.step()
+            torch.cuda.synchronize()
+            from paper_2505_03269_gb300 import tuner
+            tuner.tune(gp.plan, gp.Wp, gp.Xp, gp.Y, reps=2, store=False)
+            rp = Stepper(gp).run(max(5, args.steps // 2))
+            pms = rp["total_ms"] / max(5, args.steps // 2)
+            line["planar_step"] = {
+                "ms_per_step": pms, "value": tops(ops, pms), "pack_ms": rp["pack_ms"],
+                "gemm_ms": rp["gemm_ms"],
+                "pack_gbs": (gp.Xh.nbytes + gp.plan.packed_size(1)) / (rp["pack_ms"] * 1e-3) / 1e9,
+                "kernel_config": gp.plan.config_name(gp.plan.get_config()),
+                "how": "the same block through tcbf_transpose_pack into planes and the tuned "
+                       "planar four-MMA GEMM, for comparison with the interleaved step"}
+        finally:
+            gp.plan.close()
+            del gp
+            torch.cuda.empty_cache()
+
+    # ---- the other configured workloads, as sub-records
+    if not args.no_subs and args.workload == "radio" and args.batches is None:
+        subs = {}
+        for key, wname, mode in (("ultrasound_fp16", "ultrasound", None),
+                                 ("ultrasound_fp8split", "ultrasound", "fp8split"),
+                                 ("ultrasound_fp8", "ultrasound", "fp8"),
+                                 ("onebit", "onebit", None)):
+            sa = argparse.Namespace(**vars(args))
+            sa.workload, sa.mode, sa.layout, sa.batches, sa.m_rows = wname, mode, None, None, None
+            try:
+                subs[key] = measure_sub(key, workload(sa), args, peaks)
+            except Exception as exc:      # reported, never silently dropped
+                subs[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        try:
+            subs["serving"] = measure_serving(args)
+        except Exception as exc:
+            subs["serving"] = {"error": f"{type(exc).__name__}: {exc}"}
+        line["workloads"] = subs
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     print(json.dumps(line), flush=True)
-    plan.close()
 
 
 if __name__ == "__main__":

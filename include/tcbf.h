@@ -92,7 +92,22 @@ typedef enum {
      * TCBF_FLAG_FP8_FOUR_PRODUCTS adds Wl Xl on the hi+lo layout.  The paper
      * names 8-bit floats only as future work (Sec. VI). */
     TCBF_FLAG_FP8_HI_ONLY = 2u,
-    TCBF_FLAG_FP8_FOUR_PRODUCTS = 4u
+    TCBF_FLAG_FP8_FOUR_PRODUCTS = 4u,
+    /* FP16 only: the beamform call reads X in the caller's interleaved
+     * complex layout, [batch][K][N] binary16 (the source layout of
+     * tcbf_transpose_pack), with no transpose/pack pass (the paper's
+     * future-work item of skipping the transpose, Sec. VI).  The GEMM loads
+     * X as an MN-major tensor-core operand, issues one real MMA per K step
+     * that forms Wr X and Wi X side by side, and combines them into Re and
+     * Im in FP32 before the store.  Packed W is the FP16 layout below.  For
+     * such a plan tcbf_packed_size(1) is batch*K*N*4 bytes and
+     * tcbf_transpose_pack(which = 1) only copies (FP16 source) or rounds
+     * (FP32 source) into that layout.  Needs N % 4 == 0 for the fused
+     * kernel; other N, and uneven batch rows, run the transpose/pack into
+     * plan-owned planes and the planar kernel inside the beamform call.
+     * Not combined with TCBF_FLAG_STACKED_X.  Selects the interleaved-X
+     * kernel configurations. */
+    TCBF_FLAG_INTERLEAVED_X = 8u
 } tcbf_flag;
 
 /*
@@ -103,7 +118,9 @@ typedef enum {
  *   FP16 W : [w_batches][2][M][Kp] binary16, Kp = K rounded up to 8, zero pad
  *   FP16 X : [batch][2][N][Kp]     binary16 (X transposed: samples are rows);
  *            with TCBF_FLAG_STACKED_X [batch][3][N][Kp], planes -Xi, Xr, Xi
- *            (-Xi: the Xi plane with every sign bit flipped, its pad -0.0)
+ *            (-Xi: the Xi plane with every sign bit flipped, its pad -0.0);
+ *            with TCBF_FLAG_INTERLEAVED_X [batch][K][N] interleaved complex
+ *            binary16 (not transposed, no padding)
  *   1-bit W: [w_batches][2][M][Kw] uint32,   Kw = 4 * ceil(K / 128)
  *   1-bit X: [batch][2][N][Kw]     uint32
  * Plane 0 is the real part, plane 1 the imaginary part.  1-bit element k

@@ -23,6 +23,7 @@ SRC_CF16, SRC_CF32 = 0, 1
 FLAG_STACKED_X = 1
 FLAG_FP8_HI_ONLY = 2
 FLAG_FP8_FOUR_PRODUCTS = 4
+FLAG_INTERLEAVED_X = 8
 
 # every symbol include/tcbf.h declares
 EXPORTED = [

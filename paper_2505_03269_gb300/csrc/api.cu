@@ -69,6 +69,8 @@ size_t packed_bytes(const tcbf_plan_s &pl, int which) {
     const int64_t rows = which == 0 ? p.M : p.N;
     switch (p.mode) {
         case TCBF_MODE_FP16:
+            if (which == 1 && interleaved_x(pl))   // the caller's layout: [batch][K][N] complex
+                return static_cast<size_t>(nb * p.K * p.N * 4);
             return static_cast<size_t>(nb * (which == 0 ? 2 : x_planes(pl)) * rows * pl.Kp * 2);
         case TCBF_MODE_1BIT:
             return static_cast<size_t>(nb * 2 * rows * pl.Kw * 4);
@@ -79,6 +81,12 @@ size_t packed_bytes(const tcbf_plan_s &pl, int which) {
         default:
             return 0;
     }
+}
+
+// Packed X planes of an interleaved-X plan that the fused kernel cannot take.
+cudaError_t alloc_ix_planes(tcbf_plan_s &pl) {
+    const size_t bytes = static_cast<size_t>(pl.p.batch * 2 * pl.p.N * pl.Kp * 2);
+    return cudaMalloc(&pl.ix_planes, bytes);
 }
 
 }  // namespace
@@ -125,8 +133,10 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
         q.mode != TCBF_MODE_TF32)
         return TCBF_ERR_INVALID_ARG;
     const uint32_t fp8_flags = TCBF_FLAG_FP8_HI_ONLY | TCBF_FLAG_FP8_FOUR_PRODUCTS;
-    if ((q.flags & ~(uint32_t(TCBF_FLAG_STACKED_X) | fp8_flags)) != 0) return TCBF_ERR_INVALID_ARG;
-    if ((q.flags & TCBF_FLAG_STACKED_X) && q.mode != TCBF_MODE_FP16) return TCBF_ERR_INVALID_ARG;
+    const uint32_t f16_flags = TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X;
+    if ((q.flags & ~(f16_flags | fp8_flags)) != 0) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & f16_flags) && q.mode != TCBF_MODE_FP16) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & f16_flags) == f16_flags) return TCBF_ERR_INVALID_ARG;   // one or the other
     if ((q.flags & fp8_flags) && q.mode != TCBF_MODE_FP8SPLIT) return TCBF_ERR_INVALID_ARG;
     if ((q.flags & fp8_flags) == fp8_flags) return TCBF_ERR_INVALID_ARG;   // one or the other
     if (q.M > kMaxDim || q.N > kMaxDim || q.K > kMaxDim || q.batch > 65535)
@@ -166,6 +176,16 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
             delete pl;
             return TCBF_ERR_CUDA;
         }
+        // interleaved X that the fused kernel cannot read (rows of 4N bytes
+        // not 16-byte multiples): the beamform call packs into these planes
+        if (interleaved_x(*pl) && !ix_fused_ok(*pl)) {
+            const cudaError_t e = alloc_ix_planes(*pl);
+            if (e != cudaSuccess) {
+                cudaFree(pl->status);
+                delete pl;
+                return e == cudaErrorMemoryAllocation ? TCBF_ERR_OOM : TCBF_ERR_CUDA;
+            }
+        }
         // 1-bit: the 4-bit tensor path by default when its planes fit
         if (q.mode == TCBF_MODE_1BIT && gemm_1bit_fp4_reserve(*pl) == cudaSuccess &&
             gemm_1bit_fp4_usable(*pl))
@@ -183,6 +203,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_destroy(tcbf_plan_t plan) {
         if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
         if (plan->m_prefix) cudaFree(plan->m_prefix);
         if (plan->status) cudaFree(plan->status);
+        if (plan->ix_planes) cudaFree(plan->ix_planes);
         gemm_1bit_fp4_release(*plan);
     }
     delete plan;
@@ -212,8 +233,9 @@ TCBF_EXPORT tcbf_status tcbf_transpose_pack(tcbf_plan_t plan, int which, int src
     cudaError_t e;
     switch (plan->p.mode) {
         case TCBF_MODE_FP16:
-            e = which == 0 ? launch_pack_f16_w(*plan, src_type, src, dst, s)
-                           : launch_pack_f16_x(*plan, src_type, src, dst, s);
+            e = which == 0            ? launch_pack_f16_w(*plan, src_type, src, dst, s)
+                : interleaved_x(*plan) ? launch_copy_x_cf16(*plan, src_type, src, dst, s)
+                                       : launch_pack_f16_x(*plan, src_type, src, dst, s);
             break;
         case TCBF_MODE_1BIT:
             e = which == 0 ? launch_pack_bits_w(*plan, src_type, src, dst, s)
@@ -292,7 +314,8 @@ TCBF_EXPORT tcbf_status tcbf_debug_drop_fill(tcbf_plan_t plan, int64_t fill) {
         return TCBF_ERR_UNSUPPORTED;
     // one-SM, non-cluster tile configurations only (the cluster and pair
     // kernels share barriers across CTAs)
-    if ((plan->p.flags & TCBF_FLAG_STACKED_X) || plan->config < 0 || plan->config > 5)
+    if ((plan->p.flags & (TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X)) || plan->config < 0 ||
+        plan->config > 5)
         return TCBF_ERR_UNSUPPORTED;
     if (fill > 0x7fffffff) return TCBF_ERR_INVALID_ARG;
     plan->debug_drop_fill = fill;
@@ -364,9 +387,10 @@ TCBF_EXPORT tcbf_status tcbf_last_device_error(tcbf_plan_t plan) {
 
 TCBF_EXPORT tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count) {
     if (!plan || !count) return TCBF_ERR_INVALID_ARG;
-    *count = plan->p.mode == TCBF_MODE_1BIT              ? gemm_1bit_num_configs()
-             : (plan->p.flags & TCBF_FLAG_STACKED_X) ? gemm_f16_stacked_num_configs()
-                                                     : gemm_f16_num_configs();
+    *count = plan->p.mode == TCBF_MODE_1BIT                  ? gemm_1bit_num_configs()
+             : (plan->p.flags & TCBF_FLAG_STACKED_X)     ? gemm_f16_stacked_num_configs()
+             : (plan->p.flags & TCBF_FLAG_INTERLEAVED_X) ? gemm_f16_ix_num_configs()
+                                                         : gemm_f16_num_configs();
     return TCBF_OK;
 }
 
@@ -381,7 +405,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
     int n = 0;
     tcbf_plan_num_configs(plan, &n);
     if (config < 0 || config >= n) return TCBF_ERR_INVALID_ARG;
-    if (plan->p.mode != TCBF_MODE_1BIT && !(plan->p.flags & TCBF_FLAG_STACKED_X) &&
+    if (plan->p.mode != TCBF_MODE_1BIT &&
+        !(plan->p.flags & (TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X)) &&
         !gemm_f16_config_valid(config, plan->p.K))
         return TCBF_ERR_INVALID_ARG;
     if (plan->p.mode == TCBF_MODE_1BIT && gemm_1bit_config_fp4(config)) {
@@ -398,6 +423,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
 TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
     if (!plan) return "invalid";
     if (plan->p.flags & TCBF_FLAG_STACKED_X) return gemm_f16_stacked_config_name(config);
+    if (plan->p.flags & TCBF_FLAG_INTERLEAVED_X) return gemm_f16_ix_config_name(config);
     if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
     if (plan->p.mode == TCBF_MODE_1BIT) return gemm_1bit_config_name(config);
     if (plan->p.mode == TCBF_MODE_TF32) return gemm_tf32_config_name(config);
@@ -422,7 +448,9 @@ cudaError_t launch_beamform(const tcbf_plan_s &pl, const void *Wp, const void *X
 
 cudaError_t launch_pack_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
                           cudaStream_t s) {
-    if (pl.p.mode == TCBF_MODE_FP16) return launch_pack_f16_x(pl, src_type, src, dst, s);
+    if (pl.p.mode == TCBF_MODE_FP16)
+        return interleaved_x(pl) ? launch_copy_x_cf16(pl, src_type, src, dst, s)
+                                 : launch_pack_f16_x(pl, src_type, src, dst, s);
     if (pl.p.mode == TCBF_MODE_1BIT) return launch_pack_bits_x(pl, src_type, src, dst, s);
     if (pl.p.mode == TCBF_MODE_TF32) return launch_pack_tf32_x(pl, src_type, src, dst, s);
     return launch_pack_split8_x(pl, src_type, src, dst, s);
@@ -433,6 +461,7 @@ bool config_ok(const tcbf_plan_s &pl, int c) {
         return c >= 0 && c < gemm_1bit_num_configs() &&
                (!gemm_1bit_config_fp4(c) || gemm_1bit_fp4_usable(pl));
     if (pl.p.flags & TCBF_FLAG_STACKED_X) return c >= 0 && c < gemm_f16_stacked_num_configs();
+    if (pl.p.flags & TCBF_FLAG_INTERLEAVED_X) return c >= 0 && c < gemm_f16_ix_num_configs();
     return gemm_f16_config_valid(c, pl.p.K);
 }
 
@@ -474,6 +503,9 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_batch_rows(tcbf_plan_t plan, const int64_t
         cudaMemcpy(plan->m_prefix, host, sizeof(int) * (B + 1), cudaMemcpyHostToDevice);
     delete[] host;
     if (e != cudaSuccess) return TCBF_ERR_CUDA;
+    // interleaved X with uneven rows runs pack + planar kernel through plan-owned planes
+    if (interleaved_x(*plan) && !plan->ix_planes && alloc_ix_planes(*plan) != cudaSuccess)
+        return TCBF_ERR_OOM;
     plan->m_tiles_sum = acc;
     return TCBF_OK;
 }

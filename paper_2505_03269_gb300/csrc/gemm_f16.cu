@@ -1190,6 +1190,15 @@ cudaError_t launch_gemm_split8(const tcbf_plan_s &pl, const void *Wp, const void
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s) {
     if (pl.p.flags & TCBF_FLAG_STACKED_X) return launch_gemm_f16_stacked(pl, Wp, Xp, Y, s);
+    if (interleaved_x(pl)) {
+        if (ix_fused_ok(pl)) return launch_gemm_f16_ix(pl, Wp, Xp, Y, s);
+        // shapes the fused kernel cannot take: transpose/pack into the plan's
+        // planes, then the planar four-MMA kernel
+        if (!pl.ix_planes) return cudaErrorInvalidValue;
+        const cudaError_t e = launch_pack_f16_x(pl, TCBF_SRC_CF16, Xp, pl.ix_planes, s);
+        if (e != cudaSuccess) return e;
+        return kConfigs[0].fn(pl, Wp, pl.ix_planes, Y, s, kConfigs[0].raster);
+    }
     const int c = (pl.config >= 0 && pl.config < gemm_f16_num_configs()) ? pl.config : 0;
     return kConfigs[c].fn(pl, Wp, Xp, Y, s, kConfigs[c].raster);
 }

@@ -109,7 +109,9 @@ int64_t src_bytes(int src_type) { return src_type == TCBF_SRC_CF16 ? 4 : 8; }
 int64_t packed_x_bytes(const tcbf_plan_s &pl, int64_t nb) {
     const int64_t N = pl.p.N;
     switch (pl.p.mode) {
-        case TCBF_MODE_FP16: return nb * x_planes(pl) * N * pl.Kp * 2;
+        case TCBF_MODE_FP16:
+            if (interleaved_x(pl)) return nb * pl.p.K * N * 4;   // the caller's layout, FP16
+            return nb * x_planes(pl) * N * pl.Kp * 2;
         case TCBF_MODE_1BIT: return nb * 2 * N * pl.Kw * 4;
         case TCBF_MODE_TF32: return nb * 2 * N * pl.Kp * 4;
         default: return nb * 2 * N * pl.Kb2 + nb * N * 4;
@@ -138,8 +140,15 @@ int64_t packed_w_batch_bytes(const tcbf_plan_s &pl) {
     }
 }
 
+// Interleaved-X FP16 plans read an FP16 source as it was copied in: no pack.
+bool reads_source(const tcbf_plan_s &pl, int src_type) {
+    return pl.p.mode == TCBF_MODE_FP16 && interleaved_x(pl) && src_type == TCBF_SRC_CF16;
+}
+
 cudaError_t pack_x(const tcbf_plan_s &pl, int src_type, const void *src, void *dst, cudaStream_t s) {
-    if (pl.p.mode == TCBF_MODE_FP16) return launch_pack_f16_x(pl, src_type, src, dst, s);
+    if (pl.p.mode == TCBF_MODE_FP16)
+        return interleaved_x(pl) ? launch_copy_x_cf16(pl, src_type, src, dst, s)
+                                 : launch_pack_f16_x(pl, src_type, src, dst, s);
     if (pl.p.mode == TCBF_MODE_1BIT) return launch_pack_bits_x(pl, src_type, src, dst, s);
     if (pl.p.mode == TCBF_MODE_TF32) return launch_pack_tf32_x(pl, src_type, src, dst, s);
     return launch_pack_split8_x(pl, src_type, src, dst, s);
@@ -259,7 +268,9 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
                                 hp.h2d);
         if (e == cudaSuccess) e = cudaEventRecord(hp.ev_h2d[0], hp.h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.comp, hp.ev_h2d[0], 0);
-        if (e == cudaSuccess) e = pack_x(*plan, src_type, hp.xsrc[0], hp.xp[0], hp.comp);
+        const void *xg = reads_source(*plan, src_type) ? hp.xsrc[0] : hp.xp[0];
+        if (e == cudaSuccess && xg == hp.xp[0])
+            e = pack_x(*plan, src_type, hp.xsrc[0], hp.xp[0], hp.comp);
         int64_t c = 0;
         for (int64_t m0 = 0; m0 < p.M && e == cudaSuccess; m0 += rows, ++c) {
             const int s = static_cast<int>(c % kSlots);
@@ -275,7 +286,7 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
             // the slot's Y is free once its last copy-out ran
             for (int i = 0; i < kD2h && e == cudaSuccess && hp.used[s]; ++i)
                 e = cudaStreamWaitEvent(hp.comp, hp.ev_d2h[s][i], 0);
-            if (e == cudaSuccess) e = beamform(sub, w_sub, hp.xp[0], hp.yd[s], hp.comp);
+            if (e == cudaSuccess) e = beamform(sub, w_sub, xg, hp.yd[s], hp.comp);
             if (e == cudaSuccess) e = cudaEventRecord(hp.ev_comp[s], hp.comp);
             const int64_t ybytes = nr * p.N * 8;
             int64_t off = 0;
@@ -317,8 +328,10 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
             if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.comp, hp.ev_h2d[s], 0);
             for (int i = 0; i < kD2h && e == cudaSuccess && hp.used[s]; ++i)
                 e = cudaStreamWaitEvent(hp.comp, hp.ev_d2h[s][i], 0);
-            if (e == cudaSuccess) e = pack_x(sub, src_type, hp.xsrc[s], hp.xp[s], hp.comp);
-            if (e == cudaSuccess) e = beamform(sub, w_sub, hp.xp[s], hp.yd[s], hp.comp);
+            const void *xg = reads_source(sub, src_type) ? hp.xsrc[s] : hp.xp[s];
+            if (e == cudaSuccess && xg == hp.xp[s])
+                e = pack_x(sub, src_type, hp.xsrc[s], hp.xp[s], hp.comp);
+            if (e == cudaSuccess) e = beamform(sub, w_sub, xg, hp.yd[s], hp.comp);
             if (e == cudaSuccess) e = cudaEventRecord(hp.ev_comp[s], hp.comp);
             // copy out, split by batches (or by bytes for one batch) over the d2h streams
             const int64_t ybytes = nb * y_per_b;

@@ -81,6 +81,26 @@ int grid_for(int64_t work, int threads, int num_sms) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, int64_t(num_sms) * 16)));
 }
 
+// ------------------------------------------------ interleaved FP16 samples
+// X of plans that keep the caller's interleaved layout: FP32 values rounded
+// to FP16 in place of the layout, four complex values per thread.
+__global__ void round_cf32_to_cf16_kernel(const float4 *__restrict__ src, uint2 *__restrict__ dst,
+                                          int64_t n2) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n2;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 v = __ldg(src + i);     // two complex values
+        uint2 o;
+        o.x = CF32::to_word(v.x, v.y);
+        o.y = CF32::to_word(v.z, v.w);
+        dst[i] = o;
+    }
+}
+
+__global__ void round_tail_kernel(const float2 *__restrict__ src, uint32_t *__restrict__ dst) {
+    const float2 v = *src;
+    *dst = CF32::to_word(v.x, v.y);
+}
+
 // ------------------------------------------------------------ FP16 planes
 // W: one thread writes 8 consecutive K elements (16 bytes) of both planes.
 template <typename S>
@@ -445,6 +465,25 @@ cudaError_t launch_pack_f16_x(const tcbf_plan_s &pl, int src_type, const void *s
             vec ? run(pack_f16_x_kernel<CF32, true, 3>) : run(pack_f16_x_kernel<CF32, false, 3>);
         else
             vec ? run(pack_f16_x_kernel<CF32, true, 2>) : run(pack_f16_x_kernel<CF32, false, 2>);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_x_cf16(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s) {
+    const int64_t values = pl.p.batch * pl.p.K * pl.p.N;
+    if (src_type == TCBF_SRC_CF16) {
+        if (src == dst) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, static_cast<size_t>(values * 4), cudaMemcpyDeviceToDevice, s);
+    }
+    // values is even when N is; an odd count leaves one value for a second pass
+    const int64_t n2 = values / 2;
+    if (n2 > 0)
+        round_cf32_to_cf16_kernel<<<grid_for(n2, 256, pl.num_sms), 256, 0, s>>>(
+            static_cast<const float4 *>(src), static_cast<uint2 *>(dst), n2);
+    if (values & 1) {
+        const float2 *tail = static_cast<const float2 *>(src) + (values - 1);
+        round_tail_kernel<<<1, 1, 0, s>>>(tail, static_cast<uint32_t *>(dst) + (values - 1));
     }
     return cudaGetLastError();
 }

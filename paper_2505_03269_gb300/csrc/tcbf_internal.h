@@ -39,6 +39,10 @@ struct tcbf_plan_s {
     // when such a configuration is first set (nullptr until then)
     void *fp4_buf = nullptr;
     size_t fp4_bytes = 0;
+    // plans with TCBF_FLAG_INTERLEAVED_X that the fused kernel cannot take
+    // (N % 4 != 0, uneven batch rows): packed X planes the beamform call
+    // packs into before running the planar kernel (nullptr otherwise)
+    void *ix_planes = nullptr;
 };
 
 namespace tcbf {
@@ -95,6 +99,22 @@ int gemm_f16_stacked_num_configs();
 const char *gemm_f16_stacked_config_name(int config);
 cudaError_t launch_gemm_f16_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                                     cudaStream_t s);
+
+// FP16 GEMM on interleaved complex X (plans with TCBF_FLAG_INTERLEAVED_X).
+int gemm_f16_ix_num_configs();
+const char *gemm_f16_ix_config_name(int config);
+cudaError_t launch_gemm_f16_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, float *Y,
+                               cudaStream_t s);
+inline bool interleaved_x(const tcbf_plan_s &pl) {
+    return (pl.p.flags & TCBF_FLAG_INTERLEAVED_X) != 0;
+}
+// Whether the fused interleaved-X kernel can take the plan (else it runs
+// pack + planar kernel through ix_planes).
+inline bool ix_fused_ok(const tcbf_plan_s &pl) { return pl.p.N % 4 == 0 && !pl.m_prefix; }
+// X of an interleaved plan from a source of either type: an FP16 source is
+// copied (nothing when src == dst), an FP32 source rounded to FP16.
+cudaError_t launch_copy_x_cf16(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                               cudaStream_t s);
 
 // Split-FP8 products per 32-K step: 1 (plain FP8), 3 (hi+lo split) or 4.
 inline int split_products(const tcbf_plan_s &pl) {

@@ -22,13 +22,17 @@ def empty_bytes(n: int) -> torch.Tensor:
     return torch.empty(max(n, 16), dtype=torch.uint8, device="cuda")
 
 
-def run_fp16(W: np.ndarray, X: np.ndarray, config: int | None = None, src_type=tcbf.SRC_CF16):
-    """W [Bw,M,K,2], X [B,K,N,2] (fp16 or fp32 pairs) -> Y complex128 [B,M,N] via the GPU."""
+def run_fp16(W: np.ndarray, X: np.ndarray, config: int | None = None, src_type=tcbf.SRC_CF16,
+             flags: int = 0, rows=None):
+    """W [Bw,M,K,2], X [B,K,N,2] (fp16 or fp32 pairs) -> Y complex128 [B,M,N] via the GPU.
+    flags: plan flags (e.g. FLAG_INTERLEAVED_X); rows: per-batch beam counts."""
     Bw, M, K, _ = W.shape
     B, _, N, _ = X.shape
-    with tcbf.Plan(B, M, N, K, tcbf.MODE_FP16, w_batches=Bw) as plan:
+    with tcbf.Plan(B, M, N, K, tcbf.MODE_FP16, w_batches=Bw, flags=flags) as plan:
         if config is not None:
             plan.set_config(config)
+        if rows is not None:
+            plan.set_batch_rows(rows)
         Wd, Xd = dev(W), dev(X)
         Wp = empty_bytes(plan.packed_size(0))
         Xp = empty_bytes(plan.packed_size(1))

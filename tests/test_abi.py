@@ -57,7 +57,8 @@ def _create(lib, **kw):
 
 @pytest.mark.parametrize("bad", [dict(M=0), dict(N=0), dict(K=0), dict(batch=0),
                                  dict(batch=4, w_batches=3), dict(mode=7), dict(flags=2),
-                                 dict(flags=1, mode=1), dict(flags=1, mode=2), dict(flags=8),
+                                 dict(flags=1, mode=1), dict(flags=1, mode=2), dict(flags=16),
+                                 dict(flags=8, mode=1), dict(flags=8, mode=2), dict(flags=9),
                                  dict(flags=4, mode=0), dict(flags=2, mode=2),
                                  dict(flags=6, mode=1), dict(M=-5)])
 def test_plan_create_rejects_bad_shapes(lib, bad):

@@ -7,6 +7,8 @@ sampled outputs against the FP64 oracle.
   ultrasound block: 65536 voxels x 16384 (128 elements x 128 bins) x 256
                     frames, near-field model matrix from geometry, stacked
                     sample planes
+  both blocks also through the interleaved-X kernel (the GEMM reads X as
+  it lies, no transpose/pack pass)
 
 The oracle computes its own weights from the same geometry (FP64, rounded
 once to FP16) and the complex sum at each sampled output.  Bar: relative
@@ -83,6 +85,26 @@ def test_full_size_radio_block_sampled():
     Xh = ti.radio_x(1, B, K, N)
     # the default tile shape and the cluster-multicast shape the autotuner picks most often
     for err in _run_block(B, Bw, M, N, K, geom, Xh, configs=(0, 6)):
+        assert err <= TOL
+
+
+def test_full_size_radio_block_interleaved_x_sampled():
+    """The radio block through the interleaved-X kernel (no pack of X): both
+    tile configurations, sampled against the oracle."""
+    from paper_2505_03269_gb300 import FLAG_INTERLEAVED_X
+    B, Bw, M, K, N = 512, 256, 1024, 288, 4096
+    geom = ti.radio_geometry(0, M, K, Bw)
+    Xh = ti.radio_x(1, B, K, N)
+    for err in _run_block(B, Bw, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X, configs=(0, 1, 2)):
+        assert err <= TOL
+
+
+def test_full_size_ultrasound_interleaved_x_sampled():
+    from paper_2505_03269_gb300 import FLAG_INTERLEAVED_X
+    M, K, N = 65536, 16384, 256
+    geom = ti.ultrasound_geometry()
+    Xh = ti.ultrasound_frames(1, K, N)
+    for err in _run_block(1, 1, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X, configs=(0,)):
         assert err <= TOL
 
 
