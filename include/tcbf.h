@@ -284,7 +284,9 @@ tcbf_status tcbf_weights_from_geometry(tcbf_plan_t plan, const double *rx_pos,
  * Returns TCBF_OK, TCBF_ERR_TIMEOUT or TCBF_ERR_DEVICE. */
 tcbf_status tcbf_last_device_error(tcbf_plan_t plan);
 
-/* Test hook for the device-side failure path (every wait in the GEMM
+/* NOT PART OF THE BEAMFORMING API: test infrastructure shipped in the
+ * library so that the failure path can be exercised on a real GPU.
+ * Test hook for the device-side failure path (every wait in the GEMM
  * kernels gives up after 2 s and records it in the status word).  The next
  * tcbf_beamform_fp16 / tcbf_beamform_fp8split call on this plan launches
  * with the operand load number `fill` (0-based, in the first CTA's order of
@@ -324,7 +326,9 @@ const char *tcbf_status_string(tcbf_status s);
  * Returns TCBF_ERR_BUDGET (nothing launched) when batch*2*N*round_up(K,8)*2
  * bytes of packed samples exceed 64 MiB.  The first call on a device looks
  * up the array's device address and the device's properties; make that
- * first call before any stream capture.  Every call uses the same array and
+ * first call before any stream capture.  The lookup is repeated when the
+ * device's context has changed since (after a cudaDeviceReset by the
+ * caller), as the array then has a new address.  Every call uses the same array and
  * clears the status word it needs; the packed-sample region keeps the last
  * call's contents.  Calls whose work overlaps on the GPU (other streams, or
  * other host threads) race on the array and must be serialised by the caller.

@@ -1,6 +1,9 @@
 /*
  * tcbf_peak.h — on-chip peak microbenchmarks of the GB300 build.
  *
+ * NOT PART OF THE BEAMFORMING API: measurement infrastructure shipped in the
+ * library (the benchmark's roofline denominators and the 1-bit path choice).
+ *
  * Like the paper's tensor-core micro-benchmarks (Sec. III-A, Table I) they
  * keep operands on chip so memory bandwidth does not limit them; they supply
  * the per-precision peak denominators and the measurements behind the 1-bit

@@ -32,6 +32,7 @@ constexpr int kMaxDevices = 128;
 
 struct DeviceSetup {
     bool ready = false;
+    unsigned long long ctx_id = 0;      // context the address below belongs to (0: unknown)
     unsigned char *scratch = nullptr;   // device address of g_noalloc_scratch
     int num_sms = 0;
     bool sm103 = false;
@@ -39,12 +40,45 @@ struct DeviceSetup {
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mu;
 
-// Once per device, with that device current: the device address of the
-// static array (its host-side name is only a stand-in) and device facts.
+// Unique id of the current context (driver entry points fetched once), or 0
+// when it cannot be read.  A cudaDeviceReset by the caller gives the device
+// a new context in which the static array has a new address.
+unsigned long long current_ctx_id() {
+    typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+    typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Once per device and context, with that device current: the device address
+// of the static array (its host-side name is only a stand-in) and device
+// facts.  Repeated when the device's context has changed since (or its id
+// cannot be read).
 tcbf_status setup_device(int device, DeviceSetup &out) {
     std::lock_guard<std::mutex> lk(g_setup_mu);
     DeviceSetup &d = g_setup[device];
-    if (!d.ready) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!d.ready || ctx == 0 || ctx != d.ctx_id) {
         int major = 0, minor = 0, sms = 0;
         if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device) !=
                 cudaSuccess ||
@@ -58,6 +92,7 @@ tcbf_status setup_device(int device, DeviceSetup &out) {
         d.scratch = static_cast<unsigned char *>(p);
         d.num_sms = sms;
         d.sm103 = (major == 10 && minor == 3);
+        d.ctx_id = ctx;
         d.ready = true;
     }
     out = d;
@@ -119,9 +154,12 @@ TCBF_EXPORT tcbf_status tcbf_beamform_fp16_noalloc(const tcbf_problem *p, int de
         if (e != cudaSuccess) {
             st = TCBF_ERR_CUDA;
         } else if (check) {
+            // read the status word in order on the call's own stream (not the
+            // legacy default stream, which would also wait for unrelated work)
             uint32_t word = 0;
-            if (cudaStreamSynchronize(s) != cudaSuccess ||
-                cudaMemcpy(&word, pl.status, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess)
+            if (cudaMemcpyAsync(&word, pl.status, sizeof(word), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
                 st = TCBF_ERR_CUDA;
             else if (word != 0)
                 st = (word & 0xffu) ? TCBF_ERR_TIMEOUT : TCBF_ERR_DEVICE;

@@ -142,6 +142,16 @@ def test_default_configuration_is_the_4bit_path():
         assert plan.config_name(plan.get_config()).startswith("1bit->e2m1")
 
 
+def test_default_configuration_threshold_in_k():
+    """K <= 1024 starts on the 256 x 96 two-accumulator tiles (configuration
+    7), larger K on the 256 x 128 one-accumulator tiles (configuration 5)."""
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    with Plan(1, 256, 256, 1024, MODE_1BIT) as plan:
+        assert plan.get_config() == 7, plan.config_name(plan.get_config())
+    with Plan(1, 256, 256, 1025, MODE_1BIT) as plan:
+        assert plan.get_config() == 5, plan.config_name(plan.get_config())
+
+
 def test_expand_once_then_gemm_per_block():
     """W expanded once, then X blocks expanded and multiplied in turn: each
     block exact, and equal to the one-call path."""
