@@ -63,9 +63,11 @@ WORKLOADS = {
         desc="computational ultrasound FP16: 65536 voxels x 16384 (128 elements x 128 "
              "frequency bins) x 256 frames, near-field model matrix"),
     "onebit": dict(
-        mode="1bit", B=64, M=2048, N=8192, K=1024, w_batches=64, geometry=None,
+        mode="1bit", B=64, M=2048, N=8192, K=1024, w_batches=64, geometry="radio",
         desc="radio-astronomy 1-bit block: 64 channels x 2048 beams x 1024 receivers x "
-             "8192 samples, +-1+-i values, exact int32 output"),
+             "8192 samples, W = signs of the steering weights from geometry (110-190 MHz, "
+             "3 km disk, beams within 5 deg of zenith), X = signs of complex Gaussian "
+             "samples, +-1+-i values, exact int32 output"),
     # the paper's kernel-tuning shapes (Sec. IV, Table III), for comparison with its
     # TeraOps/s and TeraOps/J; the 1-bit one with K cut from 524288 so a step takes seconds
     "paper_fp16": dict(
@@ -269,8 +271,8 @@ def geometry_of(w):
     import tcbf_inputs as ti
     if w["geometry"] == "random":
         return None
-    if w["geometry"] == "radio":
-        return ti.radio_geometry(0, w["M"], w["K"], max(1, w["B"] // 2))
+    if w["geometry"] == "radio":     # one channel per weight batch
+        return ti.radio_geometry(0, w["M"], w["K"], w["w_batches"])
     if w["geometry"] == "ultrasound":
         g = ti.ultrasound_geometry()
         if w["M"] < len(g.targets):          # reduced profiling case: the first M voxels
@@ -304,7 +306,12 @@ def oracle_sample(w, seconds_target):
     import tcbf_inputs as ti
 
     if w["mode"] == "1bit":
-        Wb = onebit_weights(w)[:1]
+        if w["geometry"] == "radio":    # signs of the first channel's steering weights
+            geom = geometry_of(w)
+            wc = oracle.weights(geom.rx_pos, geom.targets, geom.freqs[:1], False, geom.c)
+            Wb = oracle.pack_signs_f64(wc, ti.words_per_row(w["K"]))
+        else:
+            Wb = onebit_weights(w)[:1]
         X = host_x(w) if w.get("x_phase") else ti.radio_x_batch(1, 0, w["K"], w["N"])[None]
         Xb = oracle.pack_signs(X, k_is_row=True, Kw=Wb.shape[-1])
 
@@ -436,7 +443,7 @@ class GpuWorkload:
         ydt = torch.int32 if w["mode"] == "1bit" else torch.float32
         self.Y = torch.empty((B, M, N, 2), dtype=ydt, device="cuda")
         self.weights_ms = None
-        if w["mode"] == "1bit":
+        if w["mode"] == "1bit" and w["geometry"] is None:
             self.Wbits = onebit_weights(w)
             self.Wp.copy_(torch.from_numpy(self.Wbits.view(np.uint8).ravel()).cuda())
         elif w["geometry"] == "random":
@@ -460,7 +467,8 @@ class GpuWorkload:
     def fp4(self):
         """1-bit plan on the 4-bit tensor path: W is expanded to E2M1 once
         (weights fixed over the block, as they are packed once on the FP16
-        path), and each step expands X before the GEMM."""
+        path), and each step packs X straight into its E2M1 planes
+        (tcbf_transpose_pack_expanded) before the GEMM."""
         return (self.w["mode"] == "1bit" and
                 self.plan.config_name(self.plan.get_config()).startswith("1bit->e2m1"))
 
@@ -469,12 +477,13 @@ class GpuWorkload:
             self.plan.expand_1bit(0, self.Wp)
 
     def pack(self):
-        if self.layout != "interleaved":     # interleaved X needs no pack
+        if self.fp4():                       # samples -> E2M1 planes in one pass
+            self.plan.transpose_pack_expanded(1, self.Xd, self.src_type)
+        elif self.layout != "interleaved":   # interleaved X needs no pack
             self.plan.transpose_pack(1, self.Xd, self.Xp, self.src_type)
 
     def prep(self):
-        if self.fp4():
-            self.plan.expand_1bit(1, self.Xp)
+        pass
 
     def gemm(self):
         if self.fp4():
@@ -517,17 +526,28 @@ class GpuWorkload:
         g = np.random.default_rng(123)
         if w["mode"] == "1bit":
             bad = 0
+            kw = self.plan.Kw
+            geom = getattr(self, "geom", None)
             for _ in range(4):
                 b = int(g.integers(B))
                 ms = np.sort(g.choice(M, 16, replace=False))
                 ns = np.sort(g.choice(N, 16, replace=False))
                 Xb = oracle.pack_signs(np.ascontiguousarray(self.Xh[b:b + 1][:, :, ns]),
-                                       k_is_row=True, Kw=self.Wbits.shape[-1])
+                                       k_is_row=True, Kw=kw)
                 bw = b // (B // Bw)
-                ref = oracle.bgemm(self.Wbits[bw:bw + 1][:, :, ms], Xb, K)[0]
+                if geom is None:
+                    Wsel = self.Wbits[bw:bw + 1][:, :, ms]
+                else:   # the oracle's own weights from the geometry, then their signs
+                    wc = oracle.weights(geom.rx_pos, geom.targets[ms], geom.freqs[bw:bw + 1],
+                                        geom.near_field, geom.c)
+                    Wsel = oracle.pack_signs_f64(wc, kw)
+                ref = oracle.bgemm(Wsel, Xb, K)[0]
                 got = self.Y[b][torch.from_numpy(ms).cuda()][:, torch.from_numpy(ns).cuda()]
                 bad += int(np.sum(got.cpu().numpy().astype(np.int64) != ref))
-            return {"points": 4 * 256, "mismatches": bad, "reference": "int64 oracle, exact"}
+            return {"points": 4 * 256, "mismatches": bad,
+                    "reference": "int64 oracle, exact" + (
+                        "; W signs from the oracle's own FP64 weights of the same geometry"
+                        if geom is not None else "")}
         pts = np.stack([g.integers(0, B, npts), g.integers(0, M, npts), g.integers(0, N, npts)], 1)
         ref = np.empty(npts, np.complex128)
         ref_split = np.empty(npts, np.complex128)
@@ -688,7 +708,8 @@ def measure_sub(name, w, args, peaks):
                          {"1bit": "u1", "fp8split": "e4m3x2", "fp8": "e4m3"}.get(w["mode"], "f16")),
                "kernel_config": gw.plan.config_name(gw.plan.get_config()),
                "kernels": {"gemm_ms": r["gemm_ms"], "pack_ms": r["pack_ms"],
-                           "expand_x_ms": r["prep_ms"] if gw.fp4() else None,
+                           "pack_note": ("X packed straight into the E2M1 planes" if gw.fp4()
+                                         else None),
                            "gemm_useful_tops": tops(ops_per_step(w), r["gemm_ms"])},
                "roofline": roofline_of(gw, peaks, r["gemm_ms"]),
                "clocks": r["clocks"], "device_status": status,
@@ -887,8 +908,8 @@ def main():
     gemm_tops = roof["gemm_tops"]
     pack_bytes = gw.Xh.nbytes + plan.packed_size(1)
     ops = ops_per_step(w)
-    step_desc = ("transpose_pack(X) + expand_1bit(X) + beamform_1bit_expanded "
-                 "(weights expanded once, resident)" if gw.fp4() else
+    step_desc = ("transpose_pack_expanded(X) (sign-quantised straight into E2M1 planes) + "
+                 "beamform_1bit_expanded (weights expanded once, resident)" if gw.fp4() else
                  "beamform_fp16 reading the resident interleaved samples (no transpose/pack "
                  "pass; weights resident)" if gw.layout == "interleaved" else
                  "transpose_pack(X) + beamform (weights resident)")
@@ -906,15 +927,15 @@ def main():
                          % (gw.Xh.nbytes / 1e9, gw.Y.numel() * 4 / 1e9),
                    "kernel_config": plan.config_name(plan.get_config()),
                    "parallelism": "one GPU"},
-        # kernels per step: the GEMM, plus pack(X) unless X is read interleaved;
-        # split-FP8 packs X in three kernels (column maxima, pack, exponents)
-        # after a memset; the 4-bit 1-bit path adds the expansion of X
-        "gpu_launches": ((4 if is_fp8(w) else 3 if gw.fp4() else
+        # kernels per step: the GEMM, plus pack(X) unless X is read interleaved
+        # (the 4-bit 1-bit path packs X straight into its E2M1 planes); split-FP8
+        # packs X in three kernels (column maxima, pack, exponents) after a memset
+        "gpu_launches": ((4 if is_fp8(w) else 2 if gw.fp4() else
                           1 if gw.layout == "interleaved" else 2) * args.steps),
         "roofline": roof,
         "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms if gw.layout != "interleaved" else 0.0,
                     "weights_ms_once": gw.weights_ms,
-                    "expand_x_ms": r["prep_ms"] if gw.fp4() else None,
+                    "pack_x_into_e2m1_ms": pack_ms if gw.fp4() else None,
                     "gemm_useful_tops": ops / (gemm_ms * 1e-3) / 1e12,
                     "gemm_tops": gemm_tops, "gemm_frac_of_tensor_peak": roof["gemm_frac_of_tensor_peak"],
                     "fp4_microbench_tops": fp4_micro,

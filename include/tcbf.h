@@ -261,6 +261,21 @@ tcbf_status tcbf_beamform_1bit(tcbf_plan_t plan, const uint32_t *Wbits, const ui
  */
 tcbf_status tcbf_expand_1bit(tcbf_plan_t plan, int which, const uint32_t *bits,
                              tcbf_stream_t stream);
+/*
+ * tcbf_transpose_pack_expanded: the transpose/pack of Sec. III for a 1-bit
+ * plan on the 4-bit tensor path, writing the plan's E2M1 planes straight
+ * from interleaved complex values (one pass, no packed bits):
+ *   which = 0: src is W, [w_batches][M][K] complex of type src_type;
+ *   which = 1: src is X, [batch][K][N] complex of type src_type.
+ * Each component is sign-quantised as by tcbf_transpose_pack (v >= 0 -> +1,
+ * so -0 -> +1; negative and NaN -> -1) and lands in the planes that
+ * tcbf_expand_1bit would write from the packed bits of the same values; the
+ * planes stay until the next pack or expansion of the same operand.  src
+ * DEVICE, 16-byte aligned.  Errors as for tcbf_expand_1bit, and
+ * TCBF_ERR_INVALID_ARG for a bad src_type.
+ */
+tcbf_status tcbf_transpose_pack_expanded(tcbf_plan_t plan, int which, int src_type,
+                                         const void *src, tcbf_stream_t stream);
 tcbf_status tcbf_beamform_1bit_expanded(tcbf_plan_t plan, int32_t *Y, tcbf_stream_t stream);
 
 /*

@@ -11,6 +11,7 @@ Functions and the passages they follow:
   cgemm_points(W, X, p)  Eq. 3 at chosen output points
   bgemm(Wb, Xb, K)       Eq. 3 over 1-bit values of Fig. 1, exact int64
   pack_signs(V, ...)     1-bit sign quantisation, Sec. III-D / Sec. V-A
+  pack_signs_f64(V, Kw)  the same quantisation of FP64 values (weights' signs)
   weights(geom)          w = A exp(-2 pi i f tau), Eq. 1-2
   half_to_double(h)      IEEE binary16 decoding (the FP16 storage format)
 """
@@ -165,6 +166,21 @@ def pack_signs(V: np.ndarray, k_is_row: bool, Kw: int) -> np.ndarray:
     Vc = np.ascontiguousarray(V).view(np.uint16)
     lib.oracle_pack_signs_f16(B, R, C, int(k_is_row), Kw, _ptr(Vc), _ptr(out))
     return out
+
+
+def pack_signs_f64(V: np.ndarray, Kw: int) -> np.ndarray:
+    """Sign-quantise complex FP64 values V [B, rows, K] (e.g. the steering
+    weights of ``weights``) into packed planes [B, 2, rows, Kw] without
+    rounding them to FP16 first: bit 1 iff the component is >= 0 (so -0.0
+    gives +1), element k in bit k % 32 of word k / 32, zero bits for k >= K
+    (Fig. 1; Sec. III-D)."""
+    V = np.asarray(V, np.complex128)
+    B, rows, K = V.shape
+    out = np.zeros((B, 2, rows, Kw * 32), np.uint8)
+    out[:, 0, :, :K] = V.real >= 0
+    out[:, 1, :, :K] = V.imag >= 0
+    packed = np.packbits(out, axis=-1, bitorder="little")          # 4 bytes per word
+    return np.ascontiguousarray(packed).view("<u4").reshape(B, 2, rows, Kw)
 
 
 TF32_MAX = (2.0 - 2.0 ** -10) * 2.0 ** 127

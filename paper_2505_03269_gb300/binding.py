@@ -34,7 +34,7 @@ EXPORTED = [
     "tcbf_plan_set_config", "tcbf_config_name", "tcbf_beamform_fp16_noalloc",
     "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
     "tcbf_beamform_host", "tcbf_debug_drop_fill", "tcbf_unpack_bits", "tcbf_beamform_tf32",
-    "tcbf_expand_1bit", "tcbf_beamform_1bit_expanded",
+    "tcbf_expand_1bit", "tcbf_beamform_1bit_expanded", "tcbf_transpose_pack_expanded",
 ]
 
 
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_beamform_1bit": [vp, vp, vp, vp, vp],
         "tcbf_expand_1bit": [vp, i32, vp, vp],
         "tcbf_beamform_1bit_expanded": [vp, vp, vp],
+        "tcbf_transpose_pack_expanded": [vp, i32, i32, vp, vp],
         "tcbf_weights_from_geometry": [vp, vp, vp, i32, vp, ctypes.c_double, vp, vp],
         "tcbf_last_device_error": [vp],
         "tcbf_debug_drop_fill": [vp, ctypes.c_int64],
@@ -204,6 +205,13 @@ class Plan:
         plan's E2M1 planes."""
         _check(self._lib.tcbf_expand_1bit(self.handle, int(which), _ptr(bits), _stream(stream)),
                "tcbf_expand_1bit")
+
+    def transpose_pack_expanded(self, which, src, src_type=SRC_CF16, stream=None):
+        """4-bit tensor path: sign-quantise interleaved complex W (0) or X (1)
+        straight into the plan's E2M1 planes (no packed bits)."""
+        _check(self._lib.tcbf_transpose_pack_expanded(self.handle, int(which), int(src_type),
+                                                      _ptr(src), _stream(stream)),
+               "tcbf_transpose_pack_expanded")
 
     def beamform_1bit_expanded(self, Y, stream=None):
         """4-bit tensor path: the GEMM on the planes last expanded."""

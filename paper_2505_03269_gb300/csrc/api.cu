@@ -344,6 +344,19 @@ TCBF_EXPORT tcbf_status tcbf_expand_1bit(tcbf_plan_t plan, int which, const uint
     return from_cuda(launch_expand_1bit_fp4(*plan, which, bits, static_cast<cudaStream_t>(stream)));
 }
 
+TCBF_EXPORT tcbf_status tcbf_transpose_pack_expanded(tcbf_plan_t plan, int which, int src_type,
+                                                     const void *src, tcbf_stream_t stream) {
+    if (!plan || !src || (which != 0 && which != 1)) return TCBF_ERR_INVALID_ARG;
+    if (src_type != TCBF_SRC_CF16 && src_type != TCBF_SRC_CF32) return TCBF_ERR_INVALID_ARG;
+    if (plan->p.mode != TCBF_MODE_1BIT || !aligned16(src)) return TCBF_ERR_INVALID_ARG;
+    if (!gemm_1bit_config_fp4(plan->config) || !gemm_1bit_fp4_usable(*plan))
+        return TCBF_ERR_UNSUPPORTED;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    return from_cuda(
+        launch_pack_1bit_fp4(*plan, which, src_type, src, static_cast<cudaStream_t>(stream)));
+}
+
 TCBF_EXPORT tcbf_status tcbf_beamform_1bit_expanded(tcbf_plan_t plan, int32_t *Y,
                                                     tcbf_stream_t stream) {
     if (!plan || !Y) return TCBF_ERR_INVALID_ARG;

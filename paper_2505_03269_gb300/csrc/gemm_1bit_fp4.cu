@@ -26,6 +26,8 @@
 // Tensor memory: the accumulators from column 0, the scale factors in the
 // columns above them up to 512 (from 256, or 384 for two 192-column
 // accumulators), every byte UE8M0 127, so any scale layout reads 1.0.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -101,6 +103,140 @@ __global__ void expand_x_fp4_kernel(const uint32_t *__restrict__ Xb, uint4 *__re
         Xq[((b * 3) * N + n) * Kw + w] = e2m1_word<true>(xi, valid);
         Xq[((b * 3 + 1) * N + n) * Kw + w] = e2m1_word<false>(xr, valid);
         Xq[((b * 3 + 2) * N + n) * Kw + w] = e2m1_word<false>(xi, valid);
+    }
+}
+
+// Sign of one source component as the 1-bit pack takes it: v >= 0 gives
+// +1 (so -0 gives +1), anything else (negative, NaN) -1.
+__device__ __forceinline__ uint32_t sign_of(float v) { return v >= 0.f ? 1u : 0u; }
+
+__device__ __forceinline__ void load_cf(const void *src, size_t i, bool f32, float &re, float &im) {
+    if (f32) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(src) + i);
+        re = v.x;
+        im = v.y;
+    } else {
+        const __half2 v = __ldg(reinterpret_cast<const __half2 *>(src) + i);
+        re = __low2float(v);
+        im = __high2float(v);
+    }
+}
+
+// Interleaved complex X [batch][K][N] -> E2M1 planes [batch][3][N][Kw x 16
+// bytes] (-Xi, Xr, Xi) in one pass, without the packed bits.  A block of
+// 256 threads takes 128 samples x 256 k (8 words): warp w reads the 32 rows
+// of word w, lane l samples n0 + 4l .. n0 + 4l + 3 (one 16-byte load of FP16
+// values per row when N % 4 == 0, so a warp reads 512 contiguous bytes of a
+// row; else one value at a time); the sign words go through shared memory,
+// and the block writes each sample's 8 words as 128 contiguous bytes per
+// plane.
+constexpr int kPackSamples = 128;
+constexpr int kPackWords = 8;
+
+template <bool F32, bool VEC>
+__global__ void __launch_bounds__(256) pack_x_fp4_kernel(const void *__restrict__ src,
+                                                         uint8_t *__restrict__ Xq, int K, int N,
+                                                         int Kw, int n_tiles, int w_tiles) {
+    __shared__ uint32_t bits[2][kPackSamples][kPackWords + 1];   // [re/im][sample][word]
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t b = blockIdx.y;
+    const size_t row = static_cast<size_t>(Kw) * 16;
+    for (int t = blockIdx.x; t < n_tiles * w_tiles; t += gridDim.x) {
+        const int n0 = (t % n_tiles) * kPackSamples;
+        const int w0 = (t / n_tiles) * kPackWords;
+        const int w = w0 + warp;                       // this warp's word
+        const int k0 = 32 * w;
+        const int kend = w < Kw ? max(0, min(32, K - k0)) : 0;
+        const int nl = n0 + 4 * lane;                  // this lane's first sample
+        uint32_t wr[4] = {0u, 0u, 0u, 0u}, wi[4] = {0u, 0u, 0u, 0u};
+        if (VEC && nl + 4 <= N) {
+#pragma unroll 4
+            for (int j = 0; j < kend; ++j) {
+                const size_t i = (static_cast<size_t>(b) * K + k0 + j) * N + nl;
+                float v[8];
+                if (F32) {
+                    const float4 p = __ldg(reinterpret_cast<const float4 *>(src) + i / 2);
+                    const float4 q = __ldg(reinterpret_cast<const float4 *>(src) + i / 2 + 1);
+                    v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+                    v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+                } else {
+                    const uint4 p = __ldg(reinterpret_cast<const uint4 *>(src) + i / 4);
+                    const uint32_t u[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const __half2 h = *reinterpret_cast<const __half2 *>(&u[q]);
+                        v[2 * q] = __low2float(h);
+                        v[2 * q + 1] = __high2float(h);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    wr[q] |= sign_of(v[2 * q]) << j;
+                    wi[q] |= sign_of(v[2 * q + 1]) << j;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (nl + q >= N) break;
+                for (int j = 0; j < kend; ++j) {
+                    float re, im;
+                    load_cf(src, (static_cast<size_t>(b) * K + k0 + j) * N + nl + q, F32, re, im);
+                    wr[q] |= sign_of(re) << j;
+                    wi[q] |= sign_of(im) << j;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            bits[0][4 * lane + q][warp] = wr[q];
+            bits[1][4 * lane + q][warp] = wi[q];
+        }
+        __syncthreads();
+        // 3 planes x 128 samples x 8 words of 16 bytes; 8 consecutive threads
+        // write one sample's 128 bytes of a plane
+        for (int c = threadIdx.x; c < 3 * kPackSamples * kPackWords; c += 256) {
+            const int plane = c / (kPackSamples * kPackWords);
+            const int sr = (c / kPackWords) % kPackSamples;
+            const int wd = c % kPackWords;
+            const int n = n0 + sr, ww = w0 + wd;
+            if (n >= N || ww >= Kw) continue;
+            const int valid = K - 32 * ww;
+            // planes -Xi (0), Xr (1), Xi (2)
+            const uint32_t v = bits[plane == 1 ? 0 : 1][sr][wd];
+            const uint4 q = plane == 0 ? e2m1_word<true>(v, valid) : e2m1_word<false>(v, valid);
+            *reinterpret_cast<uint4 *>(Xq + ((static_cast<size_t>(b) * 3 + plane) * N + n) * row +
+                                       16 * static_cast<size_t>(ww)) = q;
+        }
+        __syncthreads();
+    }
+}
+
+// Interleaved complex W [w_batches][M][K] -> E2M1 planes [w_batches][2][M]
+// [Kw x 16 bytes] (Wr, Wi): one warp per row and word, lane l reads k = 32 w
+// + l, a ballot forms each plane's word and four lanes write its 16 bytes.
+template <bool F32>
+__global__ void pack_w_fp4_kernel(const void *__restrict__ src, uint4 *__restrict__ Wq,
+                                  int64_t rows, int64_t M, int K, int Kw) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const int64_t total = rows * Kw;
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < total;
+         i += warps_total) {
+        const int64_t r = i / Kw;
+        const int w = static_cast<int>(i % Kw);
+        const int k = 32 * w + lane;
+        float re = -1.f, im = -1.f;
+        if (k < K) load_cf(src, static_cast<size_t>(r) * K + k, F32, re, im);
+        const uint32_t br = __ballot_sync(0xffffffffu, k < K && sign_of(re));
+        const uint32_t bi = __ballot_sync(0xffffffffu, k < K && sign_of(im));
+        const int64_t bw = r / M, m = r % M;
+        const int valid = K - 32 * w;
+        if (lane < 2) {
+            const uint4 v = e2m1_word<false>(lane == 0 ? br : bi, valid);
+            Wq[(static_cast<size_t>(bw * 2 + lane) * M + m) * Kw + w] = v;
+        }
     }
 }
 
@@ -400,10 +536,11 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
                         }
                 }
             }
-            // this warp is done with the accumulator: release it on the even CTA
+            // this warp is done with the accumulator (its values are in registers):
+            // release it on the even CTA at CTA scope
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(tempty0_lead + 8 * acc);
+            if (lane == 0) mbar_arrive_remote(tempty0_lead + 8 * acc);
         }
         if (args.tma_store && lane == 0) bulk_wait<0>();
         __syncwarp();
@@ -451,6 +588,43 @@ cudaError_t launch_expand(const tcbf_plan_s &pl, int which, const uint32_t *bits
         expand_x_fp4_kernel<<<expand_grid(p.batch * p.N * pl.Kw, pl.num_sms), 256, 0, s>>>(
             bits, reinterpret_cast<uint4 *>(Wq + fp4_w_bytes(pl)), p.batch, p.N,
             static_cast<int>(pl.Kw), static_cast<int>(p.K));
+    }
+    return cudaGetLastError();
+}
+
+// Interleaved complex W (which 0) or X (which 1) of type src_type straight
+// into the plan's E2M1 planes.
+cudaError_t launch_pack_fp4(const tcbf_plan_s &pl, int which, int src_type, const void *src,
+                            cudaStream_t s) {
+    const tcbf_problem &p = pl.p;
+    uint8_t *Wq = static_cast<uint8_t *>(pl.fp4_buf);
+    const bool f32 = src_type == TCBF_SRC_CF32;
+    if (which == 0) {
+        const int64_t rows = p.w_batches * p.M;
+        const int grid = expand_grid(rows * pl.Kw * 32, pl.num_sms);
+        auto *dst = reinterpret_cast<uint4 *>(Wq);
+        if (f32)
+            pack_w_fp4_kernel<true><<<grid, 256, 0, s>>>(src, dst, rows, p.M, int(p.K), int(pl.Kw));
+        else
+            pack_w_fp4_kernel<false><<<grid, 256, 0, s>>>(src, dst, rows, p.M, int(p.K), int(pl.Kw));
+    } else {
+        const int n_tiles = static_cast<int>(ceil_div(p.N, kPackSamples));
+        const int w_tiles = static_cast<int>(ceil_div(pl.Kw, kPackWords));
+        // blocks per batch: enough for every SM to hold several across the batches
+        const int64_t per_b = int64_t(n_tiles) * w_tiles;
+        const int bx = static_cast<int>(std::max<int64_t>(
+            1, std::min<int64_t>(per_b, ceil_div(int64_t(pl.num_sms) * 16, p.batch))));
+        dim3 grid(bx, static_cast<unsigned>(p.batch));
+        uint8_t *dst = Wq + fp4_w_bytes(pl);
+        // 16-byte loads need every row of X to start 16-byte aligned (N % 4 == 0)
+        const bool vec = p.N % 4 == 0;
+        auto run = [&](auto kern) {
+            kern<<<grid, 256, 0, s>>>(src, dst, int(p.K), int(p.N), int(pl.Kw), n_tiles, w_tiles);
+        };
+        if (f32)
+            vec ? run(pack_x_fp4_kernel<true, true>) : run(pack_x_fp4_kernel<true, false>);
+        else
+            vec ? run(pack_x_fp4_kernel<false, true>) : run(pack_x_fp4_kernel<false, false>);
     }
     return cudaGetLastError();
 }
@@ -576,6 +750,12 @@ cudaError_t launch_expand_1bit_fp4(const tcbf_plan_s &pl, int which, const uint3
                                    cudaStream_t s) {
     if (!gemm_1bit_fp4_usable(pl)) return cudaErrorNotSupported;
     return launch_expand(pl, which, bits, s);
+}
+
+cudaError_t launch_pack_1bit_fp4(const tcbf_plan_s &pl, int which, int src_type, const void *src,
+                                 cudaStream_t s) {
+    if (!gemm_1bit_fp4_usable(pl)) return cudaErrorNotSupported;
+    return launch_pack_fp4(pl, which, src_type, src, s);
 }
 
 cudaError_t launch_gemm_1bit_fp4_expanded(const tcbf_plan_s &pl, int32_t *Y, cudaStream_t s,

@@ -840,10 +840,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
-                // this warp is done with the accumulator: release it on the even CTA
+                // this warp is done with the accumulator (its values are in registers):
+                // release it on the even CTA at CTA scope
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(tempty0_lead + 8 * acc);
+                if (lane == 0) mbar_arrive_remote(tempty0_lead + 8 * acc);
             }
         }
         if (args.tma_store && lane == 0) bulk_wait<0>();

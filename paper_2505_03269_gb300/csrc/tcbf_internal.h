@@ -165,6 +165,10 @@ cudaError_t launch_expand_1bit_fp4(const tcbf_plan_s &pl, int which, const uint3
                                    cudaStream_t s);
 cudaError_t launch_gemm_1bit_fp4_expanded(const tcbf_plan_s &pl, int32_t *Y, cudaStream_t s,
                                           int variant);
+// Sign quantisation of interleaved complex W (which 0) or X (which 1)
+// straight into the E2M1 planes, without the packed bits.
+cudaError_t launch_pack_1bit_fp4(const tcbf_plan_s &pl, int which, int src_type, const void *src,
+                                 cudaStream_t s);
 // Variant (0-2) of a 4-bit configuration of the 1-bit table, -1 otherwise.
 int gemm_1bit_fp4_variant(int config);
 // The configuration a 1-bit plan starts with when it can take the 4-bit path.

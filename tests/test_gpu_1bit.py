@@ -198,3 +198,69 @@ def test_expand_needs_the_4bit_path():
         plan.set_batch_rows([3])          # uneven rows: not on the 4-bit path
         with pytest.raises(TcbfError, match="UNSUPPORTED"):
             plan.expand_1bit(0, dev(Wb))
+
+
+def test_radio_signs_from_geometry_exact():
+    """The configured 1-bit radio recipe on a reduced block: W = signs of the
+    steering weights computed by the GPU's weights kernel on a 1-bit plan,
+    X = signs of complex Gaussian samples packed by the GPU; the oracle takes
+    the signs of its own FP64 weights of the same geometry and its own sign
+    packing of the same samples.  Exact int32 output on every element."""
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, Plan
+    B, M, K, N = 4, 256, 1024, 512
+    geom = ti.radio_geometry(seed=0, n_beams=M, n_stations=K, n_channels=B)
+    X = ti.radio_x(1, B, K, N)
+    with Plan(B, M, N, K, MODE_1BIT) as plan:
+        Wp = torch.empty(plan.packed_size(0), dtype=torch.uint8, device="cuda")
+        Xp = torch.empty(plan.packed_size(1), dtype=torch.uint8, device="cuda")
+        plan.weights_from_geometry(dev(geom.rx_pos), dev(geom.targets), geom.near_field,
+                                   dev(geom.freqs), geom.c, Wp)
+        plan.transpose_pack(1, dev(X), Xp)
+        Y = torch.full((B, M, N, 2), -7, dtype=torch.int32, device="cuda")
+        plan.beamform_1bit(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        got = Y.cpu().numpy().astype(np.int64)
+        kw = plan.Kw
+        wbits_gpu = Wp.cpu().numpy().view(np.uint32).reshape(B, 2, M, kw)
+    wc = oracle.weights(geom.rx_pos, geom.targets, geom.freqs, geom.near_field, geom.c)
+    Wb = oracle.pack_signs_f64(wc, kw)
+    assert np.array_equal(wbits_gpu, Wb)
+    Xb = oracle.pack_signs(X, k_is_row=True, Kw=kw)
+    assert np.array_equal(got, oracle.bgemm(Wb, Xb, K))
+
+
+@pytest.mark.parametrize("config", [5, 6, 7])
+@pytest.mark.parametrize("B,M,N,K,f32", [(2, 300, 200, 333, False), (3, 130, 70, 64, False),
+                                         (1, 257, 129, 1025, True), (2, 64, 33, 31, True)])
+def test_pack_straight_into_e2m1_planes(config, B, M, N, K, f32):
+    """tcbf_transpose_pack_expanded (complex values -> E2M1 planes in one
+    pass) gives exactly the oracle's product of the sign-quantised values,
+    on ragged K (a partial word pair) and with -0 and NaN components (-0 is
+    +1, NaN is -1), for FP16 and FP32 sources."""
+    import torch
+    from gpu_util import dev
+    from paper_2505_03269_gb300 import MODE_1BIT, SRC_CF16, SRC_CF32, Plan
+    g = ti.rng(B * 1000 + K)
+    W = ti.complex_gaussian_fp16(g, (B, M, K))
+    X = ti.complex_gaussian_fp16(g, (B, K, N))
+    W.reshape(-1)[::17] = np.float16(-0.0)
+    X.reshape(-1)[::13] = np.float16(-0.0)
+    X.reshape(-1)[5::29] = np.float16(np.nan)
+    src_type = SRC_CF32 if f32 else SRC_CF16
+    Ws, Xs = (W.astype(np.float32), X.astype(np.float32)) if f32 else (W, X)
+    with Plan(B, M, N, K, MODE_1BIT) as plan:
+        plan.set_config(config)
+        plan.transpose_pack_expanded(0, dev(Ws), src_type)
+        plan.transpose_pack_expanded(1, dev(Xs), src_type)
+        Y = torch.full((B, M, N, 2), -7, dtype=torch.int32, device="cuda")
+        plan.beamform_1bit_expanded(Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        got = Y.cpu().numpy().astype(np.int64)
+        kw = plan.Kw
+    Wb = oracle.pack_signs(W, k_is_row=False, Kw=kw)
+    Xb = oracle.pack_signs(X, k_is_row=True, Kw=kw)
+    assert np.array_equal(got, oracle.bgemm(Wb, Xb, K))

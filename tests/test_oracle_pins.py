@@ -313,6 +313,34 @@ def test_pack_signs_definition():
     assert np.array_equal(T, P)
 
 
+def test_pack_signs_f64_definition():
+    """FP64 sign packing: the hand table of bits (values far below the FP16
+    range keep their sign: -1e-30 gives bit 0, where rounding to FP16 first
+    would give -0 and bit 1), pads beyond K zero, and equality with the FP16
+    packer wherever the values are FP16 numbers."""
+    table = [(0.0, 1), (-0.0, 1), (1e-30, 1), (-1e-30, 0), (-6e-8, 0), (2.5, 1), (-7.0, 0)]
+    K = 70
+    g = np.random.default_rng(5)
+    idx = g.integers(0, len(table), (2, 3, K, 2))
+    vals = np.array([v for v, _ in table])
+    bits = np.array([b for _, b in table])
+    V = vals[idx[..., 0]] + 1j * vals[idx[..., 1]]
+    Kw = ti.words_per_row(K)
+    P = oracle.pack_signs_f64(V, Kw)
+    assert P.shape == (2, 2, 3, Kw) and P.dtype == np.uint32
+    for b in range(2):
+        for r in range(3):
+            for p in range(2):
+                want = [0] * Kw
+                for k in range(K):
+                    want[k // 32] |= int(bits[idx[b, r, k, p]]) << (k % 32)
+                assert [int(v) for v in P[b, p, r]] == want
+    # FP16-representable values: the same planes as the FP16 packer
+    W16, _ = ti.small_fp16(seed=3, M=5, K=K, N=1, B=2)
+    Wc = W16[..., 0].astype(np.float64) + 1j * W16[..., 1].astype(np.float64)
+    assert np.array_equal(oracle.pack_signs_f64(Wc, Kw), oracle.pack_signs(W16, False, Kw))
+
+
 # ----------------------------------------------------------- split FP8 oracle
 def test_e4m3_rounding_matches_library_cast():
     """Against torch's float8_e4m3fn conversion (round to nearest even) on a
