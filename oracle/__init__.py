@@ -12,6 +12,8 @@ Functions and the passages they follow:
   bgemm(Wb, Xb, K)       Eq. 3 over 1-bit values of Fig. 1, exact int64
   pack_signs(V, ...)     1-bit sign quantisation, Sec. III-D / Sec. V-A
   pack_signs_f64(V, Kw)  the same quantisation of FP64 values (weights' signs)
+  cgemm_split(W, X, p)   split-FP8 product, per-row scales (8-bit floats: Sec. VI)
+  cgemm_split_blocks     the same with a scale per 32 K per row / sample
   weights(geom)          w = A exp(-2 pi i f tau), Eq. 1-2
   half_to_double(h)      IEEE binary16 decoding (the FP16 storage format)
 """
@@ -299,6 +301,60 @@ def split_operands(W16: np.ndarray, X16: np.ndarray):
         return np.ascontiguousarray(A.reshape(B, N, K, 2).transpose(0, 2, 1, 3))
     return ((Wh.reshape(Bw, M, K, 2), Wl.reshape(Bw, M, K, 2), eW.reshape(Bw, M)),
             (back(Xh), back(Xl), eX.reshape(B, N)))
+
+
+def split_blocks(V16: np.ndarray):
+    """V16 [R, K, 2] FP16 rows -> (hi, lo, exps): per row and 32-K block the
+    exponent e (exps [R, ceil(K/32)]), hi = RN_e4m3(v 2^e) and lo =
+    RN_e4m3(16 (v 2^e - hi)) as doubles [R, K, 2], so v ~ (hi + lo / 16) 2^-e."""
+    lib = _load()
+    f = lib.oracle_split_blocks
+    f.restype = None
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    R, K, _ = V16.shape
+    src = np.ascontiguousarray(V16).view(np.uint16)
+    hi = np.empty((R, K, 2), np.float64)
+    lo = np.empty((R, K, 2), np.float64)
+    ex = np.empty((R, (K + 31) // 32), np.int32)
+    f(R, K, _ptr(src), _ptr(hi), _ptr(lo), _ptr(ex))
+    return hi, lo, ex
+
+
+def unscaled_blocks(V16: np.ndarray):
+    """The hi and lo parts of split_blocks in their true magnitudes: rows
+    [R, K, 2] of hi 2^-e and lo 2^-(e+4), each element with its block's e
+    (exact power-of-two scalings of E4M3 values)."""
+    hi, lo, ex = split_blocks(V16)
+    e = np.repeat(ex, 32, axis=1)[:, : V16.shape[1]][..., None].astype(np.float64)
+    return np.ldexp(hi, -e.astype(np.int64)), np.ldexp(lo, -(e + 4).astype(np.int64))
+
+
+def cgemm_split_blocks(W16: np.ndarray, X16: np.ndarray, products: int = 3) -> np.ndarray:
+    """Split-FP8 beamforming with a scale per 32 consecutive k of each W row
+    (beam) and each X column (sample) in FP64: with every part taken at its
+    true magnitude (Wh, Wl from W's blocks, Xh, Xl from X's),
+    Y = Wh Xh + Wh Xl + Wl Xh (products=3), + Wl Xl (4), or Wh Xh alone (the
+    plain block-scaled E4M3 product, 1); complex128 [B, M, N]."""
+    if products not in (1, 3, 4):
+        raise ValueError("products must be 1, 3 or 4")
+    Bw, M, K, _ = W16.shape
+    B, _, N, _ = X16.shape
+    Wh, Wl = unscaled_blocks(W16.reshape(Bw * M, K, 2))
+    XT = np.ascontiguousarray(X16.transpose(0, 2, 1, 3)).reshape(B * N, K, 2)
+    Xh, Xl = unscaled_blocks(XT)
+
+    def w(A):
+        return A.reshape(Bw, M, K, 2)
+
+    def x(A):
+        return np.ascontiguousarray(A.reshape(B, N, K, 2).transpose(0, 2, 1, 3))
+    Y = cgemm(w(Wh), x(Xh))
+    if products >= 3:
+        Y = Y + cgemm(w(Wh), x(Xl)) + cgemm(w(Wl), x(Xh))
+    if products == 4:
+        Y = Y + cgemm(w(Wl), x(Xl))
+    return Y
 
 
 def cgemm_split(W16: np.ndarray, X16: np.ndarray, products: int = 3) -> np.ndarray:

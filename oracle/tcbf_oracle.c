@@ -290,3 +290,33 @@ EXPORT void oracle_split_rows(int64_t R, int64_t K, const uint16_t *src, double 
         }
     }
 }
+
+/* Block-scaled split (the FP8 forms' per-tile scales): per row and per block
+ * of 32 consecutive k (over both planes) the exponent e of the block's
+ * largest magnitude as above, hi = RN(v 2^e) and lo = RN(16 (v 2^e - hi)):
+ * the lo part is stored 16 times larger (its scale is 2^-(e + 4)) so that it
+ * keeps E4M3's precision.  rows: [R][K] complex; hi, lo: [R][K][2] doubles
+ * (scaled values); exps: [R][ceil(K / 32)]. */
+EXPORT void oracle_split_blocks(int64_t R, int64_t K, const uint16_t *src, double *hi, double *lo,
+                                int32_t *exps)
+{
+    const int64_t nblk = (K + 31) / 32;
+    for (int64_t r = 0; r < R; ++r)
+        for (int64_t j = 0; j < nblk; ++j) {
+            const int64_t k0 = 32 * j, k1 = k0 + 32 < K ? k0 + 32 : K;
+            double amax = 0.0;
+            for (int64_t i = 2 * k0; i < 2 * k1; ++i) {
+                const double a = fabs(oracle_half_to_double(src[r * 2 * K + i]));
+                if (a > amax) amax = a;
+            }
+            const int e = oracle_split_exponent(amax);
+            exps[r * nblk + j] = e;
+            for (int64_t i = 2 * k0; i < 2 * k1; ++i) {
+                const double v = ldexp(oracle_half_to_double(src[r * 2 * K + i]), e);
+                const double h = oracle_e4m3_round(v);
+                hi[r * 2 * K + i] = h;
+                lo[r * 2 * K + i] = oracle_e4m3_round(16.0 * (v - h));
+            }
+        }
+}
+

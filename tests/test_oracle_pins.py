@@ -341,6 +341,88 @@ def test_pack_signs_f64_definition():
     assert np.array_equal(oracle.pack_signs_f64(Wc, Kw), oracle.pack_signs(W16, False, Kw))
 
 
+# ----------------------------------------------- block-scaled split FP8 oracle
+def test_split_blocks_exponents_are_per_block_maxima():
+    """Each 32-k block of a row gets the largest e with amax 2^e <= 448, amax
+    over that block's k and both planes only (the last block may be short)."""
+    g = np.random.default_rng(11)
+    K = 100
+    V = (g.standard_normal((3, K, 2)) * np.exp2(g.integers(-6, 7, (3, K, 1)))).astype(np.float16)
+    hi, lo, ex = oracle.split_blocks(V)
+    assert ex.shape == (3, 4)
+    for r in range(3):
+        for j in range(4):
+            blk = np.abs(V[r, 32 * j: 32 * j + 32].astype(np.float64))
+            amax = blk.max()
+            e = int(ex[r, j])
+            assert amax * 2.0 ** e <= 448.0 < amax * 2.0 ** (e + 1)
+
+
+def test_split_blocks_exact_for_short_significands():
+    """Values with at most 8 significant bits, all within a factor 8 of their
+    block's largest (so no part falls into E4M3's subnormal range), split
+    exactly: hi + lo / 16 = v 2^e, and the four-product block-scaled GEMM
+    equals the FP64 product; with three products the dropped Wl Xl term
+    is the only difference."""
+    g = np.random.default_rng(12)
+
+    def short(shape):
+        m = g.integers(128, 256, shape).astype(np.float64)        # 8-bit significands
+        sign = np.where(g.random(shape) < 0.5, -1.0, 1.0)
+        ex = g.integers(-2, 1, shape)                              # within a factor 8
+        blk = np.repeat(g.integers(-8, 4, shape[:-2] + (shape[-2] // 32 + 1,)), 32, axis=-1)
+        blk = blk[..., : shape[-2]][..., None]                     # per-32-k block magnitude
+        return (sign * m * np.exp2(ex + blk - 8)).astype(np.float16)
+    W = short((2, 5, 70, 2))
+    XT = short((4, 9, 70, 2))
+    X = np.ascontiguousarray(XT.transpose(0, 2, 1, 3))
+    hi, lo, ex = oracle.split_blocks(W.reshape(10, 70, 2))
+    e = np.repeat(ex, 32, axis=1)[:, :70][..., None]
+    assert np.array_equal(hi + lo / 16.0, W.reshape(10, 70, 2).astype(np.float64) * np.exp2(e))
+    exact = oracle.cgemm(W, X)
+    assert oracle.rel_frobenius(oracle.cgemm_split_blocks(W, X, products=4), exact) < 1e-15
+    Wh, Wl = oracle.unscaled_blocks(W.reshape(10, 70, 2))
+    XTh, XTl = oracle.unscaled_blocks(XT.reshape(36, 70, 2))
+    Xl = np.ascontiguousarray(XTl.reshape(4, 9, 70, 2).transpose(0, 2, 1, 3))
+    three = oracle.cgemm_split_blocks(W, X, products=3)
+    assert oracle.rel_frobenius(three + oracle.cgemm(Wl.reshape(2, 5, 70, 2), Xl), exact) < 1e-15
+
+
+def test_split_blocks_scale_one_block_alone():
+    """Scaling one 32-k block of one W row by 2^s changes only that block's
+    exponent (by -s), leaves its hi and lo bytes as they were, and scales
+    that block's contribution to the product by exactly 2^s."""
+    W, X = ti.small_fp16(seed=13, M=4, K=96, N=6, B=1)
+    W2 = W.copy()
+    W2[0, 2, 32:64] = (W2[0, 2, 32:64].astype(np.float64) * 8.0).astype(np.float16)
+    h1, l1, e1 = oracle.split_blocks(W[0])
+    h2, l2, e2 = oracle.split_blocks(W2[0])
+    assert e2[2, 1] == e1[2, 1] - 3
+    mask = np.ones_like(e1, bool)
+    mask[2, 1] = False
+    assert np.array_equal(e1[mask], e2[mask])
+    assert np.array_equal(h1, h2) and np.array_equal(l1, l2)
+    Y1 = oracle.cgemm_split_blocks(W, X, products=3)
+    Y2 = oracle.cgemm_split_blocks(W2, X, products=3)
+    # the block's own contribution, from the same split restricted to k in [32, 64)
+    Wb = np.zeros_like(W)
+    Wb[0, 2, 32:64] = W[0, 2, 32:64]
+    Xb = np.zeros_like(X)
+    Xb[:, 32:64] = X[:, 32:64]
+    blk = oracle.cgemm_split_blocks(Wb, X, products=3)
+    assert np.allclose(Y2, Y1 + 7.0 * blk, rtol=0, atol=1e-12 * np.abs(Y1).max())
+
+
+def test_split_blocks_single_block_rows_match_row_scales():
+    """For K <= 32 a row is one block, so the block exponent equals the
+    per-row exponent of the per-row split and the hi parts are the same."""
+    W, _ = ti.small_fp16(seed=14, M=7, K=29, N=1, B=1)
+    hb, _, eb = oracle.split_blocks(W[0])
+    hr, _, er = oracle.split_rows(W[0])
+    assert np.array_equal(eb[:, 0], er)
+    assert np.array_equal(hb, hr)
+
+
 # ----------------------------------------------------------- split FP8 oracle
 def test_e4m3_rounding_matches_library_cast():
     """Against torch's float8_e4m3fn conversion (round to nearest even) on a
