@@ -99,6 +99,8 @@ def parse_args():
     ap.add_argument("--mode", choices=["fp16", "fp8split", "fp8", "tf32"], default=None,
                     help="arithmetic of the FP workloads (default fp16); fp8split: E4M3 hi+lo, "
                          "three products; fp8: the plain E4M3 product (hi only)")
+    ap.add_argument("--fp8-scales", choices=["row", "block"], default="row",
+                    help="FP8 scales: per row / sample, or per 32 k of each (block-scaled MMAs)")
     ap.add_argument("--layout", choices=["interleaved", "planar", "stacked"], default=None,
                     help="FP16 X layout: interleaved (no pack, the radio default), planar, stacked")
     ap.add_argument("--no-subs", action="store_true", help="skip the sub-workload records")
@@ -131,6 +133,12 @@ def workload(args):
     if getattr(args, "m_rows", None) is not None:
         w["M"] = args.m_rows
         w["desc"] += f" [{args.m_rows} rows]"
+    if getattr(args, "fp8_scales", "row") == "block" and w["mode"] in ("fp8split", "fp8"):
+        w["fp8_block"] = True
+        w["desc"] = w["desc"].replace("per-row scales", "block scales").replace(
+            "(E4M3 hi+lo)", "(E4M3 hi+lo, block scales)")
+        if "block scales" not in w["desc"]:
+            w["desc"] += " [a scale per 32 k of each row and sample]"
     if getattr(args, "layout", None) is not None and w["mode"] == "fp16":
         w["layout"] = args.layout
         w["stacked"] = args.layout == "stacked"
@@ -432,6 +440,8 @@ class GpuWorkload:
                  tcbf.FLAG_INTERLEAVED_X if lay == "interleaved" else 0)
         if w["mode"] == "fp8":
             flags = tcbf.FLAG_FP8_HI_ONLY
+        if w.get("fp8_block"):
+            flags |= tcbf.FLAG_FP8_BLOCK_SCALES
         self.layout = lay
         self.plan = tcbf.Plan(B, M, N, K, mode, w_batches=Bw, device=local, flags=flags)
         if config is not None:
@@ -572,7 +582,8 @@ class GpuWorkload:
                 ref[i] = oracle.cgemm_points(Wrow, self.Xh[b:b + 1], np.array([[0, 0, n]]))[0]
             if is_fp8(w):
                 Xcol = np.ascontiguousarray(self.Xh[b:b + 1, :, n:n + 1])
-                ref_split[i] = oracle.cgemm_split(Wrow, Xcol, products=fp8_products(w))[0, 0, 0]
+                split = oracle.cgemm_split_blocks if w.get("fp8_block") else oracle.cgemm_split
+                ref_split[i] = split(Wrow, Xcol, products=fp8_products(w))[0, 0, 0]
         t = torch.from_numpy(pts).cuda()
         Yh = self.Y[t[:, 0], t[:, 1], t[:, 2]].double().cpu().numpy()
         got = Yh[:, 0] + 1j * Yh[:, 1]
@@ -622,7 +633,7 @@ def roofline_of(gw, peaks, gemm_ms):
         peak_note = ("E4M3 tensor peak = measured bf16 burst x nominal fp8/bf16 ratio 2; "
                      + ("algorithmic flops = 3 x useful (Wh Xh + Wh Xl + Wl Xh)"
                         if fp8_products(w) == 3 else "algorithmic flops = useful (Wh Xh)"))
-        kname = "cgemm_tc_kernel<split>"
+        kname = "cgemm_tc_kernel<split-block>" if w.get("fp8_block") else "cgemm_tc_kernel<split>"
     else:
         tensor_peak = peaks["bf16_tflops"]
         peak_note = "FP16 tensor peak = measured bf16 burst (same dense rate)"
@@ -706,6 +717,8 @@ def measure_sub(name, w, args, peaks):
                "steps": args.sub_steps,
                "dtype": ("e2m1" if gw.fp4() else
                          {"1bit": "u1", "fp8split": "e4m3x2", "fp8": "e4m3"}.get(w["mode"], "f16")),
+               "fp8_scales": ("block (UE8M0 per 32 k)" if w.get("fp8_block") else
+                              "row" if is_fp8(w) else None),
                "kernel_config": gw.plan.config_name(gw.plan.get_config()),
                "kernels": {"gemm_ms": r["gemm_ms"], "pack_ms": r["pack_ms"],
                            "pack_note": ("X packed straight into the E2M1 planes" if gw.fp4()
@@ -987,12 +1000,15 @@ def main():
     # ---- the other configured workloads, as sub-records
     if not args.no_subs and args.workload == "radio" and args.batches is None:
         subs = {}
-        for key, wname, mode in (("ultrasound_fp16", "ultrasound", None),
-                                 ("ultrasound_fp8split", "ultrasound", "fp8split"),
-                                 ("ultrasound_fp8", "ultrasound", "fp8"),
-                                 ("onebit", "onebit", None)):
+        for key, wname, mode, scales in (("ultrasound_fp16", "ultrasound", None, "row"),
+                                         ("ultrasound_fp8split", "ultrasound", "fp8split", "row"),
+                                         ("ultrasound_fp8", "ultrasound", "fp8", "row"),
+                                         ("ultrasound_fp8split_block", "ultrasound", "fp8split", "block"),
+                                         ("ultrasound_fp8_block", "ultrasound", "fp8", "block"),
+                                         ("onebit", "onebit", None, "row")):
             sa = argparse.Namespace(**vars(args))
             sa.workload, sa.mode, sa.layout, sa.batches, sa.m_rows = wname, mode, None, None, None
+            sa.fp8_scales = scales
             try:
                 subs[key] = measure_sub(key, workload(sa), args, peaks)
             except Exception as exc:      # reported, never silently dropped

@@ -107,7 +107,18 @@ typedef enum {
      * plan-owned planes and the planar kernel inside the beamform call.
      * Not combined with TCBF_FLAG_STACKED_X.  Selects the interleaved-X
      * kernel configurations. */
-    TCBF_FLAG_INTERLEAVED_X = 8u
+    TCBF_FLAG_INTERLEAVED_X = 8u,
+    /* FP8-split only (with or without TCBF_FLAG_FP8_HI_ONLY /
+     * _FOUR_PRODUCTS): the scale is per 32 consecutive k of each W row and
+     * each X sample instead of per row: e is the largest integer with
+     * amax * 2^e <= 448 over the block's 32 k of both planes, hi =
+     * RN_e4m3(v 2^e) and lo = RN_e4m3(16 (v 2^e - hi)) (lo kept 16 times
+     * larger, its scale 2^-(e + 4), so it keeps E4M3's precision).  The
+     * tensor cores apply the scales themselves (block-scaled E4M3 MMAs,
+     * kind::mxf8f6f4 with UE8M0 scales).  The scales follow the packed
+     * bytes as 512-byte tiles, see the layouts below.  The paper's future
+     * work on 8-bit floats (Sec. VI); the benchmark spec's per-tile scales. */
+    TCBF_FLAG_FP8_BLOCK_SCALES = 16u
 } tcbf_flag;
 
 /*
@@ -137,6 +148,17 @@ typedef enum {
  *   exponents.  With TCBF_FLAG_FP8_HI_ONLY the rows hold the hi bytes alone,
  *   Kb2 = K rounded up to 64 (hi byte of element k at offset k), followed by
  *   the same exponents.
+ *   With TCBF_FLAG_FP8_BLOCK_SCALES the bytes are as above and the scales
+ *   follow them as UE8M0 codes (127 - e for hi, 123 - e for lo) in tiles of
+ *   512 bytes, one per (operand batch, row tile, stage of S k), S = 64
+ *   (hi+lo rows) or 128 (hi only), T = ceil(K / S) stages:
+ *     W: [w_batches][ceil(M / 128)][T][32][4][4] bytes, byte [l][g][j] the
+ *        code of row 128 t + 32 g + l;
+ *     X: [batch][ceil(N / 64)][T][32][4][4] bytes, byte [l][g][j] the code
+ *        of sample 64 t + 32 g + l (g < 2; g = 2, 3 hold 127);
+ *   j: hi codes of the stage's two 32-k blocks, then their lo codes
+ *   (hi+lo rows), or the hi codes of its four blocks (hi only).  Rows beyond
+ *   M or N hold 127.
  *   TF32 W : [w_batches][2][M][Kp] FP32, X : [batch][2][N][Kp] FP32, each
  *            value rounded to TF32 (nearest, ties to even, to 10 mantissa
  *            bits; the low 13 bits zero), zero pad.  FP16 sources convert

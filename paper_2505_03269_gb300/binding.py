@@ -24,6 +24,7 @@ FLAG_STACKED_X = 1
 FLAG_FP8_HI_ONLY = 2
 FLAG_FP8_FOUR_PRODUCTS = 4
 FLAG_INTERLEAVED_X = 8
+FLAG_FP8_BLOCK_SCALES = 16
 
 # every symbol include/tcbf.h declares
 EXPORTED = [

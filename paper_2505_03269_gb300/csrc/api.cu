@@ -75,6 +75,9 @@ size_t packed_bytes(const tcbf_plan_s &pl, int which) {
         case TCBF_MODE_1BIT:
             return static_cast<size_t>(nb * 2 * rows * pl.Kw * 4);
         case TCBF_MODE_FP8SPLIT:   // hi/lo bytes, then one int32 scale exponent per row
+            if (fp8_block_scaled(p.flags))   // ... or the scale tiles
+                return static_cast<size_t>(nb * 2 * rows * pl.Kb2 +
+                                           fp8blk_sf_bytes(nb, rows, p.K, p.flags, which));
             return static_cast<size_t>(nb * 2 * rows * pl.Kb2 + nb * rows * 4);
         case TCBF_MODE_TF32:       // FP32 planes holding TF32 values
             return static_cast<size_t>(nb * 2 * rows * pl.Kp * 4);
@@ -134,10 +137,11 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
         return TCBF_ERR_INVALID_ARG;
     const uint32_t fp8_flags = TCBF_FLAG_FP8_HI_ONLY | TCBF_FLAG_FP8_FOUR_PRODUCTS;
     const uint32_t f16_flags = TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X;
-    if ((q.flags & ~(f16_flags | fp8_flags)) != 0) return TCBF_ERR_INVALID_ARG;
+    const uint32_t blk = TCBF_FLAG_FP8_BLOCK_SCALES;
+    if ((q.flags & ~(f16_flags | fp8_flags | blk)) != 0) return TCBF_ERR_INVALID_ARG;
     if ((q.flags & f16_flags) && q.mode != TCBF_MODE_FP16) return TCBF_ERR_INVALID_ARG;
     if ((q.flags & f16_flags) == f16_flags) return TCBF_ERR_INVALID_ARG;   // one or the other
-    if ((q.flags & fp8_flags) && q.mode != TCBF_MODE_FP8SPLIT) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & (fp8_flags | blk)) && q.mode != TCBF_MODE_FP8SPLIT) return TCBF_ERR_INVALID_ARG;
     if ((q.flags & fp8_flags) == fp8_flags) return TCBF_ERR_INVALID_ARG;   // one or the other
     if (q.M > kMaxDim || q.N > kMaxDim || q.K > kMaxDim || q.batch > 65535)
         return TCBF_ERR_UNSUPPORTED;
@@ -401,6 +405,7 @@ TCBF_EXPORT tcbf_status tcbf_last_device_error(tcbf_plan_t plan) {
 TCBF_EXPORT tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count) {
     if (!plan || !count) return TCBF_ERR_INVALID_ARG;
     *count = plan->p.mode == TCBF_MODE_1BIT                  ? gemm_1bit_num_configs()
+             : fp8_block_scaled(plan->p.flags)           ? gemm_split8_blk_num_configs()
              : (plan->p.flags & TCBF_FLAG_STACKED_X)     ? gemm_f16_stacked_num_configs()
              : (plan->p.flags & TCBF_FLAG_INTERLEAVED_X) ? gemm_f16_ix_num_configs()
                                                          : gemm_f16_num_configs();
@@ -419,7 +424,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
     tcbf_plan_num_configs(plan, &n);
     if (config < 0 || config >= n) return TCBF_ERR_INVALID_ARG;
     if (plan->p.mode != TCBF_MODE_1BIT &&
-        !(plan->p.flags & (TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X)) &&
+        !(plan->p.flags & (TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X |
+                           TCBF_FLAG_FP8_BLOCK_SCALES)) &&
         !gemm_f16_config_valid(config, plan->p.K))
         return TCBF_ERR_INVALID_ARG;
     if (plan->p.mode == TCBF_MODE_1BIT && gemm_1bit_config_fp4(config)) {
@@ -440,6 +446,7 @@ TCBF_EXPORT const char *tcbf_config_name(tcbf_plan_t plan, int config) {
     if (plan->p.mode == TCBF_MODE_FP16) return gemm_f16_config_name(config);
     if (plan->p.mode == TCBF_MODE_1BIT) return gemm_1bit_config_name(config);
     if (plan->p.mode == TCBF_MODE_TF32) return gemm_tf32_config_name(config);
+    if (fp8_block_scaled(plan->p.flags)) return gemm_split8_blk_config_name(config);
     return gemm_split8_config_name(config);
 }
 
@@ -475,6 +482,7 @@ bool config_ok(const tcbf_plan_s &pl, int c) {
                (!gemm_1bit_config_fp4(c) || gemm_1bit_fp4_usable(pl));
     if (pl.p.flags & TCBF_FLAG_STACKED_X) return c >= 0 && c < gemm_f16_stacked_num_configs();
     if (pl.p.flags & TCBF_FLAG_INTERLEAVED_X) return c >= 0 && c < gemm_f16_ix_num_configs();
+    if (fp8_block_scaled(pl.p.flags)) return c >= 0 && c < gemm_split8_blk_num_configs();
     return gemm_f16_config_valid(c, pl.p.K);
 }
 

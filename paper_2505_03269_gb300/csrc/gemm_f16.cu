@@ -13,6 +13,14 @@
 // per 32-element K step, and rescales each output by 2^-(eW[m] + eX[n]),
 // the per-row power-of-two scales of the split.
 //
+// Block-scaled split-FP8 (FMT = kFmtSplit8Blk, plans with
+// TCBF_FLAG_FP8_BLOCK_SCALES): the same hi/lo rows with a UE8M0 scale per
+// 32 k of each row and sample; every stage also brings the two 512-byte
+// scale tiles of its W rows and X samples, which the MMA thread copies into
+// tensor memory (tcgen05.cp) before issuing kind::mxf8f6f4 block-scaled
+// MMAs, so the tensor cores apply the scales and the epilogue stores the
+// sums as they are.
+//
 // TF32 (for callers whose data arrives in FP32; the paper names more input
 // formats as future work, Sec. VI): FMT = kFmtTf32 reads planes of FP32
 // values already rounded to TF32, 32 per 128-byte row, and issues the same
@@ -59,11 +67,19 @@ constexpr int kChunkBlocks = 32;    // stages (x 64 K) per promoted chunk
 constexpr int kFmtF16 = 0;
 constexpr int kFmtSplit8 = 1;
 constexpr int kFmtTf32 = 2;
+constexpr int kFmtSplit8Blk = 3;
+// Tensor-memory column of the block-scaled kernel's scale factors: per
+// stage 8 columns (4 for the W tile, 4 for the X tile) above the
+// accumulators of its 64-sample tiles.
+constexpr int kSfCol = 256;
 
 struct GemmArgs {
     float *Y;
     const int32_t *w_exps;     // split-FP8 scale exponents [w_batches][M] (else unused)
     const int32_t *x_exps;     // split-FP8 scale exponents [batch][N]
+    const uint8_t *w_sf;       // block-scaled FP8: W scale tiles [w_batches][w_sf_tiles][num_kb][512]
+    const uint8_t *x_sf;       // block-scaled FP8: X scale tiles [batch][x_sf_groups][num_kb][512]
+    int w_sf_tiles, x_sf_groups;
     int tma_store;             // 1: Y written by TMA bulk tensor stores (needs N even)
     uint32_t *status;
     int M, N, K;
@@ -82,15 +98,18 @@ constexpr int pow2_cols(int c) {
     return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool BLK = false>
 struct Cfg {
     static constexpr int A_PLANE = BM * BK * 2;              // bytes of one W plane tile
     static constexpr int B_PLANE = BN * BK * 2;              // bytes of one X plane tile
     static constexpr int A_BYTES = 2 * A_PLANE;
     static constexpr int B_BYTES = 2 * B_PLANE;
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SF_BYTES = BLK ? 2 * kFp8BlkTile : 0;   // W and X scale tiles
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES + SF_BYTES;
     static constexpr int ACC_BUFS = (4 * BN <= 512) ? 2 : 1;
-    static constexpr int TMEM_COLS = pow2_cols(ACC_BUFS * 2 * BN);
+    static constexpr int TMEM_COLS = BLK ? 512 : pow2_cols(ACC_BUFS * 2 * BN);
+    static_assert(!BLK || (ACC_BUFS * 2 * BN <= kSfCol && kSfCol + 8 * STAGES <= 512),
+                  "block-scaled: accumulators below the scale columns");
     static constexpr int STAGING_BYTES = 4 * 2 * 4096;        // 4 epilogue warps x 2 x (32 rows x 128 B)
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M=128");
@@ -135,13 +154,42 @@ __device__ __forceinline__ void split_step(uint32_t d_re, uint32_t d_im, uint32_
     }
 }
 
+// Block-scaled split-FP8 MMAs of one 32-K step j, the first NP products as
+// in split_step; the scale bytes of the stage's tiles in tensor memory are
+// hi codes of its two 32-k blocks (ids 0, 1) then their lo codes (2, 3), or
+// for hi-only rows the hi codes of its four blocks (ids 0-3).
+template <int NP, int BN>
+__device__ __forceinline__ void split_step_blk(uint32_t d_re, uint32_t d_im, uint32_t a,
+                                               uint32_t bx, int a_plane, int b_plane, int j,
+                                               bool first, uint32_t sfa, uint32_t sfb) {
+#pragma unroll
+    for (int pr = 0; pr < NP; ++pr) {
+        const uint32_t wo = (pr >= 2 ? 64u : 0u) + 32u * j;
+        const uint32_t xo = ((pr & 1) ? 64u : 0u) + 32u * j;
+        const uint32_t sa = (pr >= 2 ? 2u : 0u) + static_cast<uint32_t>(j);
+        const uint32_t sb = ((pr & 1) ? 2u : 0u) + static_cast<uint32_t>(j);
+        const uint32_t idesc = idesc_mxf8(BM, BN, sa, sb, false);
+        const uint32_t idesc_neg = idesc_mxf8(BM, BN, sa, sb, true);
+        const uint64_t ar = sdesc_kmajor_sw128(a + wo);
+        const uint64_t ai = sdesc_kmajor_sw128(a + a_plane + wo);
+        const uint64_t br = sdesc_kmajor_sw128(bx + xo);
+        const uint64_t bi = sdesc_kmajor_sw128(bx + b_plane + xo);
+        const uint32_t accum = (first && pr == 0) ? 0u : 1u;
+        mma_mxf8(d_re, ar, br, idesc, sfa, sfb, accum);
+        mma_mxf8(d_re, ai, bi, idesc_neg, sfa, sfb, 1u);
+        mma_mxf8(d_im, ar, bi, idesc, sfa, sfb, accum);
+        mma_mxf8(d_im, ai, br, idesc, sfa, sfb, 1u);
+    }
+}
+
 template <int BN, int STAGES, int FMT, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmW,
                      const __grid_constant__ CUtensorMap tmX,
                      const __grid_constant__ CUtensorMap tmY, const GemmArgs args) {
-    using C = Cfg<BN, STAGES>;
-    constexpr bool SPLIT = FMT == kFmtSplit8;
+    constexpr bool BLK = FMT == kFmtSplit8Blk;
+    using C = Cfg<BN, STAGES, BLK>;
+    constexpr bool SPLIT = FMT == kFmtSplit8 || BLK;
     constexpr bool TF32 = FMT == kFmtTf32;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -236,6 +284,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
                             tma_load_3d(dst, &tmW, fb, x, mt * BM, 2 * bw);
                             tma_load_3d(dst + C::A_BYTES, &tmX, fb, x, nt * BN, 2 * b);
+                            if (BLK) {   // the stage's W and X scale tiles
+                                const uint32_t sdst = dst + C::A_BYTES + C::B_BYTES;
+                                bulk_load(sdst,
+                                          args.w_sf + ((static_cast<size_t>(bw) * args.w_sf_tiles + mt) *
+                                                           args.num_kb + kb) * kFp8BlkTile,
+                                          kFp8BlkTile, fb);
+                                bulk_load(sdst + kFp8BlkTile,
+                                          args.x_sf + ((static_cast<size_t>(b) * args.x_sf_groups + nt) *
+                                                           args.num_kb + kb) * kFp8BlkTile,
+                                          kFp8BlkTile, fb);
+                            }
                         }
                     } else {
                         mbar_arrive_expect_tx(fb, C::STAGE_BYTES);
@@ -330,6 +389,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     mma_f16(d_im, ai, br, kIdesc, 1u);
                                 }
                             }
+                        } else if (BLK) {
+                            // the stage's scale tiles into its tensor-memory columns,
+                            // ordered before this thread's MMAs below
+                            const uint32_t sft = tmem_base + kSfCol + 8 * stage;
+                            const uint32_t ssrc = bx + C::B_BYTES;
+                            tmem_cp_32x128b_x4(sft, ssrc);
+                            tmem_cp_32x128b_x4(sft + 4, ssrc + kFp8BlkTile);
+                            const int ksteps = min(args.kps / 32, (args.K - kb * args.kps + 31) / 32);
+                            for (int j = 0; j < ksteps; ++j) {
+                                const bool first = kb == kb0 && j == 0;
+                                if (args.products == 3)
+                                    split_step_blk<3, BN>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                          first, sft, sft + 4);
+                                else if (args.products == 1)
+                                    split_step_blk<1, BN>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                          first, sft, sft + 4);
+                                else
+                                    split_step_blk<4, BN>(d_re, d_im, a, bx, C::A_PLANE, C::B_PLANE, j,
+                                                          first, sft, sft + 4);
+                            }
                         } else {
                             // 32 E4M3 per step; (W part, X part) byte offsets:
                             // (hi, hi), (hi, lo), (lo, hi), (lo, lo), the first
@@ -392,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int m = mt * BM + row;
             float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
             float row_scale = 1.f;
-            if (SPLIT && m < args.M)
+            if (SPLIT && !BLK && m < args.M)
                 row_scale = pow2_neg(__ldg(args.w_exps + static_cast<size_t>(b / args.per_w) * args.M + m));
             for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
                 const int acc = ev % nbuf;
@@ -439,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     const int n0 = nt * BN + c * 16;
-                    if (SPLIT) {
+                    if (SPLIT && !BLK) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int n = min(n0 + i, args.N - 1);
@@ -871,14 +950,16 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     if (CL > 1 && pl.m_prefix)   // uneven batches walk per-batch m-tiles: no clusters
         return launch_cfg<BN, STAGES, FMT, 1>(pl, Wp, Xp, Y, s, raster);
     // row length in elements of the tensor map: FP16 elements or split-FP8 bytes
-    constexpr bool SPLIT = FMT == kFmtSplit8;
+    constexpr bool BLK = FMT == kFmtSplit8Blk;
+    constexpr bool SPLIT = FMT == kFmtSplit8 || BLK;
     constexpr bool TF32 = FMT == kFmtTf32;
+    static_assert(!BLK || BN == kFp8BlkRowsX, "block-scaled tiles span one X scale group");
     const int64_t row = SPLIT ? pl.Kb2 : pl.Kp;
     const CUtensorMapDataType dt = SPLIT  ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                    : TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const int64_t esz = SPLIT ? 1 : TF32 ? 4 : 2;
-    using C = Cfg<BN, STAGES>;
+    using C = Cfg<BN, STAGES, BLK>;
     const tcbf_problem &p = pl.p;
     CUtensorMap tmW, tmX;
     {
@@ -919,13 +1000,21 @@ cudaError_t launch_cfg(const tcbf_plan_s &pl, const void *Wp, const void *Xp, fl
     }
     GemmArgs a;
     a.Y = Y;
-    a.w_exps = !SPLIT ? nullptr
+    a.w_exps = (!SPLIT || BLK) ? nullptr
                : pl.w_exps ? pl.w_exps
                            : reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) +
                                                                p.w_batches * 2 * p.M * row);
-    a.x_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Xp) +
-                                                        p.batch * 2 * p.N * row)
-                     : nullptr;
+    a.x_exps = (SPLIT && !BLK) ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Xp) +
+                                                                   p.batch * 2 * p.N * row)
+                               : nullptr;
+    // block-scaled FP8: the scale tiles after the packed bytes (a sub-plan's
+    // W tiles given by the caller through w_exps)
+    a.w_sf = !BLK ? nullptr
+             : pl.w_exps ? reinterpret_cast<const uint8_t *>(pl.w_exps)
+                         : static_cast<const uint8_t *>(Wp) + p.w_batches * 2 * p.M * row;
+    a.x_sf = BLK ? static_cast<const uint8_t *>(Xp) + p.batch * 2 * p.N * row : nullptr;
+    a.w_sf_tiles = static_cast<int>(ceil_div(w_plane_rows(pl), kFp8BlkRowsW));
+    a.x_sf_groups = static_cast<int>(ceil_div(p.N, kFp8BlkRowsX));
     a.tma_store = tma_store;
     a.products = split_products(pl);
     a.drop_fill = (CL == 1 && pl.debug_drop_fill >= 0) ? static_cast<int>(pl.debug_drop_fill) : -1;
@@ -1049,6 +1138,9 @@ cudaError_t launch_pair(const tcbf_plan_s &pl, const void *Wp, const void *Xp, f
     a.x_exps = SPLIT ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Xp) +
                                                         p.batch * 2 * p.N * row)
                      : nullptr;
+    a.w_sf = nullptr;
+    a.x_sf = nullptr;
+    a.w_sf_tiles = a.x_sf_groups = 0;
     a.tma_store = tma_store;
     a.products = split_products(pl);
     a.drop_fill = -1;
@@ -1139,6 +1231,15 @@ const ConfigEntry kConfigsSplit[] = {
     {"fp8split 2-SM pair BM256 BN128 BK64 stages4 tmem-double", 128, 0, launch_pair<128, 4, kFmtSplit8>},
 };
 
+// block-scaled split-FP8: 128 x 64 tiles (a tile spans one 64-sample X
+// scale group; the scale columns sit above the accumulators in TMEM)
+const ConfigEntry kConfigsSplitBlk[] = {
+    {"fp8split block-scaled mxf8f6f4 BM128 BN64 BK64 stages3 tmem-double n-fastest", 64, 0,
+     launch_cfg<64, 3, kFmtSplit8Blk, 1>},
+    {"fp8split block-scaled mxf8f6f4 BM128 BN64 BK64 stages3 tmem-double m-fastest", 64, 1,
+     launch_cfg<64, 3, kFmtSplit8Blk, 1>},
+};
+
 // TF32: the same tile shapes, index for index (32 K per 128-byte stage row)
 const ConfigEntry kConfigsTf32[] = {
     {"tf32 BM128 BN128 BK32 stages3 tmem-double n-fastest", 128, 0, launch_cfg<128, 3, kFmtTf32, 1>},
@@ -1182,8 +1283,21 @@ cudaError_t launch_gemm_tf32(const tcbf_plan_s &pl, const void *Wp, const void *
     return kConfigsTf32[c].fn(pl, Wp, Xp, Y, s, kConfigsTf32[c].raster);
 }
 
+int gemm_split8_blk_num_configs() {
+    return static_cast<int>(sizeof(kConfigsSplitBlk) / sizeof(kConfigsSplitBlk[0]));
+}
+
+const char *gemm_split8_blk_config_name(int config) {
+    if (config < 0 || config >= gemm_split8_blk_num_configs()) return "invalid";
+    return kConfigsSplitBlk[config].name;
+}
+
 cudaError_t launch_gemm_split8(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                                cudaStream_t s) {
+    if (fp8_block_scaled(pl.p.flags)) {
+        const int c = (pl.config >= 0 && pl.config < gemm_split8_blk_num_configs()) ? pl.config : 0;
+        return kConfigsSplitBlk[c].fn(pl, Wp, Xp, Y, s, kConfigsSplitBlk[c].raster);
+    }
     const int c = (pl.config >= 0 && pl.config < gemm_f16_num_configs()) ? pl.config : 0;
     return kConfigsSplit[c].fn(pl, Wp, Xp, Y, s, kConfigsSplit[c].raster);
 }

@@ -114,7 +114,10 @@ int64_t packed_x_bytes(const tcbf_plan_s &pl, int64_t nb) {
             return nb * x_planes(pl) * N * pl.Kp * 2;
         case TCBF_MODE_1BIT: return nb * 2 * N * pl.Kw * 4;
         case TCBF_MODE_TF32: return nb * 2 * N * pl.Kp * 4;
-        default: return nb * 2 * N * pl.Kb2 + nb * N * 4;
+        default:
+            if (fp8_block_scaled(pl.p.flags))
+                return nb * 2 * N * pl.Kb2 + fp8blk_sf_bytes(nb, N, pl.p.K, pl.p.flags, 1);
+            return nb * 2 * N * pl.Kb2 + nb * N * 4;
     }
 }
 
@@ -252,6 +255,18 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
         p.mode == TCBF_MODE_FP8SPLIT
             ? reinterpret_cast<const int32_t *>(static_cast<const uint8_t *>(Wp) + p.w_batches * wb)
             : nullptr;
+    // block-scaled FP8: W's scale tiles (128 rows per tile, `st` stages each)
+    // instead of one exponent per row
+    const bool blk = p.mode == TCBF_MODE_FP8SPLIT && fp8_block_scaled(p.flags);
+    const int64_t st_bytes = fp8blk_stages(p.K, p.flags) * kFp8BlkTile;
+    const int64_t w_tiles = ceil_div(p.M, kFp8BlkRowsW);
+    auto w_scales = [&](int64_t wb_first, int64_t m_first) -> const int32_t * {
+        if (!w_exps_all) return nullptr;
+        if (!blk) return w_exps_all + wb_first * p.M + m_first;
+        const uint8_t *t = reinterpret_cast<const uint8_t *>(w_exps_all);
+        return reinterpret_cast<const int32_t *>(t + (wb_first * w_tiles + m_first / kFp8BlkRowsW) *
+                                                         st_bytes);
+    };
     const auto *xh = static_cast<const uint8_t *>(X_host);
     auto *yh = static_cast<uint8_t *>(Y_host);
 
@@ -281,7 +296,7 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
             sub.graph_exec = nullptr;
             sub.pipe = nullptr;
             sub.debug_drop_fill = -1;
-            sub.w_exps = w_exps_all ? w_exps_all + m0 : nullptr;
+            sub.w_exps = w_scales(0, m0);       // m0 is a multiple of 128
             const void *w_sub = static_cast<const uint8_t *>(Wp) + m0 * wrow;
             // the slot's Y is free once its last copy-out ran
             for (int i = 0; i < kD2h && e == cudaSuccess && hp.used[s]; ++i)
@@ -315,7 +330,7 @@ TCBF_EXPORT tcbf_status tcbf_beamform_host(tcbf_plan_t plan, const void *X_host,
             sub.graph_exec = nullptr;
             sub.pipe = nullptr;
             sub.debug_drop_fill = -1;
-            sub.w_exps = w_exps_all ? w_exps_all + wb0 * p.M : nullptr;
+            sub.w_exps = w_scales(wb0, 0);
             const void *w_sub = static_cast<const uint8_t *>(Wp) + wb0 * wb;
 
             // copy in (the slot's source buffer is free once its last pack ran)

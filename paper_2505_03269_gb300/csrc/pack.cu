@@ -643,6 +643,167 @@ __global__ void split8_rows_kernel(const void *__restrict__ src, uint8_t *__rest
     }
 }
 
+// ------------------------------------------------ block-scaled split FP8
+// One value v scaled by 2^e: hi = RN(v 2^e), lo = RN(16 (v 2^e - hi)) (the
+// lo part kept 16 times larger, its scale 2^-(e + 4)).
+__device__ __forceinline__ void split_value_blk(float v, uint8_t &hi, uint8_t &lo) {
+    hi = e4m3(v);
+    lo = e4m3(16.f * (v - e4m3_to_float(hi)));
+}
+
+// UE8M0 code of the scale 2^-e of a block with exponent e.
+__device__ __forceinline__ uint8_t ue8m0_code(int e) { return static_cast<uint8_t>(127 - e); }
+
+// Byte of scale tile entry (row r of the tile's 128 or 64, byte j):
+// [l][g][j] with r = 32 g + l.
+__device__ __forceinline__ int sf_entry(int r, int j) { return (r & 31) * 16 + (r >> 5) * 4 + j; }
+
+// W rows, block-scaled: one warp per row; per 64-k block of the row lanes
+// 0-15 hold k 0-31 and lanes 16-31 k 32-63 (two values each), each half
+// reducing its own 32-k block's largest magnitude over both planes.
+template <typename S, bool HI>
+__global__ void split8_rows_blk_kernel(const void *__restrict__ src, uint8_t *__restrict__ dst,
+                                       uint8_t *__restrict__ sf, int64_t rows, int64_t M, int K,
+                                       int Kb2, int stages) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const int64_t tiles = (M + kFp8BlkRowsW - 1) / kFp8BlkRowsW;
+    for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < rows;
+         r += warps_total) {
+        const int64_t bw = r / M, m = r % M;
+        uint8_t *row_re = dst + (static_cast<size_t>(bw * 2 + 0) * M + m) * Kb2;
+        uint8_t *row_im = dst + (static_cast<size_t>(bw * 2 + 1) * M + m) * Kb2;
+        uint8_t *tile_base = sf + static_cast<size_t>(bw * tiles + m / kFp8BlkRowsW) * stages * kFp8BlkTile;
+        const int rr = static_cast<int>(m % kFp8BlkRowsW);
+        constexpr int kBlk = HI ? 64 : 128;
+        for (int jj = 0; jj < Kb2 / kBlk; ++jj) {
+            float2 v[2];
+            float amax = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = 64 * jj + 2 * lane + q;
+                v[q] = make_float2(0.f, 0.f);
+                if (k < K) v[q] = load_f16_value<S>(src, static_cast<size_t>(r) * K + k);
+                amax = fmaxf(amax, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            const int e = split_exponent(amax);
+            const float sc = pow2f(e);
+            uint8_t h[2][2], l[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                split_value_blk(v[q].x * sc, h[0][q], l[0][q]);
+                split_value_blk(v[q].y * sc, h[1][q], l[1][q]);
+            }
+            *reinterpret_cast<uint16_t *>(row_re + kBlk * jj + 2 * lane) = h[0][0] | (h[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + kBlk * jj + 2 * lane) = h[1][0] | (h[1][1] << 8);
+            if (!HI) {
+                *reinterpret_cast<uint16_t *>(row_re + kBlk * jj + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
+                *reinterpret_cast<uint16_t *>(row_im + kBlk * jj + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+            }
+            if ((lane & 15) == 0) {
+                const int b2 = lane >> 4;                  // 32-k block within the 64
+                if (HI) {                                  // stages of 128 k: 4 hi codes
+                    uint8_t *t = tile_base + static_cast<size_t>(jj / 2) * kFp8BlkTile;
+                    t[sf_entry(rr, 2 * (jj & 1) + b2)] = ue8m0_code(e);
+                } else {                                   // stages of 64 k: 2 hi, 2 lo codes
+                    uint8_t *t = tile_base + static_cast<size_t>(jj) * kFp8BlkTile;
+                    t[sf_entry(rr, b2)] = ue8m0_code(e);
+                    t[sf_entry(rr, 2 + b2)] = ue8m0_code(e + 4);
+                }
+            }
+        }
+    }
+}
+
+// X transpose + block-scaled split: 64 (k) x 64 (n) tiles as in
+// split8_pack_x_kernel, with each (sample, 32-k block) exponent taken from
+// the tile itself; the tile's 64 samples are one X scale group.
+template <typename S, bool HI>
+__global__ void __launch_bounds__(256) split8_pack_x_blk_kernel(const void *__restrict__ src,
+                                                               uint8_t *__restrict__ dst,
+                                                               uint8_t *__restrict__ sf, int K,
+                                                               int N, int Kb2, int k_tiles,
+                                                               int n_tiles, int stages) {
+    __shared__ __half sre[TT][TPITCH];
+    __shared__ __half sim[TT][TPITCH];
+    __shared__ int es[TT][2];
+    const int tid = threadIdx.x;
+    const int64_t b = blockIdx.y;
+    const int64_t tiles_per_b = int64_t(k_tiles) * n_tiles;
+    for (int64_t t = blockIdx.x; t < tiles_per_b; t += gridDim.x) {
+        const int kt = static_cast<int>(t / n_tiles);
+        const int nt = static_cast<int>(t % n_tiles);
+        const int k0 = kt * TT, n0 = nt * TT;
+        const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kk = ty + 16 * i;
+            const int k = k0 + kk;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int nn = tx * 4 + q;
+                const int n = n0 + nn;
+                __half re = __float2half_rn(0.f), im = __float2half_rn(0.f);
+                if (k < K && n < N) S::load_h(src, (static_cast<size_t>(b) * K + k) * N + n, re, im);
+                sre[nn][kk] = re;
+                sim[nn][kk] = im;
+            }
+        }
+        __syncthreads();
+        // exponents of the tile's (sample, 32-k block) pairs, and their codes
+        if (tid < 2 * TT) {
+            const int nn = tid >> 1, b2 = tid & 1;
+            float amax = 0.f;
+            for (int j = 0; j < 32; ++j) {
+                amax = fmaxf(amax, fabsf(__half2float(sre[nn][32 * b2 + j])));
+                amax = fmaxf(amax, fabsf(__half2float(sim[nn][32 * b2 + j])));
+            }
+            const int e = split_exponent(amax);
+            es[nn][b2] = e;
+            if (n0 + nn < N) {
+                uint8_t *tile = sf + (static_cast<size_t>(b) * n_tiles + nt) * stages * kFp8BlkTile;
+                if (HI) {
+                    tile[static_cast<size_t>(kt / 2) * kFp8BlkTile + sf_entry(nn, 2 * (kt & 1) + b2)] =
+                        ue8m0_code(e);
+                } else {
+                    tile[static_cast<size_t>(kt) * kFp8BlkTile + sf_entry(nn, b2)] = ue8m0_code(e);
+                    tile[static_cast<size_t>(kt) * kFp8BlkTile + sf_entry(nn, 2 + b2)] = ue8m0_code(e + 4);
+                }
+            }
+        }
+        __syncthreads();
+        // thread -> (row nn, 16-byte chunk c of 8: 4 hi chunks then 4 lo chunks)
+        const int c = tid & 7;
+        constexpr int kBlk = HI ? 64 : 128;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int nn = (tid >> 3) + 32 * h;
+            const int n = n0 + nn;
+            if (n < N && !(HI && c >= 4)) {
+                const int kc = 16 * (c & 3);
+                const float sc = pow2f(es[nn][kc >> 5]);
+                const bool want_lo = c >= 4;
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    __align__(16) uint8_t out[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float v = __half2float(p == 0 ? sre[nn][kc + j] : sim[nn][kc + j]) * sc;
+                        uint8_t hi, lo;
+                        split_value_blk(v, hi, lo);
+                        out[j] = want_lo ? lo : hi;
+                    }
+                    uint8_t *row = dst + (static_cast<size_t>(b * 2 + p) * N + n) * Kb2 + kt * kBlk;
+                    *reinterpret_cast<uint4 *>(row + 16 * c) = *reinterpret_cast<const uint4 *>(out);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // X columns: the largest magnitude per (batch, sample) over K, reduced in
 // parallel: each thread scans 256 rows of one sample (consecutive threads
 // read consecutive samples of a row of X) and folds its maximum into the
@@ -866,6 +1027,23 @@ cudaError_t launch_pack_split8_w(const tcbf_plan_s &pl, int src_type, const void
     const int64_t rows = pl.p.w_batches * pl.p.M;
     const int Kb2 = static_cast<int>(pl.Kb2);
     auto *d = static_cast<uint8_t *>(dst);
+    if (fp8_block_scaled(pl.p.flags)) {
+        // scale tiles: 127 (2^0) everywhere first, so rows beyond M hold a valid code
+        uint8_t *sf = d + rows * 2 * Kb2;
+        const int64_t sfb = fp8blk_sf_bytes(pl.p.w_batches, pl.p.M, pl.p.K, pl.p.flags, 0);
+        cudaError_t e = cudaMemsetAsync(sf, 127, static_cast<size_t>(sfb), s);
+        if (e != cudaSuccess) return e;
+        const int grid = grid_for(rows * 32, 256, pl.num_sms);
+        const int st = static_cast<int>(fp8blk_stages(pl.p.K, pl.p.flags));
+        const int K = static_cast<int>(pl.p.K);
+        auto run = [&](auto kern) { kern<<<grid, 256, 0, s>>>(src, d, sf, rows, pl.p.M, K, Kb2, st); };
+        const bool hi = fp8_hi_only(pl.p.flags);
+        if (src_type == TCBF_SRC_CF16)
+            hi ? run(split8_rows_blk_kernel<CF16, true>) : run(split8_rows_blk_kernel<CF16, false>);
+        else
+            hi ? run(split8_rows_blk_kernel<CF32, true>) : run(split8_rows_blk_kernel<CF32, false>);
+        return cudaGetLastError();
+    }
     auto *ex = reinterpret_cast<int32_t *>(d + rows * 2 * Kb2);
     const int grid = grid_for(rows * 32, 256, pl.num_sms);
     const bool hi = fp8_hi_only(pl.p.flags);
@@ -885,6 +1063,29 @@ cudaError_t launch_pack_split8_x(const tcbf_plan_s &pl, int src_type, const void
     const int64_t B = pl.p.batch, N = pl.p.N;
     const int Kb2 = static_cast<int>(pl.Kb2);
     auto *d = static_cast<uint8_t *>(dst);
+    if (fp8_block_scaled(pl.p.flags)) {
+        uint8_t *sf = d + B * 2 * N * Kb2;
+        const int64_t sfb = fp8blk_sf_bytes(B, N, pl.p.K, pl.p.flags, 1);
+        cudaError_t e = cudaMemsetAsync(sf, 127, static_cast<size_t>(sfb), s);
+        if (e != cudaSuccess) return e;
+        static_assert(TT == kFp8BlkRowsX, "one transpose tile of samples per X scale group");
+        const int k_tiles = static_cast<int>(ceil_div(pl.p.K, TT));
+        const int n_tiles = static_cast<int>(ceil_div(N, TT));
+        const int64_t per_b = int64_t(k_tiles) * n_tiles;
+        const int bx = static_cast<int>(std::min<int64_t>(per_b, std::max<int64_t>(1, int64_t(pl.num_sms) * 8 / std::max<int64_t>(1, std::min<int64_t>(B, 8)))));
+        dim3 grid(bx, static_cast<unsigned>(B));
+        const int st = static_cast<int>(fp8blk_stages(pl.p.K, pl.p.flags));
+        const int K = static_cast<int>(pl.p.K), Ni = static_cast<int>(N);
+        auto run = [&](auto kern) {
+            kern<<<grid, 256, 0, s>>>(src, d, sf, K, Ni, Kb2, k_tiles, n_tiles, st);
+        };
+        const bool hi = fp8_hi_only(pl.p.flags);
+        if (src_type == TCBF_SRC_CF16)
+            hi ? run(split8_pack_x_blk_kernel<CF16, true>) : run(split8_pack_x_blk_kernel<CF16, false>);
+        else
+            hi ? run(split8_pack_x_blk_kernel<CF32, true>) : run(split8_pack_x_blk_kernel<CF32, false>);
+        return cudaGetLastError();
+    }
     auto *ex = reinterpret_cast<int32_t *>(d + B * 2 * N * Kb2);
     const int g1 = grid_for(B * N, 256, pl.num_sms);
     const bool hi = fp8_hi_only(pl.p.flags);

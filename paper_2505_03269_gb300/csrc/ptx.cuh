@@ -154,6 +154,17 @@ __device__ __forceinline__ void tma_load_5d_pair(uint32_t dst, const CUtensorMap
         : "memory");
 }
 
+// Untiled bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global memory into this CTA's shared memory, completing on
+// `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
 // shared::cluster address of the same offset in CTA `rank` of the cluster
 __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
     uint32_t r;
@@ -286,6 +297,34 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// Block-scaled E4M3 MMA on one SM (kind::mxf8f6f4, one UE8M0 scale per 32 K):
+// A and B one byte per element (K = 32 per instruction), the scales of A's
+// rows and B's columns read from tensor memory at sfa and sfb (the byte
+// within each 32-bit cell chosen by the instruction descriptor's scale ids).
+__device__ __forceinline__ void mma_mxf8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], "
+        "[%5], p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
+}
+
+// Copy of a 32-row x 16-byte shared-memory tile (rows 16 bytes apart, no
+// swizzle) into 4 tensor-memory columns, the same in all four 32-lane
+// quarters: lane 32 q + l, column taddr + c receives bytes 4c .. 4c + 3 of
+// row l.  Issued by one thread; ordered with that thread's later MMAs.
+__device__ __forceinline__ void tmem_cp_32x128b_x4(uint32_t taddr, uint32_t smem_tile) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((smem_tile & 0x3FFFFu) >> 4);   // start address >> 4
+    d |= static_cast<uint64_t>(128 >> 4) << 16;                 // leading byte offset (one column)
+    d |= static_cast<uint64_t>(128 >> 4) << 32;                 // 8-row core matrices 128 B apart
+    d |= static_cast<uint64_t>(1) << 46;                        // descriptor version; no swizzle
+    asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(d) : "memory");
 }
 
 // Arrive on an mbarrier once all tcgen05 ops issued so far by this thread complete.
@@ -587,6 +626,22 @@ __host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N, uint32_t ab_fo
 // The same with an MN-major B operand (bit 16: B transposed), K-major A.
 __host__ __device__ constexpr uint32_t idesc_f32acc_bmn(int M, int N, uint32_t ab_format) {
     return idesc_f32acc(M, N, ab_format, false) | (1u << 16);
+}
+
+// Instruction descriptor of kind::mxf8f6f4 with E4M3 A and B and UE8M0
+// scales: A's scale byte sa_id and B's sb_id within their 32-bit cells,
+// negate A optional, FP32 D implied.  Tensor memory holds the scales of A's
+// row m at lane m, column sfa + m / 32, and of B's column n at column
+// sfb + n / 32, lane n % 32 of every 32-lane quarter; both addresses are
+// multiples of 4 columns.
+__host__ __device__ constexpr uint32_t idesc_mxf8(int M, int N, uint32_t sa_id, uint32_t sb_id,
+                                                  bool negate_a) {
+    return (sb_id << 4)                                // B scale id
+           | ((negate_a ? 1u : 0u) << 13)              // negate A
+           | (static_cast<uint32_t>(N >> 3) << 17)     // N >> 3
+           | (1u << 23)                                // scale format: UE8M0
+           | (static_cast<uint32_t>(M >> 4) << 24)     // M >> 4
+           | (sa_id << 29);                            // A scale id
 }
 
 // Instruction descriptor of the block-scaled kinds for kind::mxf4: E2M1 A

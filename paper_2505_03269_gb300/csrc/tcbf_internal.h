@@ -91,6 +91,9 @@ int gemm_f16_num_configs();
 const char *gemm_f16_config_name(int config);
 bool gemm_f16_config_valid(int config, int64_t K);
 const char *gemm_split8_config_name(int config);   // split-FP8 uses the FP16 tile table
+// Block-scaled split-FP8 (TCBF_FLAG_FP8_BLOCK_SCALES) has its own table.
+int gemm_split8_blk_num_configs();
+const char *gemm_split8_blk_config_name(int config);
 cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                             cudaStream_t s);
 
@@ -130,6 +133,23 @@ inline bool fp8_hi_only(uint32_t flags) { return (flags & TCBF_FLAG_FP8_HI_ONLY)
 inline int64_t fp8_block_bytes(uint32_t flags) { return fp8_hi_only(flags) ? 64 : 128; }
 inline int64_t fp8_row_bytes(int64_t K, uint32_t flags) {
     return round_up(K, 64) / 64 * fp8_block_bytes(flags);
+}
+
+// Block-scaled FP8 (TCBF_FLAG_FP8_BLOCK_SCALES): UE8M0 codes per 32 k in
+// 512-byte tiles of 128 W rows or 64 X samples per stage of
+// fp8blk_stage_k(flags) k, after the packed bytes.
+inline bool fp8_block_scaled(uint32_t flags) { return (flags & TCBF_FLAG_FP8_BLOCK_SCALES) != 0; }
+constexpr int kFp8BlkTile = 512;
+constexpr int kFp8BlkRowsW = 128;
+constexpr int kFp8BlkRowsX = 64;
+inline int64_t fp8blk_stage_k(uint32_t flags) { return fp8_hi_only(flags) ? 128 : 64; }
+inline int64_t fp8blk_stages(int64_t K, uint32_t flags) {
+    return (K + fp8blk_stage_k(flags) - 1) / fp8blk_stage_k(flags);
+}
+// Bytes of the scale tiles of operand `which` (0: W, 1: X) of nb batches.
+inline int64_t fp8blk_sf_bytes(int64_t nb, int64_t rows, int64_t K, uint32_t flags, int which) {
+    const int64_t per = which == 0 ? kFp8BlkRowsW : kFp8BlkRowsX;
+    return nb * ((rows + per - 1) / per) * fp8blk_stages(K, flags) * kFp8BlkTile;
 }
 
 // Rows between the planes of the packed W a GEMM launch reads.

@@ -203,6 +203,84 @@ __global__ void weights_split8_kernel(Geo g, uint8_t *__restrict__ dst, int32_t 
     }
 }
 
+// Block-scaled split-FP8 (TCBF_FLAG_FP8_BLOCK_SCALES): one warp per row; per
+// 64-k block lanes 0-15 hold k 0-31 and lanes 16-31 k 32-63, each half
+// taking its 32-k block's exponent from its own largest magnitude; bytes as
+// the transpose/pack kernel writes them (lo kept 16 times larger), the
+// scale codes into the 512-byte tiles of 128 rows per stage.
+template <bool HI>
+__global__ void weights_split8_blk_kernel(Geo g, uint8_t *__restrict__ dst, uint8_t *__restrict__ sf,
+                                          int64_t Bw, int Kb2, int stages) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = Bw * g.M;
+    const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
+    const int64_t tiles = (g.M + kFp8BlkRowsW - 1) / kFp8BlkRowsW;
+    for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < rows;
+         r += warps_total) {
+        const int64_t m = r % g.M, bw = r / g.M;
+        uint8_t *row_re = dst + (static_cast<size_t>(bw * 2 + 0) * g.M + m) * Kb2;
+        uint8_t *row_im = dst + (static_cast<size_t>(bw * 2 + 1) * g.M + m) * Kb2;
+        uint8_t *tile_base = sf + static_cast<size_t>(bw * tiles + m / kFp8BlkRowsW) * stages * kFp8BlkTile;
+        const int rr = static_cast<int>(m % kFp8BlkRowsW);
+        const int tl = (rr & 31) * 16 + (rr >> 5) * 4;     // this row's entry in a tile
+        constexpr int kBlk = HI ? 64 : 128;
+        for (int jj = 0; jj < Kb2 / kBlk; ++jj) {
+            float wr[2], wi[2];
+            float amax = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = 64 * jj + 2 * lane + q;
+                wr[q] = wi[q] = 0.f;
+                if (k < g.K) {
+                    weight(g, bw, m, k, wr[q], wi[q]);
+                    // the FP16 value the other modes would see
+                    wr[q] = __half2float(__float2half_rn(wr[q]));
+                    wi[q] = __half2float(__float2half_rn(wi[q]));
+                }
+                amax = fmaxf(amax, fmaxf(fabsf(wr[q]), fabsf(wi[q])));
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            int e = 0;
+            if (amax > 0.f) {
+                int q;
+                const float f = frexpf(amax, &q);
+                e = max(-100, min(100, (f <= 0.875f) ? 9 - q : 8 - q));
+            }
+            const float sc = __int_as_float((127 + e) << 23);
+            uint8_t h[2][2], l[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const float v = (p == 0 ? wr[q] : wi[q]) * sc;
+                    h[p][q] = static_cast<uint8_t>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
+                    const float hb = __half2float(__half(__nv_cvt_fp8_to_halfraw(h[p][q], __NV_E4M3)));
+                    l[p][q] = static_cast<uint8_t>(
+                        __nv_cvt_float_to_fp8(16.f * (v - hb), __NV_SATFINITE, __NV_E4M3));
+                }
+            }
+            *reinterpret_cast<uint16_t *>(row_re + kBlk * jj + 2 * lane) = h[0][0] | (h[0][1] << 8);
+            *reinterpret_cast<uint16_t *>(row_im + kBlk * jj + 2 * lane) = h[1][0] | (h[1][1] << 8);
+            if (!HI) {
+                *reinterpret_cast<uint16_t *>(row_re + kBlk * jj + 64 + 2 * lane) = l[0][0] | (l[0][1] << 8);
+                *reinterpret_cast<uint16_t *>(row_im + kBlk * jj + 64 + 2 * lane) = l[1][0] | (l[1][1] << 8);
+            }
+            if ((lane & 15) == 0) {
+                const int b2 = lane >> 4;
+                if (HI) {
+                    tile_base[static_cast<size_t>(jj / 2) * kFp8BlkTile + tl + 2 * (jj & 1) + b2] =
+                        static_cast<uint8_t>(127 - e);
+                } else {
+                    tile_base[static_cast<size_t>(jj) * kFp8BlkTile + tl + b2] = static_cast<uint8_t>(127 - e);
+                    tile_base[static_cast<size_t>(jj) * kFp8BlkTile + tl + 2 + b2] =
+                        static_cast<uint8_t>(123 - e);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double *tg,
@@ -229,6 +307,20 @@ cudaError_t launch_weights(const tcbf_plan_s &pl, const double *rx, const double
         const int64_t work = Bw * pl.p.M * (pl.Kp / 8);
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, int64_t(pl.num_sms) * 32)));
         weights_f16_kernel<<<grid, 256, 0, s>>>(g, static_cast<__half *>(Wp), Bw, int(pl.Kp));
+    } else if (fp8_block_scaled(pl.p.flags)) {
+        const int64_t rows = Bw * pl.p.M;
+        const int Kb2 = static_cast<int>(pl.Kb2);
+        auto *d = static_cast<uint8_t *>(Wp);
+        uint8_t *sf = d + rows * 2 * Kb2;
+        const int64_t sfb = fp8blk_sf_bytes(Bw, pl.p.M, pl.p.K, pl.p.flags, 0);
+        cudaError_t e = cudaMemsetAsync(sf, 127, static_cast<size_t>(sfb), s);
+        if (e != cudaSuccess) return e;
+        const int st = static_cast<int>(fp8blk_stages(pl.p.K, pl.p.flags));
+        const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, int64_t(pl.num_sms) * 32)));
+        if (fp8_hi_only(pl.p.flags))
+            weights_split8_blk_kernel<true><<<grid, 256, 0, s>>>(g, d, sf, Bw, Kb2, st);
+        else
+            weights_split8_blk_kernel<false><<<grid, 256, 0, s>>>(g, d, sf, Bw, Kb2, st);
     } else {
         const int64_t rows = Bw * pl.p.M;
         const int Kb2 = static_cast<int>(pl.Kb2);

@@ -198,3 +198,61 @@ def test_full_size_ultrasound_plain_fp8_sampled():
     torch.cuda.empty_cache()
     assert np.linalg.norm(got - ref_fp8) / np.linalg.norm(ref_fp8) <= TOL
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-1
+
+
+@pytest.mark.parametrize("products", [3, 1])
+def test_full_size_ultrasound_block_scaled_fp8_sampled(products):
+    """Block-scaled FP8 (a scale per 32 k) on the full ultrasound shape.  Three
+    products: W from the near-field geometry on the GPU, against the
+    oracle's block split of its own FP16 weights.  One product: W drawn on
+    the host (unit-magnitude random phases in FP16) so both sides split the
+    same FP16 values (with one product a weight one FP16 unit apart can
+    land on the neighbouring E4M3 value).  Parity bar 2e-5 against the
+    oracle's block-scaled arithmetic; accuracy against the exact product
+    stated with a loose ceiling."""
+    import torch
+    from gpu_util import empty_bytes
+    from paper_2505_03269_gb300 import (FLAG_FP8_BLOCK_SCALES, FLAG_FP8_HI_ONLY, MODE_FP8SPLIT,
+                                        Plan)
+    M, K, N = 65536, 16384, 256
+    geom = ti.ultrasound_geometry()
+    Xh = ti.ultrasound_frames(1, K, N)
+    Wh = ti.random_phase_rows(3, M, K) if products == 1 else None
+    flags = FLAG_FP8_BLOCK_SCALES | (FLAG_FP8_HI_ONLY if products == 1 else 0)
+    with Plan(1, M, N, K, MODE_FP8SPLIT, flags=flags) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        Xp = empty_bytes(plan.packed_size(1))
+        if Wh is None:
+            rx = torch.from_numpy(geom.rx_pos).cuda()
+            tg = torch.from_numpy(geom.targets).cuda()
+            fr = torch.from_numpy(np.ascontiguousarray(geom.freqs[:1])).cuda()
+            plan.weights_from_geometry(rx, tg, geom.near_field, fr, geom.c, Wp)
+        else:
+            Wd = torch.from_numpy(Wh).cuda()
+            plan.transpose_pack(0, Wd, Wp)
+            del Wd
+        plan.transpose_pack(1, torch.from_numpy(Xh).cuda(), Xp)
+        Y = torch.full((1, M, N, 2), float("nan"), dtype=torch.float32, device="cuda")
+        plan.beamform_fp8split(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        g = np.random.default_rng(17)
+        ms, ns = g.integers(0, M, 48), g.integers(0, N, 48)
+        got = np.empty(48, np.complex128)
+        ref_blk = np.empty(48, np.complex128)
+        ref = np.empty(48, np.complex128)
+        for i, (m, n) in enumerate(zip(ms, ns)):
+            if Wh is None:
+                Wrow = oracle.weights_fp16(geom.rx_pos, geom.targets[m:m + 1], geom.freqs[:1],
+                                           geom.near_field, geom.c)
+            else:
+                Wrow = np.ascontiguousarray(Wh[:, m:m + 1])
+            Xcol = np.ascontiguousarray(Xh[:, :, n:n + 1])
+            ref_blk[i] = oracle.cgemm_split_blocks(Wrow, Xcol, products=products)[0, 0, 0]
+            ref[i] = oracle.cgemm(Wrow, Xcol)[0, 0, 0]
+            v = Y[0, int(m), int(n)].double().cpu().numpy()
+            got[i] = v[0] + 1j * v[1]
+        del Y
+    torch.cuda.empty_cache()
+    assert np.linalg.norm(got - ref_blk) / np.linalg.norm(ref_blk) <= TOL
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < (5e-3 if products > 1 else 1e-1)
