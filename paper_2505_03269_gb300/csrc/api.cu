@@ -190,6 +190,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
                 return e == cudaErrorMemoryAllocation ? TCBF_ERR_OOM : TCBF_ERR_CUDA;
             }
         }
+        if (interleaved_x(*pl)) pl->config = gemm_f16_ix_default_config(q.K);
         // 1-bit: the 4-bit tensor path by default when its planes fit
         if (q.mode == TCBF_MODE_1BIT && gemm_1bit_fp4_reserve(*pl) == cudaSuccess &&
             gemm_1bit_fp4_usable(*pl))
@@ -428,6 +429,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_set_config(tcbf_plan_t plan, int config) {
                            TCBF_FLAG_FP8_BLOCK_SCALES)) &&
         !gemm_f16_config_valid(config, plan->p.K))
         return TCBF_ERR_INVALID_ARG;
+    if ((plan->p.flags & TCBF_FLAG_INTERLEAVED_X) && !gemm_f16_ix_config_valid(config, plan->p.K))
+        return TCBF_ERR_INVALID_ARG;
     if (plan->p.mode == TCBF_MODE_1BIT && gemm_1bit_config_fp4(config)) {
         // the E2M1 planes live in the plan; plans the path cannot take
         // (uneven batches, K > 2^23) run configuration 0 instead
@@ -481,7 +484,7 @@ bool config_ok(const tcbf_plan_s &pl, int c) {
         return c >= 0 && c < gemm_1bit_num_configs() &&
                (!gemm_1bit_config_fp4(c) || gemm_1bit_fp4_usable(pl));
     if (pl.p.flags & TCBF_FLAG_STACKED_X) return c >= 0 && c < gemm_f16_stacked_num_configs();
-    if (pl.p.flags & TCBF_FLAG_INTERLEAVED_X) return c >= 0 && c < gemm_f16_ix_num_configs();
+    if (pl.p.flags & TCBF_FLAG_INTERLEAVED_X) return gemm_f16_ix_config_valid(c, pl.p.K);
     if (fp8_block_scaled(pl.p.flags)) return c >= 0 && c < gemm_split8_blk_num_configs();
     return gemm_f16_config_valid(c, pl.p.K);
 }

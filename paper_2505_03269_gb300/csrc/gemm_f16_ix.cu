@@ -76,10 +76,82 @@ struct IxArgs {
     int num_kb;         // K blocks of BKS
     int w5d;            // W loaded by one 5-D box per 64 K (M % 8 == 0), else per 8-beam group
     int x4d;            // X loaded by one 4-D box per stage (N % 32 == 0), else per 64 columns
+    int y4d;            // Y stored by one 4-D box per 32 samples (N % 16 == 0), else two 3-D
     int kc_blocks;      // blocks per accumulation chunk
     int chunks;
     int total_tiles;
 };
+
+// One accumulator use of an interleaved-X epilogue warp (the warp's 16
+// TMEM lanes from tP; the running sum at tS): for a chunk before the last,
+// promote it into the sum (FP32 round-to-nearest); for the last, add the sum
+// if there is one, form Re and Im of its 8 beams x 128 samples and store
+// them, 32 samples at a time: two 1 KB boxes of 8 beams x 16 samples, one
+// 4-D store of both when N % 16 == 0 (y4d: Y seen as 16-sample chunks x
+// beams x batches), else two 3-D stores.
+template <int ACC_COLS, int STAGE_BUF>
+__device__ __forceinline__ void ix_drain(uint32_t tP, uint32_t tS, int ch, int chunks, int lane,
+                                         uint32_t stage_buf, int &nstore, int nt, int N, int beam0,
+                                         int b, const CUtensorMap *tmY, int y4d) {
+    const int rb = lane >> 2;                             // beam within the group
+    const int sq = lane & 3;                              // sample within each 4
+    if (ch + 1 < chunks) {
+        // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
+#pragma unroll 1
+        for (int g = 0; g < ACC_COLS / 64; ++g) {
+            float v[32];
+            tmem_ld_16x256b_x8(tP + 64 * g, v);
+            if (ch > 0) {
+                float sv[32];
+                tmem_ld_16x256b_x8(tS + 64 * g, sv);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
+            }
+            tmem_st_16x256b_x8(tS + 64 * g, v);
+        }
+        tmem_st_wait();
+        return;
+    }
+#pragma unroll 1
+    for (int c = 0; c < ACC_COLS / 64; ++c) {
+        float v[32];
+        tmem_ld_16x256b_x8(tP + 64 * c, v);
+        if (chunks > 1) {
+            float sv[32];
+            tmem_ld_16x256b_x8(tS + 64 * c, sv);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
+        }
+        const int n0 = nt * IBN + 32 * c;     // first sample of the block
+        if (n0 < N) {
+            const uint32_t buf = stage_buf + (nstore & 1) * STAGE_BUF;
+            if (lane == 0) bulk_wait_read<1>();   // the buffer's last stores have read it
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                // v[4i..4i+3] = Wr Xr, Wr Xi, Wi Xr, Wi Xi of sample 4i + sq
+                const float re = __fsub_rn(v[4 * i], v[4 * i + 3]);
+                const float im = __fadd_rn(v[4 * i + 1], v[4 * i + 2]);
+                const int s16 = 4 * (i & 3) + sq;          // sample within its box
+                const uint32_t addr = buf + (i >> 2) * 1024 + rb * 128 +
+                                      ((((s16 >> 1) ^ rb) & 7) << 4) + ((s16 & 1) << 3);
+                st_shared_v2(addr, re, im);
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                if (y4d) {
+                    tma_store_4d(tmY, buf, 0, beam0, n0 / 16, b);
+                } else {
+                    tma_store_3d(tmY, buf, 2 * n0, beam0, b);
+                    if (n0 + 16 < N) tma_store_3d(tmY, buf + 1024, 2 * (n0 + 16), beam0, b);
+                }
+                bulk_commit();
+            }
+            ++nstore;
+        }
+    }
+}
 
 template <bool PAIR, int BKS, int STAGES>
 __global__ void __launch_bounds__(kIxThreads, 1)
@@ -335,8 +407,6 @@ __global__ void __launch_bounds__(kIxThreads, 1)
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32 + half * 16) << 16;
-        const int rb = lane >> 2;                             // beam within the group
-        const int sq = lane & 3;                              // sample within each 4
         const uint32_t stage_buf = staging0 + (warp - 2) * 2 * C::STAGE_BUF;
         const uint32_t tS = tmem_base + lane_off + C::ACC_COLS;   // running sum (promotion only)
         const int nbuf = args.chunks > 1 ? 1 : 2;
@@ -356,58 +426,8 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * C::ACC_COLS;
-                if (ch + 1 < args.chunks) {
-                    // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
-#pragma unroll 1
-                    for (int g = 0; g < C::ACC_COLS / 64; ++g) {
-                        float v[32];
-                        tmem_ld_16x256b_x8(tP + 64 * g, v);
-                        if (ch > 0) {
-                            float sv[32];
-                            tmem_ld_16x256b_x8(tS + 64 * g, sv);
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
-                        }
-                        tmem_st_16x256b_x8(tS + 64 * g, v);
-                    }
-                    tmem_st_wait();
-                } else {
-#pragma unroll 1
-                    for (int c = 0; c < C::ACC_COLS / 64; ++c) {
-                        float v[32];
-                        tmem_ld_16x256b_x8(tP + 64 * c, v);
-                        if (args.chunks > 1) {
-                            float sv[32];
-                            tmem_ld_16x256b_x8(tS + 64 * c, sv);
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
-                        }
-                        const int n0 = nt * IBN + 32 * c;     // first sample of the block
-                        if (n0 < args.N) {
-                            const uint32_t buf = stage_buf + (nstore & 1) * C::STAGE_BUF;
-                            if (lane == 0) bulk_wait_read<1>();   // the buffer's last stores have read it
-                            __syncwarp();
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                // v[4i..4i+3] = Wr Xr, Wr Xi, Wi Xr, Wi Xi of sample 4i + sq
-                                const float re = __fsub_rn(v[4 * i], v[4 * i + 3]);
-                                const float im = __fadd_rn(v[4 * i + 1], v[4 * i + 2]);
-                                const int s16 = 4 * (i & 3) + sq;          // sample within its box
-                                const uint32_t addr = buf + (i >> 2) * 1024 + rb * 128 +
-                                                      ((((s16 >> 1) ^ rb) & 7) << 4) + ((s16 & 1) << 3);
-                                st_shared_v2(addr, re, im);
-                            }
-                            fence_async_smem();
-                            __syncwarp();
-                            if (lane == 0) {
-                                tma_store_3d(&tmY, buf, 2 * n0, beam0, b);
-                                if (n0 + 16 < args.N) tma_store_3d(&tmY, buf + 1024, 2 * (n0 + 16), beam0, b);
-                                bulk_commit();
-                            }
-                            ++nstore;
-                        }
-                    }
-                }
+                ix_drain<C::ACC_COLS, C::STAGE_BUF>(tP, tS, ch, args.chunks, lane, stage_buf, nstore,
+                                                   nt, args.N, beam0, b, &tmY, args.y4d);
                 // this warp is done with the accumulator: release it (in a pair,
                 // on the even CTA's barrier; its values are in registers or
                 // staged, so no cluster-scope fence is needed)
@@ -440,6 +460,27 @@ __global__ void __launch_bounds__(kIxThreads, 1)
         else
             tmem_dealloc(tmem_base, C::TMEM_COLS);
     }
+}
+
+// Y [batch][M][2N] FP32 for the interleaved-X epilogue: 16-sample chunks x
+// beams x batches (y4d, N % 16 == 0: a box is two chunks of 8 beams, 2 KB)
+// or columns x beams x batches (boxes of one chunk of 8 beams, 1 KB).
+CUresult encode_ix_y(CUtensorMap *tmY, float *Y, const tcbf_problem &p, int y4d) {
+    if (y4d) {
+        const uint64_t dims[4] = {32, static_cast<uint64_t>(p.M), static_cast<uint64_t>(p.N / 16),
+                                  static_cast<uint64_t>(p.batch)};
+        const uint64_t strides[3] = {static_cast<uint64_t>(p.N * 8), 128,
+                                     static_cast<uint64_t>(p.M * p.N * 8)};
+        const uint32_t box[4] = {32, 8, 2, 1};
+        return encode_tiled(tmY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Y, dims, strides, box,
+                            CU_TENSOR_MAP_SWIZZLE_128B);
+    }
+    const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.M),
+                              static_cast<uint64_t>(p.batch)};
+    const uint64_t strides[2] = {static_cast<uint64_t>(p.N * 8), static_cast<uint64_t>(p.M * p.N * 8)};
+    const uint32_t box[3] = {32, 8, 1};
+    return encode_tiled(tmY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Y, dims, strides, box,
+                        CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 template <bool PAIR, int BKS, int STAGES>
@@ -495,17 +536,8 @@ cudaError_t launch_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, floa
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    {
-        // Y [batch][M][2N] FP32: boxes of 16 complex samples x 8 beams
-        const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.M),
-                                  static_cast<uint64_t>(p.batch)};
-        const uint64_t strides[2] = {static_cast<uint64_t>(p.N * 8),
-                                     static_cast<uint64_t>(p.M * p.N * 8)};
-        const uint32_t box[3] = {32, 8, 1};
-        if (encode_tiled(&tmY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Y, dims, strides, box,
-                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-    }
+    const int y4d = p.N % 16 == 0 ? 1 : 0;
+    if (encode_ix_y(&tmY, Y, p, y4d) != CUDA_SUCCESS) return cudaErrorInvalidValue;
     IxArgs a;
     a.status = pl.status;
     a.M = static_cast<int>(p.M);
@@ -519,6 +551,7 @@ cudaError_t launch_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, floa
     a.kc_blocks = p.K > kIxPromoteK ? kIxChunkK / BKS : a.num_kb;
     a.w5d = w5d;
     a.x4d = x4d;
+    a.y4d = y4d;
     a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
     const int64_t total = int64_t(a.m_tiles) * a.n_tiles * p.batch;
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
@@ -559,12 +592,404 @@ cudaError_t launch_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, floa
     return cudaGetLastError();
 }
 
+// ===========================================================================
+// Resident weights, for short K (K <= 384, the radio block's 288): each CTA of
+// a pair keeps its 64 beams of W for all of K in shared memory (up to six
+// 16 KB blocks of 64 K, 8-beam groups alternating Wr and Wi as above) and
+// runs every sample tile of its (batch, 128-beam) unit against them, so only
+// X streams through the ring: per output, half the operand bytes from L2 of
+// the streaming kernel.  A unit's W is loaded once its predecessor's MMAs
+// are done (the MMA thread commits a W-empty barrier after a unit's last
+// tile), while the producer already streams the new unit's X.  Units run
+// pair rows fastest within a batch, so the pairs working at one time share
+// each batch's X in L2.  One accumulation chunk (no promotion at this K).
+// ===========================================================================
+constexpr int kWresMaxK = 384;
+constexpr int kWresBks = 128;                 // K rows of X per stage
+
+template <int STAGES>
+struct CfgIxW {
+    static constexpr int W_BLOCK = 128 * 64 * 2;              // 64 beams x 2 planes x 64 K
+    static constexpr int B_CHUNK = kWresBks * 128;            // 64 real columns x 128 K rows
+    static constexpr int X_STAGE = 2 * B_CHUNK;               // this CTA's 128 real columns
+    static constexpr int ACC_COLS = 2 * IBN;
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;
+    static constexpr int STAGE_BUF = 2 * 8 * 128;
+    static constexpr int STAGING_BYTES = 8 * 2 * STAGE_BUF;
+    static constexpr int BAR_BYTES = 16 * STAGES + 64;
+    static_assert(BAR_BYTES <= 256, "barrier block");
+    static __host__ __device__ constexpr int smem_bytes(int kb64) {
+        return kb64 * W_BLOCK + STAGES * X_STAGE + STAGING_BYTES + 256 + 1024;
+    }
+    static_assert((kWresMaxK / 64) * W_BLOCK + STAGES * X_STAGE + STAGING_BYTES + 256 + 1024 <= 232448,
+                  "shared memory");
+};
+
+struct IxWArgs {
+    uint32_t *status;
+    int M, N, K;
+    int per_w;
+    int kb64;           // 64-K blocks of resident W
+    int m_tiles;        // 128-beam pair rows per batch
+    int n_tiles;        // 128-sample tiles per batch
+    int num_kb;         // X stages per tile
+    int total_units;    // batch x m_tiles
+    int w5d, x4d, y4d;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(kIxThreads, 1)
+    cgemm_ix_wres_kernel(const __grid_constant__ CUtensorMap tmW,
+                         const __grid_constant__ CUtensorMap tmX,
+                         const __grid_constant__ CUtensorMap tmY, const IxWArgs args) {
+    using C = CfgIxW<STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+    const uint32_t s0 = smem_u32(smem);
+    const uint32_t w0 = s0;                                        // resident W
+    const uint32_t x0 = s0 + args.kb64 * C::W_BLOCK;               // X ring
+    const uint32_t staging0 = x0 + STAGES * C::X_STAGE;
+    const uint32_t bar0 = staging0 + C::STAGING_BYTES;
+    const uint32_t full0 = bar0;                       // STAGES x 8 bytes
+    const uint32_t empty0 = full0 + 8 * STAGES;        // STAGES x 8
+    const uint32_t tfull0 = empty0 + 8 * STAGES;       // 2 x 8
+    const uint32_t tempty0 = tfull0 + 16;              // 2 x 8
+    const uint32_t done_bar = tempty0 + 16;            // 8
+    const uint32_t wfull = done_bar + 8;               // 8: this unit's W has landed
+    const uint32_t wempty = wfull + 8;                 // 8: the last unit's MMAs are done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + (bar0 - s0) + 16 * STAGES + 56);
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int rank = static_cast<int>(cluster_ctarank());
+    const bool leader = rank == 0;
+    const int u_first = static_cast<int>(cluster_id_x());
+    const int u_step = static_cast<int>(nclusters_x());
+    constexpr uint16_t kBoth = 3;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(full0 + 8 * st, 1);
+            mbar_init(empty0 + 8 * st, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, 16);     // 8 epilogue warps x 2 CTAs
+        }
+        mbar_init(done_bar, 1);
+        mbar_init(wfull, 1);
+        mbar_init(wempty, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmW);
+        tma_prefetch_desc(&tmX);
+        tma_prefetch_desc(&tmY);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t full0_lead = mapa_shared(full0, 0);
+    const uint32_t tempty0_lead = mapa_shared(tempty0, 0);
+    const uint32_t wfull_lead = mapa_shared(wfull, 0);
+
+    if (warp == 0) {
+        // ------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0, wuse = 0;
+            bool ok = true;
+            for (int u = u_first; u < args.total_units && ok; u += u_step) {
+                const int b = u / args.m_tiles, mt = u - (u / args.m_tiles) * args.m_tiles;
+                const int bw = b / args.per_w;
+                const int beam0 = mt * 128 + 64 * rank;
+                // the unit's W, once the previous unit's MMAs no longer read it
+                if (!mbar_wait(wempty, (wuse & 1u) ^ 1u) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                if (leader) mbar_arrive_expect_tx(wfull, 2 * args.kb64 * C::W_BLOCK);
+                for (int kk = 0; kk < args.kb64; ++kk) {
+                    const uint32_t wdst = w0 + kk * C::W_BLOCK;
+                    if (args.w5d) {
+                        tma_load_5d_pair(wdst, &tmW, wfull_lead, 64 * kk, 0, 0, beam0 / 8, bw);
+                    } else {
+                        for (int g = 0; g < 8; ++g)
+                            tma_load_3d_pair(wdst + g * 2048, &tmW, wfull_lead, 64 * kk, beam0 + 8 * g,
+                                             2 * bw);
+                    }
+                }
+                ++wuse;
+                for (int nt = 0; nt < args.n_tiles && ok; ++nt) {
+                    const int col0 = 2 * nt * IBN + rank * 128;
+                    for (int kb = 0; kb < args.num_kb; ++kb) {
+                        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        if (leader) mbar_arrive_expect_tx(full0 + 8 * stage, 2 * C::X_STAGE);
+                        const uint32_t fb = full0_lead + 8 * stage;
+                        const uint32_t xdst = x0 + stage * C::X_STAGE;
+                        if (args.x4d) {
+                            tma_load_4d_pair(xdst, &tmX, fb, 0, kb * kWresBks, col0 / 64, b);
+                        } else {
+                            for (int c = 0; c < 2; ++c)
+                                tma_load_3d_pair(xdst + c * C::B_CHUNK, &tmX, fb, col0 + 64 * c,
+                                                 kb * kWresBks, b);
+                        }
+                        ++issued;
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutProducer);
+                *abort_flag = 1;
+                if (leader) {
+                    // every copy started must land before the CTAs exit
+                    for (int st = 0; st < STAGES; ++st) {
+                        if (issued > static_cast<uint32_t>(st)) {
+                            const uint32_t count = (issued - st + STAGES - 1) / STAGES;
+                            if (!mbar_wait(full0 + 8 * st, (count - 1) & 1u))
+                                atomicOr(args.status, kErrTimeoutDrain);
+                        }
+                    }
+                    if (wuse > 0 && !mbar_wait(wfull, (wuse - 1) & 1u))
+                        atomicOr(args.status, kErrTimeoutDrain);
+                }
+            } else {
+                // the even CTA's releases of every slot and W this CTA filled have arrived
+                for (int st = 0; st < STAGES; ++st) {
+                    if (issued > static_cast<uint32_t>(st)) {
+                        const uint32_t count = (issued - st + STAGES - 1) / STAGES;
+                        if (!mbar_wait(empty0 + 8 * st, (count - 1) & 1u))
+                            atomicOr(args.status, kErrTimeoutDrain);
+                    }
+                }
+                if (wuse > 0 && !mbar_wait(wempty, (wuse - 1) & 1u))
+                    atomicOr(args.status, kErrTimeoutDrain);
+            }
+        }
+    } else if (warp == 1) {
+        // ----------------------------------------- MMA issuer, even CTA only
+        if (lane == 0 && leader) {
+            constexpr uint32_t kIdesc = idesc_f32acc_bmn(256, 2 * IBN, 0);
+            int stage = 0;
+            uint32_t phase = 0, wuse = 0;
+            int ev = 0;
+            bool ok = true;
+            for (int u = u_first; u < args.total_units && ok; u += u_step) {
+                if (!mbar_wait(wfull, wuse & 1u) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int nt = 0; nt < args.n_tiles && ok; ++nt, ++ev) {
+                    const int acc = ev & 1;
+                    if (!mbar_wait(tempty0 + 8 * acc, ((ev >> 1) & 1u) ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + acc * C::ACC_COLS;
+                    for (int kb = 0; kb < args.num_kb; ++kb) {
+                        if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t bx = x0 + stage * C::X_STAGE;
+                        const int ksteps = min(kWresBks / 16, (args.K - kb * kWresBks + 15) / 16);
+                        for (int j = 0; j < ksteps; ++j) {
+                            const int kg = kb * kWresBks + 16 * j;       // K of this step
+                            const uint64_t ad =
+                                sdesc_kmajor_sw128(w0 + (kg >> 6) * C::W_BLOCK + 32 * ((kg >> 4) & 3));
+                            const uint64_t bd = sdesc_mnmajor_sw128(bx + 2048 * j, C::B_CHUNK, 1024);
+                            mma_f16_pair(d, ad, bd, kIdesc, (kb > 0 || j > 0) ? 1u : 0u);
+                        }
+                        mma_commit_pair(empty0 + 8 * stage, kBoth);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit_pair(tfull0 + 8 * acc, kBoth);
+                }
+                if (!ok) break;
+                mma_commit_pair(wempty, kBoth);    // the unit's W may be replaced
+                ++wuse;
+            }
+            if (!ok) {
+                atomicOr(args.status, kErrTimeoutMma);
+                *abort_flag = 1;
+            }
+            mma_commit_pair(done_bar, 1);
+            if (!mbar_wait(done_bar, 0)) atomicOr(args.status, kErrTimeoutDrain);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t lane_off = static_cast<uint32_t>(quarter * 32 + half * 16) << 16;
+        const uint32_t stage_buf = staging0 + (warp - 2) * 2 * C::STAGE_BUF;
+        int ev = 0;
+        int nstore = 0;
+        bool ok = true;
+        for (int u = u_first; u < args.total_units && ok; u += u_step) {
+            const int b = u / args.m_tiles, mt = u - (u / args.m_tiles) * args.m_tiles;
+            const int beam0 = mt * 128 + 64 * rank + 16 * quarter + 8 * half;
+            for (int nt = 0; nt < args.n_tiles; ++nt, ++ev) {
+                const int acc = ev & 1;
+                if (!mbar_wait(tfull0 + 8 * acc, (ev >> 1) & 1u) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tP = tmem_base + lane_off + acc * C::ACC_COLS;
+                ix_drain<C::ACC_COLS, C::STAGE_BUF>(tP, tP, 0, 1, lane, stage_buf, nstore, nt, args.N,
+                                                   beam0, b, &tmY, args.y4d);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(tempty0_lead + 8 * acc);
+            }
+        }
+        if (lane == 0) bulk_wait<0>();
+        __syncwarp();
+        if (!ok && lane == 0) {
+            atomicOr(args.status, kErrTimeoutEpilogue);
+            *abort_flag = 1;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();                       // no CTA leaves while its peer may signal it
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
+    }
+}
+
+template <int STAGES>
+cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X, float *Y,
+                           cudaStream_t s) {
+    using C = CfgIxW<STAGES>;
+    const tcbf_problem &p = pl.p;
+    if (p.N % 4 != 0 || pl.m_prefix || p.K > kWresMaxK) return cudaErrorInvalidValue;
+    CUtensorMap tmW, tmX, tmY;
+    const int w5d = p.M % 8 == 0 ? 1 : 0;
+    const int x4d = p.N % 32 == 0 ? 1 : 0;
+    const uint64_t wrow = static_cast<uint64_t>(pl.Kp * 2);
+    const uint64_t wplane = static_cast<uint64_t>(w_plane_rows(pl)) * wrow;
+    if (w5d) {
+        const uint64_t dims[5] = {static_cast<uint64_t>(pl.Kp), 8, 2, static_cast<uint64_t>(p.M / 8),
+                                  static_cast<uint64_t>(p.w_batches)};
+        const uint64_t strides[4] = {wrow, wplane, 8 * wrow, 2 * wplane};
+        const uint32_t box[5] = {64, 8, 2, 8, 1};
+        if (encode_tiled(&tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 5, const_cast<void *>(Wp), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
+        const uint64_t dims[3] = {static_cast<uint64_t>(pl.Kp), static_cast<uint64_t>(p.M),
+                                  static_cast<uint64_t>(2 * p.w_batches)};
+        const uint64_t strides[2] = {wrow, wplane};
+        const uint32_t box[3] = {64, 8, 2};
+        if (encode_tiled(&tmW, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(Wp), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const uint64_t xrow = static_cast<uint64_t>(p.N * 4);
+    if (x4d) {
+        const uint64_t dims[4] = {64, static_cast<uint64_t>(p.K), static_cast<uint64_t>(2 * p.N / 64),
+                                  static_cast<uint64_t>(p.batch)};
+        const uint64_t strides[3] = {xrow, 128, static_cast<uint64_t>(p.K) * xrow};
+        const uint32_t box[4] = {64, kWresBks, 2, 1};
+        if (encode_tiled(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(X), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
+        const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.K),
+                                  static_cast<uint64_t>(p.batch)};
+        const uint64_t strides[2] = {xrow, static_cast<uint64_t>(p.K) * xrow};
+        const uint32_t box[3] = {64, kWresBks, 1};
+        if (encode_tiled(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(X), dims,
+                         strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const int y4d = p.N % 16 == 0 ? 1 : 0;
+    if (encode_ix_y(&tmY, Y, p, y4d) != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    IxWArgs a;
+    a.status = pl.status;
+    a.M = static_cast<int>(p.M);
+    a.N = static_cast<int>(p.N);
+    a.K = static_cast<int>(p.K);
+    a.per_w = static_cast<int>(pl.per_w);
+    a.kb64 = static_cast<int>(ceil_div(p.K, 64));
+    a.m_tiles = static_cast<int>(ceil_div(p.M, 128));
+    a.n_tiles = static_cast<int>(ceil_div(p.N, IBN));
+    a.num_kb = static_cast<int>(ceil_div(p.K, kWresBks));
+    a.w5d = w5d;
+    a.x4d = x4d;
+    a.y4d = y4d;
+    const int64_t units = int64_t(a.m_tiles) * p.batch;
+    if (units > 0x7fffffff) return cudaErrorInvalidValue;
+    a.total_units = static_cast<int>(units);
+    const int smem = C::smem_bytes(a.kb64);
+    auto kern = cgemm_ix_wres_kernel<STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         C::smem_bytes(kWresMaxK / 64));
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kIxThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // resident pairs per device at the largest shared-memory size, measured once
+    static std::atomic<int> max_clusters[64];
+    int mc = max_clusters[pl.device & 63].load(std::memory_order_relaxed);
+    if (mc == 0) {
+        cudaLaunchConfig_t q = cfg;
+        q.dynamicSmemBytes = C::smem_bytes(kWresMaxK / 64);
+        q.gridDim = dim3(pl.num_sms / 2 * 2);
+        e = cudaOccupancyMaxActiveClusters(&mc, kern, &q);
+        if (e != cudaSuccess) return e;
+        if (mc < 1) return cudaErrorInvalidConfiguration;
+        max_clusters[pl.device & 63].store(mc, std::memory_order_relaxed);
+    }
+    cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(units, mc)) * 2);
+    e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 struct IxConfig {
     const char *name;
     cudaError_t (*fn)(const tcbf_plan_s &, const void *, const void *, float *, cudaStream_t);
 };
 
 const IxConfig kIxConfigs[] = {
+    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 resident-W (K<=384) BK128 stages3 "
+     "tmem-double",
+     launch_ix_wres<3>},
     {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK128 stages3 tmem-double",
      launch_ix<true, 128, 3>},
     {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK64 stages6 tmem-double",
@@ -576,6 +1001,13 @@ const IxConfig kIxConfigs[] = {
 }  // namespace
 
 int gemm_f16_ix_num_configs() { return static_cast<int>(sizeof(kIxConfigs) / sizeof(kIxConfigs[0])); }
+
+bool gemm_f16_ix_config_valid(int config, int64_t K) {
+    if (config < 0 || config >= gemm_f16_ix_num_configs()) return false;
+    return config != 0 || K <= kWresMaxK;
+}
+
+int gemm_f16_ix_default_config(int64_t K) { return K <= kWresMaxK ? 0 : 1; }
 
 const char *gemm_f16_ix_config_name(int config) {
     if (config < 0 || config >= gemm_f16_ix_num_configs()) return "invalid";

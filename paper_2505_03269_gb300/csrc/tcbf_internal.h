@@ -106,6 +106,10 @@ cudaError_t launch_gemm_f16_stacked(const tcbf_plan_s &pl, const void *Wp, const
 // FP16 GEMM on interleaved complex X (plans with TCBF_FLAG_INTERLEAVED_X).
 int gemm_f16_ix_num_configs();
 const char *gemm_f16_ix_config_name(int config);
+// Configuration 0 (resident weights) needs K <= 384; the default is it there,
+// else the streaming SM-pair configuration.
+bool gemm_f16_ix_config_valid(int config, int64_t K);
+int gemm_f16_ix_default_config(int64_t K);
 cudaError_t launch_gemm_f16_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, float *Y,
                                cudaStream_t s);
 inline bool interleaved_x(const tcbf_plan_s &pl) {

@@ -95,7 +95,7 @@ def test_full_size_radio_block_interleaved_x_sampled():
     B, Bw, M, K, N = 512, 256, 1024, 288, 4096
     geom = ti.radio_geometry(0, M, K, Bw)
     Xh = ti.radio_x(1, B, K, N)
-    for err in _run_block(B, Bw, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X, configs=(0, 1, 2)):
+    for err in _run_block(B, Bw, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X, configs=(0, 1, 2, 3)):
         assert err <= TOL
 
 
@@ -104,7 +104,7 @@ def test_full_size_ultrasound_interleaved_x_sampled():
     M, K, N = 65536, 16384, 256
     geom = ti.ultrasound_geometry()
     Xh = ti.ultrasound_frames(1, K, N)
-    for err in _run_block(1, 1, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X, configs=(0,)):
+    for err in _run_block(1, 1, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X, configs=(1,)):
         assert err <= TOL
 
 

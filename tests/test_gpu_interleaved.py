@@ -20,7 +20,8 @@ import tcbf_inputs as ti
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-5
-CONFIGS = [0, 1, 2]   # SM pairs with 128-K and 64-K stages, one-SM tiles
+CONFIGS = [0, 1, 2, 3]   # resident W (K <= 384), SM pairs with 128-K / 64-K stages, one SM
+LONG_K_CONFIGS = [1, 2, 3]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -131,7 +132,7 @@ def test_fp32_source_rounds_to_nearest():
     assert oracle.rel_frobenius(Y, Yref) <= TOL
 
 
-@pytest.mark.parametrize("config", CONFIGS)
+@pytest.mark.parametrize("config", LONG_K_CONFIGS)
 @pytest.mark.parametrize("K", [4100, 8192, 16384])
 def test_long_k_within_tolerance(config, K):
     """Above K = 4096 the partial sums are promoted to FP32 every 2048 K."""
@@ -187,13 +188,13 @@ def test_autotune_and_graph_replay():
     B, K, N = X.shape[0], X.shape[1], X.shape[2]
     M = W.shape[1]
     with tcbf.Plan(B, M, N, K, tcbf.MODE_FP16, w_batches=4, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
-        assert plan.num_configs() == 3
+        assert plan.num_configs() == 4
         Wp = empty_bytes(plan.packed_size(0))
         Xd = dev(X)
         plan.transpose_pack(0, dev(W), Wp)
         Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
         best, ms = plan.autotune(Wp, Xd, Y, reps=2)
-        assert best in (0, 1, 2) and all(v > 0 for v in ms)
+        assert best in (0, 1, 2, 3) and all(v > 0 for v in ms)
         Y.zero_()
         plan.beamform_fp16(Wp, Xd, Y)
         torch.cuda.synchronize()
@@ -226,6 +227,27 @@ def test_host_pipeline():
         assert plan.last_device_error() == 0
         Y = Yh.numpy().astype(np.float64)
     assert oracle.rel_frobenius(Y[..., 0] + 1j * Y[..., 1], oracle.cgemm(W, X)) <= TOL
+
+
+def test_resident_weights_limited_to_short_k():
+    """Configuration 0 keeps W in shared memory and needs K <= 384: it is
+    the default there and refused above (the streaming pair tiles instead)."""
+    import paper_2505_03269_gb300 as tcbf
+    with tcbf.Plan(1, 8, 8, 384, tcbf.MODE_FP16, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
+        assert plan.get_config() == 0
+    with tcbf.Plan(1, 8, 8, 385, tcbf.MODE_FP16, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
+        assert plan.get_config() == 1
+        with pytest.raises(tcbf.TcbfError):
+            plan.set_config(0)
+
+
+@pytest.mark.parametrize("K", [1, 64, 129, 288, 383, 384])
+def test_resident_weights_across_k(K):
+    """Every resident-W block count (1-6 blocks of 64 K, ragged last block)
+    with several units per pair (uneven unit counts over the pairs)."""
+    W, X = ti.small_fp16(seed=K, M=300, K=K, N=520, B=3)
+    Y = _run(W, X, config=0)
+    assert oracle.rel_frobenius(Y, oracle.cgemm(W, X)) <= TOL
 
 
 def test_flag_rules():
