@@ -118,8 +118,26 @@ typedef enum {
      * kind::mxf8f6f4 with UE8M0 scales).  The scales follow the packed
      * bytes as 512-byte tiles, see the layouts below.  The paper's future
      * work on 8-bit floats (Sec. VI); the benchmark spec's per-tile scales. */
-    TCBF_FLAG_FP8_BLOCK_SCALES = 16u
+    TCBF_FLAG_FP8_BLOCK_SCALES = 16u,
+    /* FP16 only, not combined with TCBF_FLAG_STACKED_X or
+     * TCBF_FLAG_INTERLEAVED_X: the plan chooses between the planar and the
+     * stacked packed-X layout.  At creation it takes TCBF_FLAG_STACKED_X
+     * when the problem is compute-bound: its arithmetic intensity, 8 B M N K
+     * operations over the bytes of the stacked layout's packed W and X and
+     * of Y, is at least TCBF_AUTO_STACKED_MIN_INTENSITY operations per byte
+     * (above the GB300's tensor/HBM ridge of about 280, where the stacked
+     * kernel's two N = 256 MMAs per K step tend to beat the four N = 128
+     * ones), and the planar layout otherwise; tcbf_autotune_layout then
+     * replaces that guess by measurement.  The chosen bit replaces this one
+     * in the plan's flags (tcbf_plan_flags): callers that write packed X
+     * themselves read it there; tcbf_transpose_pack and tcbf_packed_size
+     * follow it. */
+    TCBF_FLAG_AUTO_LAYOUT = 32u
 } tcbf_flag;
+
+/* The intensity (operations per byte) from which TCBF_FLAG_AUTO_LAYOUT
+ * starts a plan on the stacked layout. */
+#define TCBF_AUTO_STACKED_MIN_INTENSITY 400
 
 /*
  * Packed operand layouts (produced by tcbf_transpose_pack or
@@ -173,6 +191,10 @@ tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p, int device
 /* Destroy a plan (NULL is accepted).  The caller must not have work that
  * uses the plan in flight. */
 tcbf_status tcbf_plan_destroy(tcbf_plan_t plan);
+
+/* The plan's flags as it uses them: the caller's, with
+ * TCBF_FLAG_AUTO_LAYOUT replaced by the layout it chose. */
+tcbf_status tcbf_plan_flags(tcbf_plan_t plan, uint32_t *flags);
 
 /* Bytes of the packed operand `which` (0 = W, 1 = X) for this plan. */
 tcbf_status tcbf_packed_size(tcbf_plan_t plan, int which, size_t *bytes);
@@ -409,6 +431,27 @@ tcbf_status tcbf_plan_set_batch_rows(tcbf_plan_t plan, const int64_t *rows);
  */
 tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const void *Xp, void *Y, int reps,
                           tcbf_stream_t stream, int *best, float *ms_per_config);
+
+/*
+ * Layout autotuner for plans created with TCBF_FLAG_AUTO_LAYOUT (else
+ * TCBF_ERR_INVALID_ARG).  For the planar and the stacked packed-X layout in
+ * turn it packs X_src ([batch][K][N] complex of src_type, the
+ * tcbf_transpose_pack source) into a scratch buffer it allocates, runs
+ * tcbf_autotune over that layout's configurations (`reps` rounds) and times
+ * the step, pack + beamform with the best configuration (best of `reps`
+ * after one warm-up).  The plan keeps the faster layout and its
+ * configuration; *flags (nullable) receives the plan's new flags and
+ * ms_per_layout (nullable, 2 entries) the step milliseconds of the planar
+ * and the stacked layout.  Wp is the packed W (the same bytes for both
+ * layouts); Y is overwritten.  Synchronises the stream and frees the
+ * scratch before it returns.  When the layout changes, packed X made
+ * before the call no longer fits the plan (repack it; tcbf_packed_size(1)
+ * may have changed), and the plan's tcbf_beamform_host staging and
+ * captured graph are released.
+ */
+tcbf_status tcbf_autotune_layout(tcbf_plan_t plan, const void *Wp, const void *X_src, int src_type,
+                                 void *Y, int reps, tcbf_stream_t stream, uint32_t *flags,
+                                 float *ms_per_layout);
 
 /*
  * Capture one step into a CUDA graph owned by the plan: the transpose/pack

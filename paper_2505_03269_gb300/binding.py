@@ -25,6 +25,7 @@ FLAG_FP8_HI_ONLY = 2
 FLAG_FP8_FOUR_PRODUCTS = 4
 FLAG_INTERLEAVED_X = 8
 FLAG_FP8_BLOCK_SCALES = 16
+FLAG_AUTO_LAYOUT = 32
 
 # every symbol include/tcbf.h declares
 EXPORTED = [
@@ -36,6 +37,7 @@ EXPORTED = [
     "tcbf_plan_set_batch_rows", "tcbf_autotune", "tcbf_graph_capture", "tcbf_graph_launch",
     "tcbf_beamform_host", "tcbf_debug_drop_fill", "tcbf_unpack_bits", "tcbf_beamform_tf32",
     "tcbf_expand_1bit", "tcbf_beamform_1bit_expanded", "tcbf_transpose_pack_expanded",
+    "tcbf_plan_flags", "tcbf_autotune_layout",
 ]
 
 
@@ -83,6 +85,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "tcbf_beamform_tf32": [vp, vp, vp, vp, vp],
         "tcbf_plan_num_configs": [vp, ctypes.POINTER(i32)],
         "tcbf_plan_get_config": [vp, ctypes.POINTER(i32)],
+        "tcbf_plan_flags": [vp, ctypes.POINTER(u32)],
+        "tcbf_autotune_layout": [vp, vp, vp, i32, vp, i32, vp, ctypes.POINTER(u32), vp],
         "tcbf_plan_set_config": [vp, i32],
         "tcbf_beamform_fp16_noalloc": [ctypes.POINTER(Problem), i32, vp, vp, i32, vp, i32, vp],
         "tcbf_plan_set_batch_rows": [vp, vp],
@@ -141,7 +145,10 @@ class Plan:
         self.w_batches = w_batches or batch
         self.mode = mode
         self.device = device
-        self.flags = flags
+        # the plan's own flags: TCBF_FLAG_AUTO_LAYOUT resolved to a layout
+        f = ctypes.c_uint32()
+        _check(lib.tcbf_plan_flags(h, ctypes.byref(f)), "tcbf_plan_flags")
+        self.flags = f.value
 
     def close(self):
         if getattr(self, "handle", None):
@@ -270,6 +277,19 @@ class Plan:
                                        _stream(stream), ctypes.byref(best),
                                        ctypes.cast(ms, ctypes.c_void_p)), "tcbf_autotune")
         return best.value, list(ms)
+
+    def autotune_layout(self, Wp, X_src, Y, src_type=SRC_CF16, reps=3, stream=None):
+        """tcbf_autotune_layout (plans made with FLAG_AUTO_LAYOUT): the faster
+        of the planar and stacked layouts, by the timed pack + beamform step,
+        with its best configuration.  Returns (flags, [planar_ms, stacked_ms])
+        and updates self.flags; packed X must be remade when it changed."""
+        f = ctypes.c_uint32()
+        ms = (ctypes.c_float * 2)()
+        _check(self._lib.tcbf_autotune_layout(self.handle, _ptr(Wp), _ptr(X_src), int(src_type),
+                                              _ptr(Y), int(reps), _stream(stream), ctypes.byref(f),
+                                              ms), "tcbf_autotune_layout")
+        self.flags = f.value
+        return f.value, [ms[0], ms[1]]
 
     def graph_capture(self, Xsrc, Xp, Wp, Y, src_type=SRC_CF16):
         _check(self._lib.tcbf_graph_capture(self.handle, _ptr(Xsrc), int(src_type), _ptr(Xp),

@@ -124,6 +124,28 @@ TCBF_EXPORT const char *tcbf_status_string(tcbf_status s) {
     return "unknown status";
 }
 
+namespace {
+
+// The layout TCBF_FLAG_AUTO_LAYOUT resolves to: stacked X when the shape's
+// operations per byte of the stacked layout (packed W, packed X with its
+// third plane, Y) reach the threshold, planar otherwise.
+uint32_t auto_layout(const tcbf_problem &q) {
+    const double Kp = static_cast<double>(round_up(q.K, 8));
+    const double ops = 8.0 * q.batch * q.M * q.N * q.K;
+    const double bytes = 4.0 * q.w_batches * q.M * Kp + 6.0 * q.batch * q.N * Kp +
+                         8.0 * q.batch * q.M * q.N;
+    return ops >= TCBF_AUTO_STACKED_MIN_INTENSITY * bytes ? TCBF_FLAG_STACKED_X : 0u;
+}
+
+// The FP16 transpose/pack of X into the plan's current layout.
+cudaError_t pack_x_into(const tcbf_plan_s &pl, int src_type, const void *src, void *dst,
+                        cudaStream_t s) {
+    return interleaved_x(pl) ? launch_copy_x_cf16(pl, src_type, src, dst, s)
+                             : launch_pack_f16_x(pl, src_type, src, dst, s);
+}
+
+}  // namespace
+
 TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p, int device) {
     if (!out) return TCBF_ERR_INVALID_ARG;
     *out = nullptr;
@@ -138,7 +160,10 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     const uint32_t fp8_flags = TCBF_FLAG_FP8_HI_ONLY | TCBF_FLAG_FP8_FOUR_PRODUCTS;
     const uint32_t f16_flags = TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X;
     const uint32_t blk = TCBF_FLAG_FP8_BLOCK_SCALES;
-    if ((q.flags & ~(f16_flags | fp8_flags | blk)) != 0) return TCBF_ERR_INVALID_ARG;
+    const uint32_t autol = TCBF_FLAG_AUTO_LAYOUT;
+    if ((q.flags & ~(f16_flags | fp8_flags | blk | autol)) != 0) return TCBF_ERR_INVALID_ARG;
+    if ((q.flags & autol) && (q.mode != TCBF_MODE_FP16 || (q.flags & f16_flags)))
+        return TCBF_ERR_INVALID_ARG;
     if ((q.flags & f16_flags) && q.mode != TCBF_MODE_FP16) return TCBF_ERR_INVALID_ARG;
     if ((q.flags & f16_flags) == f16_flags) return TCBF_ERR_INVALID_ARG;   // one or the other
     if ((q.flags & (fp8_flags | blk)) && q.mode != TCBF_MODE_FP8SPLIT) return TCBF_ERR_INVALID_ARG;
@@ -147,6 +172,8 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
         return TCBF_ERR_UNSUPPORTED;
     // 1-bit sums are exact integers in the FP32 accumulators while 2K < 2^24
     if (q.mode == TCBF_MODE_1BIT && q.K > (int64_t(1) << 22)) return TCBF_ERR_UNSUPPORTED;
+    const bool autolayout = (q.flags & autol) != 0;
+    if (autolayout) q.flags = (q.flags & ~autol) | auto_layout(q);
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TCBF_ERR_UNSUPPORTED;
@@ -158,6 +185,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     auto *pl = new (std::nothrow) tcbf_plan_s;
     if (!pl) return TCBF_ERR_OOM;
     pl->p = q;
+    pl->auto_layout = autolayout;
     pl->device = device;
     pl->num_sms = prop.multiProcessorCount;
     pl->per_w = q.batch / q.w_batches;
@@ -413,6 +441,12 @@ TCBF_EXPORT tcbf_status tcbf_plan_num_configs(tcbf_plan_t plan, int *count) {
     return TCBF_OK;
 }
 
+TCBF_EXPORT tcbf_status tcbf_plan_flags(tcbf_plan_t plan, uint32_t *flags) {
+    if (!plan || !flags) return TCBF_ERR_INVALID_ARG;
+    *flags = plan->p.flags;
+    return TCBF_OK;
+}
+
 TCBF_EXPORT tcbf_status tcbf_plan_get_config(tcbf_plan_t plan, int *config) {
     if (!plan || !config) return TCBF_ERR_INVALID_ARG;
     *config = plan->config;
@@ -610,6 +644,79 @@ TCBF_EXPORT tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const vo
     plan->config = (st == TCBF_OK && best_c >= 0) ? best_c : saved;
     if (best) *best = plan->config;
     return st;
+}
+
+TCBF_EXPORT tcbf_status tcbf_autotune_layout(tcbf_plan_t plan, const void *Wp, const void *X_src,
+                                             int src_type, void *Y, int reps, tcbf_stream_t stream,
+                                             uint32_t *flags, float *ms_per_layout) {
+    if (!plan || !Wp || !X_src || !Y || reps < 1) return TCBF_ERR_INVALID_ARG;
+    if (!plan->auto_layout) return TCBF_ERR_INVALID_ARG;
+    if (src_type != TCBF_SRC_CF16 && src_type != TCBF_SRC_CF32) return TCBF_ERR_INVALID_ARG;
+    if (!aligned16(Wp) || !aligned16(X_src) || !aligned16(Y)) return TCBF_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok()) return TCBF_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint32_t base = plan->p.flags & ~(TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X);
+    const uint32_t old_flags = plan->p.flags;
+    const int old_config = plan->config;
+    const uint32_t layouts[2] = {0u, TCBF_FLAG_STACKED_X};
+    // one scratch for the packed X of either layout (the stacked one is larger)
+    plan->p.flags = base | TCBF_FLAG_STACKED_X;
+    size_t xbytes = 0;
+    tcbf_packed_size(plan, 1, &xbytes);
+    void *xp = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaMalloc(&xp, xbytes);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    tcbf_status st = from_cuda(ce);
+    float ms[2] = {-1.f, -1.f};
+    int cfg[2] = {0, 0};
+    // each layout: its configurations autotuned on the packed X, then the
+    // step (pack + beamform with the best configuration) timed, best of reps
+    for (int l = 0; l < 2 && st == TCBF_OK; ++l) {
+        plan->p.flags = base | layouts[l];
+        plan->config = 0;
+        ce = pack_x_into(*plan, src_type, X_src, xp, s);
+        st = from_cuda(ce);
+        if (st == TCBF_OK) st = tcbf_autotune(plan, Wp, xp, Y, reps, stream, &cfg[l], nullptr);
+        for (int r = 0; r < reps + 1 && st == TCBF_OK; ++r) {
+            ce = cudaEventRecord(e0, s);
+            if (ce == cudaSuccess) ce = pack_x_into(*plan, src_type, X_src, xp, s);
+            if (ce == cudaSuccess) ce = launch_beamform(*plan, Wp, xp, Y, s);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            st = from_cuda(ce);
+            if (st == TCBF_OK && r > 0 && (ms[l] < 0.f || t < ms[l])) ms[l] = t;   // r = 0 warms up
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (xp) cudaFree(xp);
+    if (st != TCBF_OK) {
+        plan->p.flags = old_flags;
+        plan->config = old_config;
+        return st;
+    }
+    const int best = ms[1] < ms[0] ? 1 : 0;
+    plan->p.flags = base | layouts[best];
+    plan->config = cfg[best];
+    if (plan->p.flags != old_flags) {
+        // staging and a captured step sized for the old layout
+        host_pipe_destroy(*plan);
+        if (plan->graph_exec) {
+            cudaGraphExecDestroy(plan->graph_exec);
+            plan->graph_exec = nullptr;
+        }
+    }
+    if (flags) *flags = plan->p.flags;
+    if (ms_per_layout) {
+        ms_per_layout[0] = ms[0];
+        ms_per_layout[1] = ms[1];
+    }
+    return TCBF_OK;
 }
 
 TCBF_EXPORT tcbf_status tcbf_graph_capture(tcbf_plan_t plan, const void *X_src, int src_type,

@@ -112,16 +112,27 @@ __device__ __forceinline__ void ix_drain(uint32_t tP, uint32_t tS, int ch, int c
         tmem_st_wait();
         return;
     }
+    // the next block's tensor-memory load is issued before this block is
+    // staged and stored, so its latency overlaps the stores
+    float v[32];
+    tmem_ld_16x256b_x8_nowait(tP, v);
 #pragma unroll 1
     for (int c = 0; c < ACC_COLS / 64; ++c) {
-        float v[32];
-        tmem_ld_16x256b_x8(tP + 64 * c, v);
+        tmem_wait_ld_32(v);
         if (chunks > 1) {
             float sv[32];
             tmem_ld_16x256b_x8(tS + 64 * c, sv);
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
         }
+        // v[4i..4i+3] = Wr Xr, Wr Xi, Wi Xr, Wi Xi of sample 4i + sq
+        float re[8], im[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            re[i] = __fsub_rn(v[4 * i], v[4 * i + 3]);
+            im[i] = __fadd_rn(v[4 * i + 1], v[4 * i + 2]);
+        }
+        if (c + 1 < ACC_COLS / 64) tmem_ld_16x256b_x8_nowait(tP + 64 * (c + 1), v);
         const int n0 = nt * IBN + 32 * c;     // first sample of the block
         if (n0 < N) {
             const uint32_t buf = stage_buf + (nstore & 1) * STAGE_BUF;
@@ -129,13 +140,10 @@ __device__ __forceinline__ void ix_drain(uint32_t tP, uint32_t tS, int ch, int c
             __syncwarp();
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                // v[4i..4i+3] = Wr Xr, Wr Xi, Wi Xr, Wi Xi of sample 4i + sq
-                const float re = __fsub_rn(v[4 * i], v[4 * i + 3]);
-                const float im = __fadd_rn(v[4 * i + 1], v[4 * i + 2]);
                 const int s16 = 4 * (i & 3) + sq;          // sample within its box
                 const uint32_t addr = buf + (i >> 2) * 1024 + rb * 128 +
                                       ((((s16 >> 1) ^ rb) & 7) << 4) + ((s16 & 1) << 3);
-                st_shared_v2(addr, re, im);
+                st_shared_v2(addr, re[i], im[i]);
             }
             fence_async_smem();
             __syncwarp();

@@ -43,6 +43,9 @@ struct tcbf_plan_s {
     // (N % 4 != 0, uneven batch rows): packed X planes the beamform call
     // packs into before running the planar kernel (nullptr otherwise)
     void *ix_planes = nullptr;
+    // created with TCBF_FLAG_AUTO_LAYOUT: tcbf_autotune_layout may change
+    // the packed-X layout
+    bool auto_layout = false;
 };
 
 namespace tcbf {

@@ -60,7 +60,9 @@ def _create(lib, **kw):
                                  dict(flags=1, mode=1), dict(flags=1, mode=2), dict(flags=16),
                                  dict(flags=8, mode=1), dict(flags=8, mode=2), dict(flags=9),
                                  dict(flags=4, mode=0), dict(flags=2, mode=2),
-                                 dict(flags=6, mode=1), dict(M=-5)])
+                                 dict(flags=6, mode=1), dict(M=-5),
+                                 dict(flags=32, mode=1), dict(flags=32, mode=2), dict(flags=33),
+                                 dict(flags=40), dict(flags=64)])
 def test_plan_create_rejects_bad_shapes(lib, bad):
     st, h = _create(lib, **bad)
     assert st == 1          # TCBF_ERR_INVALID_ARG, before any device query
@@ -84,6 +86,8 @@ def test_null_arguments(lib):
     assert lib.tcbf_last_device_error(None) == 1
     assert lib.tcbf_debug_drop_fill(None, ctypes.c_int64(0)) == 1
     assert lib.tcbf_unpack_bits(None, 0, None, None, 0, None) == 1
+    f = ctypes.c_uint32()
+    assert lib.tcbf_plan_flags(None, ctypes.byref(f)) == 1
     assert lib.tcbf_plan_destroy(None) == 0
 
 

@@ -145,3 +145,94 @@ def test_stacked_host_pipeline():
         assert plan.last_device_error() == 0
     Yn = Yh.numpy().astype(np.float64)
     assert np.array_equal(Yn[..., 0] + 1j * Yn[..., 1], Yd)
+
+
+def _auto_threshold():
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "tcbf.h")).read()
+    return float(re.search(r"#define TCBF_AUTO_STACKED_MIN_INTENSITY (\d+)", hdr).group(1))
+
+
+def _intensity(B, Bw, M, N, K):
+    """8 B M N K operations over the bytes of the stacked layout: packed W
+    (2 planes), packed X (3 planes), both padded to K rounded up to 8, and
+    the complex64 output."""
+    Kp = (K + 7) // 8 * 8
+    return 8.0 * B * M * N * K / (2 * 2 * Bw * M * Kp + 3 * 2 * B * N * Kp + 8 * B * M * N)
+
+
+@pytest.mark.parametrize("B,Bw,M,N,K", [(1, 1, 4096, 4096, 4096), (1, 1, 8192, 8192, 8192),
+                                        (512, 256, 1024, 4096, 288), (1, 1, 256, 256, 256),
+                                        (1, 1, 1024, 1024, 4096), (1, 1, 1024, 1024, 2048),
+                                        (64, 64, 65536 // 64, 128, 16384)])
+def test_auto_layout_follows_the_intensity(B, Bw, M, N, K):
+    """TCBF_FLAG_AUTO_LAYOUT resolves to the stacked layout exactly when the
+    shape's operations per byte reach the documented threshold."""
+    from paper_2505_03269_gb300 import FLAG_AUTO_LAYOUT, FLAG_STACKED_X, MODE_FP16, Plan
+    with Plan(B, M, N, K, MODE_FP16, w_batches=Bw, flags=FLAG_AUTO_LAYOUT) as plan:
+        want = FLAG_STACKED_X if _intensity(B, Bw, M, N, K) >= _auto_threshold() else 0
+        assert plan.flags == want
+        Kp = (K + 7) // 8 * 8
+        assert plan.packed_size(1) == (3 if want else 2) * B * N * Kp * 2
+
+
+def test_auto_layout_plan_computes_the_stacked_product():
+    """An auto-layout plan on a compute-bound shape packs and multiplies as
+    the stacked plan does (bit for bit), and matches the oracle."""
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_AUTO_LAYOUT, FLAG_STACKED_X, MODE_FP16, Plan
+    M, N, K = 1024, 1024, 4096
+    assert _intensity(1, 1, M, N, K) >= _auto_threshold()
+    W, X = ti.small_fp16(seed=77, M=M, K=K, N=N, B=1)
+    with Plan(1, M, N, K, MODE_FP16, flags=FLAG_AUTO_LAYOUT) as plan:
+        assert plan.flags == FLAG_STACKED_X
+        Wp = empty_bytes(plan.packed_size(0))
+        Xp = empty_bytes(plan.packed_size(1))
+        Y = torch.full((1, M, N, 2), float("nan"), dtype=torch.float32, device="cuda")
+        plan.transpose_pack(0, dev(W), Wp)
+        plan.transpose_pack(1, dev(X), Xp)
+        plan.beamform_fp16(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        Yh = Y.cpu().numpy().astype(np.float64)
+    got = Yh[..., 0] + 1j * Yh[..., 1]
+    assert np.array_equal(got, _run(W, X, stacked=True))
+    rows = slice(0, 96)
+    ref = oracle.cgemm(W[:, rows], X)
+    assert oracle.rel_frobenius(got[:, rows], ref) <= TOL
+
+
+def test_autotune_layout_picks_a_timed_layout_and_stays_correct():
+    """tcbf_autotune_layout times both layouts' steps and keeps the faster
+    with its tuned configuration; it refuses plans made without the auto
+    flag, and after repacking X for the chosen layout the plan's product is
+    within the FP16 bar of the oracle."""
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import (FLAG_AUTO_LAYOUT, FLAG_STACKED_X, MODE_FP16, Plan,
+                                        TcbfError)
+    B, M, N, K = 2, 384, 320, 1000
+    W, X = ti.small_fp16(seed=5, M=M, K=K, N=N, B=B)
+    Wd, Xd = dev(W), dev(X)
+    with Plan(B, M, N, K, MODE_FP16, flags=0) as fixed:
+        Wp = empty_bytes(fixed.packed_size(0))
+        Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
+        fixed.transpose_pack(0, Wd, Wp)
+        with pytest.raises(TcbfError):          # not an auto-layout plan
+            fixed.autotune_layout(Wp, Xd, Y)
+    with Plan(B, M, N, K, MODE_FP16, flags=FLAG_AUTO_LAYOUT) as plan:
+        flags, ms = plan.autotune_layout(Wp, Xd, Y, reps=2)
+        assert flags in (0, FLAG_STACKED_X) and plan.flags == flags
+        assert ms[0] > 0 and ms[1] > 0
+        assert (ms[1] < ms[0]) == (flags == FLAG_STACKED_X)
+        Xp = empty_bytes(plan.packed_size(1))
+        plan.transpose_pack(1, Xd, Xp)
+        Y.fill_(float("nan"))
+        plan.beamform_fp16(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        Yh = Y.cpu().numpy().astype(np.float64)
+    got = Yh[..., 0] + 1j * Yh[..., 1]
+    assert oracle.rel_frobenius(got, oracle.cgemm(W, X)) <= TOL
