@@ -91,3 +91,11 @@ def test_noalloc_matches_plan_path_on_consecutive_calls():
         X16 = X.astype(np.float16) if c["f32"] else X
         ref = oracle.cgemm(W, X16)
         assert oracle.rel_frobenius(Yc[..., 0] + 1j * Yc[..., 1], ref) <= TOL
+        # the same call without the status check (no synchronisation inside)
+        Y.fill_(float("nan"))
+        st = binding.beamform_fp16_noalloc(c["B"], c["M"], c["N"], c["K"], Wp, Xd, Y,
+                                           w_batches=c["Bw"], device=0, src_type=src_type,
+                                           check=False)
+        assert st == 0, binding.status_string(st)
+        torch.cuda.synchronize()
+        assert np.array_equal(Y.cpu().numpy(), Yref)
