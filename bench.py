@@ -81,6 +81,16 @@ WORKLOADS = {
         mode="1bit", B=1, M=32768, N=8192, K=65536, w_batches=1, geometry=None, x_phase=True,
         desc="paper tuning shape 1-bit with K reduced: 32768 x 8192 x 65536 (the paper's K is "
              "524288), +-1+-i values, exact int32 output"),
+    # the paper's small roofline shapes (Sec. IV-A, Fig. 3), memory-bound
+    "paper_fp16_batched": dict(
+        mode="fp16", B=256, M=1024, N=1024, K=64, w_batches=256, geometry="random",
+        layout="interleaved",
+        desc="paper roofline shape FP16: 256 products of 1024 x 1024 x 64, W = exp(i phi) "
+             "random phases per product, X complex Gaussian, read as it lies"),
+    "paper_int1_batched": dict(
+        mode="1bit", B=256, M=1024, N=1024, K=256, w_batches=256, geometry=None,
+        desc="paper roofline shape 1-bit: 256 products of 1024 x 1024 x 256, random sign "
+             "weights per product, X = signs of complex Gaussian samples, exact int32 output"),
 }
 
 
@@ -339,8 +349,8 @@ def oracle_sample(w, seconds_target):
 
     geom = geometry_of(w)
     if w["geometry"] == "random":
-        X = host_x(w)
-        Wr = ti.random_phase_rows(0, 256, w["K"])
+        X = host_x(w)[:1]
+        Wr = ti.random_phase_rows(0, min(256, w["M"]), w["K"])
 
         def run(rows):
             t0 = time.perf_counter()
@@ -348,9 +358,9 @@ def oracle_sample(w, seconds_target):
             return time.perf_counter() - t0
         rows = 4
         dt = run(rows)
-        rows = max(4, min(256, int(rows * seconds_target / max(dt, 1e-3))))
+        rows = max(4, min(Wr.shape[1], int(rows * seconds_target / max(dt, 1e-3))))
         dt = run(rows)
-        return 8.0 * rows * w["N"] * w["K"], dt, f"{rows} of {w['M']} beam rows of the product"
+        return 8.0 * rows * w["N"] * w["K"], dt, f"{rows} of {w['M']} beam rows of one product"
     if w["geometry"] == "ultrasound":
         X = host_x(w)
 
@@ -461,7 +471,7 @@ class GpuWorkload:
             self.Wp.copy_(torch.from_numpy(self.Wbits.view(np.uint8).ravel()).cuda())
         elif w["geometry"] == "random":
             import tcbf_inputs as ti
-            self.Wh = ti.random_phase_rows(0, M, K)
+            self.Wh = ti.random_phase_rows(0, Bw * M, K).reshape(Bw, M, K, 2)
             self.plan.transpose_pack(0, torch.from_numpy(self.Wh).cuda(), self.Wp)
         else:
             self.geom = geometry_of(w)
