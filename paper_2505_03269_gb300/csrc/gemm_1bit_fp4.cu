@@ -23,9 +23,11 @@
 //   warps 2-5   scale-factor fill at start, then the epilogue: TMEM ->
 //               int32 pairs -> staged TMA stores (two buffers per warp),
 //               releasing an accumulator on the even CTA's barrier
-// Tensor memory: the accumulators from column 0, the scale factors in the
-// columns above them up to 512 (from 256, or 384 for two 192-column
-// accumulators), every byte UE8M0 127, so any scale layout reads 1.0.
+// Tensor memory: the accumulators from column 0 (two of them at columns 0
+// and a multiple of 64), the scale factors in the columns above them up to
+// 512 (from 256, 384 for two 192-column accumulators, 480 for two of 224
+// columns at 0 and 256), every byte UE8M0 127, so any scale layout the MMA
+// reads returns 1.0.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -275,18 +277,21 @@ struct CfgFp4 {
     static constexpr int W_BYTES = 2 * W_PLANE;                 // Wr, Wi (this CTA's rows)
     static constexpr int STAGE_BYTES = W_BYTES + 2 * X_PLANE;  // + this CTA's halves of B1, B2
     static constexpr int ACC_COLS = 2 * SBN;                    // [Re | Im]
-    // two accumulators when they leave at least 64 columns for the scales
-    static constexpr int ACC_BUFS = 2 * ACC_COLS + 64 <= 512 ? 2 : 1;
+    // accumulators start at multiples of 64 columns
+    static constexpr int ACC_STRIDE = (ACC_COLS + 63) / 64 * 64;
     static constexpr int TMEM_COLS = 512;
-    // scale factors: A from SF_COL, B from the middle of the rest
-    static constexpr int SF_COL = (ACC_BUFS * ACC_COLS + 63) / 64 * 64;
+    // two accumulators when they leave at least 32 columns for the scales
+    static constexpr int ACC_BUFS = ACC_STRIDE + ACC_COLS + 32 <= TMEM_COLS ? 2 : 1;
+    // scale factors: A from SF_COL, B from the middle of the rest (the MMA
+    // reads at most 4 columns of A's and 8 of B's; all of them hold 2^0)
+    static constexpr int SF_COL = ((ACC_BUFS - 1) * ACC_STRIDE + ACC_COLS + 31) / 32 * 32;
     static constexpr int SFB_COL = SF_COL + (TMEM_COLS - SF_COL) / 2;
     // two 32 x 128-byte output buffers per epilogue warp: one store in
     // flight while the next block is staged (the output stream of short-K
     // products is bound by the stores a warp keeps in flight)
     static constexpr int STAGING_BYTES = 4 * 2 * 4096;
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + STAGING_BYTES + 256 + 1024;
-    static_assert(SF_COL + 64 <= TMEM_COLS, "room for the scale columns");
+    static_assert(SF_COL + 32 <= TMEM_COLS, "room for the scale columns");
     static_assert(SBN % 16 == 0 && SBN >= 32 && 2 * SBN <= 256, "pair N");
     static_assert(X_PLANE % 1024 == 0, "swizzle atoms");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem_base + acc * C::ACC_COLS;
+                const uint32_t d = tmem_base + acc * C::ACC_STRIDE;
                 for (int kb = 0; kb < args.num_kb; ++kb) {
                     if (!mbar_wait(full0 + 8 * stage, phase) || *abort_flag) {
                         ok = false;
@@ -502,7 +507,7 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t tP = tmem_base + lane_off + acc * C::ACC_COLS;
+            const uint32_t tP = tmem_base + lane_off + acc * C::ACC_STRIDE;
 #pragma unroll 1
             for (int c = 0; c < SBN / 16; ++c) {
                 float re[16], im[16];
@@ -763,7 +768,8 @@ cudaError_t launch_gemm_1bit_fp4_expanded(const tcbf_plan_s &pl, int32_t *Y, cud
     if (!gemm_1bit_fp4_usable(pl)) return cudaErrorNotSupported;
     if (variant == 0) return launch_fp4_pair<128, 3>(pl, Y, s);
     if (variant == 1) return launch_fp4_pair<64, 4>(pl, Y, s);
-    return launch_fp4_pair<96, 3>(pl, Y, s);
+    if (variant == 2) return launch_fp4_pair<96, 3>(pl, Y, s);
+    return launch_fp4_pair<112, 3>(pl, Y, s);
 }
 
 cudaError_t launch_gemm_1bit_fp4(const tcbf_plan_s &pl, const uint32_t *Wb, const uint32_t *Xb,

@@ -178,7 +178,7 @@ bool gemm_1bit_config_fp4(int config);
 // the E2M1 planes (reserve: allocate once per plan; release: free), whether
 // a plan can take the path (scratch present, K <= 2^23, no uneven batches),
 // and the launch (variant 0: 256 x 128 pair tiles, one accumulator;
-// 1: 256 x 64, two; 2: 256 x 96, two).  cudaErrorNotSupported when the
+// 1: 256 x 64, two; 2: 256 x 96, two; 3: 256 x 112, two).  cudaErrorNotSupported when the
 // plan cannot take it.
 size_t gemm_1bit_fp4_scratch_bytes(const tcbf_plan_s &pl);
 cudaError_t gemm_1bit_fp4_reserve(tcbf_plan_s &pl);

@@ -45,7 +45,7 @@ def run_1bit(Wb, Xb, K, config=None):
 
 # 5-7: the 4-bit tensor path (bits expanded to E2M1 planes in the plan's
 # scratch, block-scaled MMAs on SM pairs)
-@pytest.mark.parametrize("config", [0, 1, 4, 5, 6, 7])
+@pytest.mark.parametrize("config", [0, 1, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("B,M,N,K", [(1, 1, 1, 1), (2, 3, 5, 7), (2, 33, 70, 45),
                                      (1, 128, 256, 1024), (3, 130, 300, 200),
                                      (2, 200, 64, 129), (1, 64, 1000, 640)])
@@ -55,7 +55,7 @@ def test_random_bits_bit_exact(config, B, M, N, K):
     assert np.array_equal(Y, oracle.bgemm(Wb, Xb, K))
 
 
-@pytest.mark.parametrize("config", [0, 4, 5, 6, 7])
+@pytest.mark.parametrize("config", [0, 4, 5, 6, 7, 8])
 def test_shared_weights_bit_exact(config):
     g = ti.rng(4)
     K = 300
@@ -99,7 +99,7 @@ def test_pack_then_gemm_pipeline():
     assert np.array_equal(Yg, oracle.bgemm(Wb, Xb, K))
 
 
-@pytest.mark.parametrize("config", [0, 5, 6, 7])
+@pytest.mark.parametrize("config", [0, 5, 6, 7, 8])
 def test_full_size_radio_1bit_sampled(config):
     """64 channels x 2048 beams x 1024 receivers x 8192 samples: the whole
     launch as timed, checked bit-exact on sampled row/column blocks."""
@@ -143,11 +143,11 @@ def test_default_configuration_is_the_4bit_path():
 
 
 def test_default_configuration_threshold_in_k():
-    """K <= 1024 starts on the 256 x 96 two-accumulator tiles (configuration
-    7), larger K on the 256 x 128 one-accumulator tiles (configuration 5)."""
+    """K <= 1024 starts on the 256 x 112 two-accumulator tiles (configuration
+    8), larger K on the 256 x 128 one-accumulator tiles (configuration 5)."""
     from paper_2505_03269_gb300 import MODE_1BIT, Plan
     with Plan(1, 256, 256, 1024, MODE_1BIT) as plan:
-        assert plan.get_config() == 7, plan.config_name(plan.get_config())
+        assert plan.get_config() == 8, plan.config_name(plan.get_config())
     with Plan(1, 256, 256, 1025, MODE_1BIT) as plan:
         assert plan.get_config() == 5, plan.config_name(plan.get_config())
 
@@ -232,7 +232,7 @@ def test_radio_signs_from_geometry_exact():
     assert np.array_equal(got, oracle.bgemm(Wb, Xb, K))
 
 
-@pytest.mark.parametrize("config", [5, 6, 7])
+@pytest.mark.parametrize("config", [5, 6, 7, 8])
 @pytest.mark.parametrize("B,M,N,K,f32", [(2, 300, 200, 333, False), (3, 130, 70, 64, False),
                                          (1, 257, 129, 1025, True), (2, 64, 33, 31, True)])
 def test_pack_straight_into_e2m1_planes(config, B, M, N, K, f32):
