@@ -89,7 +89,7 @@ struct IxArgs {
 // them, 32 samples at a time: two 1 KB boxes of 8 beams x 16 samples, one
 // 4-D store of both when N % 16 == 0 (y4d: Y seen as 16-sample chunks x
 // beams x batches), else two 3-D stores.
-template <int ACC_COLS, int STAGE_BUF>
+template <int ACC_COLS, int STAGE_BUF, int NBUF = 2>
 __device__ __forceinline__ void ix_drain(uint32_t tP, uint32_t tS, int ch, int chunks, int lane,
                                          uint32_t stage_buf, int &nstore, int nt, int N, int beam0,
                                          int b, const CUtensorMap *tmY, int y4d) {
@@ -135,8 +135,13 @@ __device__ __forceinline__ void ix_drain(uint32_t tP, uint32_t tS, int ch, int c
         if (c + 1 < ACC_COLS / 64) tmem_ld_16x256b_x8_nowait(tP + 64 * (c + 1), v);
         const int n0 = nt * IBN + 32 * c;     // first sample of the block
         if (n0 < N) {
-            const uint32_t buf = stage_buf + (nstore & 1) * STAGE_BUF;
-            if (lane == 0) bulk_wait_read<1>();   // the buffer's last stores have read it
+            const uint32_t buf = stage_buf + (NBUF == 2 ? (nstore & 1) * STAGE_BUF : 0);
+            if (lane == 0) {                       // the buffer's last stores have read it
+                if (NBUF == 2)
+                    bulk_wait_read<1>();
+                else
+                    bulk_wait_read<0>();
+            }
             __syncwarp();
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -611,25 +616,32 @@ cudaError_t launch_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, floa
 // tile), while the producer already streams the new unit's X.  Units run
 // pair rows fastest within a batch, so the pairs working at one time share
 // each batch's X in L2.  One accumulation chunk (no promotion at this K).
+// The X ring's depth is what bounds the kernel (its loads wait on L2
+// latency, not bandwidth: half the X bytes per stage ran in the same time),
+// so the four-stage form (K <= 320: up to five W blocks) gives up the
+// second staging buffer of each epilogue warp to fit a fourth 32 KB stage
+// (radio block 4.52 -> 3.97 ms); the three-stage form keeps two staging
+// buffers and covers K <= 384.
 // ===========================================================================
-constexpr int kWresMaxK = 384;
 constexpr int kWresBks = 128;                 // K rows of X per stage
 
 template <int STAGES>
 struct CfgIxW {
+    static constexpr int MAX_K = STAGES >= 4 ? 320 : 384;    // resident W: MAX_K / 64 blocks
+    static constexpr int NBUF = STAGES >= 4 ? 1 : 2;         // staging buffers per epilogue warp
     static constexpr int W_BLOCK = 128 * 64 * 2;              // 64 beams x 2 planes x 64 K
     static constexpr int B_CHUNK = kWresBks * 128;            // 64 real columns x 128 K rows
     static constexpr int X_STAGE = 2 * B_CHUNK;               // this CTA's 128 real columns
     static constexpr int ACC_COLS = 2 * IBN;
     static constexpr int TMEM_COLS = 2 * ACC_COLS;
     static constexpr int STAGE_BUF = 2 * 8 * 128;
-    static constexpr int STAGING_BYTES = 8 * 2 * STAGE_BUF;
+    static constexpr int STAGING_BYTES = 8 * NBUF * STAGE_BUF;
     static constexpr int BAR_BYTES = 16 * STAGES + 64;
     static_assert(BAR_BYTES <= 256, "barrier block");
     static __host__ __device__ constexpr int smem_bytes(int kb64) {
         return kb64 * W_BLOCK + STAGES * X_STAGE + STAGING_BYTES + 256 + 1024;
     }
-    static_assert((kWresMaxK / 64) * W_BLOCK + STAGES * X_STAGE + STAGING_BYTES + 256 + 1024 <= 232448,
+    static_assert((MAX_K / 64) * W_BLOCK + STAGES * X_STAGE + STAGING_BYTES + 256 + 1024 <= 232448,
                   "shared memory");
 };
 
@@ -851,7 +863,7 @@ __global__ void __launch_bounds__(kIxThreads, 1)
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32 + half * 16) << 16;
-        const uint32_t stage_buf = staging0 + (warp - 2) * 2 * C::STAGE_BUF;
+        const uint32_t stage_buf = staging0 + (warp - 2) * C::NBUF * C::STAGE_BUF;
         int ev = 0;
         int nstore = 0;
         bool ok = true;
@@ -866,7 +878,8 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * C::ACC_COLS;
-                ix_drain<C::ACC_COLS, C::STAGE_BUF>(tP, tP, 0, 1, lane, stage_buf, nstore, nt, args.N,
+                ix_drain<C::ACC_COLS, C::STAGE_BUF, C::NBUF>(tP, tP, 0, 1, lane, stage_buf, nstore, nt,
+                                                            args.N,
                                                    beam0, b, &tmY, args.y4d);
                 tc_fence_before();
                 __syncwarp();
@@ -896,7 +909,7 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
                            cudaStream_t s) {
     using C = CfgIxW<STAGES>;
     const tcbf_problem &p = pl.p;
-    if (p.N % 4 != 0 || pl.m_prefix || p.K > kWresMaxK) return cudaErrorInvalidValue;
+    if (p.N % 4 != 0 || pl.m_prefix || p.K > C::MAX_K) return cudaErrorInvalidValue;
     CUtensorMap tmW, tmX, tmY;
     const int w5d = p.M % 8 == 0 ? 1 : 0;
     const int x4d = p.N % 32 == 0 ? 1 : 0;
@@ -958,7 +971,7 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
     const int smem = C::smem_bytes(a.kb64);
     auto kern = cgemm_ix_wres_kernel<STAGES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         C::smem_bytes(kWresMaxK / 64));
+                                         C::smem_bytes(C::MAX_K / 64));
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -976,7 +989,7 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
     int mc = max_clusters[pl.device & 63].load(std::memory_order_relaxed);
     if (mc == 0) {
         cudaLaunchConfig_t q = cfg;
-        q.dynamicSmemBytes = C::smem_bytes(kWresMaxK / 64);
+        q.dynamicSmemBytes = C::smem_bytes(C::MAX_K / 64);
         q.gridDim = dim3(pl.num_sms / 2 * 2);
         e = cudaOccupancyMaxActiveClusters(&mc, kern, &q);
         if (e != cudaSuccess) return e;
@@ -992,18 +1005,22 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
 struct IxConfig {
     const char *name;
     cudaError_t (*fn)(const tcbf_plan_s &, const void *, const void *, float *, cudaStream_t);
+    int max_k;   // largest K the configuration takes (0: any)
 };
 
 const IxConfig kIxConfigs[] = {
+    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 resident-W (K<=320) BK128 stages4 "
+     "tmem-double",
+     launch_ix_wres<4>, CfgIxW<4>::MAX_K},
+    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK128 stages3 tmem-double",
+     launch_ix<true, 128, 3>, 0},
+    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK64 stages6 tmem-double",
+     launch_ix<true, 64, 6>, 0},
+    {"f16 interleaved-X MN-major B N256 BM64 BN128 BK64 stages4 tmem-double",
+     launch_ix<false, 64, 4>, 0},
     {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 resident-W (K<=384) BK128 stages3 "
      "tmem-double",
-     launch_ix_wres<3>},
-    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK128 stages3 tmem-double",
-     launch_ix<true, 128, 3>},
-    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK64 stages6 tmem-double",
-     launch_ix<true, 64, 6>},
-    {"f16 interleaved-X MN-major B N256 BM64 BN128 BK64 stages4 tmem-double",
-     launch_ix<false, 64, 4>},
+     launch_ix_wres<3>, CfgIxW<3>::MAX_K},
 };
 
 }  // namespace
@@ -1012,10 +1029,13 @@ int gemm_f16_ix_num_configs() { return static_cast<int>(sizeof(kIxConfigs) / siz
 
 bool gemm_f16_ix_config_valid(int config, int64_t K) {
     if (config < 0 || config >= gemm_f16_ix_num_configs()) return false;
-    return config != 0 || K <= kWresMaxK;
+    return kIxConfigs[config].max_k == 0 || K <= kIxConfigs[config].max_k;
 }
 
-int gemm_f16_ix_default_config(int64_t K) { return K <= kWresMaxK ? 0 : 1; }
+// resident W with four stages, then with three, then streamed W
+int gemm_f16_ix_default_config(int64_t K) {
+    return K <= CfgIxW<4>::MAX_K ? 0 : K <= CfgIxW<3>::MAX_K ? 4 : 1;
+}
 
 const char *gemm_f16_ix_config_name(int config) {
     if (config < 0 || config >= gemm_f16_ix_num_configs()) return "invalid";

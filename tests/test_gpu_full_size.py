@@ -89,13 +89,15 @@ def test_full_size_radio_block_sampled():
 
 
 def test_full_size_radio_block_interleaved_x_sampled():
-    """The radio block through the interleaved-X kernel (no pack of X): both
-    tile configurations, sampled against the oracle."""
+    """The radio block through the interleaved-X kernel (no pack of X): every
+    configuration (resident W with four or three stages, streamed W on SM
+    pairs or one SM), sampled against the oracle."""
     from paper_2505_03269_gb300 import FLAG_INTERLEAVED_X
     B, Bw, M, K, N = 512, 256, 1024, 288, 4096
     geom = ti.radio_geometry(0, M, K, Bw)
     Xh = ti.radio_x(1, B, K, N)
-    for err in _run_block(B, Bw, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X, configs=(0, 1, 2, 3)):
+    for err in _run_block(B, Bw, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X,
+                          configs=(0, 1, 2, 3, 4)):
         assert err <= TOL
 
 

@@ -20,7 +20,9 @@ import tcbf_inputs as ti
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-5
-CONFIGS = [0, 1, 2, 3]   # resident W (K <= 384), SM pairs with 128-K / 64-K stages, one SM
+# resident W (4 stages, K <= 320), SM pairs with 128-K / 64-K stages, one SM, resident W
+# (3 stages, K <= 384)
+CONFIGS = [0, 1, 2, 3, 4]
 LONG_K_CONFIGS = [1, 2, 3]
 
 
@@ -188,13 +190,13 @@ def test_autotune_and_graph_replay():
     B, K, N = X.shape[0], X.shape[1], X.shape[2]
     M = W.shape[1]
     with tcbf.Plan(B, M, N, K, tcbf.MODE_FP16, w_batches=4, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
-        assert plan.num_configs() == 4
+        assert plan.num_configs() == 5
         Wp = empty_bytes(plan.packed_size(0))
         Xd = dev(X)
         plan.transpose_pack(0, dev(W), Wp)
         Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
         best, ms = plan.autotune(Wp, Xd, Y, reps=2)
-        assert best in (0, 1, 2, 3) and all(v > 0 for v in ms)
+        assert best in (0, 1, 2, 3, 4) and all(v > 0 for v in ms)
         Y.zero_()
         plan.beamform_fp16(Wp, Xd, Y)
         torch.cuda.synchronize()
@@ -230,23 +232,26 @@ def test_host_pipeline():
 
 
 def test_resident_weights_limited_to_short_k():
-    """Configuration 0 keeps W in shared memory and needs K <= 384: it is
-    the default there and refused above (the streaming pair tiles instead)."""
+    """Configuration 0 keeps W in shared memory beside four X stages and
+    needs K <= 320, configuration 4 (three stages) K <= 384: each is the
+    default in its range and refused above it; longer K starts on the
+    streaming pair tiles."""
     import paper_2505_03269_gb300 as tcbf
-    with tcbf.Plan(1, 8, 8, 384, tcbf.MODE_FP16, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
-        assert plan.get_config() == 0
-    with tcbf.Plan(1, 8, 8, 385, tcbf.MODE_FP16, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
-        assert plan.get_config() == 1
-        with pytest.raises(tcbf.TcbfError):
-            plan.set_config(0)
+    for K, default, refused in ((320, 0, []), (321, 4, [0]), (384, 4, [0]), (385, 1, [0, 4])):
+        with tcbf.Plan(1, 8, 8, K, tcbf.MODE_FP16, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
+            assert plan.get_config() == default, K
+            for c in refused:
+                with pytest.raises(tcbf.TcbfError):
+                    plan.set_config(c)
 
 
-@pytest.mark.parametrize("K", [1, 64, 129, 288, 383, 384])
-def test_resident_weights_across_k(K):
-    """Every resident-W block count (1-6 blocks of 64 K, ragged last block)
-    with several units per pair (uneven unit counts over the pairs)."""
+@pytest.mark.parametrize("config,K", [(0, 1), (0, 64), (0, 129), (0, 288), (0, 319), (0, 320),
+                                      (4, 1), (4, 129), (4, 288), (4, 383), (4, 384)])
+def test_resident_weights_across_k(config, K):
+    """Every resident-W block count (1-5 or 1-6 blocks of 64 K, ragged last
+    block) with several units per pair (uneven unit counts over the pairs)."""
     W, X = ti.small_fp16(seed=K, M=300, K=K, N=520, B=3)
-    Y = _run(W, X, config=0)
+    Y = _run(W, X, config=config)
     assert oracle.rel_frobenius(Y, oracle.cgemm(W, X)) <= TOL
 
 
