@@ -623,14 +623,14 @@ cudaError_t launch_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, floa
 // (radio block 4.52 -> 3.97 ms); the three-stage form keeps two staging
 // buffers and covers K <= 384.
 // ===========================================================================
-constexpr int kWresBks = 128;                 // K rows of X per stage
-
-template <int STAGES>
+// STAGES X stages of BKS K rows each, NBUF staging buffers per epilogue
+// warp, W resident for K <= MAXK (MAXK / 64 blocks)
+template <int STAGES, int BKS, int NBUF_, int MAXK>
 struct CfgIxW {
-    static constexpr int MAX_K = STAGES >= 4 ? 320 : 384;    // resident W: MAX_K / 64 blocks
-    static constexpr int NBUF = STAGES >= 4 ? 1 : 2;         // staging buffers per epilogue warp
+    static constexpr int MAX_K = MAXK;
+    static constexpr int NBUF = NBUF_;
     static constexpr int W_BLOCK = 128 * 64 * 2;              // 64 beams x 2 planes x 64 K
-    static constexpr int B_CHUNK = kWresBks * 128;            // 64 real columns x 128 K rows
+    static constexpr int B_CHUNK = BKS * 128;                 // 64 real columns x BKS K rows
     static constexpr int X_STAGE = 2 * B_CHUNK;               // this CTA's 128 real columns
     static constexpr int ACC_COLS = 2 * IBN;
     static constexpr int TMEM_COLS = 2 * ACC_COLS;
@@ -641,6 +641,7 @@ struct CfgIxW {
     static __host__ __device__ constexpr int smem_bytes(int kb64) {
         return kb64 * W_BLOCK + STAGES * X_STAGE + STAGING_BYTES + 256 + 1024;
     }
+    static_assert(BKS % 16 == 0 && B_CHUNK % 1024 == 0, "whole 8-row swizzle atoms per stage");
     static_assert((MAX_K / 64) * W_BLOCK + STAGES * X_STAGE + STAGING_BYTES + 256 + 1024 <= 232448,
                   "shared memory");
 };
@@ -657,12 +658,12 @@ struct IxWArgs {
     int w5d, x4d, y4d;
 };
 
-template <int STAGES>
+template <int STAGES, int BKS, int NBUF, int MAXK>
 __global__ void __launch_bounds__(kIxThreads, 1)
     cgemm_ix_wres_kernel(const __grid_constant__ CUtensorMap tmW,
                          const __grid_constant__ CUtensorMap tmX,
                          const __grid_constant__ CUtensorMap tmY, const IxWArgs args) {
-    using C = CfgIxW<STAGES>;
+    using C = CfgIxW<STAGES, BKS, NBUF, MAXK>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -759,11 +760,11 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                         const uint32_t fb = full0_lead + 8 * stage;
                         const uint32_t xdst = x0 + stage * C::X_STAGE;
                         if (args.x4d) {
-                            tma_load_4d_pair(xdst, &tmX, fb, 0, kb * kWresBks, col0 / 64, b);
+                            tma_load_4d_pair(xdst, &tmX, fb, 0, kb * BKS, col0 / 64, b);
                         } else {
                             for (int c = 0; c < 2; ++c)
                                 tma_load_3d_pair(xdst + c * C::B_CHUNK, &tmX, fb, col0 + 64 * c,
-                                                 kb * kWresBks, b);
+                                                 kb * BKS, b);
                         }
                         ++issued;
                         if (++stage == STAGES) {
@@ -830,9 +831,9 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                         }
                         tc_fence_after();
                         const uint32_t bx = x0 + stage * C::X_STAGE;
-                        const int ksteps = min(kWresBks / 16, (args.K - kb * kWresBks + 15) / 16);
+                        const int ksteps = min(BKS / 16, (args.K - kb * BKS + 15) / 16);
                         for (int j = 0; j < ksteps; ++j) {
-                            const int kg = kb * kWresBks + 16 * j;       // K of this step
+                            const int kg = kb * BKS + 16 * j;       // K of this step
                             const uint64_t ad =
                                 sdesc_kmajor_sw128(w0 + (kg >> 6) * C::W_BLOCK + 32 * ((kg >> 4) & 3));
                             const uint64_t bd = sdesc_mnmajor_sw128(bx + 2048 * j, C::B_CHUNK, 1024);
@@ -904,10 +905,10 @@ __global__ void __launch_bounds__(kIxThreads, 1)
     }
 }
 
-template <int STAGES>
+template <int STAGES, int BKS, int NBUF, int MAXK>
 cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X, float *Y,
                            cudaStream_t s) {
-    using C = CfgIxW<STAGES>;
+    using C = CfgIxW<STAGES, BKS, NBUF, MAXK>;
     const tcbf_problem &p = pl.p;
     if (p.N % 4 != 0 || pl.m_prefix || p.K > C::MAX_K) return cudaErrorInvalidValue;
     CUtensorMap tmW, tmX, tmY;
@@ -937,7 +938,7 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
         const uint64_t dims[4] = {64, static_cast<uint64_t>(p.K), static_cast<uint64_t>(2 * p.N / 64),
                                   static_cast<uint64_t>(p.batch)};
         const uint64_t strides[3] = {xrow, 128, static_cast<uint64_t>(p.K) * xrow};
-        const uint32_t box[4] = {64, kWresBks, 2, 1};
+        const uint32_t box[4] = {64, BKS, 2, 1};
         if (encode_tiled(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(X), dims,
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
@@ -945,7 +946,7 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
         const uint64_t dims[3] = {static_cast<uint64_t>(2 * p.N), static_cast<uint64_t>(p.K),
                                   static_cast<uint64_t>(p.batch)};
         const uint64_t strides[2] = {xrow, static_cast<uint64_t>(p.K) * xrow};
-        const uint32_t box[3] = {64, kWresBks, 1};
+        const uint32_t box[3] = {64, BKS, 1};
         if (encode_tiled(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(X), dims,
                          strides, box, CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
@@ -961,7 +962,7 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
     a.kb64 = static_cast<int>(ceil_div(p.K, 64));
     a.m_tiles = static_cast<int>(ceil_div(p.M, 128));
     a.n_tiles = static_cast<int>(ceil_div(p.N, IBN));
-    a.num_kb = static_cast<int>(ceil_div(p.K, kWresBks));
+    a.num_kb = static_cast<int>(ceil_div(p.K, BKS));
     a.w5d = w5d;
     a.x4d = x4d;
     a.y4d = y4d;
@@ -969,7 +970,7 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
     if (units > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_units = static_cast<int>(units);
     const int smem = C::smem_bytes(a.kb64);
-    auto kern = cgemm_ix_wres_kernel<STAGES>;
+    auto kern = cgemm_ix_wres_kernel<STAGES, BKS, NBUF, MAXK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::smem_bytes(C::MAX_K / 64));
     if (e != cudaSuccess) return e;
@@ -1011,7 +1012,7 @@ struct IxConfig {
 const IxConfig kIxConfigs[] = {
     {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 resident-W (K<=320) BK128 stages4 "
      "tmem-double",
-     launch_ix_wres<4>, CfgIxW<4>::MAX_K},
+     launch_ix_wres<4, 128, 1, 320>, 320},
     {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK128 stages3 tmem-double",
      launch_ix<true, 128, 3>, 0},
     {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 BK64 stages6 tmem-double",
@@ -1020,7 +1021,13 @@ const IxConfig kIxConfigs[] = {
      launch_ix<false, 64, 4>, 0},
     {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 resident-W (K<=384) BK128 stages3 "
      "tmem-double",
-     launch_ix_wres<3>, CfgIxW<3>::MAX_K},
+     launch_ix_wres<3, 128, 2, 384>, 384},
+    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 resident-W (K<=320) BK96 stages5 "
+     "tmem-double",
+     launch_ix_wres<5, 96, 1, 320>, 320},
+    {"f16 interleaved-X MN-major B N256 2-SM pair BM128 BN128 resident-W (K<=320) BK64 stages8 "
+     "tmem-double",
+     launch_ix_wres<8, 64, 1, 320>, 320},
 };
 
 }  // namespace
@@ -1032,9 +1039,17 @@ bool gemm_f16_ix_config_valid(int config, int64_t K) {
     return kIxConfigs[config].max_k == 0 || K <= kIxConfigs[config].max_k;
 }
 
-// resident W with four stages, then with three, then streamed W
+// Resident W when it fits, then streamed W.  Up to K = 320 the ring of the
+// two resident forms that keeps more K rows of X in flight (stages x the
+// mean K of a stage over one tile): 96-K stages for K = 288 (three full
+// stages per tile) or below 97, 128-K ones for K = 256 or 320.
 int gemm_f16_ix_default_config(int64_t K) {
-    return K <= CfgIxW<4>::MAX_K ? 0 : K <= CfgIxW<3>::MAX_K ? 4 : 1;
+    if (K <= 320) {
+        const double rows128 = 4.0 * static_cast<double>(K) / static_cast<double>(ceil_div(K, 128));
+        const double rows96 = 5.0 * static_cast<double>(K) / static_cast<double>(ceil_div(K, 96));
+        return rows96 > rows128 ? 5 : 0;
+    }
+    return K <= 384 ? 4 : 1;
 }
 
 const char *gemm_f16_ix_config_name(int config) {

@@ -97,7 +97,7 @@ def test_full_size_radio_block_interleaved_x_sampled():
     geom = ti.radio_geometry(0, M, K, Bw)
     Xh = ti.radio_x(1, B, K, N)
     for err in _run_block(B, Bw, M, N, K, geom, Xh, flags=FLAG_INTERLEAVED_X,
-                          configs=(0, 1, 2, 3, 4)):
+                          configs=(0, 1, 2, 3, 4, 5, 6)):
         assert err <= TOL
 
 

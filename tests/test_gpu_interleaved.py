@@ -20,9 +20,9 @@ import tcbf_inputs as ti
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-5
-# resident W (4 stages, K <= 320), SM pairs with 128-K / 64-K stages, one SM, resident W
-# (3 stages, K <= 384)
-CONFIGS = [0, 1, 2, 3, 4]
+# resident W (4 stages of 128 K, K <= 320), SM pairs with 128-K / 64-K stages, one SM,
+# resident W (3 stages, K <= 384; 5 stages of 96 K and 8 of 64 K, K <= 320)
+CONFIGS = [0, 1, 2, 3, 4, 5, 6]
 LONG_K_CONFIGS = [1, 2, 3]
 
 
@@ -190,13 +190,13 @@ def test_autotune_and_graph_replay():
     B, K, N = X.shape[0], X.shape[1], X.shape[2]
     M = W.shape[1]
     with tcbf.Plan(B, M, N, K, tcbf.MODE_FP16, w_batches=4, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
-        assert plan.num_configs() == 5
+        assert plan.num_configs() == 7
         Wp = empty_bytes(plan.packed_size(0))
         Xd = dev(X)
         plan.transpose_pack(0, dev(W), Wp)
         Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
         best, ms = plan.autotune(Wp, Xd, Y, reps=2)
-        assert best in (0, 1, 2, 3, 4) and all(v > 0 for v in ms)
+        assert best in range(7) and all(v > 0 for v in ms)
         Y.zero_()
         plan.beamform_fp16(Wp, Xd, Y)
         torch.cuda.synchronize()
@@ -232,12 +232,14 @@ def test_host_pipeline():
 
 
 def test_resident_weights_limited_to_short_k():
-    """Configuration 0 keeps W in shared memory beside four X stages and
-    needs K <= 320, configuration 4 (three stages) K <= 384: each is the
-    default in its range and refused above it; longer K starts on the
-    streaming pair tiles."""
+    """Configurations 0, 5 and 6 keep W in shared memory beside four, five
+    or eight X stages and need K <= 320, configuration 4 (three stages)
+    K <= 384: up to 320 the plan starts on whichever of 0 and 5 keeps more
+    K rows in flight (5 at K = 288), on 4 up to 384, and on the streaming
+    pair tiles above; each resident form is refused above its K."""
     import paper_2505_03269_gb300 as tcbf
-    for K, default, refused in ((320, 0, []), (321, 4, [0]), (384, 4, [0]), (385, 1, [0, 4])):
+    for K, default, refused in ((288, 5, []), (256, 0, []), (64, 5, []), (320, 0, []),
+                                (321, 4, [0, 5, 6]), (384, 4, [0, 5, 6]), (385, 1, [0, 4, 5, 6])):
         with tcbf.Plan(1, 8, 8, K, tcbf.MODE_FP16, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
             assert plan.get_config() == default, K
             for c in refused:
@@ -246,7 +248,9 @@ def test_resident_weights_limited_to_short_k():
 
 
 @pytest.mark.parametrize("config,K", [(0, 1), (0, 64), (0, 129), (0, 288), (0, 319), (0, 320),
-                                      (4, 1), (4, 129), (4, 288), (4, 383), (4, 384)])
+                                      (4, 1), (4, 129), (4, 288), (4, 383), (4, 384),
+                                      (5, 1), (5, 95), (5, 97), (5, 288), (5, 320),
+                                      (6, 1), (6, 65), (6, 288), (6, 320)])
 def test_resident_weights_across_k(config, K):
     """Every resident-W block count (1-5 or 1-6 blocks of 64 K, ragged last
     block) with several units per pair (uneven unit counts over the pairs)."""
