@@ -120,15 +120,16 @@ typedef enum {
      * work on 8-bit floats (Sec. VI); the benchmark spec's per-tile scales. */
     TCBF_FLAG_FP8_BLOCK_SCALES = 16u,
     /* FP16 only, not combined with TCBF_FLAG_STACKED_X or
-     * TCBF_FLAG_INTERLEAVED_X: the plan chooses between the planar and the
-     * stacked packed-X layout.  At creation it takes TCBF_FLAG_STACKED_X
+     * TCBF_FLAG_INTERLEAVED_X: the plan chooses the packed-X layout.  At
+     * creation it takes TCBF_FLAG_STACKED_X
      * when the problem is compute-bound: its arithmetic intensity, 8 B M N K
      * operations over the bytes of the stacked layout's packed W and X and
      * of Y, is at least TCBF_AUTO_STACKED_MIN_INTENSITY operations per byte
      * (above the GB300's tensor/HBM ridge of about 280, where the stacked
      * kernel's two N = 256 MMAs per K step tend to beat the four N = 128
      * ones), and the planar layout otherwise; tcbf_autotune_layout then
-     * replaces that guess by measurement.  The chosen bit replaces this one
+     * replaces that guess by measurement over the planar, stacked and
+     * interleaved layouts.  The chosen bit replaces this one
      * in the plan's flags (tcbf_plan_flags): callers that write packed X
      * themselves read it there; tcbf_transpose_pack and tcbf_packed_size
      * follow it. */
@@ -434,15 +435,21 @@ tcbf_status tcbf_autotune(tcbf_plan_t plan, const void *Wp, const void *Xp, void
 
 /*
  * Layout autotuner for plans created with TCBF_FLAG_AUTO_LAYOUT (else
- * TCBF_ERR_INVALID_ARG).  For the planar and the stacked packed-X layout in
- * turn it packs X_src ([batch][K][N] complex of src_type, the
- * tcbf_transpose_pack source) into a scratch buffer it allocates, runs
- * tcbf_autotune over that layout's configurations (`reps` rounds) and times
- * the step, pack + beamform with the best configuration (best of `reps`
- * after one warm-up).  The plan keeps the faster layout and its
- * configuration; *flags (nullable) receives the plan's new flags and
- * ms_per_layout (nullable, 2 entries) the step milliseconds of the planar
- * and the stacked layout.  Wp is the packed W (the same bytes for both
+ * TCBF_ERR_INVALID_ARG).  For the planar, the stacked and (when N % 4 == 0
+ * and the batch rows are uniform, so that the fused kernel takes it) the
+ * interleaved X layout in turn it packs X_src ([batch][K][N] complex of
+ * src_type, the tcbf_transpose_pack source) into a scratch buffer it
+ * allocates (for the interleaved layout: copies it, as tcbf_transpose_pack
+ * does) and runs tcbf_autotune over that layout's configurations (`reps`
+ * rounds); then it times the layouts' steps, pack + beamform with each one's
+ * best configuration, round-robin for `reps` rounds in groups of at least
+ * about 1 ms, keeping each one's fastest group.  The plan keeps the fastest
+ * layout and
+ * its configuration; *flags (nullable) receives the plan's new flags and
+ * ms_per_layout (nullable, 3 entries) the step milliseconds of the planar,
+ * stacked and interleaved layouts (-1 for one not timed).  A plan that ends
+ * on the interleaved layout can also be given X itself instead of its copy
+ * (TCBF_FLAG_INTERLEAVED_X), which saves the copy.  Wp is the packed W (the same bytes for both
  * layouts); Y is overwritten.  Synchronises the stream and frees the
  * scratch before it returns.  When the layout changes, packed X made
  * before the call no longer fits the plan (repack it; tcbf_packed_size(1)

@@ -279,17 +279,18 @@ class Plan:
         return best.value, list(ms)
 
     def autotune_layout(self, Wp, X_src, Y, src_type=SRC_CF16, reps=3, stream=None):
-        """tcbf_autotune_layout (plans made with FLAG_AUTO_LAYOUT): the faster
-        of the planar and stacked layouts, by the timed pack + beamform step,
-        with its best configuration.  Returns (flags, [planar_ms, stacked_ms])
+        """tcbf_autotune_layout (plans made with FLAG_AUTO_LAYOUT): the fastest
+        of the planar, stacked and interleaved layouts, by the timed pack +
+        beamform step, with its best configuration.  Returns (flags,
+        [planar_ms, stacked_ms, interleaved_ms]) (-1 for a layout not timed)
         and updates self.flags; packed X must be remade when it changed."""
         f = ctypes.c_uint32()
-        ms = (ctypes.c_float * 2)()
+        ms = (ctypes.c_float * 3)()
         _check(self._lib.tcbf_autotune_layout(self.handle, _ptr(Wp), _ptr(X_src), int(src_type),
                                               _ptr(Y), int(reps), _stream(stream), ctypes.byref(f),
                                               ms), "tcbf_autotune_layout")
         self.flags = f.value
-        return f.value, [ms[0], ms[1]]
+        return f.value, [ms[0], ms[1], ms[2]]
 
     def graph_capture(self, Xsrc, Xp, Wp, Y, src_type=SRC_CF16):
         _check(self._lib.tcbf_graph_capture(self.handle, _ptr(Xsrc), int(src_type), _ptr(Xp),

@@ -659,8 +659,11 @@ TCBF_EXPORT tcbf_status tcbf_autotune_layout(tcbf_plan_t plan, const void *Wp, c
     const uint32_t base = plan->p.flags & ~(TCBF_FLAG_STACKED_X | TCBF_FLAG_INTERLEAVED_X);
     const uint32_t old_flags = plan->p.flags;
     const int old_config = plan->config;
-    const uint32_t layouts[2] = {0u, TCBF_FLAG_STACKED_X};
-    // one scratch for the packed X of either layout (the stacked one is larger)
+    const uint32_t layouts[3] = {0u, TCBF_FLAG_STACKED_X, TCBF_FLAG_INTERLEAVED_X};
+    // the interleaved layout only where the fused kernel takes it
+    plan->p.flags = base | TCBF_FLAG_INTERLEAVED_X;
+    const int n_layouts = ix_fused_ok(*plan) ? 3 : 2;
+    // one scratch for the packed X of any layout (the stacked one is the largest)
     plan->p.flags = base | TCBF_FLAG_STACKED_X;
     size_t xbytes = 0;
     tcbf_packed_size(plan, 1, &xbytes);
@@ -670,28 +673,48 @@ TCBF_EXPORT tcbf_status tcbf_autotune_layout(tcbf_plan_t plan, const void *Wp, c
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     tcbf_status st = from_cuda(ce);
-    float ms[2] = {-1.f, -1.f};
-    int cfg[2] = {0, 0};
+    float ms[3] = {-1.f, -1.f, -1.f};
+    int cfg[3] = {0, 0, 0};
     // each layout: its configurations autotuned on the packed X, then the
-    // step (pack + beamform with the best configuration) timed, best of reps
-    for (int l = 0; l < 2 && st == TCBF_OK; ++l) {
+    // step (pack + beamform with the best configuration; for the interleaved
+    // layout the pack is tcbf_transpose_pack's copy) timed, best of reps
+    for (int l = 0; l < n_layouts && st == TCBF_OK; ++l) {
         plan->p.flags = base | layouts[l];
         plan->config = 0;
         ce = pack_x_into(*plan, src_type, X_src, xp, s);
         st = from_cuda(ce);
         if (st == TCBF_OK) st = tcbf_autotune(plan, Wp, xp, Y, reps, stream, &cfg[l], nullptr);
-        for (int r = 0; r < reps + 1 && st == TCBF_OK; ++r) {
-            ce = cudaEventRecord(e0, s);
-            if (ce == cudaSuccess) ce = pack_x_into(*plan, src_type, X_src, xp, s);
-            if (ce == cudaSuccess) ce = launch_beamform(*plan, Wp, xp, Y, s);
-            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
-            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-            float t = 0.f;
-            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
-            st = from_cuda(ce);
-            if (st == TCBF_OK && r > 0 && (ms[l] < 0.f || t < ms[l])) ms[l] = t;   // r = 0 warms up
-        }
     }
+    // then the steps of the layouts timed round-robin, each in groups of at
+    // least about 1 ms after a warm-up step, keeping each one's fastest
+    // group: a drift of the clocks (power, temperature) affects them alike
+    int group[3] = {1, 1, 1};
+    auto timed = [&](int l, int steps, float &t) -> cudaError_t {
+        plan->p.flags = base | layouts[l];
+        plan->config = cfg[l];
+        cudaError_t e = cudaEventRecord(e0, s);
+        for (int i = 0; i < steps && e == cudaSuccess; ++i) {
+            e = pack_x_into(*plan, src_type, X_src, xp, s);
+            if (e == cudaSuccess) e = launch_beamform(*plan, Wp, xp, Y, s);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        return e;
+    };
+    for (int l = 0; l < n_layouts && st == TCBF_OK; ++l) {
+        float t = 0.f;
+        st = from_cuda(timed(l, 1, t));
+        if (st == TCBF_OK) st = from_cuda(timed(l, 1, t));
+        group[l] = std::max(1, std::min(1000, static_cast<int>(1.0f / std::max(t, 1e-4f)) + 1));
+    }
+    for (int r = 0; r < reps && st == TCBF_OK; ++r)
+        for (int l = 0; l < n_layouts && st == TCBF_OK; ++l) {
+            float t = 0.f;
+            st = from_cuda(timed(l, group[l], t));
+            t /= group[l];
+            if (st == TCBF_OK && (ms[l] < 0.f || t < ms[l])) ms[l] = t;
+        }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (xp) cudaFree(xp);
@@ -700,7 +723,9 @@ TCBF_EXPORT tcbf_status tcbf_autotune_layout(tcbf_plan_t plan, const void *Wp, c
         plan->config = old_config;
         return st;
     }
-    const int best = ms[1] < ms[0] ? 1 : 0;
+    int best = 0;
+    for (int l = 1; l < n_layouts; ++l)
+        if (ms[l] >= 0.f && ms[l] < ms[best]) best = l;
     plan->p.flags = base | layouts[best];
     plan->config = cfg[best];
     if (plan->p.flags != old_flags) {
@@ -712,10 +737,8 @@ TCBF_EXPORT tcbf_status tcbf_autotune_layout(tcbf_plan_t plan, const void *Wp, c
         }
     }
     if (flags) *flags = plan->p.flags;
-    if (ms_per_layout) {
-        ms_per_layout[0] = ms[0];
-        ms_per_layout[1] = ms[1];
-    }
+    if (ms_per_layout)
+        for (int l = 0; l < 3; ++l) ms_per_layout[l] = ms[l];
     return TCBF_OK;
 }
 

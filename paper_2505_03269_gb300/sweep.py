@@ -58,8 +58,9 @@ def run_size(mode: str, S: int, layout: str = "auto", seed: int = 0, rounds: int
         Wp = torch.empty(dplan.packed_size(0), dtype=torch.uint8, device="cuda")
         dplan.transpose_pack(0, W, Wp)
         default_layout = layout_name(dplan.flags) if m == tcbf.MODE_FP16 else "1-bit"
+        layout_ms = None
         if flags == LAYOUT_FLAGS["auto"]:
-            tplan.autotune_layout(Wp, X, Y, reps=3)
+            _, layout_ms = tplan.autotune_layout(Wp, X, Y, reps=3)
         plans = []
         for plan in (dplan, tplan):
             Xp = torch.empty(plan.packed_size(1), dtype=torch.uint8, device="cuda")
@@ -78,7 +79,8 @@ def run_size(mode: str, S: int, layout: str = "auto", seed: int = 0, rounds: int
                 "tuned_layout": layout_name(tplan.flags) if m == tcbf.MODE_FP16 else "1-bit",
                 "default_ms": best[0], "default_tops": ops / (best[0] * 1e-3) / 1e12,
                 "tuned": tplan.config_name(tplan.get_config()), "tuned_ms": best[1],
-                "tuned_tops": ops / (best[1] * 1e-3) / 1e12, "status": status}
+                "tuned_tops": ops / (best[1] * 1e-3) / 1e12, "layout_ms": layout_ms,
+                "status": status}
 
 
 def layout_name(flags: int) -> str:

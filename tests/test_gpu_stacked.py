@@ -205,14 +205,14 @@ def test_auto_layout_plan_computes_the_stacked_product():
 
 
 def test_autotune_layout_picks_a_timed_layout_and_stays_correct():
-    """tcbf_autotune_layout times both layouts' steps and keeps the faster
-    with its tuned configuration; it refuses plans made without the auto
-    flag, and after repacking X for the chosen layout the plan's product is
-    within the FP16 bar of the oracle."""
+    """tcbf_autotune_layout times the planar, stacked and interleaved steps
+    and keeps the fastest with its tuned configuration; it refuses plans made
+    without the auto flag, and after repacking X for the chosen layout the
+    plan's product is within the FP16 bar of the oracle."""
     import torch
     from gpu_util import dev, empty_bytes
-    from paper_2505_03269_gb300 import (FLAG_AUTO_LAYOUT, FLAG_STACKED_X, MODE_FP16, Plan,
-                                        TcbfError)
+    from paper_2505_03269_gb300 import (FLAG_AUTO_LAYOUT, FLAG_INTERLEAVED_X, FLAG_STACKED_X,
+                                        MODE_FP16, Plan, TcbfError)
     B, M, N, K = 2, 384, 320, 1000
     W, X = ti.small_fp16(seed=5, M=M, K=K, N=N, B=B)
     Wd, Xd = dev(W), dev(X)
@@ -224,9 +224,10 @@ def test_autotune_layout_picks_a_timed_layout_and_stays_correct():
             fixed.autotune_layout(Wp, Xd, Y)
     with Plan(B, M, N, K, MODE_FP16, flags=FLAG_AUTO_LAYOUT) as plan:
         flags, ms = plan.autotune_layout(Wp, Xd, Y, reps=2)
-        assert flags in (0, FLAG_STACKED_X) and plan.flags == flags
-        assert ms[0] > 0 and ms[1] > 0
-        assert (ms[1] < ms[0]) == (flags == FLAG_STACKED_X)
+        layouts = (0, FLAG_STACKED_X, FLAG_INTERLEAVED_X)
+        assert flags in layouts and plan.flags == flags
+        assert all(t > 0 for t in ms)
+        assert flags == layouts[int(np.argmin(ms))]
         Xp = empty_bytes(plan.packed_size(1))
         plan.transpose_pack(1, Xd, Xp)
         Y.fill_(float("nan"))
@@ -236,3 +237,19 @@ def test_autotune_layout_picks_a_timed_layout_and_stays_correct():
         Yh = Y.cpu().numpy().astype(np.float64)
     got = Yh[..., 0] + 1j * Yh[..., 1]
     assert oracle.rel_frobenius(got, oracle.cgemm(W, X)) <= TOL
+
+
+def test_autotune_layout_skips_interleaved_when_n_is_not_a_multiple_of_four():
+    """Rows of 4N bytes that are not 16-byte multiples: the fused
+    interleaved kernel cannot read X, so only planar and stacked are timed."""
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_AUTO_LAYOUT, FLAG_STACKED_X, MODE_FP16, Plan
+    W, X = ti.small_fp16(seed=8, M=128, K=64, N=130, B=1)
+    with Plan(1, 128, 130, 64, MODE_FP16, flags=FLAG_AUTO_LAYOUT) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        plan.transpose_pack(0, dev(W), Wp)
+        Y = torch.empty((1, 128, 130, 2), dtype=torch.float32, device="cuda")
+        flags, ms = plan.autotune_layout(Wp, dev(X), Y, reps=1)
+        assert ms[2] == -1 and ms[0] > 0 and ms[1] > 0
+        assert flags in (0, FLAG_STACKED_X)
