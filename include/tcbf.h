@@ -274,7 +274,7 @@ tcbf_status tcbf_beamform_tf32(tcbf_plan_t plan, const void *Wp, const void *Xp,
  * K <= 2^23 (every partial sum an integer of magnitude <= 2K in FP32).
  * tcbf_plan_create gives a 1-bit plan the 4-bit path by default when
  * K <= 2^23 and its planes fit in device memory (256 x 112 tiles with two
- * accumulators for K <= 1024, else 256 x 128 tiles with one): (w_batches x 2 x M +
+ * accumulators for K <= 6144, else 256 x 128 tiles with one): (w_batches x 2 x M +
  * batch x 3 x N) rows of 16 x Kw bytes, owned by the plan and freed by
  * tcbf_plan_destroy; otherwise configuration 0 (E4M3).  Selecting a 4-bit
  * configuration with tcbf_plan_set_config allocates the planes if needed

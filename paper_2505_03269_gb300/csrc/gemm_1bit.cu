@@ -563,14 +563,14 @@ int gemm_1bit_fp4_variant(int config) {
     return gemm_1bit_config_fp4(config) ? config - kFirstFp4Config : -1;
 }
 
-// Short K: 256 x 112 tiles with two accumulators (columns 0 and 256), so
-// each tile's drain overlaps the next tile's MMAs; longer K: the full-width
-// N = 256 tiles with one accumulator.  Measured (GEMM on expanded planes):
-// the radio 1-bit block (K = 1024, 64 batches) 1.82 ms against 1.94 for
-// 256 x 96 tiles and 2.51 for N = 256; single products M = N = K = 2048 to
-// 8192 1-9% faster with the N = 256 tiles, and K = 65536 16.5 ms against
-// 18.3 (256 x 112) and 20.5 (256 x 96).
-int gemm_1bit_fp4_default_config(int64_t K) { return K <= 1024 ? kFirstFp4Config + 3 : kFirstFp4Config; }
+// K up to 6144: 256 x 112 tiles with two accumulators (columns 0 and 256),
+// so each tile's drain overlaps the next tile's MMAs; longer K: the
+// full-width N = 256 tiles with one accumulator.  Measured (GEMM on
+// expanded planes): the radio 1-bit block (K = 1024, 64 batches) 1.82 ms
+// against 1.94 for 256 x 96 tiles and 2.51 for N = 256; single products
+// M = N = K = 2000 to 6144 3-10% faster with the 256 x 112 tiles, 8192 the
+// same, and K = 65536 16.5 ms against 18.3 (256 x 112).
+int gemm_1bit_fp4_default_config(int64_t K) { return K <= 6144 ? kFirstFp4Config + 3 : kFirstFp4Config; }
 
 const char *gemm_1bit_config_name(int config) {
     if (config < 0 || config >= gemm_1bit_num_configs()) return "invalid";

@@ -143,12 +143,12 @@ def test_default_configuration_is_the_4bit_path():
 
 
 def test_default_configuration_threshold_in_k():
-    """K <= 1024 starts on the 256 x 112 two-accumulator tiles (configuration
+    """K <= 6144 starts on the 256 x 112 two-accumulator tiles (configuration
     8), larger K on the 256 x 128 one-accumulator tiles (configuration 5)."""
     from paper_2505_03269_gb300 import MODE_1BIT, Plan
-    with Plan(1, 256, 256, 1024, MODE_1BIT) as plan:
+    with Plan(1, 256, 256, 6144, MODE_1BIT) as plan:
         assert plan.get_config() == 8, plan.config_name(plan.get_config())
-    with Plan(1, 256, 256, 1025, MODE_1BIT) as plan:
+    with Plan(1, 256, 256, 6145, MODE_1BIT) as plan:
         assert plan.get_config() == 5, plan.config_name(plan.get_config())
 
 
