@@ -613,9 +613,11 @@ cudaError_t launch_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, floa
 // X streams through the ring: per output, half the operand bytes from L2 of
 // the streaming kernel.  A unit's W is loaded once its predecessor's MMAs
 // are done (the MMA thread commits a W-empty barrier after a unit's last
-// tile), while the producer already streams the new unit's X.  Units run
-// pair rows fastest within a batch, so the pairs working at one time share
-// each batch's X in L2.  One accumulation chunk (no promotion at this K).
+// tile), while the producer already streams the new unit's X.  A pair runs
+// the per_w products that share a weight batch back to back on the same
+// resident W (one W load per super-unit of weight batch x 128 beams), and
+// super-units run beam rows fastest, so the pairs working at one time share
+// the same products' X in L2.  One accumulation chunk (no promotion at this K).
 // The X ring's depth is what bounds the kernel (its loads wait on L2
 // latency, not bandwidth: half the X bytes per stage ran in the same time),
 // so the four-stage form (K <= 320: up to five W blocks) gives up the
@@ -654,7 +656,7 @@ struct IxWArgs {
     int m_tiles;        // 128-beam pair rows per batch
     int n_tiles;        // 128-sample tiles per batch
     int num_kb;         // X stages per tile
-    int total_units;    // batch x m_tiles
+    int total_su;       // w_batches x m_tiles: (weight batch, 128-beam row) super-units
     int w5d, x4d, y4d;
 };
 
@@ -689,6 +691,18 @@ __global__ void __launch_bounds__(kIxThreads, 1)
     const int u_first = static_cast<int>(cluster_id_x());
     const int u_step = static_cast<int>(nclusters_x());
     constexpr uint16_t kBoth = 3;
+    // The pair's i-th unit: super-units (weight batch, 128-beam row) strided
+    // over the pairs, each run as the per_w products that share its W one
+    // after the other, so the resident W is loaded once per super-unit.
+    auto unit = [&](int i, int &b, int &mt, int &sub) -> bool {
+        const int su = u_first + (i / args.per_w) * u_step;
+        if (su >= args.total_su) return false;
+        sub = i - (i / args.per_w) * args.per_w;
+        const int bw = su / args.m_tiles;
+        mt = su - bw * args.m_tiles;
+        b = bw * args.per_w + sub;
+        return true;
+    };
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) {
@@ -728,27 +742,29 @@ __global__ void __launch_bounds__(kIxThreads, 1)
             uint32_t phase = 0;
             uint32_t issued = 0, wuse = 0;
             bool ok = true;
-            for (int u = u_first; u < args.total_units && ok; u += u_step) {
-                const int b = u / args.m_tiles, mt = u - (u / args.m_tiles) * args.m_tiles;
+            int b, mt, sub;
+            for (int i = 0; ok && unit(i, b, mt, sub); ++i) {
                 const int bw = b / args.per_w;
                 const int beam0 = mt * 128 + 64 * rank;
-                // the unit's W, once the previous unit's MMAs no longer read it
-                if (!mbar_wait(wempty, (wuse & 1u) ^ 1u) || *abort_flag) {
-                    ok = false;
-                    break;
-                }
-                if (leader) mbar_arrive_expect_tx(wfull, 2 * args.kb64 * C::W_BLOCK);
-                for (int kk = 0; kk < args.kb64; ++kk) {
-                    const uint32_t wdst = w0 + kk * C::W_BLOCK;
-                    if (args.w5d) {
-                        tma_load_5d_pair(wdst, &tmW, wfull_lead, 64 * kk, 0, 0, beam0 / 8, bw);
-                    } else {
-                        for (int g = 0; g < 8; ++g)
-                            tma_load_3d_pair(wdst + g * 2048, &tmW, wfull_lead, 64 * kk, beam0 + 8 * g,
-                                             2 * bw);
+                if (sub == 0) {
+                    // the super-unit's W, once the previous one's MMAs no longer read it
+                    if (!mbar_wait(wempty, (wuse & 1u) ^ 1u) || *abort_flag) {
+                        ok = false;
+                        break;
                     }
+                    if (leader) mbar_arrive_expect_tx(wfull, 2 * args.kb64 * C::W_BLOCK);
+                    for (int kk = 0; kk < args.kb64; ++kk) {
+                        const uint32_t wdst = w0 + kk * C::W_BLOCK;
+                        if (args.w5d) {
+                            tma_load_5d_pair(wdst, &tmW, wfull_lead, 64 * kk, 0, 0, beam0 / 8, bw);
+                        } else {
+                            for (int g = 0; g < 8; ++g)
+                                tma_load_3d_pair(wdst + g * 2048, &tmW, wfull_lead, 64 * kk,
+                                                 beam0 + 8 * g, 2 * bw);
+                        }
+                    }
+                    ++wuse;
                 }
-                ++wuse;
                 for (int nt = 0; nt < args.n_tiles && ok; ++nt) {
                     const int col0 = 2 * nt * IBN + rank * 128;
                     for (int kb = 0; kb < args.num_kb; ++kb) {
@@ -810,12 +826,15 @@ __global__ void __launch_bounds__(kIxThreads, 1)
             uint32_t phase = 0, wuse = 0;
             int ev = 0;
             bool ok = true;
-            for (int u = u_first; u < args.total_units && ok; u += u_step) {
-                if (!mbar_wait(wfull, wuse & 1u) || *abort_flag) {
-                    ok = false;
-                    break;
+            int b, mt, sub;
+            for (int i = 0; ok && unit(i, b, mt, sub); ++i) {
+                if (sub == 0) {
+                    if (!mbar_wait(wfull, wuse & 1u) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                 }
-                tc_fence_after();
                 for (int nt = 0; nt < args.n_tiles && ok; ++nt, ++ev) {
                     const int acc = ev & 1;
                     if (!mbar_wait(tempty0 + 8 * acc, ((ev >> 1) & 1u) ^ 1u)) {
@@ -849,8 +868,10 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                     mma_commit_pair(tfull0 + 8 * acc, kBoth);
                 }
                 if (!ok) break;
-                mma_commit_pair(wempty, kBoth);    // the unit's W may be replaced
-                ++wuse;
+                if (sub == args.per_w - 1) {
+                    mma_commit_pair(wempty, kBoth);    // the super-unit's W may be replaced
+                    ++wuse;
+                }
             }
             if (!ok) {
                 atomicOr(args.status, kErrTimeoutMma);
@@ -868,8 +889,8 @@ __global__ void __launch_bounds__(kIxThreads, 1)
         int ev = 0;
         int nstore = 0;
         bool ok = true;
-        for (int u = u_first; u < args.total_units && ok; u += u_step) {
-            const int b = u / args.m_tiles, mt = u - (u / args.m_tiles) * args.m_tiles;
+        int b, mt, sub;
+        for (int i = 0; ok && unit(i, b, mt, sub); ++i) {
             const int beam0 = mt * 128 + 64 * rank + 16 * quarter + 8 * half;
             for (int nt = 0; nt < args.n_tiles; ++nt, ++ev) {
                 const int acc = ev & 1;
@@ -966,9 +987,9 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
     a.w5d = w5d;
     a.x4d = x4d;
     a.y4d = y4d;
-    const int64_t units = int64_t(a.m_tiles) * p.batch;
-    if (units > 0x7fffffff) return cudaErrorInvalidValue;
-    a.total_units = static_cast<int>(units);
+    const int64_t units = int64_t(a.m_tiles) * p.w_batches;
+    if (units > 0x7fffffff || int64_t(a.m_tiles) * p.batch > 0x7fffffff) return cudaErrorInvalidValue;
+    a.total_su = static_cast<int>(units);
     const int smem = C::smem_bytes(a.kb64);
     auto kern = cgemm_ix_wres_kernel<STAGES, BKS, NBUF, MAXK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -269,3 +269,15 @@ def test_flag_rules():
     with tcbf.Plan(1, 8, 8, 8, tcbf.MODE_FP16, flags=tcbf.FLAG_INTERLEAVED_X) as plan:
         with pytest.raises(tcbf.TcbfError):  # the failure-path hook is one-SM planar only
             plan.debug_drop_fill(0)
+
+
+@pytest.mark.parametrize("config", [0, 4, 5, 6])
+@pytest.mark.parametrize("B,Bw", [(6, 2), (6, 1), (5, 5)])
+def test_resident_weights_shared_by_several_products(config, B, Bw):
+    """Products that share a weight batch run back to back on one resident
+    W (one W load per weight batch and 128 beams): every product of the
+    group against the oracle, with ragged beam and sample counts."""
+    W, _ = ti.small_fp16(seed=B * 10 + Bw, M=300, K=288, N=8, B=Bw)
+    X = ti.complex_gaussian_fp16(ti.rng(B + Bw), (B, 288, 520))
+    Y = _run(W, X, config=config)
+    assert oracle.rel_frobenius(Y, oracle.cgemm(W, X)) <= TOL
