@@ -615,9 +615,10 @@ cudaError_t launch_ix(const tcbf_plan_s &pl, const void *Wp, const void *X, floa
 // are done (the MMA thread commits a W-empty barrier after a unit's last
 // tile), while the producer already streams the new unit's X.  A pair runs
 // the per_w products that share a weight batch back to back on the same
-// resident W (one W load per super-unit of weight batch x 128 beams), and
-// super-units run beam rows fastest, so the pairs working at one time share
-// the same products' X in L2.  One accumulation chunk (no promotion at this K).
+// resident W (one W load per super-unit of weight batch x 128 beams) unless
+// those coarser super-units would leave the last wave of pairs emptier (small
+// batches), and super-units run beam rows fastest, so the pairs working at
+// one time share the same products' X in L2.  One accumulation chunk (no promotion at this K).
 // The X ring's depth is what bounds the kernel (its loads wait on L2
 // latency, not bandwidth: half the X bytes per stage ran in the same time),
 // so the four-stage form (K <= 320: up to five W blocks) gives up the
@@ -656,7 +657,8 @@ struct IxWArgs {
     int m_tiles;        // 128-beam pair rows per batch
     int n_tiles;        // 128-sample tiles per batch
     int num_kb;         // X stages per tile
-    int total_su;       // w_batches x m_tiles: (weight batch, 128-beam row) super-units
+    int group;          // products per super-unit: 1, or per_w (they share W)
+    int total_su;       // batch / group x m_tiles super-units
     int w5d, x4d, y4d;
 };
 
@@ -691,16 +693,17 @@ __global__ void __launch_bounds__(kIxThreads, 1)
     const int u_first = static_cast<int>(cluster_id_x());
     const int u_step = static_cast<int>(nclusters_x());
     constexpr uint16_t kBoth = 3;
-    // The pair's i-th unit: super-units (weight batch, 128-beam row) strided
-    // over the pairs, each run as the per_w products that share its W one
-    // after the other, so the resident W is loaded once per super-unit.
+    // The pair's i-th unit: super-units (group of products, 128-beam row)
+    // strided over the pairs, each run as its `group` products one after the
+    // other; when the group is the products that share a weight batch, the
+    // resident W is loaded once per super-unit.
     auto unit = [&](int i, int &b, int &mt, int &sub) -> bool {
-        const int su = u_first + (i / args.per_w) * u_step;
+        const int su = u_first + (i / args.group) * u_step;
         if (su >= args.total_su) return false;
-        sub = i - (i / args.per_w) * args.per_w;
-        const int bw = su / args.m_tiles;
-        mt = su - bw * args.m_tiles;
-        b = bw * args.per_w + sub;
+        sub = i - (i / args.group) * args.group;
+        const int bg = su / args.m_tiles;
+        mt = su - bg * args.m_tiles;
+        b = bg * args.group + sub;
         return true;
     };
 
@@ -868,7 +871,7 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                     mma_commit_pair(tfull0 + 8 * acc, kBoth);
                 }
                 if (!ok) break;
-                if (sub == args.per_w - 1) {
+                if (sub == args.group - 1) {
                     mma_commit_pair(wempty, kBoth);    // the super-unit's W may be replaced
                     ++wuse;
                 }
@@ -987,8 +990,19 @@ cudaError_t launch_ix_wres(const tcbf_plan_s &pl, const void *Wp, const void *X,
     a.w5d = w5d;
     a.x4d = x4d;
     a.y4d = y4d;
-    const int64_t units = int64_t(a.m_tiles) * p.w_batches;
-    if (units > 0x7fffffff || int64_t(a.m_tiles) * p.batch > 0x7fffffff) return cudaErrorInvalidValue;
+    // products sharing a weight batch run back to back on one resident W
+    // unless the coarser super-units would fill the last wave of pairs
+    // worse (small batches)
+    const int64_t pairs = std::max(1, pl.num_sms / 2);
+    auto fill = [&](int64_t n) {
+        return static_cast<double>(n) / static_cast<double>(ceil_div(n, pairs) * pairs);
+    };
+    const int64_t per_unit = int64_t(a.m_tiles) * p.batch;
+    if (per_unit > 0x7fffffff) return cudaErrorInvalidValue;
+    a.group = (pl.per_w > 1 && fill(per_unit / pl.per_w) >= fill(per_unit) - 0.01)
+                  ? static_cast<int>(pl.per_w)
+                  : 1;
+    const int64_t units = per_unit / a.group;
     a.total_su = static_cast<int>(units);
     const int smem = C::smem_bytes(a.kb64);
     auto kern = cgemm_ix_wres_kernel<STAGES, BKS, NBUF, MAXK>;
