@@ -253,3 +253,29 @@ def test_autotune_layout_skips_interleaved_when_n_is_not_a_multiple_of_four():
         flags, ms = plan.autotune_layout(Wp, dev(X), Y, reps=1)
         assert ms[2] == -1 and ms[0] > 0 and ms[1] > 0
         assert flags in (0, FLAG_STACKED_X)
+
+
+def test_autotune_layout_then_host_pipeline():
+    """A layout change releases the plan's host-pipeline staging (sized for
+    the old layout): the end-to-end call made before and after the tuner
+    both match the oracle."""
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_AUTO_LAYOUT, MODE_FP16, Plan
+    B, M, N, K = 4, 200, 256, 288
+    W, X = ti.small_fp16(seed=31, M=M, K=K, N=N, B=B)
+    ref = oracle.cgemm(W, X)
+    with Plan(B, M, N, K, MODE_FP16, flags=FLAG_AUTO_LAYOUT) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        plan.transpose_pack(0, dev(W), Wp)
+        Xh = torch.from_numpy(X).pin_memory()
+        for tune in (False, True):
+            if tune:
+                Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
+                plan.autotune_layout(Wp, dev(X), Y, reps=1)
+            Yh = torch.full((B, M, N, 2), float("nan"), dtype=torch.float32).pin_memory()
+            plan.beamform_host(Xh, Wp, Yh, chunk=2)
+            torch.cuda.synchronize()
+            assert plan.last_device_error() == 0
+            y = Yh.numpy().astype(np.float64)
+            assert oracle.rel_frobenius(y[..., 0] + 1j * y[..., 1], ref) <= TOL
