@@ -272,12 +272,15 @@ def test_flag_rules():
 
 
 @pytest.mark.parametrize("config", [0, 4, 5, 6])
-@pytest.mark.parametrize("B,Bw", [(6, 2), (6, 1), (5, 5)])
-def test_resident_weights_shared_by_several_products(config, B, Bw):
+@pytest.mark.parametrize("B,Bw,M,N", [(6, 2, 300, 520), (6, 1, 300, 520), (5, 5, 300, 520),
+                                      (152, 76, 100, 64), (304, 76, 100, 36)])
+def test_resident_weights_shared_by_several_products(config, B, Bw, M, N):
     """Products that share a weight batch run back to back on one resident
-    W (one W load per weight batch and 128 beams): every product of the
-    group against the oracle, with ragged beam and sample counts."""
-    W, _ = ti.small_fp16(seed=B * 10 + Bw, M=300, K=288, N=8, B=Bw)
-    X = ti.complex_gaussian_fp16(ti.rng(B + Bw), (B, 288, 520))
+    W (one W load per weight batch and 128 beams) when that fills the last
+    wave of SM pairs as well: 152 and 304 products of one 128-beam row on
+    76 pairs take groups of 2 and 4; the ragged cases keep one product per
+    unit.  Every product against the oracle."""
+    W, _ = ti.small_fp16(seed=B * 10 + Bw, M=M, K=288, N=8, B=Bw)
+    X = ti.complex_gaussian_fp16(ti.rng(B + Bw), (B, 288, N))
     Y = _run(W, X, config=config)
     assert oracle.rel_frobenius(Y, oracle.cgemm(W, X)) <= TOL
