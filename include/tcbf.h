@@ -145,7 +145,8 @@ typedef enum {
  * tcbf_weights_from_geometry, consumed by tcbf_beamform_*).  The GEMM
  * needs its inputs split into real and imaginary planes (Sec. VI) and tiled
  * in device memory (Sec. III); here both operands are stored K-contiguous:
- *   FP16 W : [w_batches][2][M][Kp] binary16, Kp = K rounded up to 8, zero pad
+ *   FP16 W : [w_batches][2][M][Kp] binary16, Kp = K rounded up to 64 (rows of
+ *            whole 128-byte lines), zero pad
  *   FP16 X : [batch][2][N][Kp]     binary16 (X transposed: samples are rows);
  *            with TCBF_FLAG_STACKED_X [batch][3][N][Kp], planes -Xi, Xr, Xi
  *            (-Xi: the Xi plane with every sign bit flipped, its pad -0.0);
@@ -383,7 +384,7 @@ const char *tcbf_status_string(tcbf_status s);
  *   Y:       [batch][M][N] interleaved complex FP32 output.
  *   check:   0 = return after launching; nonzero = wait for the stream and
  *            report a device-side timeout as TCBF_ERR_TIMEOUT.
- * Returns TCBF_ERR_BUDGET (nothing launched) when batch*2*N*round_up(K,8)*2
+ * Returns TCBF_ERR_BUDGET (nothing launched) when batch*2*N*round_up(K,64)*2
  * bytes of packed samples exceed 64 MiB.  The first call on a device looks
  * up the array's device address and the device's properties; make that
  * first call before any stream capture.  The lookup is repeated when the

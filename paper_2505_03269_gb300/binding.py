@@ -175,7 +175,7 @@ class Plan:
 
     @property
     def Kp(self):
-        return (self.K + 7) // 8 * 8
+        return (self.K + 63) // 64 * 64
 
     @property
     def Kw(self):

@@ -130,7 +130,7 @@ namespace {
 // operations per byte of the stacked layout (packed W, packed X with its
 // third plane, Y) reach the threshold, planar otherwise.
 uint32_t auto_layout(const tcbf_problem &q) {
-    const double Kp = static_cast<double>(round_up(q.K, 8));
+    const double Kp = static_cast<double>(packed_row_k(q.K));
     const double ops = 8.0 * q.batch * q.M * q.N * q.K;
     const double bytes = 4.0 * q.w_batches * q.M * Kp + 6.0 * q.batch * q.N * Kp +
                          8.0 * q.batch * q.M * q.N;
@@ -189,7 +189,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
     pl->device = device;
     pl->num_sms = prop.multiProcessorCount;
     pl->per_w = q.batch / q.w_batches;
-    pl->Kp = round_up(q.K, 8);
+    pl->Kp = packed_row_k(q.K);
     pl->Kw = round_up(q.K, 128) / 32;
     pl->Kb2 = fp8_row_bytes(q.K, q.flags);
     pl->config = 0;

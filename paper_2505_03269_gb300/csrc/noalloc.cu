@@ -121,7 +121,7 @@ TCBF_EXPORT tcbf_status tcbf_beamform_fp16_noalloc(const tcbf_problem *p, int de
         q.batch > 65535)
         return TCBF_ERR_UNSUPPORTED;
     // the packed samples must fit the static scratch
-    const int64_t Kp = round_up(q.K, 8);
+    const int64_t Kp = packed_row_k(q.K);
     const double need = double(q.batch) * 2.0 * double(q.N) * double(Kp) * 2.0;
     if (need > double(kNoallocScratchBytes)) return TCBF_ERR_BUDGET;
 

@@ -149,7 +149,7 @@ double now_s(const tcbf_server_s *s) {
 
 size_t packed_bytes_for(int mode, int64_t rows, int64_t K) {
     switch (mode) {
-        case TCBF_MODE_FP16: return size_t(2 * rows * round_up(K, 8) * 2);
+        case TCBF_MODE_FP16: return size_t(2 * rows * packed_row_k(K) * 2);
         case TCBF_MODE_1BIT: return size_t(2 * rows * (round_up(K, 128) / 32) * 4);
         default: return size_t(2 * rows * 2 * round_up(K, 64) + rows * 4);
     }
@@ -167,7 +167,7 @@ tcbf_plan_s request_plan(const tcbf_server_s *s, const Req &q) {
     pl.device = s->device;
     pl.num_sms = s->num_sms;
     pl.per_w = 1;
-    pl.Kp = round_up(q.K, 8);
+    pl.Kp = packed_row_k(q.K);
     pl.Kw = round_up(q.K, 128) / 32;
     pl.Kb2 = fp8_row_bytes(q.K, pl.p.flags);
     pl.config = 0;

@@ -42,7 +42,7 @@ def _expected_planes(V16, k_axis_last):
     if not k_axis_last:                     # X [B][K][N][2] -> rows are N
         V16 = np.ascontiguousarray(V16.transpose(0, 2, 1, 3))
     nb, rows, K, _ = V16.shape
-    Kp = (K + 7) // 8 * 8
+    Kp = (K + 63) // 64 * 64
     out = np.zeros((nb, 2, rows, Kp), np.float16)
     out[:, 0, :, :K] = V16[..., 0]
     out[:, 1, :, :K] = V16[..., 1]

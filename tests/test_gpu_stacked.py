@@ -50,7 +50,7 @@ def _run(W, X, stacked=True, config=None, src_type=0, rows=None, packed=False):
         Yh = Y.cpu().numpy().astype(np.float64)
         out = Yh[..., 0] + 1j * Yh[..., 1]
         if packed:
-            return out, Xp.cpu().numpy(), (K + 7) // 8 * 8
+            return out, Xp.cpu().numpy(), (K + 63) // 64 * 64
         return out
 
 
@@ -156,9 +156,9 @@ def _auto_threshold():
 
 def _intensity(B, Bw, M, N, K):
     """8 B M N K operations over the bytes of the stacked layout: packed W
-    (2 planes), packed X (3 planes), both padded to K rounded up to 8, and
+    (2 planes), packed X (3 planes), both padded to K rounded up to 64, and
     the complex64 output."""
-    Kp = (K + 7) // 8 * 8
+    Kp = (K + 63) // 64 * 64
     return 8.0 * B * M * N * K / (2 * 2 * Bw * M * Kp + 3 * 2 * B * N * Kp + 8 * B * M * N)
 
 
@@ -173,7 +173,7 @@ def test_auto_layout_follows_the_intensity(B, Bw, M, N, K):
     with Plan(B, M, N, K, MODE_FP16, w_batches=Bw, flags=FLAG_AUTO_LAYOUT) as plan:
         want = FLAG_STACKED_X if _intensity(B, Bw, M, N, K) >= _auto_threshold() else 0
         assert plan.flags == want
-        Kp = (K + 7) // 8 * 8
+        Kp = (K + 63) // 64 * 64
         assert plan.packed_size(1) == (3 if want else 2) * B * N * Kp * 2
 
 
