@@ -40,8 +40,13 @@
 // error grows linearly with K (measured ~2.4e-9 K, biased toward zero).
 // For K > kPromoteK the K loop is cut into chunks of kChunkBlocks stages;
 // each chunk accumulates from zero into a TMEM partial P and the epilogue
-// warps add P into a running sum S (second TMEM region) with FP32
-// round-to-nearest adds, so the error stays at the chunk's level.
+// warps add P into a running sum S with FP32 round-to-nearest adds, so the
+// error stays at the chunk's level.  The chunks alternate between the two
+// accumulators: chunk c's P lands in one while the other holds S (the sum
+// of chunks before c); the epilogue writes S + P over P, which then holds
+// the sum, and frees S's accumulator for chunk c + 1.  The MMAs wait only
+// for that add, and a tile's output drains while the next tile's first
+// chunk runs.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -344,7 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;                                  // accumulator hand-offs so far
-            const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
+            // promoted long K alternates the two accumulators (the launchers
+            // take K > kPromoteK only when two fit)
+            const int nbuf = C::ACC_BUFS;
             bool ok = true;
             for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
                 for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
@@ -460,9 +467,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t stage_buf = staging0 + (warp - 2) * 8192;
         const bool vec_ok = (args.N & 1) == 0;
         int ev = 0;
-        const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
+        const int nbuf = C::ACC_BUFS;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-        const uint32_t tS = tmem_base + lane_off + 2 * BN;    // running sum (promotion only)
         int chunk_count = 0;
         bool ok = true;
         for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
@@ -482,41 +488,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * 2 * BN;
-                if (ch + 1 < args.chunks) {
-                    // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
+                if (ch > 0) {
+                    // promote: the running sum S (the previous chunk's accumulator)
+                    // plus this chunk's P, FP32 round-to-nearest, into this
+                    // accumulator; then S's accumulator is free for the next chunk
+                    const uint32_t tS = tmem_base + lane_off + (acc ^ 1) * 2 * BN;
 #pragma unroll 1
                     for (int g = 0; g < BN / 16; ++g) {
-                        float pr[16], pi[16];
+                        float pr[16], pi[16], sr[16], si[16];
                         tmem_ld_2x16(tP + g * 16, tP + BN + g * 16, pr, pi);
-                        if (ch > 0) {
-                            float sr[16], si[16];
-                            tmem_ld_2x16(tS + g * 16, tS + BN + g * 16, sr, si);
+                        tmem_ld_2x16(tS + g * 16, tS + BN + g * 16, sr, si);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                pr[i] = __fadd_rn(sr[i], pr[i]);
-                                pi[i] = __fadd_rn(si[i], pi[i]);
-                            }
+                        for (int i = 0; i < 16; ++i) {
+                            pr[i] = __fadd_rn(sr[i], pr[i]);
+                            pi[i] = __fadd_rn(si[i], pi[i]);
                         }
-                        tmem_st_2x16(tS + g * 16, tS + BN + g * 16, pr, pi);
+                        tmem_st_2x16(tP + g * 16, tP + BN + g * 16, pr, pi);
                     }
                     tmem_st_wait();
                     tc_fence_before();
-                    mbar_arrive(tempty0 + 8 * acc);
-                    continue;
+                    mbar_arrive(tempty0 + 8 * (acc ^ 1));
                 }
+                // a chunk before the last keeps its sum in its accumulator
+                if (ch + 1 < args.chunks) continue;
 #pragma unroll 1
                 for (int c = 0; c < BN / 16; ++c) {
                     float re[16], im[16];
                     tmem_ld_2x16(tP + c * 16, tP + BN + c * 16, re, im);
-                    if (args.chunks > 1) {
-                        float sr[16], si[16];
-                        tmem_ld_2x16(tS + c * 16, tS + BN + c * 16, sr, si);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            re[i] = __fadd_rn(sr[i], re[i]);
-                            im[i] = __fadd_rn(si[i], im[i]);
-                        }
-                    }
                     const int n0 = nt * BN + c * 16;
                     if (SPLIT && !BLK) {
 #pragma unroll
@@ -737,7 +735,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;
-            const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
+            // promoted long K alternates the two accumulators (the launchers
+            // take K > kPromoteK only when two fit)
+            const int nbuf = C::ACC_BUFS;
             bool ok = true;
             for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
                 for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
@@ -820,9 +820,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t stage_buf = staging0 + (warp - 2) * 8192;
         const bool vec_ok = (args.N & 1) == 0;
         int ev = 0;
-        const int nbuf = args.chunks > 1 ? 1 : C::ACC_BUFS;
+        const int nbuf = C::ACC_BUFS;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-        const uint32_t tS = tmem_base + lane_off + 2 * BN;
         int chunk_count = 0;
         bool ok = true;
         for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
@@ -843,37 +842,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * 2 * BN;
-                if (ch + 1 < args.chunks) {
+                if (ch > 0) {
+                    // promote: the running sum S (the previous chunk's accumulator)
+                    // plus this chunk's P, FP32 round-to-nearest, into this
+                    // accumulator; then S's accumulator is free for the next chunk
+                    const uint32_t tS = tmem_base + lane_off + (acc ^ 1) * 2 * BN;
 #pragma unroll 1
                     for (int g = 0; g < BN / 16; ++g) {
-                        float pr[16], pi[16];
+                        float pr[16], pi[16], sr[16], si[16];
                         tmem_ld_2x16(tP + g * 16, tP + BN + g * 16, pr, pi);
-                        if (ch > 0) {
-                            float sr[16], si[16];
-                            tmem_ld_2x16(tS + g * 16, tS + BN + g * 16, sr, si);
+                        tmem_ld_2x16(tS + g * 16, tS + BN + g * 16, sr, si);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                pr[i] = __fadd_rn(sr[i], pr[i]);
-                                pi[i] = __fadd_rn(si[i], pi[i]);
-                            }
+                        for (int i = 0; i < 16; ++i) {
+                            pr[i] = __fadd_rn(sr[i], pr[i]);
+                            pi[i] = __fadd_rn(si[i], pi[i]);
                         }
-                        tmem_st_2x16(tS + g * 16, tS + BN + g * 16, pr, pi);
+                        tmem_st_2x16(tP + g * 16, tP + BN + g * 16, pr, pi);
                     }
                     tmem_st_wait();
-                } else {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_remote(tempty0_lead + 8 * (acc ^ 1));
+                }
+                // a chunk before the last keeps its sum in its accumulator
+                if (ch + 1 < args.chunks) continue;
+                {
 #pragma unroll 1
                     for (int c = 0; c < BN / 16; ++c) {
                         float re[16], im[16];
                         tmem_ld_2x16(tP + c * 16, tP + BN + c * 16, re, im);
-                        if (args.chunks > 1) {
-                            float sr[16], si[16];
-                            tmem_ld_2x16(tS + c * 16, tS + BN + c * 16, sr, si);
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                re[i] = __fadd_rn(sr[i], re[i]);
-                                im[i] = __fadd_rn(si[i], im[i]);
-                            }
-                        }
                         const int n0 = nt * BN + c * 16;
                         if (SPLIT) {
 #pragma unroll

@@ -24,8 +24,9 @@
 // beams of W and 64 samples (128 real columns) of X.  A tile's accumulator
 // takes 256 TMEM columns, so two of them let one tile drain while the next
 // tile's MMAs run.  Long K is accumulated in promoted chunks as in the
-// planar kernels: the chunk's partial in columns 0-255, the FP32
-// round-to-nearest running sum in 256-511.  Every wait is bounded.
+// planar kernels: the chunks alternate between the two accumulators, the
+// FP32 round-to-nearest running sum moving into each new chunk's one.
+// Every wait is bounded.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -82,36 +83,34 @@ struct IxArgs {
     int total_tiles;
 };
 
-// One accumulator use of an interleaved-X epilogue warp (the warp's 16
-// TMEM lanes from tP; the running sum at tS): for a chunk before the last,
-// promote it into the sum (FP32 round-to-nearest); for the last, add the sum
-// if there is one, form Re and Im of its 8 beams x 128 samples and store
-// them, 32 samples at a time: two 1 KB boxes of 8 beams x 16 samples, one
-// 4-D store of both when N % 16 == 0 (y4d: Y seen as 16-sample chunks x
-// beams x batches), else two 3-D stores.
+// Promotion of a long-K chunk by an interleaved-X epilogue warp (its 16
+// TMEM lanes): the running sum S (at tS, the previous chunk's accumulator)
+// plus the chunk's P (at tP), FP32 round-to-nearest, written over P.
+template <int ACC_COLS>
+__device__ __forceinline__ void ix_promote(uint32_t tP, uint32_t tS) {
+#pragma unroll 1
+    for (int g = 0; g < ACC_COLS / 64; ++g) {
+        float v[32], sv[32];
+        tmem_ld_16x256b_x8(tP + 64 * g, v);
+        tmem_ld_16x256b_x8(tS + 64 * g, sv);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
+        tmem_st_16x256b_x8(tP + 64 * g, v);
+    }
+    tmem_st_wait();
+}
+
+// The output of one tile by an interleaved-X epilogue warp (the warp's 16
+// TMEM lanes from tP): Re and Im of its 8 beams x 128 samples, stored 32
+// samples at a time: two 1 KB boxes of 8 beams x 16 samples, one 4-D store
+// of both when N % 16 == 0 (y4d: Y seen as 16-sample chunks x beams x
+// batches), else two 3-D stores.
 template <int ACC_COLS, int STAGE_BUF, int NBUF = 2>
-__device__ __forceinline__ void ix_drain(uint32_t tP, uint32_t tS, int ch, int chunks, int lane,
-                                         uint32_t stage_buf, int &nstore, int nt, int N, int beam0,
-                                         int b, const CUtensorMap *tmY, int y4d) {
+__device__ __forceinline__ void ix_drain(uint32_t tP, int lane, uint32_t stage_buf, int &nstore,
+                                         int nt, int N, int beam0, int b, const CUtensorMap *tmY,
+                                         int y4d) {
     const int rb = lane >> 2;                             // beam within the group
     const int sq = lane & 3;                              // sample within each 4
-    if (ch + 1 < chunks) {
-        // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
-#pragma unroll 1
-        for (int g = 0; g < ACC_COLS / 64; ++g) {
-            float v[32];
-            tmem_ld_16x256b_x8(tP + 64 * g, v);
-            if (ch > 0) {
-                float sv[32];
-                tmem_ld_16x256b_x8(tS + 64 * g, sv);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
-            }
-            tmem_st_16x256b_x8(tS + 64 * g, v);
-        }
-        tmem_st_wait();
-        return;
-    }
     // the next block's tensor-memory load is issued before this block is
     // staged and stored, so its latency overlaps the stores
     float v[32];
@@ -119,12 +118,6 @@ __device__ __forceinline__ void ix_drain(uint32_t tP, uint32_t tS, int ch, int c
 #pragma unroll 1
     for (int c = 0; c < ACC_COLS / 64; ++c) {
         tmem_wait_ld_32(v);
-        if (chunks > 1) {
-            float sv[32];
-            tmem_ld_16x256b_x8(tS + 64 * c, sv);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(sv[i], v[i]);
-        }
         // v[4i..4i+3] = Wr Xr, Wr Xi, Wi Xr, Wi Xi of sample 4i + sq
         float re[8], im[8];
 #pragma unroll
@@ -345,7 +338,7 @@ __global__ void __launch_bounds__(kIxThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;
-            const int nbuf = args.chunks > 1 ? 1 : 2;
+            const int nbuf = 2;   // promoted long K alternates them too
             bool ok = true;
             for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
                 for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
@@ -421,8 +414,7 @@ __global__ void __launch_bounds__(kIxThreads, 1)
         const int half = (warp - 2) >> 2;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32 + half * 16) << 16;
         const uint32_t stage_buf = staging0 + (warp - 2) * 2 * C::STAGE_BUF;
-        const uint32_t tS = tmem_base + lane_off + C::ACC_COLS;   // running sum (promotion only)
-        const int nbuf = args.chunks > 1 ? 1 : 2;
+        const int nbuf = 2;
         int ev = 0;
         int nstore = 0;
         bool ok = true;
@@ -439,8 +431,23 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * C::ACC_COLS;
-                ix_drain<C::ACC_COLS, C::STAGE_BUF>(tP, tS, ch, args.chunks, lane, stage_buf, nstore,
-                                                   nt, args.N, beam0, b, &tmY, args.y4d);
+                if (ch > 0) {
+                    // the sum moves into this chunk's accumulator; the previous
+                    // one is then free for the next chunk's MMAs
+                    ix_promote<C::ACC_COLS>(tP, tmem_base + lane_off + (acc ^ 1) * C::ACC_COLS);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (PAIR)
+                            mbar_arrive_remote(tempty0_lead + 8 * (acc ^ 1));
+                        else
+                            mbar_arrive(tempty0 + 8 * (acc ^ 1));
+                    }
+                }
+                // a chunk before the last keeps its sum in its accumulator
+                if (ch + 1 < args.chunks) continue;
+                ix_drain<C::ACC_COLS, C::STAGE_BUF>(tP, lane, stage_buf, nstore, nt, args.N, beam0,
+                                                   b, &tmY, args.y4d);
                 // this warp is done with the accumulator: release it (in a pair,
                 // on the even CTA's barrier; its values are in registers or
                 // staged, so no cluster-scope fence is needed)
@@ -903,7 +910,7 @@ __global__ void __launch_bounds__(kIxThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * C::ACC_COLS;
-                ix_drain<C::ACC_COLS, C::STAGE_BUF, C::NBUF>(tP, tP, 0, 1, lane, stage_buf, nstore, nt,
+                ix_drain<C::ACC_COLS, C::STAGE_BUF, C::NBUF>(tP, lane, stage_buf, nstore, nt,
                                                             args.N,
                                                    beam0, b, &tmY, args.y4d);
                 tc_fence_before();

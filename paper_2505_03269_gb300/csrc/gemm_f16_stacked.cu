@@ -17,8 +17,9 @@
 // every stage.  K is staged in 32-element blocks with 64-byte swizzle (one
 // stage: both W planes 16 KB + three X planes 24 KB) so that five stages
 // fit beside the output staging.  Long K is accumulated in promoted chunks
-// exactly as in the one-SM kernel (Sec. III-B's FP32 accumulation, here
-// with the partial in TMEM columns 0-255 and the running sum in 256-511).
+// as in the planar kernels (Sec. III-B's FP32 accumulation): the chunks
+// alternate between the accumulators in TMEM columns 0-255 and 256-511, the
+// running sum moving into each new chunk's accumulator.
 // The default configuration runs the same product on SM pairs (M = 256,
 // cta_group::2), see cgemm_stacked_pair_kernel.
 #include <cuda_fp16.h>
@@ -206,12 +207,11 @@ __global__ void __launch_bounds__(kStkThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;                                  // accumulator hand-offs so far
-            const int nbuf = args.chunks > 1 ? 1 : 2;
             bool ok = true;
             for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
                 for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
-                    const int acc = ev % nbuf;
-                    const uint32_t aphase = (ev / nbuf) & 1;
+                    const int acc = ev & 1;
+                    const uint32_t aphase = (ev >> 1) & 1;
                     if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
                         ok = false;
                         break;
@@ -270,9 +270,7 @@ __global__ void __launch_bounds__(kStkThreads, 1)
         const uint32_t stage_buf = staging0 + (warp - 2) * 4096;
         const bool vec_ok = (args.N & 1) == 0;
         int ev = 0;
-        const int nbuf = args.chunks > 1 ? 1 : 2;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-        const uint32_t tS = tmem_base + lane_off + 2 * SBN;    // running sum (promotion only)
         bool ok = true;
         for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
             int b, mt, nt;
@@ -280,49 +278,41 @@ __global__ void __launch_bounds__(kStkThreads, 1)
             const int m = mt * SBM + row;
             float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
             for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
-                const int acc = ev % nbuf;
-                const uint32_t aphase = (ev / nbuf) & 1;
+                const int acc = ev & 1;
+                const uint32_t aphase = (ev >> 1) & 1;
                 if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * 2 * SBN;
-                if (ch + 1 < args.chunks) {
-                    // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
+                if (ch > 0) {
+                    // promote: the running sum S (the previous chunk's accumulator)
+                    // plus this chunk's P, FP32 round-to-nearest, into this
+                    // accumulator; then S's accumulator is free for the next chunk
+                    const uint32_t tS = tmem_base + lane_off + (acc ^ 1) * 2 * SBN;
 #pragma unroll 1
                     for (int g = 0; g < SBN / 16; ++g) {
-                        float pr[16], pi[16];
+                        float pr[16], pi[16], sr[16], si[16];
                         tmem_ld_2x16(tP + g * 16, tP + SBN + g * 16, pr, pi);
-                        if (ch > 0) {
-                            float sr[16], si[16];
-                            tmem_ld_2x16(tS + g * 16, tS + SBN + g * 16, sr, si);
+                        tmem_ld_2x16(tS + g * 16, tS + SBN + g * 16, sr, si);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                pr[i] = __fadd_rn(sr[i], pr[i]);
-                                pi[i] = __fadd_rn(si[i], pi[i]);
-                            }
+                        for (int i = 0; i < 16; ++i) {
+                            pr[i] = __fadd_rn(sr[i], pr[i]);
+                            pi[i] = __fadd_rn(si[i], pi[i]);
                         }
-                        tmem_st_2x16(tS + g * 16, tS + SBN + g * 16, pr, pi);
+                        tmem_st_2x16(tP + g * 16, tP + SBN + g * 16, pr, pi);
                     }
                     tmem_st_wait();
                     tc_fence_before();
-                    mbar_arrive(tempty0 + 8 * acc);
-                    continue;
+                    mbar_arrive(tempty0 + 8 * (acc ^ 1));
                 }
+                // a chunk before the last keeps its sum in its accumulator
+                if (ch + 1 < args.chunks) continue;
 #pragma unroll 1
                 for (int c = 0; c < SBN / 16; ++c) {
                     float re[16], im[16];
                     tmem_ld_2x16(tP + c * 16, tP + SBN + c * 16, re, im);
-                    if (args.chunks > 1) {
-                        float sr[16], si[16];
-                        tmem_ld_2x16(tS + c * 16, tS + SBN + c * 16, sr, si);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            re[i] = __fadd_rn(sr[i], re[i]);
-                            im[i] = __fadd_rn(si[i], im[i]);
-                        }
-                    }
                     const int n0 = nt * SBN + c * 16;
                     if (args.tma_store) {
                         if (n0 < args.N) {
@@ -647,12 +637,11 @@ __global__ void __launch_bounds__(kStkThreads, 1)
             int stage = 0;
             uint32_t phase = 0;
             int ev = 0;
-            const int nbuf = args.chunks > 1 ? 1 : 2;
             bool ok = true;
             for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
                 for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
-                    const int acc = ev % nbuf;
-                    const uint32_t aphase = (ev / nbuf) & 1;
+                    const int acc = ev & 1;
+                    const uint32_t aphase = (ev >> 1) & 1;
                     if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
                         ok = false;
                         break;
@@ -703,9 +692,7 @@ __global__ void __launch_bounds__(kStkThreads, 1)
         const uint32_t stage_buf = staging0 + (warp - 2) * 4096;
         const bool vec_ok = (args.N & 1) == 0;
         int ev = 0;
-        const int nbuf = args.chunks > 1 ? 1 : 2;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
-        const uint32_t tS = tmem_base + lane_off + 2 * SBN;    // running sum (promotion only)
         bool ok = true;
         for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
             int b, mp, nt;
@@ -714,77 +701,72 @@ __global__ void __launch_bounds__(kStkThreads, 1)
             const int m = mrow0 + row;
             float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
             for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
-                const int acc = ev % nbuf;
-                const uint32_t aphase = (ev / nbuf) & 1;
+                const int acc = ev & 1;
+                const uint32_t aphase = (ev >> 1) & 1;
                 if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * 2 * SBN;
-                if (ch + 1 < args.chunks) {
-                    // promote: S = P (first chunk) or S = S + P, FP32 round-to-nearest
+                if (ch > 0) {
+                    // promote: the running sum S (the previous chunk's accumulator)
+                    // plus this chunk's P, FP32 round-to-nearest, into this
+                    // accumulator; then S's accumulator is free for the next chunk
+                    const uint32_t tS = tmem_base + lane_off + (acc ^ 1) * 2 * SBN;
 #pragma unroll 1
                     for (int g = 0; g < SBN / 16; ++g) {
-                        float pr[16], pi[16];
+                        float pr[16], pi[16], sr[16], si[16];
                         tmem_ld_2x16(tP + g * 16, tP + SBN + g * 16, pr, pi);
-                        if (ch > 0) {
-                            float sr[16], si[16];
-                            tmem_ld_2x16(tS + g * 16, tS + SBN + g * 16, sr, si);
+                        tmem_ld_2x16(tS + g * 16, tS + SBN + g * 16, sr, si);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                pr[i] = __fadd_rn(sr[i], pr[i]);
-                                pi[i] = __fadd_rn(si[i], pi[i]);
-                            }
+                        for (int i = 0; i < 16; ++i) {
+                            pr[i] = __fadd_rn(sr[i], pr[i]);
+                            pi[i] = __fadd_rn(si[i], pi[i]);
                         }
-                        tmem_st_2x16(tS + g * 16, tS + SBN + g * 16, pr, pi);
+                        tmem_st_2x16(tP + g * 16, tP + SBN + g * 16, pr, pi);
                     }
                     tmem_st_wait();
-                } else {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_remote(tempty0_lead + 8 * (acc ^ 1));
+                }
+                // a chunk before the last keeps its sum in its accumulator
+                if (ch + 1 < args.chunks) continue;
 #pragma unroll 1
-                    for (int c = 0; c < SBN / 16; ++c) {
-                        float re[16], im[16];
-                        tmem_ld_2x16(tP + c * 16, tP + SBN + c * 16, re, im);
-                        if (args.chunks > 1) {
-                            float sr[16], si[16];
-                            tmem_ld_2x16(tS + c * 16, tS + SBN + c * 16, sr, si);
+                for (int c = 0; c < SBN / 16; ++c) {
+                    float re[16], im[16];
+                    tmem_ld_2x16(tP + c * 16, tP + SBN + c * 16, re, im);
+                    const int n0 = nt * SBN + c * 16;
+                    if (args.tma_store) {
+                        if (n0 < args.N) {
+                            if (lane == 0) bulk_wait_read<0>();
+                            __syncwarp();
+                            const uint32_t rbase = stage_buf + lane * 128;
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                re[i] = __fadd_rn(sr[i], re[i]);
-                                im[i] = __fadd_rn(si[i], im[i]);
+                            for (int j = 0; j < 8; ++j)
+                                st_shared_v4(rbase + ((j ^ (lane & 7)) << 4), re[2 * j], im[2 * j],
+                                             re[2 * j + 1], im[2 * j + 1]);
+                            fence_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                tma_store_3d(&tmY, stage_buf, 2 * n0, mrow0 + quarter * 32, b);
+                                bulk_commit();
                             }
                         }
-                        const int n0 = nt * SBN + c * 16;
-                        if (args.tma_store) {
-                            if (n0 < args.N) {
-                                if (lane == 0) bulk_wait_read<0>();
-                                __syncwarp();
-                                const uint32_t rbase = stage_buf + lane * 128;
+                    } else if (m < args.M && n0 < args.N) {
+                        if (vec_ok && n0 + 16 <= args.N) {
+                            float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
 #pragma unroll
-                                for (int j = 0; j < 8; ++j)
-                                    st_shared_v4(rbase + ((j ^ (lane & 7)) << 4), re[2 * j], im[2 * j],
-                                                 re[2 * j + 1], im[2 * j + 1]);
-                                fence_async_smem();
-                                __syncwarp();
-                                if (lane == 0) {
-                                    tma_store_3d(&tmY, stage_buf, 2 * n0, mrow0 + quarter * 32, b);
-                                    bulk_commit();
+                            for (int i = 0; i < 8; ++i)
+                                dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                if (n0 + i < args.N) {
+                                    yrow[2 * (n0 + i)] = re[i];
+                                    yrow[2 * (n0 + i) + 1] = im[i];
                                 }
-                            }
-                        } else if (m < args.M && n0 < args.N) {
-                            if (vec_ok && n0 + 16 <= args.N) {
-                                float4 *dst = reinterpret_cast<float4 *>(yrow + 2 * n0);
-#pragma unroll
-                                for (int i = 0; i < 8; ++i)
-                                    dst[i] = make_float4(re[2 * i], im[2 * i], re[2 * i + 1], im[2 * i + 1]);
-                            } else {
-#pragma unroll
-                                for (int i = 0; i < 16; ++i)
-                                    if (n0 + i < args.N) {
-                                        yrow[2 * (n0 + i)] = re[i];
-                                        yrow[2 * (n0 + i) + 1] = im[i];
-                                    }
-                            }
                         }
                     }
                 }
