@@ -219,6 +219,14 @@ TCBF_EXPORT tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p
             }
         }
         if (interleaved_x(*pl)) pl->config = gemm_f16_ix_default_config(q.K);
+        // stacked X (or a layout the tuner may set to it) with promoted long
+        // K: the workspace that lets the pair kernel split its last wave; a
+        // plan without it runs those tiles whole
+        if (q.mode == TCBF_MODE_FP16 && (q.flags & (TCBF_FLAG_STACKED_X | TCBF_FLAG_AUTO_LAYOUT))) {
+            const size_t ws = stacked_tail_ws_bytes(*pl);
+            if (ws > 0 && cudaMalloc(&pl->tail_ws, ws) == cudaSuccess) pl->tail_ws_bytes = ws;
+            else pl->tail_ws = nullptr;
+        }
         // 1-bit: the 4-bit tensor path by default when its planes fit
         if (q.mode == TCBF_MODE_1BIT && gemm_1bit_fp4_reserve(*pl) == cudaSuccess &&
             gemm_1bit_fp4_usable(*pl))
@@ -237,6 +245,7 @@ TCBF_EXPORT tcbf_status tcbf_plan_destroy(tcbf_plan_t plan) {
         if (plan->m_prefix) cudaFree(plan->m_prefix);
         if (plan->status) cudaFree(plan->status);
         if (plan->ix_planes) cudaFree(plan->ix_planes);
+        if (plan->tail_ws) cudaFree(plan->tail_ws);
         gemm_1bit_fp4_release(*plan);
     }
     delete plan;

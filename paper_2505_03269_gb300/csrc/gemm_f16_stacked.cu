@@ -67,6 +67,12 @@ struct StkArgs {
     int kc_blocks;         // blocks per accumulation chunk
     int chunks;
     int total_tiles;
+    // SM-pair tiles from split_first on (the last, partial wave) run as
+    // split_parts units of whole accumulation chunks each (split_first =
+    // total_tiles: no split); total_units counts whole tiles and parts
+    int split_first;
+    int split_parts;
+    int total_units;
 };
 
 template <int STAGES, int CL>
@@ -432,6 +438,9 @@ cudaError_t launch_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp
     const int64_t total = m_units * a.tiles.n_tiles;     // tiles, or cluster tiles
     if (total > 0x7fffffff) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
+    a.split_first = a.total_tiles;                       // one-SM tiles run whole
+    a.split_parts = 1;
+    a.total_units = a.total_tiles;
     auto kern = cgemm_stacked_kernel<STAGES, CL>;
     cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
@@ -484,6 +493,7 @@ cudaError_t launch_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp
 // ===========================================================================
 constexpr int PBK = 64;                  // K per stage: one 128-byte row
 constexpr int kStkPairChunkBlocks = 32;  // stages (x 64 K) per promoted chunk
+constexpr int kStkPairStages = 3;
 // Pair tiles run in groups of kPairGroupM pair rows, samples fastest within
 // a group: the clusters running at one time then share their W rows and
 // their X columns in L2.  With samples fastest over all rows, a product
@@ -501,11 +511,46 @@ struct CfgStkPair {
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
+// (batch, 256-row pair tile, sample tile) of pair tile t: groups of
+// kPairGroupM pair rows (the last one possibly shorter), pair rows fastest
+// inside a group, then sample tiles
+__host__ __device__ __forceinline__ void pair_decode(const StkArgs &a, int t, int &b, int &mp,
+                                                     int &nt) {
+    const int m_pairs = (a.tiles.m_tiles + 1) / 2;
+    const int per_b = m_pairs * a.tiles.n_tiles;
+    b = t / per_b;
+    const int local = t - b * per_b;
+    const int group = local / (kPairGroupM * a.tiles.n_tiles);
+    const int first = group * kPairGroupM;
+    const int gm = min(kPairGroupM, m_pairs - first);
+    const int in = local - group * kPairGroupM * a.tiles.n_tiles;
+    mp = first + in % gm;
+    nt = in / gm;
+}
+
+// Unit u of the SM-pair kernel: whole tile u, or, from split_first on, part
+// j of a tail tile, its chunks [c0, c1).  Returns whether it is a part.
+__device__ __forceinline__ bool pair_unit(const StkArgs &a, int u, int &t, int &c0, int &c1) {
+    if (u < a.split_first) {
+        t = u;
+        c0 = 0;
+        c1 = a.chunks;
+        return false;
+    }
+    const int v = u - a.split_first;
+    const int j = v % a.split_parts;
+    t = a.split_first + v / a.split_parts;
+    c0 = j * a.chunks / a.split_parts;
+    c1 = (j + 1) * a.chunks / a.split_parts;
+    return true;
+}
+
 template <int STAGES>
 __global__ void __launch_bounds__(kStkThreads, 1)
     cgemm_stacked_pair_kernel(const __grid_constant__ CUtensorMap tmW,
                               const __grid_constant__ CUtensorMap tmX,
-                              const __grid_constant__ CUtensorMap tmY, const StkArgs args) {
+                              const __grid_constant__ CUtensorMap tmY,
+                              const __grid_constant__ CUtensorMap tmS, const StkArgs args) {
     using C = CfgStkPair<STAGES>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
@@ -532,21 +577,6 @@ __global__ void __launch_bounds__(kStkThreads, 1)
     // packed planes -Xi (0), Xr (1), Xi (2): this CTA's rows of B1 and of B2
     const int plane_b1 = leader ? 1 : 2;
     const int plane_b2 = leader ? 0 : 1;
-    // (batch, 256-row pair tile, sample tile) of pair tile t: groups of
-    // kPairGroupM pair rows (the last one possibly shorter), pair rows
-    // fastest inside a group, then sample tiles
-    auto decode = [&](int t, int &b, int &mp, int &nt) {
-        const int m_pairs = (args.tiles.m_tiles + 1) / 2;
-        const int per_b = m_pairs * args.tiles.n_tiles;
-        b = t / per_b;
-        const int local = t - b * per_b;
-        const int group = local / (kPairGroupM * args.tiles.n_tiles);
-        const int first = group * kPairGroupM;
-        const int gm = min(kPairGroupM, m_pairs - first);
-        const int in = local - group * kPairGroupM * args.tiles.n_tiles;
-        mp = first + in % gm;
-        nt = in / gm;
-    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -563,6 +593,7 @@ __global__ void __launch_bounds__(kStkThreads, 1)
         tma_prefetch_desc(&tmW);
         tma_prefetch_desc(&tmX);
         if (args.tma_store) tma_prefetch_desc(&tmY);
+        if (args.split_first < args.total_tiles) tma_prefetch_desc(&tmS);
     }
     if (warp == 1) {
         tmem_alloc_pair(smem_u32(tmem_slot), C::TMEM_COLS);
@@ -583,11 +614,13 @@ __global__ void __launch_bounds__(kStkThreads, 1)
             uint32_t phase = 0;
             uint32_t issued = 0;
             bool ok = true;
-            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
-                int b, mp, nt;
-                decode(t, b, mp, nt);
+            for (int u = t_first; u < args.total_units && ok; u += t_step) {
+                int t, c0, c1, b, mp, nt;
+                pair_unit(args, u, t, c0, c1);
+                pair_decode(args, t, b, mp, nt);
                 const int bw = b / args.per_w;
-                for (int kb = 0; kb < args.num_kb; ++kb) {
+                const int kb_end = min(args.num_kb, c1 * args.kc_blocks);
+                for (int kb = c0 * args.kc_blocks; kb < kb_end; ++kb) {
                     if (!mbar_wait(empty0 + 8 * stage, phase ^ 1u) || *abort_flag) {
                         ok = false;
                         break;
@@ -638,8 +671,10 @@ __global__ void __launch_bounds__(kStkThreads, 1)
             uint32_t phase = 0;
             int ev = 0;
             bool ok = true;
-            for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
-                for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+            for (int u = t_first; u < args.total_units && ok; u += t_step) {
+                int t, c0, c1;
+                pair_unit(args, u, t, c0, c1);
+                for (int ch = c0; ch < c1; ++ch, ++ev) {
                     const int acc = ev & 1;
                     const uint32_t aphase = (ev >> 1) & 1;
                     if (!mbar_wait(tempty0 + 8 * acc, aphase ^ 1u)) {
@@ -694,13 +729,14 @@ __global__ void __launch_bounds__(kStkThreads, 1)
         int ev = 0;
         const uint32_t lane_off = static_cast<uint32_t>(quarter * 32) << 16;
         bool ok = true;
-        for (int t = t_first; t < args.total_tiles && ok; t += t_step) {
-            int b, mp, nt;
-            decode(t, b, mp, nt);
+        for (int u = t_first; u < args.total_units && ok; u += t_step) {
+            int t, c0, c1, b, mp, nt;
+            const bool part = pair_unit(args, u, t, c0, c1);
+            pair_decode(args, t, b, mp, nt);
             const int mrow0 = mp * 256 + 128 * rank;           // this CTA's first row
             const int m = mrow0 + row;
             float *yrow = args.Y + (static_cast<size_t>(b) * args.M + m) * args.N * 2;
-            for (int ch = 0; ch < args.chunks; ++ch, ++ev) {
+            for (int ch = c0; ch < c1; ++ch, ++ev) {
                 const int acc = ev & 1;
                 const uint32_t aphase = (ev >> 1) & 1;
                 if (!mbar_wait(tfull0 + 8 * acc, aphase) || *abort_flag) {
@@ -709,7 +745,7 @@ __global__ void __launch_bounds__(kStkThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t tP = tmem_base + lane_off + acc * 2 * SBN;
-                if (ch > 0) {
+                if (!part && ch > 0) {
                     // promote: the running sum S (the previous chunk's accumulator)
                     // plus this chunk's P, FP32 round-to-nearest, into this
                     // accumulator; then S's accumulator is free for the next chunk
@@ -732,7 +768,11 @@ __global__ void __launch_bounds__(kStkThreads, 1)
                     if (lane == 0) mbar_arrive_remote(tempty0_lead + 8 * (acc ^ 1));
                 }
                 // a chunk before the last keeps its sum in its accumulator
-                if (ch + 1 < args.chunks) continue;
+                if (!part && ch + 1 < c1) continue;
+                // a part stores each of its chunks: a tail tile's first chunk to
+                // Y, the later ones to its workspace slots (a second kernel adds them)
+                const bool to_ws = part && ch > 0;
+                const int slot = (t - args.split_first) * (args.chunks - 1) + ch - 1;
 #pragma unroll 1
                 for (int c = 0; c < SBN / 16; ++c) {
                     float re[16], im[16];
@@ -750,7 +790,10 @@ __global__ void __launch_bounds__(kStkThreads, 1)
                             fence_async_smem();
                             __syncwarp();
                             if (lane == 0) {
-                                tma_store_3d(&tmY, stage_buf, 2 * n0, mrow0 + quarter * 32, b);
+                                if (to_ws)
+                                    tma_store_3d(&tmS, stage_buf, 32 * c, 128 * rank + quarter * 32, slot);
+                                else
+                                    tma_store_3d(&tmY, stage_buf, 2 * n0, mrow0 + quarter * 32, b);
                                 bulk_commit();
                             }
                         }
@@ -793,6 +836,101 @@ __global__ void __launch_bounds__(kStkThreads, 1)
         tc_fence_after();
         tmem_dealloc_pair(tmem_base, C::TMEM_COLS);
     }
+}
+
+// After a launch whose last wave was split: Y holds the first chunk of each
+// tail tile; its later chunks come from the workspace and are added in chunk
+// order with FP32 round-to-nearest, as the unsplit kernel promotes them, so
+// the result is the same bit for bit.
+__global__ void stacked_tail_fixup_kernel(const StkArgs args, const float2 *__restrict__ ws) {
+    constexpr int kPerTile = 256 * SBN;     // (row, sample) pairs of a pair tile
+    const int64_t total = int64_t(args.total_tiles - args.split_first) * kPerTile;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int tt = static_cast<int>(i / kPerTile);
+        const int e = static_cast<int>(i - int64_t(tt) * kPerTile);
+        const int r = e / SBN;
+        int b, mp, nt;
+        pair_decode(args, args.split_first + tt, b, mp, nt);
+        const int m = mp * 256 + r;
+        const int n = nt * SBN + (e - r * SBN);
+        if (m >= args.M || n >= args.N) continue;
+        float2 *y = reinterpret_cast<float2 *>(args.Y) + (static_cast<size_t>(b) * args.M + m) * args.N + n;
+        float2 v = *y;
+        const float2 *q = ws + static_cast<size_t>(tt) * (args.chunks - 1) * kPerTile + e;
+        for (int c = 1; c < args.chunks; ++c, q += kPerTile) {
+            const float2 w = __ldg(q);
+            v.x = __fadd_rn(v.x, w.x);
+            v.y = __fadd_rn(v.y, w.y);
+        }
+        *y = v;
+    }
+}
+
+// Pair tiles and accumulation chunks of a plan on the SM-pair kernel.
+void pair_shape(const tcbf_plan_s &pl, StkArgs &a) {
+    const tcbf_problem &p = pl.p;
+    a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, 128));
+    a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, SBN));
+    a.num_kb = static_cast<int>(ceil_div(p.K, PBK));
+    a.kc_blocks = p.K > kStkPromoteK ? kStkPairChunkBlocks : a.num_kb;
+    a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
+}
+
+// Resident SM pairs of the pair kernel on the plan's device, measured once
+// (benign if two threads both measure).
+template <int STAGES>
+cudaError_t pair_max_clusters(const tcbf_plan_s &pl, int &mc) {
+    static std::atomic<int> cache[64];
+    mc = cache[pl.device & 63].load(std::memory_order_relaxed);
+    if (mc > 0) return cudaSuccess;
+    using C = CfgStkPair<STAGES>;
+    auto kern = cgemm_stacked_pair_kernel<STAGES>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.num_sms / 2 * 2);
+    cfg.blockDim = dim3(kStkThreads);
+    cfg.dynamicSmemBytes = C::SMEM_BYTES;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (mc < 1) return cudaErrorInvalidConfiguration;
+    cache[pl.device & 63].store(mc, std::memory_order_relaxed);
+    return cudaSuccess;
+}
+
+// The split of the last, partial wave: its r pair tiles run as s units each
+// of whole accumulation chunks on the SM pairs the wave leaves idle, s =
+// min(chunks, pairs / r) >= 2.  Only for promoted long K (two or more
+// chunks) with Y stored by the TMA, and while the workspace for the tail
+// tiles' later chunks (r x (chunks - 1) pair tiles of 256 KB) stays within
+// kTailWsMaxBytes.
+constexpr size_t kTailWsMaxBytes = size_t(64) << 20;
+constexpr size_t kTailSlotBytes = size_t(256) * SBN * 8;
+void pair_split(StkArgs &a, int pairs) {
+    a.split_first = a.total_tiles;
+    a.split_parts = 1;
+    a.total_units = a.total_tiles;
+    if (!a.tma_store || a.chunks < 2 || pairs < 2) return;
+    const int r = a.total_tiles % pairs;
+    if (r == 0) return;
+    const int parts = std::min(a.chunks, pairs / r);
+    if (parts < 2 || size_t(r) * (a.chunks - 1) * kTailSlotBytes > kTailWsMaxBytes) return;
+    a.split_first = a.total_tiles - r;
+    a.split_parts = parts;
+    a.total_units = a.split_first + r * parts;
+}
+
+size_t pair_split_ws_bytes(const StkArgs &a) {
+    return size_t(a.total_tiles - a.split_first) * (a.chunks - 1) * kTailSlotBytes;
 }
 
 template <int STAGES>
@@ -847,19 +985,30 @@ cudaError_t launch_stacked_pair(const tcbf_plan_s &pl, const void *Wp, const voi
     a.per_w = static_cast<int>(pl.per_w);
     a.tiles.prefix = nullptr;
     a.tiles.batch = static_cast<int>(p.batch);
-    a.tiles.m_tiles = static_cast<int>(ceil_div(p.M, 128));
-    a.tiles.n_tiles = static_cast<int>(ceil_div(p.N, SBN));
     a.tiles.raster = 0;
-    a.num_kb = static_cast<int>(ceil_div(p.K, PBK));
-    a.kc_blocks = p.K > kStkPromoteK ? kStkPairChunkBlocks : a.num_kb;
-    a.chunks = (a.num_kb + a.kc_blocks - 1) / a.kc_blocks;
+    pair_shape(pl, a);
     const int64_t total = ceil_div(a.tiles.m_tiles, 2) * p.batch * a.tiles.n_tiles;   // pair tiles
-    if (total > 0x7fffffff) return cudaErrorInvalidValue;
+    if (total > 0x7fffffff / 8) return cudaErrorInvalidValue;
     a.total_tiles = static_cast<int>(total);
-    auto kern = cgemm_stacked_pair_kernel<STAGES>;
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    int mc = 0;
+    cudaError_t e = pair_max_clusters<STAGES>(pl, mc);
     if (e != cudaSuccess) return e;
+    pair_split(a, mc);
+    // the split needs the plan's workspace (made with the plan); without it,
+    // or with a smaller one, the tiles run whole (the same results)
+    CUtensorMap tmS = tmX;
+    const bool split = a.split_first < a.total_tiles;
+    if (split && (!pl.tail_ws || pl.tail_ws_bytes < pair_split_ws_bytes(a))) pair_split(a, 0);
+    if (a.split_first < a.total_tiles) {
+        const uint64_t dims[3] = {uint64_t(2 * SBN), 256,
+                                  uint64_t(pair_split_ws_bytes(a) / kTailSlotBytes)};
+        const uint64_t strides[2] = {uint64_t(2 * SBN * 4), uint64_t(kTailSlotBytes)};
+        const uint32_t box[3] = {32, 32, 1};
+        if (encode_tiled(&tmS, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pl.tail_ws, dims, strides, box,
+                         CU_TENSOR_MAP_SWIZZLE_128B) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    auto kern = cgemm_stacked_pair_kernel<STAGES>;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
@@ -871,19 +1020,14 @@ cudaError_t launch_stacked_pair(const tcbf_plan_s &pl, const void *Wp, const voi
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // resident pairs per device, measured once (benign if two threads both measure)
-    static std::atomic<int> max_clusters[64];
-    int mc = max_clusters[pl.device & 63].load(std::memory_order_relaxed);
-    if (mc == 0) {
-        cfg.gridDim = dim3(pl.num_sms / 2 * 2);
-        e = cudaOccupancyMaxActiveClusters(&mc, kern, &cfg);
-        if (e != cudaSuccess) return e;
-        if (mc < 1) return cudaErrorInvalidConfiguration;
-        max_clusters[pl.device & 63].store(mc, std::memory_order_relaxed);
-    }
-    cfg.gridDim = dim3(static_cast<unsigned>(std::min<int64_t>(total, mc)) * 2);
-    e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, a);
+    cfg.gridDim = dim3(static_cast<unsigned>(std::min(a.total_units, mc)) * 2);
+    e = cudaLaunchKernelEx(&cfg, kern, tmW, tmX, tmY, tmS, a);
     if (e != cudaSuccess) return e;
+    if (a.split_first < a.total_tiles) {
+        const int64_t n = int64_t(a.total_tiles - a.split_first) * 256 * SBN;
+        const int grid = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), int64_t(pl.num_sms) * 8));
+        stacked_tail_fixup_kernel<<<grid, 256, 0, s>>>(a, static_cast<const float2 *>(pl.tail_ws));
+    }
     return cudaGetLastError();
 }
 
@@ -894,7 +1038,8 @@ struct StkConfig {
 };
 
 const StkConfig kStkConfigs[] = {
-    {"f16 stacked-X N256 2-SM pair BM256 BN128 BK64 stages3 tmem-double", 0, launch_stacked_pair<3>},
+    {"f16 stacked-X N256 2-SM pair BM256 BN128 BK64 stages3 tmem-double", 0,
+     launch_stacked_pair<kStkPairStages>},
     {"f16 stacked-X N256 BM128 BN128 BK32-sw64 stages5 tmem-double cluster2 X-multicast", 0,
      launch_stacked<5, 2>},
     {"f16 stacked-X N256 BM128 BN128 BK32-sw64 stages5 tmem-double n-fastest", 0, launch_stacked<5, 1>},
@@ -912,6 +1057,20 @@ int gemm_f16_stacked_num_configs() {
 const char *gemm_f16_stacked_config_name(int config) {
     if (config < 0 || config >= gemm_f16_stacked_num_configs()) return "invalid";
     return kStkConfigs[config].name;
+}
+
+size_t stacked_tail_ws_bytes(const tcbf_plan_s &pl) {
+    if (pl.m_prefix) return 0;
+    StkArgs a = {};
+    a.tma_store = (pl.p.N % 2 == 0) ? 1 : 0;
+    pair_shape(pl, a);
+    const int64_t total = ceil_div(a.tiles.m_tiles, 2) * pl.p.batch * a.tiles.n_tiles;
+    if (total > 0x7fffffff / 8) return 0;
+    a.total_tiles = static_cast<int>(total);
+    int mc = 0;
+    if (pair_max_clusters<kStkPairStages>(pl, mc) != cudaSuccess) return 0;
+    pair_split(a, mc);
+    return a.split_first < a.total_tiles ? pair_split_ws_bytes(a) : 0;
 }
 
 cudaError_t launch_gemm_f16_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,

@@ -46,6 +46,11 @@ struct tcbf_plan_s {
     // created with TCBF_FLAG_AUTO_LAYOUT: tcbf_autotune_layout may change
     // the packed-X layout
     bool auto_layout = false;
+    // FP16 plans that may run the stacked SM-pair kernel with promoted long
+    // K: partial chunk sums of the tiles of a split last wave (nullptr: no
+    // split, the tiles run whole)
+    void *tail_ws = nullptr;
+    size_t tail_ws_bytes = 0;
 };
 
 namespace tcbf {
@@ -110,6 +115,9 @@ cudaError_t launch_gemm_f16(const tcbf_plan_s &pl, const void *Wp, const void *X
 // Stacked-plane FP16 GEMM (plans with TCBF_FLAG_STACKED_X).
 int gemm_f16_stacked_num_configs();
 const char *gemm_f16_stacked_config_name(int config);
+// Workspace the stacked SM-pair kernel needs to split the plan's last wave
+// of tiles (0: it runs them whole).
+size_t stacked_tail_ws_bytes(const tcbf_plan_s &pl);
 cudaError_t launch_gemm_f16_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp, float *Y,
                                     cudaStream_t s);
 

@@ -117,6 +117,88 @@ def test_stacked_long_k_within_tolerance(K, config):
     assert oracle.rel_frobenius(_run(W, X, config=config), oracle.cgemm(W, X)) <= TOL
 
 
+def _pair_split(B, M, N, K, pairs=76):
+    """The SM-pair kernel's split of its last wave (host rule, for the test
+    shapes below): (tail tiles, parts per tail tile) or None.  K above 4096 is
+    summed in chunks of 2048; the r tiles of a partial last wave run as
+    min(chunks, pairs // r) units of whole chunks each."""
+    tiles = (M + 255) // 256 * ((N + 127) // 128) * B
+    chunks = (K + 2047) // 2048 if K > 4096 else 1
+    r = tiles % pairs
+    if chunks < 2 or r == 0 or min(chunks, pairs // r) < 2:
+        return None
+    return r, min(chunks, pairs // r)
+
+
+@pytest.mark.parametrize("B,M,N,K", [(1, 1024, 1024, 8192), (3, 300, 200, 5000),
+                                     (1, 2052, 2052, 4100)])
+def test_stacked_pair_split_last_wave_bit_for_bit(B, M, N, K):
+    """Tiles of a partial last wave run as parts of whole accumulation chunks
+    on the idle SM pairs, the later chunks added by a second kernel in chunk
+    order: the same bits as the one-SM kernel (which runs every tile whole),
+    the same bits on a second call, and within the bar of the oracle at
+    points of the split tiles."""
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_STACKED_X, MODE_FP16, Plan
+    props = torch.cuda.get_device_properties(0)
+    if props.multi_processor_count == 152:
+        assert _pair_split(B, M, N, K) is not None
+    W, _ = ti.small_fp16(seed=K + M, M=M, K=K, N=8)
+    X = ti.complex_gaussian_fp16(ti.rng(K + N), (B, K, N))
+    with Plan(B, M, N, K, MODE_FP16, w_batches=1, flags=FLAG_STACKED_X) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        Xp = empty_bytes(plan.packed_size(1))
+        plan.transpose_pack(0, dev(W), Wp)
+        plan.transpose_pack(1, dev(X), Xp)
+        outs = []
+        for config in (0, 0, 1):
+            plan.set_config(config)
+            Y = torch.full((B, M, N, 2), float("nan"), dtype=torch.float32, device="cuda")
+            plan.beamform_fp16(Wp, Xp, Y)
+            torch.cuda.synchronize()
+            assert plan.last_device_error() == 0
+            outs.append(Y.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+    # points in the last tiles of the tile order (the last batch's last
+    # sample tiles and rows), against the FP64 oracle
+    g = ti.rng(5)
+    pts = np.stack([np.full(64, B - 1), g.integers(max(0, M - 300), M, 64),
+                    g.integers(max(0, N - 256), N, 64)], axis=1)
+    Yc = outs[0][..., 0].astype(np.float64) + 1j * outs[0][..., 1].astype(np.float64)
+    got = Yc[pts[:, 0], pts[:, 1], pts[:, 2]]
+    want = oracle.cgemm_points(W, X, pts)
+    assert np.linalg.norm(got - want) <= TOL * np.linalg.norm(want)
+
+
+def test_stacked_pair_split_in_a_captured_step():
+    """A captured step (pack + split GEMM + the chunk sums) replays to the
+    direct launches' bits."""
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_STACKED_X, MODE_FP16, Plan
+    B, M, N, K = 1, 1024, 1024, 8192
+    W, _ = ti.small_fp16(seed=3, M=M, K=K, N=8)
+    X = ti.complex_gaussian_fp16(ti.rng(4), (B, K, N))
+    with Plan(B, M, N, K, MODE_FP16, w_batches=1, flags=FLAG_STACKED_X) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        Xp = empty_bytes(plan.packed_size(1))
+        Xd = dev(X)
+        plan.transpose_pack(0, dev(W), Wp)
+        Y = torch.empty((B, M, N, 2), dtype=torch.float32, device="cuda")
+        plan.graph_capture(Xd, Xp, Wp, Y)
+        plan.graph_launch()
+        torch.cuda.synchronize()
+        Yg = Y.cpu().numpy().copy()
+        plan.transpose_pack(1, Xd, Xp)
+        Y.fill_(float("nan"))
+        plan.beamform_fp16(Wp, Xp, Y)
+        torch.cuda.synchronize()
+        assert plan.last_device_error() == 0
+        assert np.array_equal(Y.cpu().numpy(), Yg)
+
+
 def test_stacked_uneven_beam_counts():
     rows = [300, 1, 129]
     W, _ = ti.small_fp16(seed=21, M=300, K=100, N=8, B=3)
