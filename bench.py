@@ -534,9 +534,10 @@ class GpuWorkload:
 
     def fp4_plane_bytes(self):
         """Bytes the 4-bit 1-bit GEMM actually reads: its E2M1 planes (W: Wr,
-        Wi; X: -Xi, Xr, Xi; 16 bytes per word of bits) and Y."""
-        w, kw = self.w, self.plan.Kw
-        return (w["w_batches"] * 2 * w["M"] + w["B"] * 3 * w["N"]) * kw * 16 + self.Y.numel() * 4
+        Wi; X: -Xi, Xr, Xi; 16 bytes per word of bits, rows of whole 128-byte
+        lines) and Y."""
+        w, kq = self.w, (self.plan.Kw + 7) // 8 * 8
+        return (w["w_batches"] * 2 * w["M"] + w["B"] * 3 * w["N"]) * kq * 16 + self.Y.numel() * 4
 
 
 def fp8_error_vs_fp16(gw):

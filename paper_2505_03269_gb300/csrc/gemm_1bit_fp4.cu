@@ -73,38 +73,42 @@ __device__ __forceinline__ uint4 e2m1_word(uint32_t w, int valid) {
                       e2m1_byte<NEG>(w >> 16, valid - 16), e2m1_byte<NEG>(w >> 24, valid - 24));
 }
 
-// W bits [w_batches][2][w_rows][Kw] -> E2M1 [w_batches][2][M][Kw x 16 bytes].
+// E2M1 rows hold Kq = Kw rounded up to 8 words (16 bytes each), so every row
+// starts on a 128-byte line: each 128-byte box row of the GEMM's tensor loads
+// is then one whole line.  Words at or beyond Kw (k >= K) are 0.
+
+// W bits [w_batches][2][w_rows][Kw] -> E2M1 [w_batches][2][M][Kq x 16 bytes].
 __global__ void expand_w_fp4_kernel(const uint32_t *__restrict__ Wb, uint4 *__restrict__ Wq,
-                                    int64_t rows, int M, int64_t w_rows, int Kw, int K) {
-    const int64_t total = rows * Kw;
+                                    int64_t rows, int M, int64_t w_rows, int Kw, int Kq, int K) {
+    const int64_t total = rows * Kq;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = i / Kw;
-        const int w = static_cast<int>(i - r * Kw);
+        const int64_t r = i / Kq;
+        const int w = static_cast<int>(i - r * Kq);
         const int64_t plane = r / M;
         const int64_t m = r - plane * M;
-        const uint32_t bits = __ldg(Wb + (plane * w_rows + m) * Kw + w);
+        const uint32_t bits = w < Kw ? __ldg(Wb + (plane * w_rows + m) * Kw + w) : 0u;
         Wq[i] = e2m1_word<false>(bits, K - 32 * w);
     }
 }
 
-// X bits [batch][2][N][Kw] -> E2M1 planes [batch][3][N][Kw x 16 bytes]:
+// X bits [batch][2][N][Kw] -> E2M1 planes [batch][3][N][Kq x 16 bytes]:
 // -Xi, Xr, Xi.
 __global__ void expand_x_fp4_kernel(const uint32_t *__restrict__ Xb, uint4 *__restrict__ Xq,
-                                    int64_t batch, int64_t N, int Kw, int K) {
-    const int64_t total = batch * N * Kw;
+                                    int64_t batch, int64_t N, int Kw, int Kq, int K) {
+    const int64_t total = batch * N * Kq;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = i / Kw;            // b * N + n
-        const int w = static_cast<int>(i - r * Kw);
+        const int64_t r = i / Kq;            // b * N + n
+        const int w = static_cast<int>(i - r * Kq);
         const int64_t b = r / N;
         const int64_t n = r - b * N;
-        const uint32_t xr = __ldg(Xb + ((b * 2) * N + n) * Kw + w);
-        const uint32_t xi = __ldg(Xb + ((b * 2 + 1) * N + n) * Kw + w);
+        const uint32_t xr = w < Kw ? __ldg(Xb + ((b * 2) * N + n) * Kw + w) : 0u;
+        const uint32_t xi = w < Kw ? __ldg(Xb + ((b * 2 + 1) * N + n) * Kw + w) : 0u;
         const int valid = K - 32 * w;
-        Xq[((b * 3) * N + n) * Kw + w] = e2m1_word<true>(xi, valid);
-        Xq[((b * 3 + 1) * N + n) * Kw + w] = e2m1_word<false>(xr, valid);
-        Xq[((b * 3 + 2) * N + n) * Kw + w] = e2m1_word<false>(xi, valid);
+        Xq[((b * 3) * N + n) * Kq + w] = e2m1_word<true>(xi, valid);
+        Xq[((b * 3 + 1) * N + n) * Kq + w] = e2m1_word<false>(xr, valid);
+        Xq[((b * 3 + 2) * N + n) * Kq + w] = e2m1_word<false>(xi, valid);
     }
 }
 
@@ -124,7 +128,7 @@ __device__ __forceinline__ void load_cf(const void *src, size_t i, bool f32, flo
     }
 }
 
-// Interleaved complex X [batch][K][N] -> E2M1 planes [batch][3][N][Kw x 16
+// Interleaved complex X [batch][K][N] -> E2M1 planes [batch][3][N][Kq x 16
 // bytes] (-Xi, Xr, Xi) in one pass, without the packed bits.  A block of
 // 256 threads takes 128 samples x 256 k (8 words): warp w reads the 32 rows
 // of word w, lane l samples n0 + 4l .. n0 + 4l + 3 (one 16-byte load of FP16
@@ -138,12 +142,12 @@ constexpr int kPackWords = 8;
 template <bool F32, bool VEC>
 __global__ void __launch_bounds__(256) pack_x_fp4_kernel(const void *__restrict__ src,
                                                          uint8_t *__restrict__ Xq, int K, int N,
-                                                         int Kw, int n_tiles, int w_tiles) {
+                                                         int Kw, int Kq, int n_tiles, int w_tiles) {
     __shared__ uint32_t bits[2][kPackSamples][kPackWords + 1];   // [re/im][sample][word]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t b = blockIdx.y;
-    const size_t row = static_cast<size_t>(Kw) * 16;
+    const size_t row = static_cast<size_t>(Kq) * 16;
     for (int t = blockIdx.x; t < n_tiles * w_tiles; t += gridDim.x) {
         const int n0 = (t % n_tiles) * kPackSamples;
         const int w0 = (t / n_tiles) * kPackWords;
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(256) pack_x_fp4_kernel(const void *__restrict_
             const int sr = (c / kPackWords) % kPackSamples;
             const int wd = c % kPackWords;
             const int n = n0 + sr, ww = w0 + wd;
-            if (n >= N || ww >= Kw) continue;
+            if (n >= N || ww >= Kq) continue;
             const int valid = K - 32 * ww;
             // planes -Xi (0), Xr (1), Xi (2)
             const uint32_t v = bits[plane == 1 ? 0 : 1][sr][wd];
@@ -216,18 +220,18 @@ __global__ void __launch_bounds__(256) pack_x_fp4_kernel(const void *__restrict_
 }
 
 // Interleaved complex W [w_batches][M][K] -> E2M1 planes [w_batches][2][M]
-// [Kw x 16 bytes] (Wr, Wi): one warp per row and word, lane l reads k = 32 w
-// + l, a ballot forms each plane's word and four lanes write its 16 bytes.
+// [Kq x 16 bytes] (Wr, Wi): one warp per row and word, lane l reads k = 32 w
+// + l, a ballot forms each plane's word and two lanes write its 16 bytes.
 template <bool F32>
 __global__ void pack_w_fp4_kernel(const void *__restrict__ src, uint4 *__restrict__ Wq,
-                                  int64_t rows, int64_t M, int K, int Kw) {
+                                  int64_t rows, int64_t M, int K, int Kq) {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = int64_t(gridDim.x) * (blockDim.x >> 5);
-    const int64_t total = rows * Kw;
+    const int64_t total = rows * Kq;
     for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < total;
          i += warps_total) {
-        const int64_t r = i / Kw;
-        const int w = static_cast<int>(i % Kw);
+        const int64_t r = i / Kq;
+        const int w = static_cast<int>(i % Kq);
         const int k = 32 * w + lane;
         float re = -1.f, im = -1.f;
         if (k < K) load_cf(src, static_cast<size_t>(r) * K + k, F32, re, im);
@@ -237,7 +241,7 @@ __global__ void pack_w_fp4_kernel(const void *__restrict__ src, uint4 *__restric
         const int valid = K - 32 * w;
         if (lane < 2) {
             const uint4 v = e2m1_word<false>(lane == 0 ? br : bi, valid);
-            Wq[(static_cast<size_t>(bw * 2 + lane) * M + m) * Kw + w] = v;
+            Wq[(static_cast<size_t>(bw * 2 + lane) * M + m) * Kq + w] = v;
         }
     }
 }
@@ -565,7 +569,9 @@ __global__ void __launch_bounds__(kFp4Threads, 1)
     }
 }
 
-int64_t fp4_row_bytes(const tcbf_plan_s &pl) { return pl.Kw * 16; }
+// E2M1 row length in 16-byte words: Kw rounded up to 8 (128-byte rows)
+int64_t fp4_words(const tcbf_plan_s &pl) { return round_up(pl.Kw, 8); }
+int64_t fp4_row_bytes(const tcbf_plan_s &pl) { return fp4_words(pl) * 16; }
 
 size_t fp4_w_bytes(const tcbf_plan_s &pl) {
     return static_cast<size_t>(pl.p.w_batches) * 2 * pl.p.M * fp4_row_bytes(pl);
@@ -586,13 +592,13 @@ cudaError_t launch_expand(const tcbf_plan_s &pl, int which, const uint32_t *bits
     uint8_t *Wq = static_cast<uint8_t *>(pl.fp4_buf);
     if (which == 0) {
         const int64_t rows = p.w_batches * 2 * p.M;
-        expand_w_fp4_kernel<<<expand_grid(rows * pl.Kw, pl.num_sms), 256, 0, s>>>(
+        expand_w_fp4_kernel<<<expand_grid(rows * fp4_words(pl), pl.num_sms), 256, 0, s>>>(
             bits, reinterpret_cast<uint4 *>(Wq), rows, static_cast<int>(p.M), w_plane_rows(pl),
-            static_cast<int>(pl.Kw), static_cast<int>(p.K));
+            static_cast<int>(pl.Kw), static_cast<int>(fp4_words(pl)), static_cast<int>(p.K));
     } else {
-        expand_x_fp4_kernel<<<expand_grid(p.batch * p.N * pl.Kw, pl.num_sms), 256, 0, s>>>(
+        expand_x_fp4_kernel<<<expand_grid(p.batch * p.N * fp4_words(pl), pl.num_sms), 256, 0, s>>>(
             bits, reinterpret_cast<uint4 *>(Wq + fp4_w_bytes(pl)), p.batch, p.N,
-            static_cast<int>(pl.Kw), static_cast<int>(p.K));
+            static_cast<int>(pl.Kw), static_cast<int>(fp4_words(pl)), static_cast<int>(p.K));
     }
     return cudaGetLastError();
 }
@@ -606,15 +612,16 @@ cudaError_t launch_pack_fp4(const tcbf_plan_s &pl, int which, int src_type, cons
     const bool f32 = src_type == TCBF_SRC_CF32;
     if (which == 0) {
         const int64_t rows = p.w_batches * p.M;
-        const int grid = expand_grid(rows * pl.Kw * 32, pl.num_sms);
+        const int Kq = static_cast<int>(fp4_words(pl));
+        const int grid = expand_grid(rows * Kq * 32, pl.num_sms);
         auto *dst = reinterpret_cast<uint4 *>(Wq);
         if (f32)
-            pack_w_fp4_kernel<true><<<grid, 256, 0, s>>>(src, dst, rows, p.M, int(p.K), int(pl.Kw));
+            pack_w_fp4_kernel<true><<<grid, 256, 0, s>>>(src, dst, rows, p.M, int(p.K), Kq);
         else
-            pack_w_fp4_kernel<false><<<grid, 256, 0, s>>>(src, dst, rows, p.M, int(p.K), int(pl.Kw));
+            pack_w_fp4_kernel<false><<<grid, 256, 0, s>>>(src, dst, rows, p.M, int(p.K), Kq);
     } else {
         const int n_tiles = static_cast<int>(ceil_div(p.N, kPackSamples));
-        const int w_tiles = static_cast<int>(ceil_div(pl.Kw, kPackWords));
+        const int w_tiles = static_cast<int>(fp4_words(pl) / kPackWords);
         // blocks per batch: enough for every SM to hold several across the batches
         const int64_t per_b = int64_t(n_tiles) * w_tiles;
         const int bx = static_cast<int>(std::max<int64_t>(
@@ -624,7 +631,8 @@ cudaError_t launch_pack_fp4(const tcbf_plan_s &pl, int which, int src_type, cons
         // 16-byte loads need every row of X to start 16-byte aligned (N % 4 == 0)
         const bool vec = p.N % 4 == 0;
         auto run = [&](auto kern) {
-            kern<<<grid, 256, 0, s>>>(src, dst, int(p.K), int(p.N), int(pl.Kw), n_tiles, w_tiles);
+            kern<<<grid, 256, 0, s>>>(src, dst, int(p.K), int(p.N), int(pl.Kw), int(fp4_words(pl)),
+                                      n_tiles, w_tiles);
         };
         if (f32)
             vec ? run(pack_x_fp4_kernel<true, true>) : run(pack_x_fp4_kernel<true, false>);
