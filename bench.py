@@ -529,8 +529,16 @@ class GpuWorkload:
         """Algorithmic bytes of the GEMM: its operands in the method's own
         encoding (packed FP16 / FP8 / TF32 planes or the interleaved samples;
         for 1-bit the packed sign bits, 2 bits per complex value) read once,
-        and Y written once."""
-        return self.plan.packed_size(0) + self.plan.packed_size(1) + self.Y.numel() * 4
+        and Y written once.  FP16 and TF32 planes count K elements per row:
+        their rows are padded to K rounded up to 64 (whole 128-byte lines),
+        and the pad is zeros of the layout, not data."""
+        w_bytes, x_bytes = self.plan.packed_size(0), self.plan.packed_size(1)
+        if self.w["mode"] in ("fp16", "tf32"):
+            K, Kp = self.w["K"], self.plan.Kp
+            w_bytes = w_bytes * K // Kp
+            if self.layout != "interleaved":
+                x_bytes = x_bytes * K // Kp
+        return w_bytes + x_bytes + self.Y.numel() * 4
 
     def fp4_plane_bytes(self):
         """Bytes the 4-bit 1-bit GEMM actually reads: its E2M1 planes (W: Wr,
@@ -538,6 +546,25 @@ class GpuWorkload:
         lines) and Y."""
         w, kq = self.w, (self.plan.Kw + 7) // 8 * 8
         return (w["w_batches"] * 2 * w["M"] + w["B"] * 3 * w["N"]) * kq * 16 + self.Y.numel() * 4
+
+
+def stacked_split_launches(gw):
+    """1 when the stacked SM-pair GEMM splits its last wave (FP16, stacked X,
+    configuration 0, K > 4096 in chunks of 2048, a partial last wave of r
+    pair tiles with min(chunks, pairs // r) >= 2, N even, the chunk
+    workspace within 64 MiB): a second kernel then adds the later chunks."""
+    import torch
+    w = gw.w
+    if w["mode"] != "fp16" or gw.layout != "stacked" or gw.plan.get_config() != 0:
+        return 0
+    if w["K"] <= 4096 or w["N"] % 2:
+        return 0
+    pairs = torch.cuda.get_device_properties(0).multi_processor_count // 2
+    tiles = -(-w["M"] // 256) * -(-w["N"] // 128) * w["B"]
+    chunks, r = -(-w["K"] // 2048), tiles % pairs
+    if r == 0 or min(chunks, pairs // r) < 2 or r * (chunks - 1) * 256 * 1024 > 64 << 20:
+        return 0
+    return 1
 
 
 def fp8_error_vs_fp16(gw):
@@ -906,7 +933,8 @@ def main():
         # (the 4-bit 1-bit path packs X straight into its E2M1 planes); split-FP8
         # packs X in three kernels (column maxima, pack, exponents) after a memset
         "gpu_launches": ((4 if is_fp8(w) else 2 if gw.fp4() else
-                          1 if gw.layout == "interleaved" else 2) * args.steps),
+                          1 if gw.layout == "interleaved" else 2 + stacked_split_launches(gw))
+                         * args.steps),
         "roofline": roof,
         "kernels": {"gemm_ms": gemm_ms, "pack_ms": pack_ms if gw.layout != "interleaved" else 0.0,
                     "weights_ms_once": gw.weights_ms,
