@@ -12,8 +12,13 @@
  * Conventions that hold for every call:
  *  - All buffers are owned by the caller.  Unless stated otherwise a pointer
  *    argument is DEVICE memory of the plan's device, 256-byte aligned (any
- *    torch/cudaMalloc allocation is).  The plan owns only host state plus a
- *    small device status word.
+ *    torch/cudaMalloc allocation is).  The plan owns host state, a small
+ *    device status word and the device scratch some configurations need,
+ *    which it allocates itself: the E2M1 planes of 1-bit plans on the 4-bit
+ *    path, the planes an interleaved-X plan packs into when the fused kernel
+ *    cannot read X, and the chunk sums of a stacked-X FP16 plan whose last
+ *    partial wave of tiles is split (K > 4096; at most 64 MiB).  Calls on
+ *    one plan share these and must not overlap on the GPU.
  *  - Calls that take a stream are asynchronous and stream-ordered; argument
  *    errors are returned synchronously and nothing is launched.  Errors that
  *    only the device can see (a bounded wait that ran out) are recorded in
@@ -187,7 +192,8 @@ typedef enum {
 
 /* Create a plan for problem *p on CUDA device `device`.  Validates the
  * shape, checks for an sm_103 device and allocates the plan's 256-byte
- * device status word.  *out is set to NULL on error. */
+ * device status word and the scratch its default configuration and layout
+ * need.  *out is set to NULL on error. */
 tcbf_status tcbf_plan_create(tcbf_plan_t *out, const tcbf_problem *p, int device);
 
 /* Destroy a plan (NULL is accepted).  The caller must not have work that
@@ -241,6 +247,11 @@ tcbf_status tcbf_unpack_bits(tcbf_plan_t plan, int which, const uint32_t *src, v
  *   Wp, Xp: FP16 packed operands of this plan (mode TCBF_MODE_FP16).
  *   Y: [batch][M][N] interleaved complex FP32 (8 bytes per value), written
  *      in full.  Y must not overlap Wp or Xp.
+ * Above K = 4096 the sums are promoted to FP32 round-to-nearest every 2048 K.
+ * A stacked-X plan on SM pairs may run the tiles of its last partial wave as
+ * parts of whole 2048-K chunks on the pairs that wave leaves idle, and then
+ * launches a second kernel that adds their later chunks in chunk order (the
+ * same bits as whole tiles).
  */
 tcbf_status tcbf_beamform_fp16(tcbf_plan_t plan, const void *Wp, const void *Xp, float *Y,
                                tcbf_stream_t stream);
