@@ -1009,6 +1009,8 @@ cudaError_t launch_stacked_pair(const tcbf_plan_s &pl, const void *Wp, const voi
             return cudaErrorInvalidValue;
     }
     auto kern = cgemm_stacked_pair_kernel<STAGES>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
