@@ -229,6 +229,31 @@ def test_stacked_host_pipeline():
     assert np.array_equal(Yn[..., 0] + 1j * Yn[..., 1], Yd)
 
 
+@pytest.mark.parametrize("B,M,N,K", [(1, 600, 300, 5000), (4, 300, 260, 4500)])
+def test_stacked_host_pipeline_long_k(B, M, N, K):
+    """tcbf_beamform_host with promoted long K on stacked planes: its
+    sub-plans (row ranges of W, or chunks of batches) may split their last
+    wave with the plan's chunk workspace, one after the other on one
+    stream; the result equals the device-resident call bit for bit."""
+    import torch
+    from gpu_util import dev, empty_bytes
+    from paper_2505_03269_gb300 import FLAG_STACKED_X, MODE_FP16, Plan
+    W, _ = ti.small_fp16(seed=M + K, M=M, K=K, N=8)
+    X = ti.complex_gaussian_fp16(ti.rng(N + K), (B, K, N))
+    Yd = _run(W, X)
+    with Plan(B, M, N, K, MODE_FP16, w_batches=1, flags=FLAG_STACKED_X) as plan:
+        Wp = empty_bytes(plan.packed_size(0))
+        plan.transpose_pack(0, dev(W), Wp)
+        Xh = torch.from_numpy(X).pin_memory()
+        Yh = torch.empty((B, M, N, 2), dtype=torch.float32).pin_memory()
+        s = torch.cuda.Stream()
+        plan.beamform_host(Xh, Wp, Yh, stream=s)
+        s.synchronize()
+        assert plan.last_device_error() == 0
+    Yn = Yh.numpy().astype(np.float64)
+    assert np.array_equal(Yn[..., 0] + 1j * Yn[..., 1], Yd)
+
+
 def _auto_threshold():
     import os
     import re
