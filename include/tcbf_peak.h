@@ -38,6 +38,19 @@ extern "C" {
  */
 tcbf_status tcbf_peak_run(int kind, int device, int iters, double *seconds, double *ops);
 
+/*
+ * HBM stream with a chosen read/write mix, the ceiling of a memory-bound
+ * kernel's byte mix (the beamformer's output-heavy steps): read_bytes are
+ * read with 16-byte loads, then write_bytes written with 16-byte stores, by
+ * blocks_per_sm x SMs blocks of 256 threads (each thread reads its share,
+ * then writes its share; the threads' reads and writes overlap).  Both sizes
+ * multiples of 16 bytes; blocks_per_sm in [1, 64].  Allocates and frees the
+ * two device buffers.  *seconds: the fastest of three timed launches after a
+ * warm-up (CUDA events).  TCBF_ERR_OOM when the buffers do not fit.
+ */
+tcbf_status tcbf_peak_stream(int device, int64_t read_bytes, int64_t write_bytes, int blocks_per_sm,
+                             double *seconds);
+
 #ifdef __cplusplus
 }
 #endif

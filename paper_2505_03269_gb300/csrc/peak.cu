@@ -156,10 +156,85 @@ __global__ void __launch_bounds__(256) warp_peak_kernel(int iters, int seed, uin
     }
 }
 
+// HBM stream with a given read/write mix: each thread reads its share of
+// `src` with 16-byte loads (folded into one value), then writes its share of
+// `dst` with 16-byte stores.  The reads and writes of all threads overlap.
+__global__ void stream_mix_kernel(const uint4 *__restrict__ src, uint4 *__restrict__ dst,
+                                  int64_t nr, int64_t nw) {
+    const int64_t tid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
+    uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t i = tid; i < nr; i += nth) {
+        const uint4 v = __ldg(src + i);
+        acc.x ^= v.x;
+        acc.y ^= v.y;
+        acc.z ^= v.z;
+        acc.w ^= v.w;
+    }
+    for (int64_t i = tid; i < nw; i += nth) dst[i] = acc;
+}
+
 }  // namespace
 }  // namespace tcbf
 
 using namespace tcbf;
+
+TCBF_EXPORT tcbf_status tcbf_peak_stream(int device, int64_t read_bytes, int64_t write_bytes,
+                                         int blocks_per_sm, double *seconds) {
+    if (!seconds || read_bytes < 16 || write_bytes < 16 || (read_bytes & 15) ||
+        (write_bytes & 15) || blocks_per_sm < 1 || blocks_per_sm > 64)
+        return TCBF_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return TCBF_ERR_UNSUPPORTED;
+    if (device < 0 || device >= ndev) return TCBF_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    tcbf_status st = TCBF_OK;
+    void *src = nullptr, *dst = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&src, size_t(read_bytes)) != cudaSuccess ||
+        cudaMalloc(&dst, size_t(write_bytes)) != cudaSuccess ||
+        cudaMemset(src, 0, size_t(read_bytes)) != cudaSuccess) {
+        cudaGetLastError();
+        st = TCBF_ERR_OOM;
+    }
+    if (st == TCBF_OK) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const int grid = sms * blocks_per_sm;
+        auto launch = [&]() {
+            stream_mix_kernel<<<grid, 256>>>(static_cast<const uint4 *>(src),
+                                             static_cast<uint4 *>(dst), read_bytes / 16,
+                                             write_bytes / 16);
+            return cudaGetLastError();
+        };
+        cudaError_t e = launch();   // warm-up
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        float best = 1e30f;
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0);
+            e = launch();
+            cudaEventRecord(e1);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best)
+                best = ms;
+        }
+        if (e != cudaSuccess)
+            st = TCBF_ERR_CUDA;
+        else
+            *seconds = best * 1e-3;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (src) cudaFree(src);
+    if (dst) cudaFree(dst);
+    cudaSetDevice(prev);
+    return st;
+}
 
 TCBF_EXPORT tcbf_status tcbf_peak_run(int kind, int device, int iters, double *seconds,
                                       double *ops) {

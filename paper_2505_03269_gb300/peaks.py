@@ -2,6 +2,10 @@
 print one JSON object: TeraOps/s per kind, with the SM clock seen.
 
   python -m paper_2505_03269_gb300.peaks [--device D] [--scale S]
+  python -m paper_2505_03269_gb300.peaks --stream READ_GB WRITE_GB [--device D]
+
+--stream times an HBM stream with that read/write mix instead (the
+ceiling of a memory-bound step's byte mix) for 4, 8 and 16 blocks per SM.
 """
 from __future__ import annotations
 
@@ -55,6 +59,27 @@ def measure(kind: int, device: int = 0) -> float:
     return ops.value / sec.value / 1e12
 
 
+def stream(read_gb: float, write_gb: float, device: int = 0) -> dict:
+    """GB/s of tcbf_peak_stream for the given read and write volumes."""
+    tcbf_build.build()
+    lib = binding.load()
+    f = lib.tcbf_peak_stream
+    f.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                  ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    rb = int(read_gb * 1e9) // 16 * 16
+    wb = int(write_gb * 1e9) // 16 * 16
+    res = {"read_bytes": rb, "write_bytes": wb}
+    for per_sm in (4, 8, 16):
+        sec = ctypes.c_double()
+        st = f(device, rb, wb, per_sm, ctypes.byref(sec))
+        if st != 0:
+            raise binding.TcbfError(st, "tcbf_peak_stream")
+        res[f"blocks_per_sm_{per_sm}"] = {"ms": sec.value * 1e3,
+                                          "gbs": (rb + wb) / sec.value / 1e9}
+    return res
+
+
 def run(device: int = 0, scale: float = 1.0) -> dict:
     tcbf_build.build()
     f = _peak_fn()
@@ -74,5 +99,9 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--device", type=int, default=0)
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--stream", type=float, nargs=2, metavar=("READ_GB", "WRITE_GB"))
     a = ap.parse_args()
-    print(json.dumps(run(a.device, a.scale)))
+    if a.stream:
+        print(json.dumps(stream(a.stream[0], a.stream[1], a.device)))
+    else:
+        print(json.dumps(run(a.device, a.scale)))

@@ -89,6 +89,15 @@ def test_null_arguments(lib):
     f = ctypes.c_uint32()
     assert lib.tcbf_plan_flags(None, ctypes.byref(f)) == 1
     assert lib.tcbf_plan_destroy(None) == 0
+    # the stream microbenchmark checks its sizes before touching a device
+    sec = ctypes.c_double()
+    ps = lib.tcbf_peak_stream
+    ps.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                   ctypes.POINTER(ctypes.c_double)]
+    assert ps(0, 1 << 20, 1 << 20, 4, None) == 1
+    assert ps(0, 24, 1 << 20, 4, ctypes.byref(sec)) == 1        # not a multiple of 16
+    assert ps(0, 1 << 20, 0, 4, ctypes.byref(sec)) == 1
+    assert ps(0, 1 << 20, 1 << 20, 0, ctypes.byref(sec)) == 1
 
 
 def test_no_device_reports_unsupported(lib):
