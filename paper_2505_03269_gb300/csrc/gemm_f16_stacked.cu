@@ -490,6 +490,10 @@ cudaError_t launch_stacked(const tcbf_plan_s &pl, const void *Wp, const void *Xp
 // CTAs' loads complete on the even CTA's full barrier, its MMA completions
 // are committed to both CTAs, and both CTAs' epilogues release an
 // accumulator on the even CTA's barrier.  Promotion as in the one-SM kernel.
+// With promoted long K, the tiles of a partial last wave can run as parts of
+// whole chunks on the pairs that wave leaves idle (pair_split); a part stores
+// its chunks to Y or to the plan's workspace, and stacked_tail_fixup_kernel
+// adds them in chunk order after the launch.
 // ===========================================================================
 constexpr int PBK = 64;                  // K per stage: one 128-byte row
 constexpr int kStkPairChunkBlocks = 32;  // stages (x 64 K) per promoted chunk
