@@ -649,6 +649,19 @@ def roofline_of(gw, peaks, gemm_ms):
         roof["algorithmic_bytes_note"] = ("packed sign bits of W and X (2 bits per complex "
                                           "value) + int32 Y; the E2M1 planes the kernel reads "
                                           "are an intermediate of this design (kernel_plane_bytes)")
+    if roof["bound"] == "hbm":
+        # the same read and write bytes streamed alone: what this byte mix allows
+        from paper_2505_03269_gb300 import peaks as tcbf_peaks
+        wbytes = gw.Y.numel() * 4
+        kbytes = roof.get("kernel_plane_bytes") or gbytes
+        st = tcbf_peaks.stream((kbytes - wbytes) / 1e9, wbytes / 1e9)
+        ceil_gbs = max(v["gbs"] for k, v in st.items() if k.startswith("blocks_per_sm"))
+        kgbs = kbytes / (gemm_ms * 1e-3) / 1e9
+        roof["byte_mix_ceiling"] = {
+            "read_bytes": st["read_bytes"], "write_bytes": st["write_bytes"], "gbs": ceil_gbs,
+            "kernel_gbs": kgbs, "frac": kgbs / ceil_gbs,
+            "how": "tcbf_peak_stream: the GEMM's read bytes with 16-byte loads, then its write "
+                   "bytes with 16-byte stores, fastest of 4, 8 and 16 blocks per SM"}
     return roof
 
 
@@ -907,19 +920,6 @@ def main():
     full_size = args.batches is None and args.m_rows is None
     traffic_key = f"{args.workload}/{w['mode']}" if full_size else None
     roof["traffic"] = recorded_traffic(kname, traffic_key, plan.config_name(plan.get_config()))
-    if roof["bound"] == "hbm":
-        # the same read and write bytes streamed alone: what this byte mix allows
-        from paper_2505_03269_gb300 import peaks as tcbf_peaks
-        wbytes = gw.Y.numel() * 4
-        kbytes = roof.get("kernel_plane_bytes") or roof["algorithmic_bytes"]
-        st = tcbf_peaks.stream((kbytes - wbytes) / 1e9, wbytes / 1e9)
-        ceil_gbs = max(v["gbs"] for k, v in st.items() if k.startswith("blocks_per_sm"))
-        kgbs = kbytes / (gemm_ms * 1e-3) / 1e9
-        roof["byte_mix_ceiling"] = {
-            "read_bytes": st["read_bytes"], "write_bytes": st["write_bytes"], "gbs": ceil_gbs,
-            "kernel_gbs": kgbs, "frac": kgbs / ceil_gbs,
-            "how": "tcbf_peak_stream: the GEMM's read bytes with 16-byte loads, then its write "
-                   "bytes with 16-byte stores, fastest of 4, 8 and 16 blocks per SM"}
     gemm_tops = roof["gemm_tops"]
     pack_bytes = gw.Xh.nbytes + plan.packed_size(1)
     ops = ops_per_step(w)
