@@ -654,7 +654,11 @@ def roofline_of(gw, peaks, gemm_ms):
         from paper_2505_03269_gb300 import peaks as tcbf_peaks
         wbytes = gw.Y.numel() * 4
         kbytes = roof.get("kernel_plane_bytes") or gbytes
-        st = tcbf_peaks.stream((kbytes - wbytes) / 1e9, wbytes / 1e9)
+        try:
+            st = tcbf_peaks.stream((kbytes - wbytes) / 1e9, wbytes / 1e9)
+        except Exception as exc:      # e.g. no room for the two buffers beside the workload
+            roof["byte_mix_ceiling"] = {"unavailable": str(exc)}
+            return roof
         ceil_gbs = max(v["gbs"] for k, v in st.items() if k.startswith("blocks_per_sm"))
         kgbs = kbytes / (gemm_ms * 1e-3) / 1e9
         roof["byte_mix_ceiling"] = {
