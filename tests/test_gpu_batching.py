@@ -42,11 +42,12 @@ def _c(Y):
     return Yh[..., 0] + 1j * Yh[..., 1]
 
 
+@pytest.mark.parametrize("K", [100, 5000])
 @pytest.mark.parametrize("config", [0, 3])
-def test_uneven_beam_counts_one_launch(config):
+def test_uneven_beam_counts_one_launch(config, K):
     import torch
     rows = [300, 1, 129, 128, 257]
-    B, M, N, K = len(rows), max(rows), 200, 100
+    B, M, N = len(rows), max(rows), 200
     W, _ = ti.small_fp16(seed=21, M=M, K=K, N=8, B=B)
     X = ti.complex_gaussian_fp16(ti.rng(22), (B, K, N))
     plan, Wp, Xd, Xp, Y = _setup_fp16(W, X)

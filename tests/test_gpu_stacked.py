@@ -201,10 +201,13 @@ def test_stacked_pair_split_in_a_captured_step():
         assert np.array_equal(Y.cpu().numpy(), Yg)
 
 
-def test_stacked_uneven_beam_counts():
+@pytest.mark.parametrize("K", [100, 5000])
+def test_stacked_uneven_beam_counts(K):
+    """Uneven beam counts run the one-SM stacked tiles (per-batch m-tiles),
+    K = 5000 with its promoted chunks on the alternating accumulators."""
     rows = [300, 1, 129]
-    W, _ = ti.small_fp16(seed=21, M=300, K=100, N=8, B=3)
-    X = ti.complex_gaussian_fp16(ti.rng(22), (3, 100, 200))
+    W, _ = ti.small_fp16(seed=21, M=300, K=K, N=8, B=3)
+    X = ti.complex_gaussian_fp16(ti.rng(22), (3, K, 200))
     Y = _run(W, X, rows=rows)
     Yref = oracle.cgemm(W, X)
     for b, r in enumerate(rows):
